@@ -1,0 +1,362 @@
+"""The encrypted semi-parallel GWAS circuit over the O1 evaluator.
+
+TEST INFRASTRUCTURE ONLY.  Written from Algorithms 1-11 of the paper and the
+readings listed in the design notes; the CUDA library implements the same
+op sequence independently.  Every step below names the algorithm it follows.
+
+Slot layouts (M = N/2 slots, nb = next power of two >= n, B = M/nb blocks):
+  vector v (length n)        slots 0..n-1, zeros elsewhere
+  CP matrix (Alg. 2)         one ciphertext per column
+  REP row (section REP)      entry c repeated nb times: slot c*nb + t
+  CCP matrix (Alg. 4)        column c in slots c*nb .. c*nb + nb - 1
+  S batch (REP, complex)     row j of S_i: slot b*nb + t = S[j, 2b] + i S[j, 2b+1]
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from .ckks import Ct, OracleCKKS
+
+# encryption ids (the nonce of each input ciphertext's randomness)
+ENC_X = 0x100
+ENC_A = 0x200
+ENC_Y = 0x300
+ENC_BETA0 = 0x301
+ENC_DUPW = 0x302
+ENC_DUPWZ = 0x303
+ENC_XTREP = 0x10000
+ENC_DUPM = 0x20000
+ENC_S = 0x1000000
+
+SIGMA7_A = (-1.73496 / 8.0, 4.19407 / 8.0 ** 3, -5.43402 / 8.0 ** 5, 2.50739 / 8.0 ** 7)
+
+BATCH_LEVEL = 4  # level at which a SNP batch enters (S', num, WS', WSS/WSC)
+
+
+@dataclass
+class Layout:
+    logN: int
+    n: int
+    d: int
+    k: int
+
+    @property
+    def M(self):
+        return 1 << (self.logN - 1)
+
+    @property
+    def nb(self):
+        """next power of two >= n (the padded column length)."""
+        return 1 << max(0, math.ceil(math.log2(self.n)))
+
+    @property
+    def B(self):
+        """complex SNP columns per ciphertext (blocks of nb slots)."""
+        return self.M // self.nb
+
+    @property
+    def tau(self):
+        """SNPs per batch: eq. numSNPinBatch read as N / nb (two per slot)."""
+        return 2 * self.B
+
+    @property
+    def batches(self):
+        return -(-self.k // self.tau)
+
+    @property
+    def H(self):
+        """ciphertexts holding the n x n CCP matrix M (nb^2 may exceed M)."""
+        return -(-self.n // self.B)
+
+    def check(self):
+        if self.nb > self.M:
+            raise ValueError("a column of nb slots does not fit one ciphertext")
+
+
+def rotation_steps(layout: Layout):
+    """All rotations the circuit uses: 2^i for i < log2(M) (ladders of Alg. 1,
+    4, 5, 7 all rotate by powers of two)."""
+    return [1 << i for i in range(layout.logN - 1)]
+
+
+class Circuit:
+    def __init__(self, ev: OracleCKKS, layout: Layout):
+        self.ev = ev
+        self.lay = layout
+        layout.check()
+
+    # --------------------------------------------------------- primitives
+    def e_slot(self, c):
+        z = np.zeros(self.lay.M)
+        z[c] = 1.0
+        return z
+
+    def mac_relin_rescale(self, pairs):
+        """sum of tensors, one relinearisation, one rescale (Alg. 2, 8 bodies)."""
+        ev = self.ev
+        acc = None
+        for a, b in pairs:
+            t = ev.tensor(a, b)
+            acc = t if acc is None else ev.add(acc, t)
+        return ev.rescale(ev.relin(acc))
+
+    def replicate(self, v: Ct, c: int) -> Ct:
+        """Alg. 1 for entry c: mask slot c, then a log2(M) rotate-and-add ladder."""
+        ev = self.ev
+        t = ev.mul_mask(v, self.e_slot(c))
+        for i in range(self.lay.logN - 1):
+            t = ev.add(t, ev.rotate(t, 1 << i))
+        return t
+
+    def cp_matvec(self, cols, v: Ct, m: int) -> Ct:
+        """Alg. 2: sum_c A(c) * Replicate(v)(c)."""
+        reps = [self.replicate(v, c) for c in range(m)]
+        lv = reps[0].level
+        return self.mac_relin_rescale([(self.ev.drop(cols[c], lv), reps[c]) for c in range(m)])
+
+    def dotprod(self, a: Ct, b: Ct) -> Ct:
+        """Alg. 5: C = A * B, then C += Rotate(C, 2^i) for i < log2(M)."""
+        ev = self.ev
+        t = ev.mult(a, b)
+        for i in range(self.lay.logN - 1):
+            t = ev.add(t, ev.rotate(t, 1 << i))
+        return t
+
+    def rp_matvec(self, rows, v: Ct, m: int) -> Ct:
+        """Alg. 6: sum_c DotProd(A(c), v) * e_c, masks accumulated, one rescale."""
+        ev = self.ev
+        acc = None
+        for c in range(m):
+            dp = self.dotprod(ev.drop(rows[c], v.level), v)
+            ql = float(ev.q[dp.level - 1])
+            t = ev.mul_plain(dp, ev.encode(self.e_slot(c), ql, dp.level), ql)
+            acc = t if acc is None else ev.add(acc, t)
+        return ev.rescale(acc)
+
+    def colsum(self, v: Ct) -> Ct:
+        """Alg. 4: log2(nb) rotate-and-add steps; sums land at slots c*nb."""
+        ev = self.ev
+        for i in range(int(math.log2(self.lay.nb))):
+            v = ev.add(v, ev.rotate(v, 1 << i))
+        return v
+
+    def duplicate(self, v: Ct) -> Ct:
+        """Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks."""
+        ev = self.ev
+        for i in range(int(math.log2(self.lay.B))):
+            v = ev.add(v, ev.rotate(v, self.lay.nb << i))
+        return v
+
+    def sigma7(self, x: Ct) -> Ct:
+        """eq. sigma7 at depth 3: 0.5 + a1 x + a3 x^3 + a5 x^5 + a7 x^7 with
+        a_k = c_k / 8^k; constants multiply at scale q_last (rescaled)."""
+        ev = self.ev
+        a1, a3, a5, a7 = SIGMA7_A
+        x2 = ev.mult(x, x)
+        x4 = ev.mult(x2, x2)
+        b1 = ev.mul_const(x, a1)
+        b3 = ev.mul_const(x, a3)
+        b5 = ev.mul_const(x, a5)
+        b7 = ev.mul_const(x, a7)
+        t3 = ev.mult(b3, x2)
+        t7a = ev.mult(b7, x2)
+        t5 = ev.mult(ev.drop(b5, x4.level), x4)
+        t7 = ev.mult(t7a, x4)
+        lv = t7.level
+        r = ev.add(ev.drop(b1, lv), ev.drop(t3, lv))
+        r = ev.add(r, t5)
+        r = ev.add(r, t7)
+        return ev.add_const(r, 0.5)
+
+    def add_plain_vec(self, ct: Ct, z) -> Ct:
+        """add a public slot vector encoded at the ciphertext's scale."""
+        ev = self.ev
+        pt = ev.encode(z, ct.scale, ct.level)
+        out = ct.c.copy()
+        for i in range(ct.level):
+            q = np.uint64(ev.q[i])
+            s = out[0, i] + pt[i]
+            out[0, i] = np.where(s >= q, s - q, s)
+        return Ct(out, ct.scale)
+
+    # --------------------------------------------------------- inputs
+    def encrypt_vector(self, v, enc_id, level=None, scale=None):
+        ev = self.ev
+        level = ev.L if level is None else level
+        scale = ev.delta if scale is None else scale
+        z = np.zeros(self.lay.M, complex)
+        z[: len(v)] = v
+        return ev.encrypt(ev.encode(z, scale, level), enc_id, scale)
+
+    def encrypt_inputs(self, X, A, y):
+        """X as CP, (X^T X)^-1 as CP, y, beta0 = Enc(0), X^T as REP (Alg. 11
+        inputs and the walk-through after it)."""
+        lay = self.lay
+        n, d = X.shape
+        self.X = [self.encrypt_vector(X[:, c], ENC_X + c) for c in range(d)]
+        self.A = [self.encrypt_vector(A[:, c], ENC_A + c) for c in range(d)]
+        self.y = self.encrypt_vector(y, ENC_Y)
+        self.beta0 = self.encrypt_vector(np.zeros(1), ENC_BETA0)
+        self.XtREP = []
+        for c in range(d):
+            row = []
+            for h in range(lay.H):
+                z = np.zeros(lay.M)
+                for b in range(lay.B):
+                    col = h * lay.B + b
+                    if col < n:
+                        z[b * lay.nb:(b + 1) * lay.nb] = X[col, c]
+                row.append(self.encrypt_vector(z, ENC_XTREP + c * 4096 + h))
+            self.XtREP.append(row)
+
+    def snp_batch_slots(self, S, i):
+        """REP rows of batch i: list over samples j of M complex slot values."""
+        lay = self.lay
+        n, k = S.shape
+        rows = []
+        for j in range(n):
+            z = np.zeros(lay.M, complex)
+            for b in range(lay.B):
+                c0 = i * lay.tau + 2 * b
+                re = S[j, c0] if c0 < k else 0.0
+                im = S[j, c0 + 1] if c0 + 1 < k else 0.0
+                z[b * lay.nb:(b + 1) * lay.nb] = re + 1j * im
+            rows.append(z)
+        return rows
+
+    def encrypt_snp_batch(self, S, i):
+        lay = self.lay
+        return [self.encrypt_vector(z, ENC_S + i * lay.n + j, level=BATCH_LEVEL)
+                for j, z in enumerate(self.snp_batch_slots(S, i))]
+
+    # --------------------------------------------------------- covariate phase
+    def fit(self, kappa: int):
+        """Alg. 9 then the preamble of Alg. 11: w, w^-1, z, z', M, Dup(M_j)."""
+        ev, lay = self.ev, self.lay
+        d, n = len(self.X), lay.n
+        # Alg. 9
+        beta = self.beta0
+        p = ymp = None
+        for _ in range(kappa):
+            xb = self.cp_matvec(self.X, beta, d)
+            p = self.sigma7(xb)
+            ymp = ev.sub(ev.drop(self.y, p.level), p)
+            g = self.rp_matvec(self.X, ymp, d)
+            ag = self.cp_matvec(self.A, g, d)
+            ag4 = ev.mul_int(ag, 4)
+            beta = ev.sub(ev.drop(beta, ag4.level), ag4)
+        self.beta = beta
+        # w = p(1 - p), masked copy for the duplicated weights
+        w = ev.mult(p, ev.add_const(ev.negate(p), 1.0))
+        mask_n = np.zeros(lay.M)
+        mask_n[:n] = 1.0
+        w_m = ev.mul_mask(w, mask_n)
+        # Alg. 10 (first step uses the integer guess 3: no rescale)
+        t = ev.mul_int(w, 3)
+        u = ev.add_const(ev.negate(t), 2.0)
+        g = ev.mul_int(u, 3)
+        for _ in range(2):
+            t = ev.mult(ev.drop(w, g.level), g)
+            u = ev.add_const(ev.negate(t), 2.0)
+            g = ev.mult(ev.drop(g, u.level), u)
+        winv = g
+        # eq. z
+        xb = self.cp_matvec(self.X, beta, d)
+        lv = min(winv.level, ymp.level)
+        r = ev.mult(ev.drop(winv, lv), ev.drop(ymp, lv))
+        lv = min(xb.level, r.level)
+        z = ev.add(ev.drop(xb, lv), ev.drop(r, lv))
+        # eq. zprime, second form: z' = z - X (A (X^T z))
+        xtz = self.rp_matvec(self.X, z, d)
+        axtz = self.cp_matvec(self.A, xtz, d)
+        xaxtz = self.cp_matvec(self.X, axtz, d)
+        zp = ev.sub(ev.drop(z, xaxtz.level), xaxtz)
+        wzp = ev.mult(ev.drop(w_m, zp.level), zp)
+        self.z, self.zp, self.w_m, self.wzp = z, zp, w_m, wzp
+        # eq. M: M = I - X A X^T via Alg. 3 (CP-MatMult) and Alg. 8 (CP-REP)
+        XA = [self.cp_matvec(self.X, self.A[r], d) for r in range(d)]
+        dupXA = [self.duplicate(XA[r]) for r in range(d)]
+        self.Mct = []
+        for h in range(lay.H):
+            lv = dupXA[0].level
+            acc = self.mac_relin_rescale([(dupXA[r], ev.drop(self.XtREP[r][h], lv))
+                                          for r in range(d)])
+            eye = np.zeros(lay.M)
+            for b in range(lay.B):
+                col = h * lay.B + b
+                if col < n:
+                    eye[b * lay.nb + col] = 1.0
+            self.Mct.append(self.add_plain_vec(ev.negate(acc), eye))
+        self.make_dup_state()
+
+    def make_dup_state(self):
+        """Dup(M_j) for every column j (mask its block, Alg. 7), Dup(w), Dup(w z')."""
+        ev, lay = self.ev, self.lay
+        lb = BATCH_LEVEL
+        if self.wzp.level < lb - 1:
+            raise ValueError("depth exhausted before the SNP batches")
+        src = [ev.drop(m, lb + 1) for m in self.Mct]
+        self.DupM = []
+        for j in range(lay.n):
+            h, b = divmod(j, lay.B)
+            mask = np.zeros(lay.M)
+            mask[b * lay.nb:b * lay.nb + lay.n] = 1.0
+            self.DupM.append(self.duplicate(ev.mul_mask(src[h], mask)))
+        self.DupW = self.duplicate(ev.drop(self.w_m, lb - 1))
+        self.DupWZ = self.duplicate(ev.drop(self.wzp, lb - 1))
+
+    def load_split_state(self, M, w, wzp):
+        """Split mode (small rings without the fit's depth): the client
+        encrypts Dup(M_j), Dup(w), Dup(w z') computed in plaintext."""
+        lay = self.lay
+        n = lay.n
+        lb = BATCH_LEVEL
+
+        def dup(v):
+            z = np.zeros(lay.M)
+            for b in range(lay.B):
+                z[b * lay.nb:b * lay.nb + n] = v
+            return z
+
+        self.DupM = [self.encrypt_vector(dup(M[:, j]), ENC_DUPM + j, level=lb)
+                     for j in range(n)]
+        self.DupW = self.encrypt_vector(dup(w), ENC_DUPW, level=lb - 1)
+        self.DupWZ = self.encrypt_vector(dup(wzp), ENC_DUPWZ, level=lb - 1)
+
+    # --------------------------------------------------------- per batch
+    def snp_batch(self, Srow):
+        """Alg. 11 loop body for one batch: S' = sum_j Dup(M_j) S_ij (Alg. 8),
+        numerator = colSum(Dup(w z') S'), WSS, WSC, denEven/denOdd (the 1/2
+        kept as scale metadata), colSum of each."""
+        ev = self.ev
+        lb = BATCH_LEVEL
+        Sp = self.mac_relin_rescale([(self.DupM[j], Srow[j]) for j in range(len(Srow))])
+        num = self.colsum(ev.mult(self.DupWZ, Sp))
+        ws = ev.mult(self.DupW, Sp)
+        s1 = ev.drop(Sp, lb - 2)
+        wss = ev.mult(ws, s1)
+        wsc = ev.mult(ws, ev.conj(s1))
+        den_e = ev.add(wsc, wss)
+        den_e.scale *= 2.0
+        den_o = ev.sub(wsc, wss)
+        den_o.scale *= 2.0
+        return num, self.colsum(den_e), self.colsum(den_o)
+
+    def extract(self, num: Ct, den_e: Ct, den_o: Ct, batch: int):
+        """Decrypt and split the packed pairs: slot b*nb of num gives SNP 2b
+        (real part) and 2b+1 (imaginary part); denEven / denOdd real parts."""
+        lay = self.lay
+        zn = self.ev.decrypt_decode(num)
+        ze = self.ev.decrypt_decode(den_e)
+        zo = self.ev.decrypt_decode(den_o)
+        nums, dens = [], []
+        for b in range(lay.B):
+            s = b * lay.nb
+            nums += [zn[s].real, zn[s].imag]
+            dens += [ze[s].real, zo[s].real]
+        lo = batch * lay.tau
+        cnt = min(lay.tau, lay.k - lo)
+        return np.array(nums[:cnt]), np.array(dens[:cnt])

@@ -1,0 +1,144 @@
+"""Pins of O2 (FP64 approximated GWAS), O3 (exact references) and of the
+oracle's encrypted circuit, against closed forms, invariants, the values the
+paper prints, and brute force on tiny inputs."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gwas_exact, gwas_fp64
+from oracle.circuit import Circuit, Layout, rotation_steps
+from oracle.ckks import OracleCKKS, galois_conj, galois_rot
+from paper_1902_04303_gb300.datagen import make_gwas
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def test_sigma7_coefficients_and_values():
+    g = GOLD["sigma7_coefficients"]
+    assert gwas_fp64.SIGMA7_C0 == g["c0"]
+    assert gwas_fp64.SIGMA7_C == (g["c1"], g["c3"], g["c5"], g["c7"])
+    assert gwas_fp64.sigma7(0.0) == 0.5
+    # at x = 8 the polynomial is the sum of its coefficients
+    assert gwas_fp64.sigma7(8.0) == pytest.approx(0.5 - 1.73496 + 4.19407 - 5.43402 + 2.50739,
+                                                  abs=1e-15)
+    assert gwas_fp64.sigma7(2.0) == pytest.approx(0.1266391, abs=1e-6)
+    # odd part: sigma7(x) + sigma7(-x) = 1
+    x = np.linspace(-8, 8, 33)
+    assert np.allclose(gwas_fp64.sigma7(x) + gwas_fp64.sigma7(-x), 1.0, atol=1e-15)
+    # as printed it tracks the logistic function of -x on [-8, 8] (reading A-13)
+    assert np.max(np.abs(gwas_fp64.sigma7(x) - gwas_exact.sigmoid(-x))) < 0.04
+
+
+def test_inverse_slots_closed_form():
+    g = GOLD["inverse_slots"]
+    w = np.linspace(0.001, g["w_upper_bound"], 200)
+    got = gwas_fp64.inverse_slots(w, guess=g["guess"], iters=g["iterations"])
+    closed = (1.0 - (1.0 - 3.0 * w) ** 8) / w
+    assert np.allclose(got, closed, rtol=1e-12)
+    assert gwas_fp64.inverse_slots(np.array([0.25]))[0] == 3.99993896484375
+    assert gwas_fp64.inverse_slots(np.array([0.01]))[0] == pytest.approx(21.6257, abs=1e-4)
+
+
+def test_batch_geometry_matches_paper():
+    g = GOLD["batch_geometry"]
+    lay = Layout(g["logN"], g["n"], 5, g["k"])
+    assert lay.tau == g["tau"] and lay.batches == g["batches"]
+    for n, logN in GOLD["subject_limit"]["cases"]:
+        nb = 1 << math.ceil(math.log2(n))
+        # the paper's packed layout needs nb^2 slots, i.e. N >= 2 nb^2
+        assert (1 << logN) >= 2 * nb * nb
+        assert (1 << (logN - 1)) < 2 * nb * nb
+
+
+def test_pow2_rotation_count():
+    for r, cnt in GOLD["pow2_rotations"]["examples"]:
+        assert bin(r).count("1") == cnt
+
+
+@pytest.fixture(scope="module")
+def data():
+    d = make_gwas(64, 4, 48, seed=21)
+    return d
+
+
+def test_M_projection_invariants(data):
+    res = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1)
+    M = res["M"]
+    assert np.max(np.abs(M @ M - M)) < 1e-12
+    assert np.max(np.abs(M @ data.X)) < 1e-12
+    assert np.max(np.abs(M - M.T)) < 1e-12
+
+
+def test_complex_route_equals_direct(data):
+    res = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=2)
+    direct = (res["w"][:, None] * res["Sp"] ** 2).sum(axis=0)
+    assert np.max(np.abs(res["den"] - direct) / direct) < 1e-12
+    # odd k: the padded column is ignored
+    den = gwas_fp64.complex_route_den(res["Sp"][:, :7], res["w"])
+    assert np.allclose(den, direct[:7], rtol=1e-12)
+
+
+def test_sign_slips_cancel(data):
+    """reading A-13: literal beta = -corrected beta exactly; p, w, z', b' identical."""
+    for kappa in (1, 2, 3):
+        lit = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa)
+        cor = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa, corrected=True)
+        assert np.array_equal(lit["beta"], -cor["beta"])
+        assert np.array_equal(lit["p"], cor["p"])
+        assert np.allclose(lit["zp"], cor["zp"], atol=1e-11)
+        assert np.allclose(lit["b"], cor["b"], atol=1e-11)
+
+
+def test_bohning_fixed_point_is_mle(data):
+    """with the exact logistic function the Bohning iteration converges to the MLE."""
+    A = gwas_fp64.xtx_inv(data.X)
+    # corrected=True evaluates f(-X beta); f(-x) = logistic(x) here
+    beta, _ = gwas_fp64.hom_logreg(data.X, data.y, A, kappa=400, corrected=True,
+                                   sigmoid=lambda x: gwas_exact.sigmoid(-x))
+    mle = gwas_exact.newton_logreg(data.X, data.y)
+    assert np.max(np.abs(beta - mle)) < 1e-8
+
+
+def test_o2_tracks_exact_references(data):
+    """reported, loose: the approximated GWAS follows the exact semi-parallel
+    method and the per-SNP brute force (the paper's accuracy comparison)."""
+    X, y, S = data.X, data.y, data.S[:, :24]
+    o2 = gwas_fp64.semi_parallel_fp64(X, y, S, kappa=3)
+    sp = gwas_exact.semi_parallel_exact(X, y, S)
+    bf = gwas_exact.per_snp_logreg(X, y, S)
+    assert np.corrcoef(o2["b"], sp["b"])[0, 1] > 0.95
+    assert np.corrcoef(sp["b"], bf["b"])[0, 1] > 0.95
+    assert np.max(np.abs(sp["b"] - bf["b"])) < 0.5
+
+
+def test_encrypted_circuit_matches_o2():
+    """the oracle's own encrypted circuit (Alg. 9-11 over O1) decrypts to O2
+    within the acceptance tolerances |d b'| <= 5e-3, |d(-log10 p)| <= 0.05."""
+    logN, n, d, k = 10, 16, 3, 40
+    dat = make_gwas(n, d, k, seed=5)
+    A = gwas_fp64.xtx_inv(dat.X)
+    o = OracleCKKS(logN=logN, L=21, K=7, dnum=3, seed=11)
+    lay = Layout(logN, n, d, k)
+    o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay)] + [galois_conj(logN)])
+    c = Circuit(o, lay)
+    c.encrypt_inputs(dat.X, A, dat.y)
+    c.fit(kappa=1)
+    nums, dens = [], []
+    for i in range(lay.batches):
+        num, de, do = c.snp_batch(c.encrypt_snp_batch(dat.S, i))
+        a, b = c.extract(num, de, do, i)
+        nums.append(a)
+        dens.append(b)
+    num = np.concatenate(nums)
+    den = np.concatenate(dens)
+    ref = gwas_fp64.semi_parallel_fp64(dat.X, dat.y, dat.S, kappa=1, A=A)
+    ok = np.abs(ref["den"]) > 1e-6  # monomorphic SNPs have den = 0 (degenerate)
+    assert np.max(np.abs(den[~ok])) < 1e-4
+    b = num[ok] / den[ok]
+    assert np.max(np.abs(b - ref["b"][ok])) < 5e-3
+    dl = np.abs(gwas_fp64.neglog10p(b, 1 / den[ok]) - gwas_fp64.neglog10p(ref["b"][ok],
+                                                                          ref["err"][ok]))
+    assert np.max(dl) < 0.05
