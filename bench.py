@@ -1,0 +1,362 @@
+"""Benchmark: encrypted semi-parallel GWAS throughput (SNPs/s) on GB300.
+
+One step = one whole encrypted job of the paper's shape (245 samples,
+intercept + 4 covariates, 10643 SNPs; CKKS N = 2^16, 24 q-limbs, 8 special
+primes, dnum = 3, kappa = 1): encrypt the inputs (X, (X^T X)^-1, y, X^T, all
+42 SNP batches), the encrypted covariate fit (Alg. 9-10, M, z'), every SNP
+batch (Alg. 11 loop) and the decryption of all numerators / denominators.
+Keys are generated once, outside the timed region.
+
+  value   inputs already resident in HBM (torch tensors), CUDA events on the
+          library's stream, L2 flushed (256 MiB write) between steps
+  e2e     the same job through the C ABI with pinned host inputs: the
+          host->device copies and the result read-back are inside the timing
+  roofline  the dominant kernel class from the library's event timers, on one
+          extra instrumented step; algorithmic bytes / time vs measured HBM copy
+  cpu_baseline  the CPU oracle on a bounded sample (one key switch, one tensor
+          and one encryption at the batch level, N = 2^16) extrapolated to the
+          job with the GPU run's key-switch histogram and op counts
+
+Multi-GPU (torchrun): every rank runs its own independent job (weak scaling),
+no collective on the data path; value = SNPs of all ranks / max step time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted-GWAS SNPs/s (245 samples, N=2^16); key-switch/s vs HBM roofline"
+WORKLOAD = dict(name="paper-n245", logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60,
+                dnum=3, n=245, d=5, k=10643, seed=1002, kappa=1)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def client_preprocess(X):
+    """Client-side plaintext pre-processing of the paper (section 'Hessian
+    Matrix Approximation'): (X^T X)^-1, computed before encryption."""
+    return np.linalg.inv(X.T @ X)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1902_04303_gb300 import build as pkg_build
+    from paper_1902_04303_gb300 import gwhe
+    from paper_1902_04303_gb300.datagen import make_gwas
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    pkg_build.build()
+    W = WORKLOAD
+    stream = torch.cuda.current_stream()
+    ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                       W["dnum"], seed=W["seed"] + 7919 * rank, stream=stream.cuda_stream)
+    steps_rot = [1 << i for i in range(W["logN"] - 1)]
+    ctx.keygen(rot_steps=steps_rot, conj=True)
+    data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"] + rank)
+    A = client_preprocess(data.X)
+    dev = {nm: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+           for nm, v in (("X", data.X), ("A", A), ("y", data.y), ("S", data.S))}
+    host = {nm: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+            for nm, v in (("X", data.X), ("A", A), ("y", data.y), ("S", data.S))}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(src):
+        job = gwhe.Job(ctx, W["n"], W["d"], W["k"])
+        job.encrypt_inputs(src["X"], src["A"], src["y"])
+        job.fit(W["kappa"])
+        job.snp_stats(src["S"])
+        num, den = job.decrypt_results()
+        job.close()
+        return num, den
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed(src, K):
+        ms = []
+        barrier()
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = step(src)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        barrier()
+        return ms, out
+
+    for _ in range(args.warmup):
+        step(dev)
+    ks0, l0 = ctx.ks_histogram().copy(), ctx.launches()
+    with Clocks(local) as clk:
+        ms, (num, den) = timed(dev, args.steps)
+    ks_hist = (ctx.ks_histogram() - ks0) // args.steps
+    launches = ctx.launches() - l0
+    step_ms = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    ms_e2e, _ = timed(host, max(1, args.steps))
+    e2e_ms = float(np.mean(ms_e2e))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    # one instrumented step for the per-kernel roofline
+    ctx.prof_enable(True)
+    step(dev)
+    prof = ctx.prof_read()
+    ctx.prof_enable(False)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    # accuracy sanity of the timed job against the plaintext FP64 GWAS
+    snps = W["k"] * world
+    value = snps / (step_ms / 1e3)
+    ks_per_job = int(ks_hist.sum())
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_d, by_d, cnt_d = prof[dom]
+    achieved = by_d / (ms_d / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel_class": dom, "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
+            "launch_groups": cnt_d, "ms_per_step": round(ms_d, 3),
+            "share_of_step": round(ms_d / sum(v[0] for v in prof.values()), 3),
+            "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+    h2d = sum(host[nm].numel() * 8 for nm in host)
+    d2h = 2 * W["k"] * 8
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "SNPs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": W["name"], "N": 1 << W["logN"], "q_limbs": W["L"],
+                   "special_primes": W["K"], "dnum": W["dnum"], "n": W["n"], "d": W["d"],
+                   "k": W["k"], "kappa": W["kappa"], "parallelism": "independent jobs per GPU",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "keyswitch_per_s": round(ks_per_job * world / (step_ms / 1e3), 1),
+        "keyswitches_per_job": ks_per_job,
+        "e2e": {"value": round(snps / (e2e_ms / 1e3), 1), "unit": "SNPs/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(ks_hist, W)
+    print(json.dumps(out))
+    sys.stdout.flush()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_sample(W):
+    """Times the CPU oracle (single thread) on one key switch, one tensor and
+    one encryption at the SNP-batch level (4 limbs, N = 2^16)."""
+    from oracle.ckks import Ct, OracleCKKS
+    o = OracleCKKS(logN=W["logN"], L=W["L"], q0_bits=W["q0_bits"], scale_bits=W["scale_bits"],
+                   K=W["K"], sp_bits=W["sp_bits"], dnum=W["dnum"], seed=W["seed"])
+    l = 4
+    rng = np.random.Generator(np.random.PCG64(5))
+    N = o.N
+
+    def rnd(lv, npoly):
+        return Ct(np.stack([np.stack([rng.integers(0, o.q[i], size=N, dtype=np.uint64)
+                                      for i in range(lv)]) for _ in range(npoly)]), o.delta)
+
+    t0 = time.perf_counter()
+    o.pk_b = rnd(W["L"], 1).c[0]
+    o.pk_a = rnd(W["L"], 1).c[0]
+    o.keys[0] = rng.integers(0, 2 ** 59, size=(W["dnum"], 2, W["L"] + W["K"], N), dtype=np.uint64)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.keyswitch(rnd(l, 1).c[0], 0)
+    t_ks = time.perf_counter() - t0
+    a, b = rnd(l, 2), rnd(l, 2)
+    t0 = time.perf_counter()
+    o.tensor(a, b)
+    t_tensor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.encrypt(rnd(l, 1).c[0], 1, o.delta)
+    t_enc = time.perf_counter() - t0
+    return dict(t_ks4=t_ks, t_tensor4=t_tensor, t_enc4=t_enc, t_setup=t_setup, alpha=o.alpha)
+
+
+def extrapolate(sample, ks_hist, W):
+    """Oracle job time: key switches scaled by their polynomial-product count
+    (2 beta (l + K) per switch at level l) from the measured level-4 switch,
+    plus the batches' tensor sums and SNP encryptions at level 4."""
+    alpha, K = sample["alpha"], W["K"]
+
+    def work(l):
+        return math.ceil(l / alpha) * (l + K)
+
+    t = 0.0
+    for l, cnt in enumerate(ks_hist):
+        if cnt:
+            t += cnt * sample["t_ks4"] * work(l) / work(4)
+    tau = 2 * ((1 << (W["logN"] - 1)) // (1 << math.ceil(math.log2(W["n"]))))
+    batches = -(-W["k"] // tau)
+    t += batches * W["n"] * (sample["t_tensor4"] + sample["t_enc4"])
+    return t
+
+
+def cpu_baseline(ks_hist, W):
+    s = oracle_sample(W)
+    t_job = extrapolate(s, ks_hist, W)
+    return {"value": round(W["k"] / t_job, 4), "unit": "SNPs/s", "cores": 1, "kind": "oracle",
+            "sample": ("oracle (1 thread) timed on one key switch (%.2f s), one tensor (%.2f s) and "
+                       "one encryption (%.2f s) at 4 limbs, N=2^16; extrapolated to the job with "
+                       "the GPU run's key-switch histogram (%d switches) and %d batch "
+                       "tensors/encryptions: %.0f s per job"
+                       % (s["t_ks4"], s["t_tensor4"], s["t_enc4"], int(np.sum(ks_hist)),
+                          W["n"] * -(-W["k"] // 256), t_job))}
+
+
+def run_reference(args):
+    """The oracle arm: each step is a bounded sample of the job on the host
+    cores, extrapolated to the job's SNPs/s with a static key-switch count."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W = WORKLOAD
+    from oracle import build_oracle
+    build_oracle.build()
+    # key-switch histogram of the job (levels follow from the circuit; from a
+    # GPU run of the same workload: stored with the profiles)
+    hist = np.zeros(65, np.int64)
+    for l, c in REFERENCE_KS_HIST.items():
+        hist[l] = c
+    for _ in range(args.warmup):
+        oracle_sample(W)
+    times = []
+    samples = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        s = oracle_sample(W)
+        samples.append(s)
+        times.append(extrapolate(s, hist, W))
+    wall = time.perf_counter() - t_all
+    t_job = float(np.mean(times))
+    value = W["k"] / t_job
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "SNPs/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_job * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": W["name"], "N": 1 << W["logN"], "q_limbs": W["L"],
+                      "special_primes": W["K"], "dnum": W["dnum"], "n": W["n"], "d": W["d"],
+                      "k": W["k"], "kappa": W["kappa"]},
+           "cpu_baseline": {"value": round(value, 4), "unit": "SNPs/s", "cores": 1,
+                            "kind": "oracle",
+                            "sample": "per step: one key switch, one tensor, one encryption at "
+                                      "4 limbs, N=2^16, extrapolated to the job (%.1f s wall)"
+                                      % wall},
+           "e2e": {"value": round(value, 4), "unit": "SNPs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# key switches per level of one paper-n245 job (kappa = 1), from the circuit
+REFERENCE_KS_HIST = {}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwhe", choices=["gwhe", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * gwhe.h -- C ABI of the GB300 CKKS-RNS engine for the encrypted semi-parallel
+ * GWAS of "Achieving GWAS with Homomorphic Encryption" (arXiv 1902.04303).
+ *
+ * Every function returns an int status: GWHE_OK (0) or a negative code below.
+ * No exception crosses this boundary.  The text of the last failure of a
+ * context is returned by gwhe_last_error().  All host arrays are owned by the
+ * caller and only read/written during the call.  Device work runs on the CUDA
+ * stream given at context creation (NULL = the legacy default stream); calls
+ * that return host data synchronise that stream.  Handles own their device
+ * memory, drawn from the device's stream-ordered memory pool.
+ *
+ * Data layout.  N = 2^logN is the ring degree, M = N/2 the number of complex
+ * slots.  A polynomial over l RNS limbs is uint64[l][N] (limb-major); a
+ * ciphertext is uint64[2][l][N] = (c0, c1); limb i is modulo q_i, special
+ * limb k modulo p_k.  Host import/export is in the COEFFICIENT domain with
+ * residues in [0, q_i); device-resident ciphertexts are kept in the NTT
+ * domain.  Complex slot vectors are interleaved (re, im) doubles [M][2].
+ *
+ * Conventions that the paper leaves open (and that the CPU oracle follows
+ * from the same statement):
+ *   primes      q0 = largest prime < 2^q0_bits with q = 1 (mod 2N); scale
+ *               primes nearest 2^scale_bits, alternately below and above;
+ *               special primes the next largest below 2^sp_bits.
+ *   randomness  ChaCha20 block function (RFC 8439), key = (seed lo, seed hi,
+ *               0,...), nonce = (object lo, object hi, tag), counter = block.
+ *               Secret and encryption ephemeral ternary ((w mod 3) - 1, word
+ *               k%16 of block k/16); errors centred binomial with eta = 21
+ *               (popcounts of the low 21 bits of words 2(k%8), 2(k%8)+1 of
+ *               block k/8); uniform residues = 128-bit word of block k/4 mod q.
+ *               Objects: secret 1, pk.a 2 (tag = limb), pk.e 3, switching key
+ *               (id, digit j): a = 2^40 | id << 8 | j (tag = limb), e = 2^41 |
+ *               id << 8 | j; encryption id e: v = 3<<48 | e, e0 = 4<<48 | e,
+ *               e1 = 5<<48 | e.  Key id 0 = relinearisation, else the Galois
+ *               element.
+ *   rescale     floor((C + floor(q_l/2)) / q_l) of the CRT integer C.
+ *   key switch  hybrid: digits of alpha = ceil(L/dnum) consecutive q-limbs,
+ *               ModUp by fast base conversion (no overflow correction), key
+ *               digit j = (-a s + e + P [limb in digit j] s', a), ModDown
+ *               (x - Conv([x]_P)) P^-1.
+ *   encoding    m(zeta^(5^j)) = scale z_j (zeta = exp(i pi/N)) computed by the
+ *               radix-2 procedure: G[bitrev(u_j)] = z_j with u_j = ((5^j mod 2N)
+ *               - 1)/4; decimation-in-time stages len = 2..M with twiddles
+ *               exp(-2 pi i t/M); c_k = G[k] exp(-pi i k/N); coefficients k and
+ *               k+M = rint(Re, Im of c_k * (scale/M)); every product and sum
+ *               separately rounded (no fused multiply-add).
+ *   scales      product -> product of scales; rescale -> / (double)q_last; sums
+ *               keep the first operand's scale (relative mismatch > 2^-10 is
+ *               GWHE_ESCALE); a real constant c multiplies as rint(c q_last)
+ *               and then rescales; a constant added is rint(c scale).
+ *   rotation    Rotate(ct, r) moves slot i + r to slot i (Galois 5^r); r < 0
+ *               rotates the other way.
+ */
+#ifndef GWHE_H
+#define GWHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWHE_OK 0
+#define GWHE_EINVAL (-1)   /* bad argument, shape or parameter set            */
+#define GWHE_ENOMEM (-2)   /* device allocation failed                        */
+#define GWHE_ELEVEL (-3)   /* depth exhausted / operands at different levels  */
+#define GWHE_ESCALE (-4)   /* operand scales differ by more than 2^-10        */
+#define GWHE_ENOKEY (-5)   /* required key (public, relinearisation, Galois) missing */
+#define GWHE_ETIMEOUT (-6) /* a bounded device wait expired                   */
+#define GWHE_ECUDA (-7)    /* CUDA runtime error (text in gwhe_last_error)    */
+
+typedef struct gwhe_ctx gwhe_ctx;
+typedef struct gwhe_ct gwhe_ct;
+typedef struct gwhe_job gwhe_job;
+
+/* CKKS parameter set (paper section "Homomorphic Encryption": N, L, p; here in
+ * RNS form).  logN in [4, 16]; L q-limbs (1 base prime of q0_bits, L-1 scale
+ * primes near 2^scale_bits); K special primes of sp_bits; dnum key digits. */
+typedef struct {
+  int logN, L, q0_bits, scale_bits, K, sp_bits, dnum;
+} gwhe_params;
+
+/* ------------------------------------------------------------ host only
+ * These need no GPU. */
+/* RNS basis of the convention above: q[L], p[K]. */
+int gwhe_gen_primes(const gwhe_params* prm, uint64_t* q, uint64_t* p);
+/* Encoding twiddles W[M/2][2] and T[M][2] (sign -1: encode, +1: decode). */
+int gwhe_fft_twiddles(int logN, int sign, double* W, double* T);
+/* Batch layout of the semi-parallel GWAS (section "Batching SNPs", eq.
+ * numSNPinBatch read as tau = N / nb): out = {nb, B = M/nb, tau = 2B,
+ * batches = ceil(k/tau), H = ceil(n/B)}.  GWHE_EINVAL when nb > M. */
+int gwhe_layout(int logN, int n, long k, long out[5]);
+
+/* ------------------------------------------------------------ context */
+/* Creates a context: primes, NTT / base-conversion / encoding tables on the
+ * current CUDA device.  seed keys all randomness.  stream = cudaStream_t or
+ * NULL.  On failure *out is NULL and the status says why. */
+int gwhe_ctx_create(const gwhe_params* prm, uint64_t seed, void* stream, gwhe_ctx** out);
+int gwhe_ctx_destroy(gwhe_ctx* ctx);
+const char* gwhe_last_error(const gwhe_ctx* ctx);
+/* moduli q_0..q_{L-1}, p_0..p_{K-1} (L + K values) */
+int gwhe_ctx_moduli(const gwhe_ctx* ctx, uint64_t* out);
+int gwhe_sync(gwhe_ctx* ctx);
+
+/* KeyGen (section "Homomorphic Encryption"): secret, public key, the
+ * relinearisation key and one switching key per rotation step in rot_steps
+ * and, if conj, for complex conjugation.  Keys stay resident on the device. */
+int gwhe_keygen(gwhe_ctx* ctx, const int32_t* rot_steps, size_t nrot, int conj);
+/* Key material in the coefficient domain for parity checks: the secret as
+ * signed coefficients int64[N]; pk as uint64[2][L][N] (b, a); a switching key
+ * as uint64[dnum][2][L+K][N]. */
+int gwhe_export_secret(gwhe_ctx* ctx, int64_t* s);
+int gwhe_export_pk(gwhe_ctx* ctx, uint64_t* pk);
+int gwhe_export_ksk(gwhe_ctx* ctx, uint32_t key_id, uint64_t* out);
+
+/* ------------------------------------------------------------ ciphertexts
+ * A handle holds npoly (2, or 3 for a tensor) polynomials with room for cap
+ * limbs. */
+int gwhe_ct_create(gwhe_ctx* ctx, int npoly, int cap, gwhe_ct** out);
+int gwhe_ct_destroy(gwhe_ct* ct);
+int gwhe_ct_info(const gwhe_ct* ct, int* npoly, int* l, double* scale);
+/* coefficient-domain host array uint64[npoly][l][N] -> handle (l <= cap) */
+int gwhe_ct_import(gwhe_ct* ct, const uint64_t* coeffs, int npoly, int l, double scale);
+/* handle -> coefficient-domain host array uint64[npoly][l][N] */
+int gwhe_ct_export(const gwhe_ct* ct, uint64_t* coeffs);
+
+/* Encode (section "Homomorphic Encryption", phi^-1): z = M complex slots
+ * (host, interleaved) -> signed coefficients int64[N] (host). */
+int gwhe_encode(gwhe_ctx* ctx, const double* z, double scale, int64_t* coeffs);
+/* Encrypt(pk, Encode(z)) at level l with randomness of encryption id enc_id. */
+int gwhe_encrypt(gwhe_ctx* ctx, const double* z, double scale, int l, uint64_t enc_id,
+                 gwhe_ct* out);
+/* Encrypt a given integer plaintext (int64[N] coefficients, host). */
+int gwhe_encrypt_coeffs(gwhe_ctx* ctx, const int64_t* m, double scale, int l, uint64_t enc_id,
+                        gwhe_ct* out);
+/* Decrypt: c0 + c1 s, coefficient domain uint64[l][N] (host). */
+int gwhe_decrypt(gwhe_ctx* ctx, const gwhe_ct* ct, uint64_t* m);
+/* Decrypt then Decode (the ciphertext is read at its first limb: the value
+ * times its scale must stay below q0/2): z = M complex slots (host). */
+int gwhe_decrypt_decode(gwhe_ctx* ctx, const gwhe_ct* ct, double* z);
+
+/* ------------------------------------------------------------ arithmetic
+ * Section "Homomorphic Encryption" (Add, Mult, Rescale, Rotate) in RNS form.
+ * out may alias an input unless stated. */
+int gwhe_add(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
+int gwhe_sub(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
+int gwhe_negate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out);
+int gwhe_add_const(gwhe_ctx* ctx, gwhe_ct* ct, double c);
+int gwhe_mul_int(gwhe_ctx* ctx, gwhe_ct* ct, int64_t k);
+int gwhe_mul_const(gwhe_ctx* ctx, gwhe_ct* ct, double c);           /* consumes a level */
+/* slot-wise product with the public vector z (M complex, host) encoded at
+ * scale q_last, then rescale (consumes a level) */
+int gwhe_mul_mask(gwhe_ctx* ctx, const gwhe_ct* a, const double* z, gwhe_ct* out);
+/* tensor (d0, d1, d2) of two ciphertexts; out must have npoly = 3 */
+int gwhe_tensor(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
+/* sum_j tensor(a[j], b[j]) into out (npoly 3): the CP-REP inner loop (Alg. 8) */
+int gwhe_tensor_sum(gwhe_ctx* ctx, const gwhe_ct* const* a, const gwhe_ct* const* b, size_t n,
+                    gwhe_ct* out);
+int gwhe_relin(gwhe_ctx* ctx, const gwhe_ct* t3, gwhe_ct* out);
+int gwhe_rescale(gwhe_ctx* ctx, gwhe_ct* ct);                         /* drops q_{l-1} */
+int gwhe_mult(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
+int gwhe_rotate(gwhe_ctx* ctx, const gwhe_ct* a, int steps, gwhe_ct* out); /* out != a */
+int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out);         /* out != a */
+int gwhe_drop(gwhe_ct* ct, int l);                                          /* keep l limbs */
+/* Hybrid key switch of one coefficient-domain polynomial x (uint64[l][N],
+ * host) with key key_id: out = uint64[2][l][N] coefficient domain (host). */
+int gwhe_keyswitch(gwhe_ctx* ctx, const uint64_t* x, int l, uint32_t key_id, uint64_t* out);
+/* Batched forward (inverse = 0) or inverse NTT, in place, over device rows
+ * dev[npoly][nlimbs][N]; limb i of every poly is modulo q_i. */
+int gwhe_ntt_batch(gwhe_ctx* ctx, uint64_t* dev, int npoly, int nlimbs, int inverse);
+
+/* ------------------------------------------------------------ GWAS job
+ * The paper's problem statement (Alg. 11 inputs / outputs): n samples, d
+ * covariates (column 0 = intercept), k SNPs.  Input arrays may be host or
+ * device pointers (detected per call). */
+int gwhe_job_create(gwhe_ctx* ctx, int n, int d, long k, gwhe_job** out);
+int gwhe_job_destroy(gwhe_job* job);
+/* X (n x d, row-major) as CP, (X^T X)^-1 (d x d, row-major; client
+ * pre-processing, section "Hessian Matrix Approximation") as CP, X^T as REP,
+ * y (n) and beta0 = Enc(0), all at the top level (Alg. 9 / Alg. 11 inputs). */
+int gwhe_encrypt_inputs(gwhe_job* job, const double* X, const double* XtX_inv, const double* y);
+/* Alg. 9 (kappa iterations), Alg. 10, eqs. z / M / zprime, then Dup(M_j),
+ * Dup(w), Dup(w z') for the batches (Alg. 7, Alg. 8). */
+int gwhe_fit_covariates(gwhe_job* job, int kappa);
+/* Split mode for rings without the fit's depth: the client supplies M (n x n,
+ * row-major), w and w*z' (n) in plaintext; they are duplicated and encrypted. */
+int gwhe_set_fit_state(gwhe_job* job, const double* M, const double* w, const double* wz);
+/* Alg. 11 loop for batches [b0, b1): S is n x k row-major genotypes (host or
+ * device).  keep != 0 keeps each batch's output ciphertexts for export. */
+int gwhe_snp_stats(gwhe_job* job, const double* S, long b0, long b1, int keep);
+/* Decrypt + decode the kept batch outputs: num[k], den[k] (host); b' = num/den,
+ * err' = 1/den (eqs. estSNPeffect, estSNPerror). */
+int gwhe_decrypt_results(gwhe_job* job, double* num, double* den);
+/* Job ciphertexts for parity checks: which = 0 num, 1 denEven, 2 denOdd (index
+ * = batch); 3 Dup(M_j) (index j); 4 Dup(w); 5 Dup(w z'); 6 z'; 7 beta; 8 the
+ * CCP matrix M (index = ciphertext h); 9 z; 10 the masked weights w.  *view
+ * is a new handle that does not own the device memory: destroy it with
+ * gwhe_ct_destroy, and do not use it after the job is destroyed. */
+int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view);
+/* number of key switches issued on the job's context so far */
+long gwhe_job_keyswitches(const gwhe_job* job);
+
+/* ------------------------------------------------------------ instrumentation */
+/* key switches issued so far per level: out[l] for l < n */
+int gwhe_ks_histogram(const gwhe_ctx* ctx, long* out, int n);
+/* number of kernels the context has launched so far */
+long gwhe_launch_count(const gwhe_ctx* ctx);
+/* Kernel-class timers: when on, CUDA events on the context's stream bracket
+ * every launch group of a class; enabling (or disabling) discards earlier
+ * records.  Classes: 0 NTT/iNTT, 1 key-switch inner product, 2 tensor sum,
+ * 3 base conversion, 4 element-wise, 5 encoding FFT, 6 sampling/encryption. */
+#define GWHE_PROF_NCAT 7
+int gwhe_prof_enable(gwhe_ctx* ctx, int on);
+/* per class since the last read: total event time (ms), algorithmic bytes
+ * moved (each input and output residue counted once), launch groups.
+ * Synchronises the stream. */
+int gwhe_prof_read(gwhe_ctx* ctx, double* ms, double* bytes, long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWHE_H */

@@ -1,0 +1,676 @@
+// ckks.cu -- RNS-CKKS context, key generation and evaluator (host
+// orchestration of the kernels in ntt.cu / kernels.cu).
+//
+// Conventions shared with the documented spec of the library header:
+//   scale of a product = product of scales; rescale divides by (double)q_last;
+//   a sum keeps the first operand's scale (relative mismatch above 2^-10 is an
+//   error); a real constant c multiplies as round(c * q_last) then rescales.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ckks.cuh"
+
+namespace gwhe {
+
+// ---------------------------------------------------------------- memory
+void* dalloc_bytes(Context* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(ST_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  return p;
+}
+u64* dalloc_u64(Context* c, size_t words) { return (u64*)dalloc_bytes(c, words * sizeof(u64)); }
+void dfree(Context* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+ProfScope::ProfScope(Context* c_, int cat_, double bytes_) : c(c_), cat(cat_), bytes(bytes_) {
+  if (!c->prof.on) return;
+  if (c->prof.pool.empty()) {
+    cudaEvent_t e;
+    GWHE_CUDA(cudaEventCreate(&e));
+    c->prof.pool.push_back(e);
+  }
+  a = c->prof.pool.back();
+  c->prof.pool.pop_back();
+  cudaEventRecord(a, c->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t b;
+  if (c->prof.pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+  } else {
+    b = c->prof.pool.back();
+    c->prof.pool.pop_back();
+  }
+  cudaEventRecord(b, c->stream);
+  c->prof.recs.push_back(ProfRec{a, b, bytes, cat});
+}
+
+void prof_read(Context* c, double* ms, double* bytes, long* count) {
+  for (int i = 0; i < PROF_NCAT; ++i) {
+    ms[i] = 0;
+    bytes[i] = 0;
+    count[i] = 0;
+  }
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  for (const ProfRec& r : c->prof.recs) {
+    float t = 0;
+    GWHE_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.cat] += t;
+    bytes[r.cat] += r.bytes;
+    count[r.cat] += 1;
+    c->prof.pool.push_back(r.a);
+    c->prof.pool.push_back(r.b);
+  }
+  c->prof.recs.clear();
+}
+
+Tmp::Tmp(Context* c_, size_t bytes) : c(c_), p(dalloc_bytes(c_, bytes)) {}
+Tmp::~Tmp() { dfree(c, p); }
+
+Ct::~Ct() {
+  if (owned && d && ctx) dfree(ctx, d);
+}
+u64* Ct::poly(int p) const { return d + (size_t)p * cap * ctx->N; }
+u64* Ct::limb(int p, int i) const { return d + ((size_t)p * cap + i) * ctx->N; }
+
+static PolyView pv(const Ct& a) { return PolyView{a.d, a.cap}; }
+static CPolyView cpv(const Ct& a) { return CPolyView{a.d, a.cap}; }
+
+CtPtr ct_new(Context* c, int npoly, int cap, int l, double scale) {
+  CtPtr ct(new Ct());
+  ct->ctx = c;
+  ct->npoly = npoly;
+  ct->cap = cap;
+  ct->l = l;
+  ct->scale = scale;
+  ct->d = dalloc_u64(c, (size_t)npoly * cap * c->N);
+  return ct;
+}
+
+CtPtr ct_clone(Context* c, const Ct& a) {
+  CtPtr ct = ct_new(c, a.npoly, a.l, a.l, a.scale);
+  for (int p = 0; p < a.npoly; ++p)
+    GWHE_CUDA(cudaMemcpyAsync(ct->poly(p), a.poly(p), sizeof(u64) * a.l * c->N,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  return ct;
+}
+
+// ---------------------------------------------------------------- context
+template <class T>
+static T* upload(Context* c, const std::vector<T>& v) {
+  T* d = nullptr;
+  GWHE_CUDA(cudaMalloc(&d, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  GWHE_CUDA(cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return d;
+}
+
+Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
+  GWHE_REQUIRE(P.logN >= 4 && P.logN <= 16, ST_EINVAL, "logN must be in [4, 16]");
+  GWHE_REQUIRE(P.L >= 1 && P.L <= kMaxRowLimbs && P.K >= 1 && P.K <= 16, ST_EINVAL,
+               "need 1 <= L <= 64 and 1 <= K <= 16");
+  GWHE_REQUIRE(P.dnum >= 1 && P.dnum <= P.L, ST_EINVAL, "need 1 <= dnum <= L");
+  GWHE_REQUIRE(P.L + P.K <= kMaxMod, ST_EINVAL, "too many moduli");
+  GWHE_REQUIRE(P.q0_bits <= 60 && P.sp_bits <= 60 && P.scale_bits <= 60, ST_EINVAL,
+               "moduli must stay below 2^60");
+  const int alpha = (P.L + P.dnum - 1) / P.dnum;
+  GWHE_REQUIRE(alpha <= 16, ST_EINVAL, "digits wider than 16 limbs are not supported");
+  // the special modulus P must dominate every digit for the switch noise to stay small
+  const int digit_bits = P.q0_bits + (alpha - 1) * (P.scale_bits + 1);
+  GWHE_REQUIRE(P.K * P.sp_bits + 4 >= digit_bits, ST_EINVAL,
+               "special primes too small for the digit size (need K*sp_bits >= digit bits)");
+
+  std::unique_ptr<Context> c(new Context());
+  c->P = P;
+  c->logN = P.logN;
+  c->N = 1 << P.logN;
+  c->alpha = alpha;
+  c->nmod = P.L + P.K;
+  c->seed = seed;
+  c->stream = stream;
+  const int N = c->N, L = P.L, K = P.K, nm = c->nmod;
+  c->mod.resize(nm);
+  if (gen_primes(P.logN, L, P.q0_bits, P.scale_bits, K, P.sp_bits, c->mod.data(),
+                 c->mod.data() + L) != ST_OK)
+    throw Error(ST_EINVAL, "prime generation failed");
+  for (u64 q : c->mod) c->hmod.push_back(make_devmod(q));
+  c->d_mod = upload(c.get(), c->hmod);
+
+  // stream-ordered pool: keep freed blocks for reuse
+  cudaMemPool_t pool;
+  int dev = 0;
+  GWHE_CUDA(cudaGetDevice(&dev));
+  GWHE_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  GWHE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+
+  // NTT tables
+  {
+    std::vector<u64> psi((size_t)nm * N), psi_sh((size_t)nm * N), ipsi((size_t)nm * N),
+        ipsi_sh((size_t)nm * N), ninv(nm), ninv_sh(nm), pw(N), ipw(N);
+    for (int u = 0; u < nm; ++u) {
+      const u64 q = c->mod[u];
+      const u64 r = find_psi(q, P.logN), ri = host_inv(r, q);
+      pw[0] = ipw[0] = 1;
+      for (int k = 1; k < N; ++k) {
+        pw[k] = host_mulmod(pw[k - 1], r, q);
+        ipw[k] = host_mulmod(ipw[k - 1], ri, q);
+      }
+      for (int i = 0; i < N; ++i) {
+        const int b = bitrev_host(i, P.logN);
+        const size_t o = (size_t)u * N + i;
+        psi[o] = pw[b];
+        psi_sh[o] = shoup_companion(psi[o], q);
+        ipsi[o] = ipw[b];
+        ipsi_sh[o] = shoup_companion(ipsi[o], q);
+      }
+      ninv[u] = host_inv((u64)N % q, q);
+      ninv_sh[u] = shoup_companion(ninv[u], q);
+    }
+    c->d_psi = upload(c.get(), psi);
+    c->d_psi_sh = upload(c.get(), psi_sh);
+    c->d_ipsi = upload(c.get(), ipsi);
+    c->d_ipsi_sh = upload(c.get(), ipsi_sh);
+    c->d_ninv = upload(c.get(), ninv);
+    c->d_ninv_sh = upload(c.get(), ninv_sh);
+  }
+  // rescale: entry (l, i) = q_{l-1}^-1 mod q_i for i < l - 1
+  {
+    std::vector<u64> t((size_t)(L + 1) * L * 2, 0);
+    for (int l = 2; l <= L; ++l)
+      for (int i = 0; i < l - 1; ++i) {
+        const u64 q = c->mod[i];
+        const u64 v = host_inv(c->mod[l - 1] % q, q);
+        t[((size_t)l * L + i) * 2] = v;
+        t[((size_t)l * L + i) * 2 + 1] = shoup_companion(v, q);
+      }
+    c->d_rescale = upload(c.get(), t);
+  }
+  // base conversion tables
+  {
+    std::vector<u64> store;
+    std::vector<std::pair<ConvTable*, size_t>> fix;
+    auto add_table = [&](ConvTable& t, const std::vector<int>& in_mod, const std::vector<int>& out_mod) {
+      t.n_in = (int)in_mod.size();
+      t.n_out = (int)out_mod.size();
+      const size_t base = store.size();
+      store.resize(base + 2 * t.n_in + (size_t)t.n_in * t.n_out);
+      for (int i = 0; i < t.n_in; ++i) {
+        const u64 qi = c->mod[in_mod[i]];
+        u64 h = 1;
+        for (int i2 = 0; i2 < t.n_in; ++i2)
+          if (i2 != i) h = host_mulmod(h, c->mod[in_mod[i2]] % qi, qi);
+        const u64 hinv = host_inv(h, qi);
+        store[base + i] = hinv;
+        store[base + t.n_in + i] = shoup_companion(hinv, qi);
+        for (int o = 0; o < t.n_out; ++o) {
+          const u64 mo = c->mod[out_mod[o]];
+          u64 hm = 1;
+          for (int i2 = 0; i2 < t.n_in; ++i2)
+            if (i2 != i) hm = host_mulmod(hm, c->mod[in_mod[i2]] % mo, mo);
+          store[base + 2 * t.n_in + (size_t)i * t.n_out + o] = hm;
+        }
+      }
+      fix.push_back({&t, base});
+    };
+    for (int l = 1; l <= L; ++l) {
+      const int beta = (l + alpha - 1) / alpha;
+      for (int j = 0; j < beta; ++j) {
+        const int lo = j * alpha, hi = std::min(lo + alpha, l);
+        ConvTable& t = c->modup[{l, j}];
+        t.in_lo = lo;
+        std::vector<int> in_mod, out_mod;
+        for (int i = lo; i < hi; ++i) in_mod.push_back(i);
+        for (int i = 0; i < l; ++i)
+          if (i < lo || i >= hi) {
+            out_mod.push_back(i);
+            t.out_limb.push_back((uint16_t)i);
+          }
+        for (int k = 0; k < K; ++k) {
+          out_mod.push_back(L + k);
+          t.out_limb.push_back((uint16_t)(l + k));
+        }
+        for (int m : out_mod) t.out_pidx.push_back((uint8_t)m);
+        add_table(t, in_mod, out_mod);
+      }
+    }
+    {
+      ConvTable& t = c->moddown;
+      t.in_lo = L;
+      std::vector<int> in_mod, out_mod;
+      for (int k = 0; k < K; ++k) in_mod.push_back(L + k);
+      for (int i = 0; i < L; ++i) {
+        out_mod.push_back(i);
+        t.out_limb.push_back((uint16_t)i);
+        t.out_pidx.push_back((uint8_t)i);
+      }
+      add_table(t, in_mod, out_mod);
+    }
+    c->d_conv_store = upload(c.get(), store);
+    for (auto& f : fix) f.first->dev = c->d_conv_store + f.second;
+    std::vector<u64> pinv((size_t)L * 2);
+    for (int i = 0; i < L; ++i) {
+      const u64 q = c->mod[i];
+      u64 Pm = 1;
+      for (int k = 0; k < K; ++k) Pm = host_mulmod(Pm, c->mod[L + k] % q, q);
+      pinv[2 * i] = host_inv(Pm, q);
+      pinv[2 * i + 1] = shoup_companion(pinv[2 * i], q);
+    }
+    c->d_pinv = upload(c.get(), pinv);
+  }
+  // encoding tables
+  {
+    const int M = N / 2, logM = P.logN - 1;
+    std::vector<double> W(M), T(2 * M);
+    std::vector<double2> w2(M / 2), t2(M);
+    auto pack = [&](void) {
+      for (int t = 0; t < M / 2; ++t) w2[t] = make_double2(W[2 * t], W[2 * t + 1]);
+      for (int k = 0; k < M; ++k) t2[k] = make_double2(T[2 * k], T[2 * k + 1]);
+    };
+    fft_twiddles(P.logN, -1, W.data(), T.data());
+    pack();
+    c->d_fftW_enc = upload(c.get(), w2);
+    c->d_fftT_enc = upload(c.get(), t2);
+    fft_twiddles(P.logN, +1, W.data(), T.data());
+    pack();
+    c->d_fftW_dec = upload(c.get(), w2);
+    c->d_fftT_dec = upload(c.get(), t2);
+    std::vector<int> pos(M), uu(M);
+    u64 g = 1;
+    const u64 twoN = (u64)2 * N;
+    for (int j = 0; j < M; ++j) {
+      uu[j] = (int)((g - 1) / 4);
+      pos[j] = bitrev_host(uu[j], logM);
+      g = (g * 5) % twoN;
+    }
+    c->d_slot_pos = upload(c.get(), pos);
+    c->d_slot_u = upload(c.get(), uu);
+  }
+  return c.release();
+}
+
+void ctx_destroy(Context* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_psi_sh, (void*)c->d_ipsi,
+                  (void*)c->d_ipsi_sh, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
+                  (void*)c->d_pinv, (void*)c->d_conv_store, (void*)c->d_fftW_enc,
+                  (void*)c->d_fftT_enc, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
+                  (void*)c->d_slot_pos, (void*)c->d_slot_u})
+    if (p) cudaFree(p);
+  for (auto& kv : c->masks) cudaFree(kv.second);
+  for (auto& r : c->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  if (c->d_sk) cudaFreeAsync(c->d_sk, c->stream);
+  if (c->d_pk) cudaFreeAsync(c->d_pk, c->stream);
+  for (auto& kv : c->ksk)
+    if (kv.second.d) cudaFreeAsync(kv.second.d, c->stream);
+  cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+// ---------------------------------------------------------------- keys
+static RowMap rows_all(const Context* c, int first, int count, int poly_stride, int npoly) {
+  RowMap rm;
+  rm.npoly = npoly;
+  rm.nl = count;
+  rm.poly_stride = poly_stride;
+  for (int i = 0; i < count; ++i) {
+    rm.off[i] = (uint16_t)i;
+    rm.pidx[i] = (uint8_t)(first + i);
+  }
+  return rm;
+}
+
+static void make_ksk(Context* c, u32 key_id, const u64* target) {
+  const int N = c->N, L = c->P.L, K = c->P.K, nm = L + K;
+  Ksk k;
+  k.d = dalloc_u64(c, c->ksk_words());
+  Tmp e(c, sizeof(u64) * nm * N);
+  std::vector<uint8_t> pidx(nm);
+  for (int u = 0; u < nm; ++u) pidx[u] = (uint8_t)u;
+  for (int j = 0; j < c->P.dnum; ++j) {
+    u64* bj = k.d + ((size_t)j * 2 + 0) * nm * N;
+    u64* aj = k.d + ((size_t)j * 2 + 1) * nm * N;
+    sample_cbd_rns(c, obj_ksk_e(key_id, j), e.u(), pidx.data(), nm);
+    ntt_forward(c, e.u(), rows_all(c, 0, nm, nm, 1));
+    for (int u = 0; u < nm; ++u) sample_uniform(c, obj_ksk_a(key_id, j), (u32)u, u, aj + (size_t)u * N);
+    ntt_forward(c, aj, rows_all(c, 0, nm, nm, 1));
+    const int lo = j * c->alpha, hi = std::min(lo + c->alpha, L);
+    for (int u = 0; u < nm; ++u) {
+      u64 pm = 0;
+      const u64* t = nullptr;
+      if (u >= lo && u < hi) {
+        pm = 1;
+        for (int kk = 0; kk < K; ++kk) pm = host_mulmod(pm, c->mod[L + kk] % c->mod[u], c->mod[u]);
+        t = target + (size_t)u * N;
+      }
+      ksk_combine(c, bj + (size_t)u * N, aj + (size_t)u * N, e.u() + (size_t)u * N,
+                  c->d_sk + (size_t)u * N, t, pm, u);
+    }
+  }
+  auto it = c->ksk.find(key_id);
+  if (it != c->ksk.end() && it->second.d) dfree(c, it->second.d);
+  c->ksk[key_id] = k;
+}
+
+void add_galois_key(Context* c, u32 g) {
+  const int N = c->N, nm = c->nmod;
+  Tmp t(c, sizeof(u64) * nm * N);
+  automorph_ntt(c, PolyView{t.u(), nm}, CPolyView{c->d_sk, nm}, 1, nm, g);
+  make_ksk(c, g, t.u());
+}
+
+void keygen(Context* c, const std::vector<u32>& galois) {
+  const int N = c->N, L = c->P.L, nm = c->nmod;
+  std::vector<uint8_t> pidx(nm);
+  for (int u = 0; u < nm; ++u) pidx[u] = (uint8_t)u;
+  if (!c->d_sk) c->d_sk = dalloc_u64(c, (size_t)nm * N);
+  sample_ternary_rns(c, kObjSk, c->d_sk, pidx.data(), nm);
+  ntt_forward(c, c->d_sk, rows_all(c, 0, nm, nm, 1));
+  if (!c->d_pk) c->d_pk = dalloc_u64(c, (size_t)2 * L * N);
+  {
+    Tmp e(c, sizeof(u64) * L * N);
+    sample_cbd_rns(c, kObjPkE, e.u(), pidx.data(), L);
+    ntt_forward(c, e.u(), rows_all(c, 0, L, L, 1));
+    u64* a = c->d_pk + (size_t)L * N;
+    for (int i = 0; i < L; ++i) sample_uniform(c, kObjPkA, (u32)i, i, a + (size_t)i * N);
+    ntt_forward(c, a, rows_all(c, 0, L, L, 1));
+    for (int i = 0; i < L; ++i)
+      ksk_combine(c, c->d_pk + (size_t)i * N, a + (size_t)i * N, e.u() + (size_t)i * N,
+                  c->d_sk + (size_t)i * N, nullptr, 0, i);
+  }
+  {
+    // relinearisation: target s^2 (limb u of the secret lies modulo mod[u])
+    Tmp s2(c, sizeof(u64) * nm * N);
+    ew_mul_plain(c, PolyView{s2.u(), nm}, CPolyView{c->d_sk, nm}, 1, nm, c->d_sk);
+    make_ksk(c, 0, s2.u());
+  }
+  for (u32 g : galois) add_galois_key(c, g);
+  c->have_keys = true;
+}
+
+u32 galois_for_rotation(const Context* c, int r) {
+  const int M = c->N / 2;
+  const u64 twoN = (u64)2 * c->N;
+  int e = ((r % M) + M) % M;
+  u64 g = 1;
+  for (int i = 0; i < e; ++i) g = (g * 5) % twoN;
+  return (u32)g;
+}
+u32 galois_conj(const Context* c) { return (u32)(2 * c->N - 1); }
+
+// ---------------------------------------------------------------- arithmetic
+static void check_scales(double a, double b) {
+  if (std::fabs(a / b - 1.0) > std::ldexp(1.0, -10))
+    throw Error(ST_ESCALE, "scale mismatch: " + std::to_string(a) + " vs " + std::to_string(b));
+}
+
+void op_addsub(Context* c, const Ct& a, const Ct& b, Ct& out, bool sub) {
+  GWHE_REQUIRE(a.l == b.l && a.npoly == b.npoly, ST_ELEVEL, "operands at different levels");
+  GWHE_REQUIRE(out.cap >= a.l && out.npoly == a.npoly, ST_EINVAL, "output too small");
+  check_scales(a.scale, b.scale);
+  ew_addsub(c, pv(out), cpv(a), cpv(b), a.npoly, a.l, sub);
+  out.l = a.l;
+  out.scale = a.scale;
+}
+
+void op_negate(Context* c, const Ct& a, Ct& out) {
+  ew_negate(c, pv(out), cpv(a), a.npoly, a.l);
+  out.l = a.l;
+  out.scale = a.scale;
+}
+
+static std::vector<u64> signed_residues(const Context* c, i64 v, int l) {
+  std::vector<u64> r(l);
+  for (int i = 0; i < l; ++i) {
+    const u64 q = c->mod[i];
+    if (v >= 0) {
+      r[i] = (u64)v % q;
+    } else {
+      const u64 t = ((u64)(-(v + 1)) + 1) % q;
+      r[i] = t ? q - t : 0;
+    }
+  }
+  return r;
+}
+
+void op_add_const(Context* c, Ct& ct, double v) {
+  const i64 m0 = std::llrint(v * ct.scale);
+  const std::vector<u64> r = signed_residues(c, m0, ct.l);
+  ew_add_scalar_poly0(c, pv(ct), ct.l, r.data());
+}
+
+void op_mul_int(Context* c, Ct& ct, i64 k) {
+  const std::vector<u64> r = signed_residues(c, k, ct.l);
+  ew_mul_scalar(c, pv(ct), cpv(ct), ct.npoly, ct.l, r.data());
+}
+
+void op_mul_const(Context* c, Ct& ct, double v) {
+  GWHE_REQUIRE(ct.l >= 2, ST_ELEVEL, "no level left for a constant product");
+  const u64 ql = c->mod[ct.l - 1];
+  const i64 m0 = std::llrint(v * (double)ql);
+  const std::vector<u64> r = signed_residues(c, m0, ct.l);
+  ew_mul_scalar(c, pv(ct), cpv(ct), ct.npoly, ct.l, r.data());
+  ct.scale = ct.scale * (double)ql;
+  op_rescale(c, ct);
+}
+
+void op_mul_plain(Context* c, const Ct& a, const u64* pt, double pt_scale, Ct& out) {
+  ew_mul_plain(c, pv(out), cpv(a), a.npoly, a.l, pt);
+  out.l = a.l;
+  out.scale = a.scale * pt_scale;
+}
+
+void op_add_plain(Context* c, Ct& ct, const u64* pt) { ew_add_plain_poly0(c, pv(ct), ct.l, pt); }
+
+void op_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& terms, Ct& out3) {
+  GWHE_REQUIRE(!terms.empty(), ST_EINVAL, "empty tensor sum");
+  const int l = terms[0].first->l;
+  std::vector<MacPair> hp;
+  for (auto& t : terms) {
+    GWHE_REQUIRE(t.first->l == l && t.second->l == l, ST_ELEVEL, "tensor operands at different levels");
+    check_scales(t.first->scale * t.second->scale,
+                 terms[0].first->scale * terms[0].second->scale);
+    hp.push_back(MacPair{t.first->d, t.second->d, t.first->cap, t.second->cap});
+  }
+  Tmp dp(c, sizeof(MacPair) * hp.size());
+  GWHE_CUDA(cudaMemcpyAsync(dp.p, hp.data(), sizeof(MacPair) * hp.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+  GWHE_REQUIRE(out3.npoly == 3 && out3.cap >= l, ST_EINVAL, "tensor output too small");
+  tensor_mac(c, pv(out3), dp.as<MacPair>(), (int)hp.size(), l);
+  out3.l = l;
+  out3.scale = terms[0].first->scale * terms[0].second->scale;
+}
+
+void keyswitch(Context* c, const u64* x_ntt, int l, const Ksk& key, u64* out0, u64* out1,
+               const u64* add0, const u64* add1) {
+  const int N = c->N, K = c->P.K, L = c->P.L, ne = l + K;
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  ++c->ks_count;
+  ++c->ks_by_level[l];
+  Tmp xc(c, sizeof(u64) * l * N);
+  GWHE_CUDA(cudaMemcpyAsync(xc.p, x_ntt, sizeof(u64) * l * N, cudaMemcpyDeviceToDevice, c->stream));
+  ntt_inverse(c, xc.u(), rows_q(1, l, l));
+  Tmp ext(c, sizeof(u64) * beta * ne * N);
+  modup_convert(c, xc.u(), l, ext.u());
+  for (int j = 0; j < beta; ++j) {
+    const ConvTable& t = c->modup.at({l, j});
+    RowMap rm;
+    rm.npoly = 1;
+    rm.nl = t.n_out;
+    rm.poly_stride = ne;
+    for (int o = 0; o < t.n_out; ++o) {
+      rm.off[o] = t.out_limb[o];
+      rm.pidx[o] = t.out_pidx[o];
+    }
+    ntt_forward(c, ext.u() + (size_t)j * ne * N, rm);
+  }
+  Tmp acc(c, sizeof(u64) * 2 * ne * N);
+  ks_inner(c, x_ntt, l, ext.u(), key.d, acc.u());
+  RowMap rk;
+  rk.npoly = 2;
+  rk.nl = K;
+  rk.poly_stride = ne;
+  for (int k = 0; k < K; ++k) {
+    rk.off[k] = (uint16_t)(l + k);
+    rk.pidx[k] = (uint8_t)(L + k);
+  }
+  ntt_inverse(c, acc.u(), rk);
+  Tmp conv(c, sizeof(u64) * 2 * l * N);
+  moddown_convert(c, acc.u(), l, conv.u());
+  ntt_forward(c, conv.u(), rows_q(2, l, l));
+  moddown_combine(c, acc.u(), conv.u(), l, out0, out1, add0, add1);
+}
+
+void op_relin(Context* c, const Ct& t3, Ct& out) {
+  GWHE_REQUIRE(t3.npoly == 3, ST_EINVAL, "relinearisation needs a tensor");
+  auto it = c->ksk.find(0);
+  GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "no relinearisation key");
+  const int l = t3.l;
+  GWHE_REQUIRE(out.cap >= l && out.npoly == 2, ST_EINVAL, "output too small");
+  keyswitch(c, t3.poly(2), l, it->second, out.poly(0), out.poly(1), t3.poly(0), t3.poly(1));
+  out.l = l;
+  out.scale = t3.scale;
+}
+
+void op_rescale(Context* c, Ct& ct) {
+  const int l = ct.l, np = ct.npoly, N = c->N;
+  GWHE_REQUIRE(l >= 2, ST_ELEVEL, "no level left to rescale");
+  Tmp last(c, sizeof(u64) * np * N);
+  for (int p = 0; p < np; ++p)
+    GWHE_CUDA(cudaMemcpyAsync(last.u() + (size_t)p * N, ct.limb(p, l - 1), sizeof(u64) * N,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  RowMap rl;
+  rl.npoly = np;
+  rl.nl = 1;
+  rl.poly_stride = 1;
+  rl.off[0] = 0;
+  rl.pidx[0] = (uint8_t)(l - 1);
+  ntt_inverse(c, last.u(), rl);
+  Tmp tmp(c, sizeof(u64) * np * (l - 1) * N);
+  rescale_prep(c, last.u(), np, l, tmp.u());
+  ntt_forward(c, tmp.u(), rows_q(np, l - 1, l - 1));
+  rescale_combine(c, pv(ct), tmp.u(), np, l);
+  ct.l = l - 1;
+  ct.scale = ct.scale / (double)c->mod[l - 1];
+}
+
+void op_mult(Context* c, const Ct& a, const Ct& b, Ct& out) {
+  GWHE_REQUIRE(a.l == b.l, ST_ELEVEL, "operands at different levels");
+  CtPtr t = ct_new(c, 3, a.l, a.l, 1.0);
+  op_tensor_mac(c, {{&a, &b}}, *t);
+  op_relin(c, *t, out);
+  op_rescale(c, out);
+}
+
+void op_galois(Context* c, const Ct& a, u32 g, Ct& out) {
+  auto it = c->ksk.find(g);
+  GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "missing Galois key " + std::to_string(g));
+  GWHE_REQUIRE(&a != &out && a.d != out.d, ST_EINVAL, "automorphism output must not alias");
+  GWHE_REQUIRE(out.cap >= a.l, ST_EINVAL, "output too small");
+  const int l = a.l;
+  automorph_ntt(c, pv(out), cpv(a), 2, l, g);
+  keyswitch(c, out.poly(1), l, it->second, out.poly(0), out.poly(1), out.poly(0), nullptr);
+  out.l = l;
+  out.scale = a.scale;
+}
+
+void op_rotate(Context* c, const Ct& a, int r, Ct& out) { op_galois(c, a, galois_for_rotation(c, r), out); }
+void op_conj(Context* c, const Ct& a, Ct& out) { op_galois(c, a, galois_conj(c), out); }
+
+void op_drop(Ct& ct, int l) {
+  GWHE_REQUIRE(l >= 1 && l <= ct.l, ST_ELEVEL, "cannot raise a level");
+  ct.l = l;
+}
+
+// ---------------------------------------------------------------- encoding
+void encode_to_ntt(Context* c, const double2* z, int count, double scale, int l, u64* pt) {
+  const int N = c->N;
+  Tmp work(c, sizeof(double2) * count * (N / 2));
+  Tmp ints(c, sizeof(i64) * count * N);
+  encode_batch(c, z, count, scale, ints.as<i64>(), work.as<double2>());
+  int_to_rns(c, ints.as<i64>(), count, l, pt);
+  ntt_forward(c, pt, rows_q(count, l, l));
+}
+
+const u64* mask_pt(Context* c, int kind, long index, int l, double scale,
+                   const std::vector<double2>& slots) {
+  auto key = std::make_tuple(kind, index, l, scale);
+  auto it = c->masks.find(key);
+  if (it != c->masks.end()) return it->second;
+  const int M = c->N / 2;
+  GWHE_REQUIRE((int)slots.size() == M, ST_EINVAL, "mask must hold N/2 slots");
+  Tmp z(c, sizeof(double2) * M);
+  GWHE_CUDA(cudaMemcpyAsync(z.p, slots.data(), sizeof(double2) * M, cudaMemcpyHostToDevice,
+                            c->stream));
+  u64* pt = nullptr;
+  GWHE_CUDA(cudaMalloc(&pt, sizeof(u64) * l * c->N));
+  encode_to_ntt(c, z.as<double2>(), 1, scale, l, pt);
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  c->masks[key] = pt;
+  return pt;
+}
+
+void encrypt_coeffs(Context* c, const i64* m, int count, int l, u64 id0, u64* out, int out_cap) {
+  GWHE_REQUIRE(c->d_pk, ST_ENOKEY, "no public key");
+  const int N = c->N;
+  Tmp tmp(c, sizeof(u64) * count * 3 * l * N);
+  enc_sample(c, id0, count, l, m, tmp.u());
+  ntt_forward(c, tmp.u(), rows_q(count * 3, l, l));
+  enc_combine(c, tmp.u(), count, l, out, out_cap, (size_t)2 * out_cap * N);
+}
+
+void encrypt_slots(Context* c, const double2* z, int count, double scale, int l, u64 id0, u64* out,
+                   int out_cap) {
+  const int N = c->N;
+  Tmp work(c, sizeof(double2) * count * (N / 2));
+  Tmp ints(c, sizeof(i64) * count * N);
+  encode_batch(c, z, count, scale, ints.as<i64>(), work.as<double2>());
+  encrypt_coeffs(c, ints.as<i64>(), count, l, id0, out, out_cap);
+}
+
+// ---------------------------------------------------------------- transfers
+void ct_import(Context* c, Ct& ct, const u64* host_coeff, int npoly, int l, double scale) {
+  GWHE_REQUIRE(ct.npoly == npoly && ct.cap >= l, ST_EINVAL, "ciphertext too small");
+  const size_t N = c->N;
+  for (int p = 0; p < npoly; ++p)
+    GWHE_CUDA(cudaMemcpyAsync(ct.poly(p), host_coeff + (size_t)p * l * N, sizeof(u64) * l * N,
+                              cudaMemcpyHostToDevice, c->stream));
+  RowMap rm = rows_q(npoly, l, ct.cap);
+  ntt_forward(c, ct.d, rm);
+  ct.l = l;
+  ct.scale = scale;
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void ct_export(Context* c, const Ct& ct, u64* host_coeff) {
+  const size_t N = c->N;
+  Tmp t(c, sizeof(u64) * ct.npoly * ct.l * N);
+  for (int p = 0; p < ct.npoly; ++p)
+    GWHE_CUDA(cudaMemcpyAsync(t.u() + (size_t)p * ct.l * N, ct.poly(p), sizeof(u64) * ct.l * N,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  ntt_inverse(c, t.u(), rows_q(ct.npoly, ct.l, ct.l));
+  GWHE_CUDA(cudaMemcpyAsync(host_coeff, t.p, sizeof(u64) * ct.npoly * ct.l * N,
+                            cudaMemcpyDeviceToHost, c->stream));
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void decrypt_coeff(Context* c, const Ct& ct, u64* dev_out) {
+  GWHE_REQUIRE(c->d_sk, ST_ENOKEY, "no secret key");
+  decrypt_ntt(c, cpv(ct), ct.l, dev_out);
+  ntt_inverse(c, dev_out, rows_q(1, ct.l, ct.l));
+}
+
+}  // namespace gwhe

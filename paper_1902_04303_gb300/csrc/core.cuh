@@ -1,0 +1,274 @@
+// core.cuh -- shared types of the gwhe library: 64-bit modular arithmetic on
+// the GPU, the RNS context, ciphertext handles and launch helpers.
+//
+// Residues are uint64 limbs of a polynomial in Z_q[X]/(X^N + 1), stored
+// limb-major ([poly][limb][N]) and, on the device, in the NTT domain unless a
+// buffer is documented as coefficient-domain.  Moduli are below 2^62 so that
+// lazy (Harvey) butterflies can keep values in [0, 4q).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace gwhe {
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef uint32_t u32;
+typedef unsigned __int128 u128;
+
+constexpr int kMaxMod = 96;     // q-limbs + special primes
+constexpr int kMaxRowLimbs = 64;
+
+// Status codes of the C ABI.
+enum Status {
+  ST_OK = 0,
+  ST_EINVAL = -1,
+  ST_ENOMEM = -2,
+  ST_ELEVEL = -3,
+  ST_ESCALE = -4,
+  ST_ENOKEY = -5,
+  ST_ETIMEOUT = -6,
+  ST_ECUDA = -7,
+};
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define GWHE_CUDA(call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw ::gwhe::Error(::gwhe::ST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define GWHE_CHECK_LAUNCH() GWHE_CUDA(cudaGetLastError())
+// every kernel launch of the library goes through this: counts and checks it
+#define GWHE_LAUNCHED(ctx, n)         \
+  do {                                \
+    (ctx)->launches += (n);           \
+    GWHE_CUDA(cudaGetLastError());    \
+  } while (0)
+
+#define GWHE_REQUIRE(cond, code, msg)                    \
+  do {                                                   \
+    if (!(cond)) throw ::gwhe::Error((code), (msg));     \
+  } while (0)
+
+// Per-modulus constants.  R = 2^64 mod q with its Shoup companion, and the
+// 64-bit Barrett factor floor(2^64 / q).
+struct DevMod {
+  u64 q, twoq, R, Rsh, mu;
+};
+
+// ---------------------------------------------------------------- device math
+#if defined(__CUDACC__)
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+// Shoup product x*w mod q for a constant w < q with wsh = floor(w 2^64 / q);
+// valid for any x < 2^64, result in [0, 2q).
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 wsh, u64 q) {
+  u64 h = __umul64hi(x, wsh);
+  return x * w - h * q;
+}
+__device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wsh, u64 q) {
+  return csub(shoup_lazy(x, w, wsh, q), q);
+}
+
+// (hi 2^64 + lo) mod q: hi 2^64 = hi R (mod q) by a Shoup product, lo by a
+// 64-bit Barrett step (quotient estimate off by at most one).
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const DevMod& m) {
+  u64 a = csub(shoup_lazy(hi, m.R, m.Rsh, m.q), m.q);
+  u64 b = csub(lo - __umul64hi(lo, m.mu) * m.q, m.q);
+  return csub(a + b, m.q);
+}
+__device__ __forceinline__ u64 mulmod(u64 a, u64 b, const DevMod& m) {
+  return reduce128(a * b, __umul64hi(a, b), m);
+}
+__device__ __forceinline__ u64 reduce64(u64 x, const DevMod& m) {
+  return csub(x - __umul64hi(x, m.mu) * m.q, m.q);
+}
+__device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) {
+  u64 s = a + b;
+  return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// 128-bit accumulator: safe for up to 128 products of residues below 2^60.
+struct Acc128 {
+  u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128& a, u64 x, u64 y) {
+  u64 l = x * y, h = __umul64hi(x, y);
+  a.lo += l;
+  a.hi += h + (a.lo < l ? 1 : 0);
+}
+
+#endif  // __CUDACC__
+
+// Maps the rows of a batched transform to memory and moduli:
+// row r -> poly r / nl, limb r % nl at data + (poly * poly_stride + off[limb]) * N,
+// modulus index pidx[limb].
+struct RowMap {
+  int npoly;
+  int nl;
+  int poly_stride;
+  uint16_t off[kMaxRowLimbs];
+  uint8_t pidx[kMaxRowLimbs];
+};
+
+// Tables of the negacyclic NTT for one modulus index u, each of length N:
+// psi[i] = psi^brv(i), ipsi[i] = psi^-brv(i), plus Shoup companions.
+struct NttTables {
+  const u64* psi;
+  const u64* psi_sh;
+  const u64* ipsi;
+  const u64* ipsi_sh;
+  const u64* ninv;     // [nmod] N^-1 mod q_u
+  const u64* ninv_sh;  // [nmod]
+  const DevMod* mod;   // [nmod]
+};
+
+struct Context;
+
+// A ciphertext (npoly = 2) or a tensor (npoly = 3) in the NTT domain on the
+// device: poly p, limb i at d + (p * cap + i) * N.
+struct Ct {
+  Context* ctx = nullptr;
+  u64* d = nullptr;
+  int npoly = 2;
+  int cap = 0;
+  int l = 0;
+  double scale = 1.0;
+  bool owned = true;
+  ~Ct();
+  u64* poly(int p) const;
+  u64* limb(int p, int i) const;
+};
+typedef std::unique_ptr<Ct> CtPtr;
+
+// Switching key in the NTT domain: [dnum][2][L+K][N].
+struct Ksk {
+  u64* d = nullptr;
+};
+
+struct Params {
+  int logN, L, q0_bits, scale_bits, K, sp_bits, dnum;
+};
+
+struct ConvTable {  // fast base conversion constants, on the device
+  const u64* dev;   // [n_in] hinv, [n_in] hinv_sh, [n_in][n_out] hmod
+  int n_in, n_out;
+  int in_lo;                          // first input q-limb (ModUp digits)
+  std::vector<uint8_t> out_pidx;      // modulus index of each output limb
+  std::vector<uint16_t> out_limb;     // position of each output limb in the extended basis
+};
+
+// Kernel classes timed by the optional profiler (CUDA events on the stream).
+enum ProfCat {
+  PROF_NTT = 0,
+  PROF_KS_INNER = 1,
+  PROF_TENSOR_MAC = 2,
+  PROF_BASECONV = 3,
+  PROF_ELEMWISE = 4,
+  PROF_ENCODE = 5,
+  PROF_SAMPLE = 6,
+  PROF_NCAT = 7
+};
+struct ProfRec {
+  cudaEvent_t a, b;
+  double bytes;
+  int cat;
+};
+struct Prof {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+struct Context {
+  Params P;
+  int N = 0, logN = 0, alpha = 0, nmod = 0;
+  u64 seed = 0;
+  cudaStream_t stream = 0;
+  std::vector<u64> mod;        // [L + K]: q_0..q_{L-1}, p_0..p_{K-1}
+  std::vector<DevMod> hmod;
+  DevMod* d_mod = nullptr;
+  u64 *d_psi = nullptr, *d_psi_sh = nullptr, *d_ipsi = nullptr, *d_ipsi_sh = nullptr;
+  u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;
+  // rescale: q_{l-1}^-1 mod q_i for every level l and i < l - 1 (value, Shoup)
+  u64* d_rescale = nullptr;    // [L][L][2]
+  // ModUp tables per (level l, digit j) and the ModDown table
+  std::map<std::pair<int, int>, ConvTable> modup;
+  ConvTable moddown;
+  u64* d_pinv = nullptr;       // [L][2] P^-1 mod q_i (value, Shoup)
+  u64* d_conv_store = nullptr; // backing store of all conversion tables
+  // encoding procedure tables
+  double2* d_fftW_enc = nullptr;  // [M/2]
+  double2* d_fftT_enc = nullptr;  // [M]
+  double2* d_fftW_dec = nullptr;
+  double2* d_fftT_dec = nullptr;
+  int* d_slot_pos = nullptr;      // [M] bitrev(u_j) for slot j
+  int* d_slot_u = nullptr;        // [M] u_j
+  // keys
+  u64* d_sk = nullptr;            // [L+K][N] NTT domain
+  u64* d_pk = nullptr;            // [2][L][N] NTT domain (b, a)
+  std::map<u32, Ksk> ksk;         // key id -> switching key
+  bool have_keys = false;
+  // encoded public plaintexts (masks), keyed by (kind, index, level, scale)
+  std::map<std::tuple<int, long, int, double>, u64*> masks;
+  long ks_count = 0;              // key switches issued (relinearisations + automorphisms)
+  long launches = 0;              // kernels launched
+  long ks_by_level[kMaxRowLimbs + 1] = {};  // key switches per level
+  Prof prof;
+  std::string last_error;
+  NttTables tables() const {
+    return NttTables{d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh, d_mod};
+  }
+  size_t ksk_words() const { return (size_t)P.dnum * 2 * (P.L + P.K) * N; }
+};
+
+// ---------------------------------------------------------------- host helpers
+// params.cpp
+int gen_primes(int logN, int L, int q0_bits, int scale_bits, int K, int sp_bits, u64* q, u64* p);
+u64 host_mulmod(u64 a, u64 b, u64 m);
+u64 host_powmod(u64 a, u64 e, u64 m);
+u64 host_inv(u64 a, u64 m);
+u64 find_psi(u64 q, int logN);
+u64 shoup_companion(u64 w, u64 q);
+DevMod make_devmod(u64 q);
+void fft_twiddles(int logN, int sign, double* W, double* T);
+int bitrev_host(int x, int bits);
+
+// Records CUDA events around the launches in its scope when profiling is on;
+// bytes = the algorithmic traffic of those launches.
+struct ProfScope {
+  Context* c;
+  int cat;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(Context* c_, int cat_, double bytes_);
+  ~ProfScope();
+};
+void prof_read(Context* c, double* ms, double* bytes, long* count);
+
+// device memory helpers (stream-ordered pool)
+u64* dalloc_u64(Context* c, size_t words);
+void dfree(Context* c, void* p);
+void* dalloc_bytes(Context* c, size_t bytes);
+
+// ntt.cu
+void ntt_forward(Context* c, u64* data, const RowMap& rm);
+void ntt_inverse(Context* c, u64* data, const RowMap& rm);
+RowMap rows_q(int npoly, int l, int poly_stride);  // limbs 0..l-1 of q-primes
+
+}  // namespace gwhe

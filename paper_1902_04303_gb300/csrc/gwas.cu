@@ -1,0 +1,537 @@
+// gwas.cu -- the encrypted semi-parallel GWAS (paper section "Semi-Parallel
+// GWAS with Homomorphic Encryption", Algorithms 1-11) as sequences of
+// evaluator operations.
+//
+// Slot layouts (M = N/2 slots, nb = padded column length, B = M / nb):
+//   vector v (length n)   slots 0..n-1, zeros elsewhere
+//   CP matrix             one ciphertext per column (Alg. 2)
+//   REP row               entry c repeated nb times: slots c*nb .. c*nb+nb-1
+//   CCP matrix            column c in slots c*nb .. (Alg. 4)
+//   S batch (REP)         row j: slot b*nb + t = S[j, 2b] + i S[j, 2b+1]
+// The op order below is the specification that the CPU oracle's circuit
+// follows as well; ciphertext bits depend on it (every key switch and rescale
+// rounds).
+#include <algorithm>
+#include <cmath>
+
+#include "gwas.cuh"
+
+namespace gwhe {
+
+namespace {
+
+constexpr u64 kEncX = 0x100, kEncA = 0x200, kEncY = 0x300, kEncBeta0 = 0x301, kEncDupW = 0x302,
+              kEncDupWZ = 0x303, kEncXtRep = 0x10000, kEncDupM = 0x20000, kEncS = 0x1000000;
+
+// mask kinds for the plaintext cache
+enum MaskKind { kMaskSlot = 1, kMaskPrefix = 2, kMaskBlock = 3, kMaskEye = 4 };
+
+// eq. sigma7 coefficients of x^1, x^3, x^5, x^7 (the printed c_k / 8^k)
+const double kSig[4] = {-1.73496 / 8.0, 4.19407 / 512.0, -5.43402 / 32768.0,
+                        2.50739 / 2097152.0};
+
+int ilog2(long v) {
+  int r = 0;
+  while ((1L << r) < v) ++r;
+  return r;
+}
+
+struct Eval {
+  Context* c;
+  const Layout& lay;
+
+  CtPtr fresh(int l, double scale = 1.0) { return ct_new(c, 2, l, l, scale); }
+
+  // non-owning view of a at level l (the paper's implicit mod-drop)
+  CtPtr view(const Ct& a, int l) {
+    GWHE_REQUIRE(l <= a.l, ST_ELEVEL, "cannot raise a level");
+    CtPtr v(new Ct());
+    v->ctx = c;
+    v->d = a.d;
+    v->npoly = a.npoly;
+    v->cap = a.cap;
+    v->l = l;
+    v->scale = a.scale;
+    v->owned = false;
+    return v;
+  }
+  CtPtr clone_at(const Ct& a, int l) {
+    CtPtr v = view(a, l);
+    return ct_clone(c, *v);
+  }
+
+  std::vector<double2> slots_zero() { return std::vector<double2>(lay.M, make_double2(0, 0)); }
+
+  CtPtr mul_mask(const Ct& v, int kind, long idx, const std::vector<double2>& z) {
+    const double ql = (double)c->mod[v.l - 1];
+    const u64* pt = mask_pt(c, kind, idx, v.l, ql, z);
+    CtPtr out = fresh(v.l);
+    op_mul_plain(c, v, pt, ql, *out);
+    op_rescale(c, *out);
+    return out;
+  }
+  std::vector<double2> e_slot(int s) {
+    auto z = slots_zero();
+    z[s] = make_double2(1, 0);
+    return z;
+  }
+
+  // t += Rotate(t, step) for step in steps, in place
+  void ladder(Ct& t, const std::vector<int>& steps) {
+    CtPtr r = fresh(t.l);
+    for (int s : steps) {
+      op_rotate(c, t, s, *r);
+      op_addsub(c, t, *r, t, false);
+    }
+  }
+  std::vector<int> pow2_steps(int count, int base = 1) {
+    std::vector<int> s;
+    for (int i = 0; i < count; ++i) s.push_back(base << i);
+    return s;
+  }
+
+  CtPtr mac_relin_rescale(const std::vector<std::pair<const Ct*, const Ct*>>& pairs) {
+    const int l = pairs[0].first->l;
+    CtPtr t3 = ct_new(c, 3, l, l, 1.0);
+    op_tensor_mac(c, pairs, *t3);
+    CtPtr out = fresh(l);
+    op_relin(c, *t3, *out);
+    op_rescale(c, *out);
+    return out;
+  }
+  CtPtr mult(const Ct& a, const Ct& b) {
+    CtPtr out = fresh(a.l);
+    op_mult(c, a, b, *out);
+    return out;
+  }
+  CtPtr add(const Ct& a, const Ct& b) {
+    CtPtr out = fresh(a.l);
+    op_addsub(c, a, b, *out, false);
+    return out;
+  }
+  CtPtr sub(const Ct& a, const Ct& b) {
+    CtPtr out = fresh(a.l);
+    op_addsub(c, a, b, *out, true);
+    return out;
+  }
+  CtPtr negate(const Ct& a) {
+    CtPtr out = fresh(a.l);
+    op_negate(c, a, *out);
+    return out;
+  }
+
+  // Alg. 1 for one entry: mask slot cidx, then rotate-and-add over log2(M) steps
+  CtPtr replicate(const Ct& v, int cidx) {
+    CtPtr t = mul_mask(v, kMaskSlot, cidx, e_slot(cidx));
+    ladder(*t, pow2_steps(lay.logN - 1));
+    return t;
+  }
+  // Alg. 2: sum_c A(c) * Replicate(v)(c)
+  CtPtr cp_matvec(const std::vector<CtPtr>& cols, const Ct& v, int m) {
+    std::vector<CtPtr> reps, views;
+    for (int cidx = 0; cidx < m; ++cidx) reps.push_back(replicate(v, cidx));
+    const int lv = reps[0]->l;
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
+    for (int cidx = 0; cidx < m; ++cidx) {
+      views.push_back(view(*cols[cidx], lv));
+      pairs.push_back({views.back().get(), reps[cidx].get()});
+    }
+    return mac_relin_rescale(pairs);
+  }
+  // Alg. 5: C = A * B then C += Rotate(C, 2^i) for i < log2(M)
+  CtPtr dotprod(const Ct& a, const Ct& b) {
+    CtPtr t = mult(a, b);
+    ladder(*t, pow2_steps(lay.logN - 1));
+    return t;
+  }
+  // Alg. 6: sum_c DotProd(A(c), v) * e_c, masks summed before one rescale
+  CtPtr rp_matvec(const std::vector<CtPtr>& rows, const Ct& v, int m) {
+    CtPtr acc;
+    for (int cidx = 0; cidx < m; ++cidx) {
+      CtPtr rv = view(*rows[cidx], v.l);
+      CtPtr dp = dotprod(*rv, v);
+      const double ql = (double)c->mod[dp->l - 1];
+      const u64* pt = mask_pt(c, kMaskSlot, cidx, dp->l, ql, e_slot(cidx));
+      CtPtr t = fresh(dp->l);
+      op_mul_plain(c, *dp, pt, ql, *t);
+      if (!acc)
+        acc = std::move(t);
+      else
+        op_addsub(c, *acc, *t, *acc, false);
+    }
+    op_rescale(c, *acc);
+    return acc;
+  }
+  // Alg. 4: log2(nb) rotate-and-add steps; block sums land at slots c*nb
+  void colsum(Ct& v) { ladder(v, pow2_steps(ilog2(lay.nb))); }
+  // Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks
+  void duplicate(Ct& v) { ladder(v, pow2_steps(ilog2(lay.B), lay.nb)); }
+
+  // eq. sigma7 at depth 3
+  CtPtr sigma7(const Ct& x) {
+    CtPtr x2 = mult(x, x);
+    CtPtr x4 = mult(*x2, *x2);
+    CtPtr b[4];
+    for (int i = 0; i < 4; ++i) {
+      b[i] = ct_clone(c, x);
+      op_mul_const(c, *b[i], kSig[i]);
+    }
+    CtPtr t3 = mult(*b[1], *x2);
+    CtPtr t7a = mult(*b[3], *x2);
+    CtPtr b5 = view(*b[2], x4->l);
+    CtPtr t5 = mult(*b5, *x4);
+    CtPtr t7 = mult(*t7a, *x4);
+    const int lv = t7->l;
+    CtPtr b1v = view(*b[0], lv), t3v = view(*t3, lv);
+    CtPtr r = add(*b1v, *t3v);
+    op_addsub(c, *r, *t5, *r, false);
+    op_addsub(c, *r, *t7, *r, false);
+    op_add_const(c, *r, 0.5);
+    return r;
+  }
+
+  CtPtr encrypt_vec(const std::vector<double2>& z, u64 id, int level, double scale) {
+    Tmp dz(c, sizeof(double2) * lay.M);
+    GWHE_CUDA(cudaMemcpyAsync(dz.p, z.data(), sizeof(double2) * lay.M, cudaMemcpyHostToDevice,
+                              c->stream));
+    CtPtr ct = fresh(level, scale);
+    encrypt_slots(c, dz.as<double2>(), 1, scale, level, id, ct->d, ct->cap);
+    return ct;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+std::vector<double> to_host(Context* c, const double* p, size_t n) {
+  std::vector<double> h(n);
+  if (is_device_ptr(p)) {
+    GWHE_CUDA(cudaMemcpyAsync(h.data(), p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  } else {
+    std::copy(p, p + n, h.begin());
+  }
+  return h;
+}
+
+}  // namespace
+
+Layout make_layout(int logN, int n, int d, long k) {
+  Layout L;
+  L.logN = logN;
+  L.n = n;
+  L.d = d;
+  L.k = k;
+  L.M = 1 << (logN - 1);
+  L.nb = 1 << ilog2(n);
+  GWHE_REQUIRE(n >= 1 && L.nb <= L.M, ST_EINVAL, "a column of nb slots must fit one ciphertext");
+  L.B = L.M / L.nb;
+  L.tau = 2 * L.B;
+  L.batches = (k + L.tau - 1) / L.tau;
+  L.H = (n + L.B - 1) / L.B;
+  return L;
+}
+
+Job::~Job() {
+  if (DupM_store && c) dfree(c, DupM_store);
+}
+
+Job* job_create(Context* c, int n, int d, long k) {
+  GWHE_REQUIRE(d >= 1 && d <= 64 && k >= 1, ST_EINVAL, "bad job shape");
+  Job* j = new Job();
+  j->c = c;
+  j->lay = make_layout(c->logN, n, d, k);
+  return j;
+}
+
+void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double* yp) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  Eval ev{c, lay};
+  const int n = lay.n, d = lay.d, L = c->P.L;
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  const std::vector<double> X = to_host(c, Xp, (size_t)n * d), A = to_host(c, Ap, (size_t)d * d),
+                            y = to_host(c, yp, n);
+  j->X.clear();
+  j->A.clear();
+  j->XtREP.clear();
+  j->XtREP.resize(d);
+  for (int col = 0; col < d; ++col) {
+    auto z = ev.slots_zero();
+    for (int t = 0; t < n; ++t) z[t] = make_double2(X[(size_t)t * d + col], 0);
+    j->X.push_back(ev.encrypt_vec(z, kEncX + col, L, delta));
+  }
+  for (int col = 0; col < d; ++col) {
+    auto z = ev.slots_zero();
+    for (int r = 0; r < d; ++r) z[r] = make_double2(A[(size_t)r * d + col], 0);
+    j->A.push_back(ev.encrypt_vec(z, kEncA + col, L, delta));
+  }
+  {
+    auto z = ev.slots_zero();
+    for (int t = 0; t < n; ++t) z[t] = make_double2(y[t], 0);
+    j->y = ev.encrypt_vec(z, kEncY, L, delta);
+    j->beta0 = ev.encrypt_vec(ev.slots_zero(), kEncBeta0, L, delta);
+  }
+  for (int col = 0; col < d; ++col)
+    for (int h = 0; h < lay.H; ++h) {
+      auto z = ev.slots_zero();
+      for (int b = 0; b < lay.B; ++b) {
+        const int s = h * lay.B + b;
+        if (s >= n) continue;
+        for (int t = 0; t < lay.nb; ++t) z[b * lay.nb + t] = make_double2(X[(size_t)s * d + col], 0);
+      }
+      j->XtREP[col].push_back(ev.encrypt_vec(z, kEncXtRep + (u64)col * 4096 + h, L, delta));
+    }
+}
+
+static void make_dup_state(Job* j, Eval& ev) {
+  const Layout& lay = j->lay;
+  const int lb = kBatchLevel;
+  GWHE_REQUIRE(j->wzp->l >= lb - 1, ST_ELEVEL, "depth exhausted before the SNP batches");
+  std::vector<CtPtr> src;
+  for (auto& m : j->Mct) src.push_back(ev.view(*m, lb + 1));
+  j->DupM.clear();
+  for (int jj = 0; jj < lay.n; ++jj) {
+    const int h = jj / lay.B, b = jj % lay.B;
+    auto z = ev.slots_zero();
+    for (int t = 0; t < lay.n; ++t) z[b * lay.nb + t] = make_double2(1, 0);
+    CtPtr mj = ev.mul_mask(*src[h], kMaskBlock, ((long)lay.n << 32) | ((long)lay.nb << 16) | b, z);
+    ev.duplicate(*mj);
+    j->DupM.push_back(std::move(mj));
+  }
+  j->DupW = ev.clone_at(*j->w_m, lb - 1);
+  ev.duplicate(*j->DupW);
+  j->DupWZ = ev.clone_at(*j->wzp, lb - 1);
+  ev.duplicate(*j->DupWZ);
+
+}
+
+void job_fit(Job* j, int kappa) {
+  GWHE_REQUIRE(kappa >= 1, ST_EINVAL, "kappa >= 1");
+  GWHE_REQUIRE(!j->X.empty(), ST_EINVAL, "inputs not encrypted");
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  Eval ev{c, lay};
+  const int d = lay.d, n = lay.n;
+  // Alg. 9
+  CtPtr beta = ev.clone_at(*j->beta0, j->beta0->l);
+  CtPtr p, ymp;
+  for (int it = 0; it < kappa; ++it) {
+    CtPtr xb = ev.cp_matvec(j->X, *beta, d);
+    p = ev.sigma7(*xb);
+    CtPtr yv = ev.view(*j->y, p->l);
+    ymp = ev.sub(*yv, *p);
+    CtPtr g = ev.rp_matvec(j->X, *ymp, d);
+    CtPtr ag = ev.cp_matvec(j->A, *g, d);
+    op_mul_int(c, *ag, 4);
+    CtPtr bv = ev.view(*beta, ag->l);
+    beta = ev.sub(*bv, *ag);
+  }
+  j->beta = ev.clone_at(*beta, beta->l);
+  // w = p (1 - p); the masked copy feeds Dup(w) and w z'
+  CtPtr omp = ev.negate(*p);
+  op_add_const(c, *omp, 1.0);
+  CtPtr w = ev.mult(*p, *omp);
+  {
+    auto z = ev.slots_zero();
+    for (int t = 0; t < n; ++t) z[t] = make_double2(1, 0);
+    j->w_m = ev.mul_mask(*w, kMaskPrefix, ((long)n << 16) | lay.nb, z);
+  }
+  // Alg. 10: guess 3; the first step multiplies by integers only
+  CtPtr g = ct_clone(c, *w);
+  op_mul_int(c, *g, 3);
+  {
+    CtPtr u = ev.negate(*g);
+    op_add_const(c, *u, 2.0);
+    op_mul_int(c, *u, 3);
+    g = std::move(u);
+  }
+  for (int it = 0; it < 2; ++it) {
+    CtPtr wv = ev.view(*w, g->l);
+    CtPtr t = ev.mult(*wv, *g);
+    CtPtr u = ev.negate(*t);
+    op_add_const(c, *u, 2.0);
+    CtPtr gv = ev.view(*g, u->l);
+    g = ev.mult(*gv, *u);
+  }
+  CtPtr winv = std::move(g);
+  // eq. z
+  CtPtr xb = ev.cp_matvec(j->X, *beta, d);
+  int lv = std::min(winv->l, ymp->l);
+  CtPtr wi = ev.view(*winv, lv), ym = ev.view(*ymp, lv);
+  CtPtr r = ev.mult(*wi, *ym);
+  lv = std::min(xb->l, r->l);
+  CtPtr xbv = ev.view(*xb, lv), rv = ev.view(*r, lv);
+  j->z = ev.add(*xbv, *rv);
+  // eq. zprime, second form: z' = z - X (A (X^T z))
+  CtPtr xtz = ev.rp_matvec(j->X, *j->z, d);
+  CtPtr axtz = ev.cp_matvec(j->A, *xtz, d);
+  CtPtr xaxtz = ev.cp_matvec(j->X, *axtz, d);
+  CtPtr zv = ev.view(*j->z, xaxtz->l);
+  j->zp = ev.sub(*zv, *xaxtz);
+  CtPtr wmv = ev.view(*j->w_m, j->zp->l);
+  j->wzp = ev.mult(*wmv, *j->zp);
+  // eq. M = I - X A X^T: Alg. 3 (CP-MatMult) then Alg. 8 (CP-REP-MatMult)
+  std::vector<CtPtr> dupXA;
+  for (int rr = 0; rr < d; ++rr) {
+    CtPtr xa = ev.cp_matvec(j->X, *j->A[rr], d);
+    ev.duplicate(*xa);
+    dupXA.push_back(std::move(xa));
+  }
+  j->Mct.clear();
+  for (int h = 0; h < lay.H; ++h) {
+    const int l0 = dupXA[0]->l;
+    std::vector<CtPtr> views;
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
+    for (int rr = 0; rr < d; ++rr) {
+      views.push_back(ev.view(*j->XtREP[rr][h], l0));
+      pairs.push_back({dupXA[rr].get(), views.back().get()});
+    }
+    CtPtr acc = ev.mac_relin_rescale(pairs);
+    CtPtr m = ev.negate(*acc);
+    auto z = ev.slots_zero();
+    for (int b = 0; b < lay.B; ++b) {
+      const int col = h * lay.B + b;
+      if (col < n) z[b * lay.nb + col] = make_double2(1, 0);
+    }
+    const u64* pt = mask_pt(c, kMaskEye, ((long)n << 32) | ((long)lay.nb << 16) | h, m->l,
+                            m->scale, z);
+    op_add_plain(c, *m, pt);
+    j->Mct.push_back(std::move(m));
+  }
+  make_dup_state(j, ev);
+}
+
+void job_set_fit_state(Job* j, const double* Mp, const double* wp, const double* wzp) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  Eval ev{c, lay};
+  const int n = lay.n, lb = kBatchLevel;
+  GWHE_REQUIRE(c->P.L >= lb, ST_ELEVEL, "need at least 4 limbs for the SNP batches");
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  const std::vector<double> M = to_host(c, Mp, (size_t)n * n), w = to_host(c, wp, n),
+                            wz = to_host(c, wzp, n);
+  auto dup = [&](const std::vector<double>& v, size_t stride, size_t off) {
+    auto z = ev.slots_zero();
+    for (int b = 0; b < lay.B; ++b)
+      for (int t = 0; t < n; ++t) z[b * lay.nb + t] = make_double2(v[(size_t)t * stride + off], 0);
+    return z;
+  };
+  j->DupM.clear();
+  for (int jj = 0; jj < n; ++jj) j->DupM.push_back(ev.encrypt_vec(dup(M, n, jj), kEncDupM + jj, lb, delta));
+  j->DupW = ev.encrypt_vec(dup(w, 1, 0), kEncDupW, lb - 1, delta);
+  j->DupWZ = ev.encrypt_vec(dup(wz, 1, 0), kEncDupWZ, lb - 1, delta);
+}
+
+void job_snp_stats(Job* j, const double* S, long b0, long b1) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  Eval ev{c, lay};
+  const int n = lay.n, lb = kBatchLevel, N = c->N;
+  GWHE_REQUIRE((int)j->DupM.size() == n && j->DupW && j->DupWZ, ST_EINVAL,
+               "covariate phase not done (fit or set the fit state first)");
+  GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  const bool dev = is_device_ptr(S);
+  const double* Sd = S;
+  std::unique_ptr<Tmp> Sbuf;
+  if (!dev) {
+    Sbuf.reset(new Tmp(c, sizeof(double) * (size_t)n * lay.k));
+    GWHE_CUDA(cudaMemcpyAsync(Sbuf->p, S, sizeof(double) * (size_t)n * lay.k,
+                              cudaMemcpyHostToDevice, c->stream));
+    Sd = Sbuf->as<double>();
+  }
+  if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
+  Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
+  Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
+  std::vector<Ct> srow(n);
+  for (int jj = 0; jj < n; ++jj) {
+    srow[jj].ctx = c;
+    srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
+    srow[jj].cap = lb;
+    srow[jj].l = lb;
+    srow[jj].scale = delta;
+    srow[jj].owned = false;
+  }
+  for (long bi = b0; bi < b1; ++bi) {
+    // Alg. 11 input: the REP rows of batch bi, encoded and encrypted on the device
+    build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
+    encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
+    // S' = sum_j Dup(M_j) S_ij (Alg. 8), one relinearisation and rescale
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
+    for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
+    CtPtr Sp = ev.mac_relin_rescale(pairs);
+    // numerator = colSum(Dup(w z') S')
+    CtPtr num = ev.mult(*j->DupWZ, *Sp);
+    ev.colsum(*num);
+    // WS' = Dup(w) S'; WSS = WS' S'; WSC = WS' conj(S')
+    CtPtr ws = ev.mult(*j->DupW, *Sp);
+    CtPtr s1 = ev.view(*Sp, lb - 2);
+    CtPtr wss = ev.mult(*ws, *s1);
+    CtPtr cj = ev.fresh(s1->l);
+    op_conj(c, *s1, *cj);
+    CtPtr wsc = ev.mult(*ws, *cj);
+    // denEven / denOdd; the 1/2 is kept as scale metadata
+    CtPtr de = ev.add(*wsc, *wss);
+    de->scale *= 2.0;
+    CtPtr dO = ev.sub(*wsc, *wss);
+    dO->scale *= 2.0;
+    ev.colsum(*de);
+    ev.colsum(*dO);
+    j->out[bi] = {std::move(num), std::move(de), std::move(dO)};
+  }
+}
+
+void job_decrypt(Job* j, double* num, double* den) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  const int N = c->N, M = lay.M;
+  std::vector<long> have;
+  for (long bi = 0; bi < (long)j->out.size(); ++bi)
+    if (j->out[bi][0]) have.push_back(bi);
+  GWHE_REQUIRE(!have.empty(), ST_EINVAL, "no batch results to decrypt");
+  const int cnt = (int)have.size() * 3;
+  Tmp m(c, sizeof(u64) * (size_t)cnt * N);
+  for (size_t h = 0; h < have.size(); ++h)
+    for (int o = 0; o < 3; ++o) {
+      Ct v = *j->out[have[h]][o];
+      v.owned = false;
+      v.l = 1;
+      decrypt_coeff(c, v, m.u() + (h * 3 + o) * (size_t)N);
+    }
+  Tmp z(c, sizeof(double2) * (size_t)cnt * M);
+  Tmp work(c, sizeof(double2) * (size_t)cnt * M);
+  // scales differ per output: decode with scale 1 and divide on the host
+  decode_batch(c, m.u(), cnt, 1.0, z.as<double2>(), work.as<double2>());
+  std::vector<double2> hz((size_t)cnt * M);
+  GWHE_CUDA(cudaMemcpyAsync(hz.data(), z.p, sizeof(double2) * hz.size(), cudaMemcpyDeviceToHost,
+                            c->stream));
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t h = 0; h < have.size(); ++h) {
+    const long bi = have[h];
+    const double sn = j->out[bi][0]->scale, se = j->out[bi][1]->scale, so = j->out[bi][2]->scale;
+    const double2* zn = hz.data() + (h * 3 + 0) * M;
+    const double2* ze = hz.data() + (h * 3 + 1) * M;
+    const double2* zo = hz.data() + (h * 3 + 2) * M;
+    for (int b = 0; b < lay.B; ++b) {
+      const long s0 = bi * lay.tau + 2L * b;
+      const int slot = b * lay.nb;
+      if (s0 < lay.k) {
+        num[s0] = zn[slot].x / sn;
+        den[s0] = ze[slot].x / se;
+      }
+      if (s0 + 1 < lay.k) {
+        num[s0 + 1] = zn[slot].y / sn;
+        den[s0 + 1] = zo[slot].x / so;
+      }
+    }
+  }
+}
+
+}  // namespace gwhe

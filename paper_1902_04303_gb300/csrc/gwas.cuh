@@ -1,0 +1,46 @@
+// gwas.cuh -- the encrypted semi-parallel GWAS job (Algorithms 1-11 of the
+// paper) on the gwhe evaluator.
+#pragma once
+
+#include <array>
+
+#include "ckks.cuh"
+
+namespace gwhe {
+
+// Slot geometry (section "Batching SNPs"): nb = next power of two >= n,
+// B = M / nb blocks (complex SNP columns per ciphertext), tau = 2B SNPs per
+// batch (eq. numSNPinBatch read as N / nb), H = ceil(n / B) ciphertexts for the
+// n x n CCP matrix M.
+struct Layout {
+  int logN = 0, n = 0, d = 0;
+  long k = 0;
+  int M = 0, nb = 0, B = 0, tau = 0, H = 0;
+  long batches = 0;
+};
+Layout make_layout(int logN, int n, int d, long k);
+
+constexpr int kBatchLevel = 4;  // limbs with which a SNP batch enters the loop
+
+struct Job {
+  Context* c = nullptr;
+  Layout lay;
+  std::vector<CtPtr> X, A;
+  std::vector<std::vector<CtPtr>> XtREP;  // [d][H]
+  CtPtr y, beta0, beta, z, zp, w_m, wzp;
+  std::vector<CtPtr> Mct;                 // [H]
+  std::vector<CtPtr> DupM;                // [n]
+  CtPtr DupW, DupWZ;
+  std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd
+  u64* DupM_store = nullptr;              // contiguous storage of DupM (split mode)
+  ~Job();
+};
+
+Job* job_create(Context* c, int n, int d, long k);
+void job_encrypt_inputs(Job* j, const double* X, const double* A, const double* y);
+void job_fit(Job* j, int kappa);
+void job_set_fit_state(Job* j, const double* M, const double* w, const double* wz);
+void job_snp_stats(Job* j, const double* S_dev, long b0, long b1);
+void job_decrypt(Job* j, double* num, double* den);
+
+}  // namespace gwhe

@@ -1,0 +1,830 @@
+// kernels.cu -- element-wise ring arithmetic, the tensor sum of the CP-REP
+// product, fast base conversion (ModUp / ModDown), the key inner product,
+// rescale, Galois automorphisms, ChaCha20 sampling, and the FP64 encoding
+// procedure of the gwhe library.  See kernels.cuh for the interfaces.
+#include "kernels.cuh"
+
+namespace gwhe {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline dim3 grid_rows(int N, int rows) { return dim3((N + kThreads - 1) / kThreads, rows); }
+
+struct LimbVals {
+  u64 v[kMaxRowLimbs];
+  u64 sh[kMaxRowLimbs];
+};
+
+// ------------------------------------------------------------- element-wise
+__global__ void k_addsub(PolyView out, CPolyView a, CPolyView b, int l, int N,
+                         const DevMod* __restrict__ mod, int sub) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 q = mod[i].q;
+  const u64 x = a.d[((size_t)p * a.cap + i) * N + k];
+  const u64 y = b.d[((size_t)p * b.cap + i) * N + k];
+  out.d[((size_t)p * out.cap + i) * N + k] = sub ? submod(x, y, q) : addmod(x, y, q);
+}
+
+__global__ void k_negate(PolyView out, CPolyView a, int l, int N, const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 x = a.d[((size_t)p * a.cap + i) * N + k];
+  out.d[((size_t)p * out.cap + i) * N + k] = x ? mod[i].q - x : 0;
+}
+
+__global__ void k_mul_scalar(PolyView out, CPolyView a, int l, int N, const DevMod* __restrict__ mod,
+                             const LimbVals v) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 x = a.d[((size_t)p * a.cap + i) * N + k];
+  out.d[((size_t)p * out.cap + i) * N + k] = shoup(x, v.v[i], v.sh[i], mod[i].q);
+}
+
+__global__ void k_add_scalar0(PolyView ct, int N, const DevMod* __restrict__ mod, const LimbVals v) {
+  const int i = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  u64* p = ct.d + (size_t)i * N + k;
+  *p = addmod(*p, v.v[i], mod[i].q);
+}
+
+__global__ void k_mul_plain(PolyView out, CPolyView a, const u64* __restrict__ pt, int l, int N,
+                            const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 x = a.d[((size_t)p * a.cap + i) * N + k];
+  out.d[((size_t)p * out.cap + i) * N + k] = mulmod(x, pt[(size_t)i * N + k], mod[i]);
+}
+
+__global__ void k_add_plain0(PolyView ct, const u64* __restrict__ pt, int N,
+                             const DevMod* __restrict__ mod) {
+  const int i = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  u64* p = ct.d + (size_t)i * N + k;
+  *p = addmod(*p, pt[(size_t)i * N + k], mod[i].q);
+}
+
+// Sum over pairs of (a0 b0, a0 b1 + a1 b0, a1 b1), 128-bit accumulation with a
+// reduction every 32 pairs (at most 64 products of < 2^120 per accumulator).
+__global__ void k_tensor_mac(PolyView out, const MacPair* __restrict__ pairs, int npairs, int l,
+                             int N, const DevMod* __restrict__ mod) {
+  const int i = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const DevMod m = mod[i];
+  Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
+  u64 r0 = 0, r1 = 0, r2 = 0;
+  const size_t off = (size_t)i * N + k;
+  for (int j = 0; j < npairs; ++j) {
+    const MacPair P = pairs[j];
+    const u64 a0 = P.a[off], a1 = P.a[(size_t)P.capa * N + off];
+    const u64 b0 = P.b[off], b1 = P.b[(size_t)P.capb * N + off];
+    mac128(s0, a0, b0);
+    mac128(s1, a0, b1);
+    mac128(s1, a1, b0);
+    mac128(s2, a1, b1);
+    if ((j & 31) == 31) {
+      r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
+      r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
+      r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
+      s0 = Acc128{0, 0};
+      s1 = Acc128{0, 0};
+      s2 = Acc128{0, 0};
+    }
+  }
+  r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
+  r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
+  r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
+  out.d[off] = r0;
+  out.d[(size_t)out.cap * N + off] = r1;
+  out.d[(size_t)2 * out.cap * N + off] = r2;
+}
+
+// ------------------------------------------------------------- base conversion
+struct ConvArgs {
+  const u64* tab;  // [n_in] hinv, [n_in] hinv_sh, [n_in][n_out] hmod
+  int n_in, n_out, hm_stride, in_mod0;
+  uint8_t out_pidx[kMaxRowLimbs];
+  uint16_t out_row[kMaxRowLimbs];
+};
+constexpr int kMaxConvIn = 16;
+
+// y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o
+__global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __restrict__ out,
+                           size_t out_pstride, const ConvArgs a, int N,
+                           const DevMod* __restrict__ mod) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int p = blockIdx.y;
+  const u64* xp = x + p * x_pstride;
+  u64* op = out + p * out_pstride;
+  u64 y[kMaxConvIn];
+#pragma unroll
+  for (int i = 0; i < kMaxConvIn; ++i) {
+    if (i < a.n_in) {
+      const u64 q = mod[a.in_mod0 + i].q;
+      y[i] = shoup(xp[(size_t)i * N + k], a.tab[i], a.tab[a.n_in + i], q);
+    }
+  }
+  const u64* hm = a.tab + 2 * a.n_in;
+  for (int o = 0; o < a.n_out; ++o) {
+    Acc128 s{0, 0};
+#pragma unroll
+    for (int i = 0; i < kMaxConvIn; ++i)
+      if (i < a.n_in) mac128(s, y[i], hm[i * a.hm_stride + o]);
+    op[(size_t)a.out_row[o] * N + k] = reduce128(s.lo, s.hi, mod[a.out_pidx[o]]);
+  }
+}
+
+// acc_p[u] = sum_j x_j[u] * key_j[p][u] over digits, for the l + K extended limbs;
+// x_j[u] is the input limb itself when u lies in digit j, else the converted limb.
+__global__ void k_ks_inner(const u64* __restrict__ c_ntt, const u64* __restrict__ ext,
+                           const u64* __restrict__ key, u64* __restrict__ acc, int l, int K, int L,
+                           int alpha, int beta, int N, const DevMod* __restrict__ mod) {
+  const int u = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int ne = l + K;
+  const int mi = u < l ? u : L + (u - l);
+  const size_t LK = (size_t)(L + K);
+  Acc128 s0{0, 0}, s1{0, 0};
+  for (int j = 0; j < beta; ++j) {
+    const int lo = j * alpha, hi = min(lo + alpha, l);
+    const u64 x = (u >= lo && u < hi) ? c_ntt[(size_t)u * N + k] : ext[((size_t)j * ne + u) * N + k];
+    const u64 b = key[(((size_t)j * 2 + 0) * LK + mi) * N + k];
+    const u64 a = key[(((size_t)j * 2 + 1) * LK + mi) * N + k];
+    mac128(s0, x, b);
+    mac128(s1, x, a);
+  }
+  const DevMod m = mod[mi];
+  acc[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
+  acc[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+}
+
+// out_p[i] = (acc_p[i] - conv_p[i]) P^-1 mod q_i (+ add_p[i])
+__global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __restrict__ conv, int l,
+                                  int K, u64* out0, u64* out1, const u64* add0, const u64* add1,
+                                  const u64* __restrict__ pinv, int N,
+                                  const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 q = mod[i].q;
+  const int ne = l + K;
+  const u64 a = acc[((size_t)p * ne + i) * N + k];
+  const u64 cv = conv[((size_t)p * l + i) * N + k];
+  u64 v = shoup(submod(a, cv, q), pinv[2 * i], pinv[2 * i + 1], q);
+  const u64* add = p ? add1 : add0;
+  if (add) v = addmod(v, add[(size_t)i * N + k], q);
+  (p ? out1 : out0)[(size_t)i * N + k] = v;
+}
+
+// ------------------------------------------------------------- rescale
+__global__ void k_rescale_prep(const u64* __restrict__ last, int l, u64* __restrict__ tmp, int N,
+                               const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, lm1 = l - 1, p = row / lm1, i = row - p * lm1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 ql = mod[l - 1].q, h = ql >> 1;
+  const u64 x = last[(size_t)p * N + k];
+  const u64 r = (x + h >= ql) ? x + h - ql : x + h;  // (x + h) mod ql
+  const DevMod m = mod[i];
+  u64 v;
+  if (r >= h) {
+    v = reduce64(r - h, m);
+  } else {
+    const u64 t = reduce64(h - r, m);
+    v = t ? m.q - t : 0;
+  }
+  tmp[((size_t)p * lm1 + i) * N + k] = v;
+}
+
+__global__ void k_rescale_combine(PolyView ct, const u64* __restrict__ tmp, int l, int N,
+                                  const DevMod* __restrict__ mod, const u64* __restrict__ qlinv) {
+  const int row = blockIdx.y, lm1 = l - 1, p = row / lm1, i = row - p * lm1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 q = mod[i].q;
+  u64* c = ct.d + ((size_t)p * ct.cap + i) * N + k;
+  const u64 t = tmp[((size_t)p * lm1 + i) * N + k];
+  *c = shoup(submod(*c, t, q), qlinv[2 * i], qlinv[2 * i + 1], q);
+}
+
+// ------------------------------------------------------------- automorphism
+// NTT slot j holds a(psi^(2 brv(j) + 1)); X -> X^g maps it to slot
+// brv((g (2 brv(j) + 1) mod 2N - 1) / 2) of the input.
+__global__ void k_automorph(PolyView out, CPolyView in, int l, int logN, u64 g) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int N = 1 << logN;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const u64 twoN_mask = ((u64)2 << logN) - 1;
+  const u64 e = 2 * (u64)(__brev((unsigned)j) >> (32 - logN)) + 1;
+  const u64 f = (g * e) & twoN_mask;
+  const unsigned src = __brev((unsigned)((f - 1) >> 1)) >> (32 - logN);
+  out.d[((size_t)p * out.cap + i) * N + j] = in.d[((size_t)p * in.cap + i) * N + src];
+}
+
+// ------------------------------------------------------------- ChaCha20
+__device__ __forceinline__ void qround(u32& a, u32& b, u32& c, u32& d) {
+  a += b; d ^= a; d = __funnelshift_l(d, d, 16);
+  c += d; b ^= c; b = __funnelshift_l(b, b, 12);
+  a += b; d ^= a; d = __funnelshift_l(d, d, 8);
+  c += d; b ^= c; b = __funnelshift_l(b, b, 7);
+}
+
+// ChaCha20 block (RFC 8439): key words (seed lo, seed hi, 0 x 6), counter,
+// nonce words (obj lo, obj hi, tag).
+__device__ void chacha_block(u64 seed, u64 obj, u32 tag, u32 counter, u32 out[16]) {
+  u32 s[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u, (u32)seed, (u32)(seed >> 32),
+               0u, 0u, 0u, 0u, 0u, 0u, counter, (u32)obj, (u32)(obj >> 32), tag};
+  u32 x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = s[i];
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    qround(x[0], x[4], x[8], x[12]);
+    qround(x[1], x[5], x[9], x[13]);
+    qround(x[2], x[6], x[10], x[14]);
+    qround(x[3], x[7], x[11], x[15]);
+    qround(x[0], x[5], x[10], x[15]);
+    qround(x[1], x[6], x[11], x[12]);
+    qround(x[2], x[7], x[8], x[13]);
+    qround(x[3], x[4], x[9], x[14]);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) out[i] = x[i] + s[i];
+}
+
+__device__ __forceinline__ int cbd21(u32 a, u32 b) {
+  return __popc(a & 0x1FFFFFu) - __popc(b & 0x1FFFFFu);
+}
+
+__device__ __forceinline__ u64 signed_to_res(i64 v, const DevMod& m) {
+  if (v >= 0) return reduce64((u64)v, m);
+  const u64 t = reduce64((u64)(-(v + 1)) + 1, m);
+  return t ? m.q - t : 0;
+}
+
+struct PidxList {
+  uint8_t u[kMaxMod];
+};
+
+// ternary: coefficient k = word k % 16 of block k / 16, value (w mod 3) - 1
+__global__ void k_sample_ternary(u64 seed, u64 obj, u64* out, PidxList pl, int nl, int N,
+                                 const DevMod* __restrict__ mod) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b * 16 >= N) return;
+  u32 w[16];
+  chacha_block(seed, obj, 0, (u32)b, w);
+  for (int li = 0; li < nl; ++li) {
+    const u64 q = mod[pl.u[li]].q;
+    u64* o = out + (size_t)li * N + (size_t)b * 16;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int v = (int)(w[m] % 3u) - 1;
+      o[m] = v < 0 ? q - 1 : (u64)v;
+    }
+  }
+}
+
+// centred binomial (eta 21): coefficient k = words 2(k%8), 2(k%8)+1 of block k / 8
+__global__ void k_sample_cbd(u64 seed, u64 obj, u64* out, PidxList pl, int nl, int N,
+                             const DevMod* __restrict__ mod) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b * 8 >= N) return;
+  u32 w[16];
+  chacha_block(seed, obj, 0, (u32)b, w);
+  for (int li = 0; li < nl; ++li) {
+    const u64 q = mod[pl.u[li]].q;
+    u64* o = out + (size_t)li * N + (size_t)b * 8;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int e = cbd21(w[2 * m], w[2 * m + 1]);
+      o[m] = e < 0 ? q - (u64)(-e) : (u64)e;
+    }
+  }
+}
+
+// uniform mod q_u: coefficient k = 128-bit word 4(k%4).. of block k / 4 of (obj, tag)
+__global__ void k_sample_uniform(u64 seed, u64 obj, u32 tag, int u, u64* out, int N,
+                                 const DevMod* __restrict__ mod) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b * 4 >= N) return;
+  u32 w[16];
+  chacha_block(seed, obj, tag, (u32)b, w);
+  const DevMod m = mod[u];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const u64 lo = (u64)w[4 * r] | ((u64)w[4 * r + 1] << 32);
+    const u64 hi = (u64)w[4 * r + 2] | ((u64)w[4 * r + 3] << 32);
+    out[(size_t)b * 4 + r] = reduce128(lo, hi, m);
+  }
+}
+
+// encryption randomness for ct idx (enc id id0 + idx), 16 coefficients per thread
+__global__ void k_enc_sample(u64 seed, u64 id0, int count, int l, const i64* __restrict__ m_coeff,
+                             u64* __restrict__ tmp, int N, const DevMod* __restrict__ mod) {
+  const int per = N / 16;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= count * per) return;
+  const int idx = gid / per, b = gid - idx * per;
+  const u64 id = id0 + (u64)idx;
+  u32 wv[16], wa[16], wb[16];
+  chacha_block(seed, (3ull << 48) | id, 0, (u32)b, wv);
+  int v[16], e0[16], e1[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = (int)(wv[m] % 3u) - 1;
+  chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b), wa);
+  chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b + 1), wb);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    e0[m] = cbd21(wa[2 * m], wa[2 * m + 1]);
+    e0[m + 8] = cbd21(wb[2 * m], wb[2 * m + 1]);
+  }
+  chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b), wa);
+  chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b + 1), wb);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    e1[m] = cbd21(wa[2 * m], wa[2 * m + 1]);
+    e1[m + 8] = cbd21(wb[2 * m], wb[2 * m + 1]);
+  }
+  const i64* mc = m_coeff + (size_t)idx * N + (size_t)b * 16;
+  i64 me[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) me[m] = mc[m] + (i64)e0[m];
+  u64* t = tmp + (size_t)idx * 3 * l * N + (size_t)b * 16;
+  for (int i = 0; i < l; ++i) {
+    const DevMod md = mod[i];
+    u64* t0 = t + (size_t)i * N;
+    u64* t1 = t + ((size_t)l + i) * N;
+    u64* t2 = t + ((size_t)2 * l + i) * N;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      t0[m] = v[m] < 0 ? md.q - 1 : (u64)v[m];
+      t1[m] = signed_to_res(me[m], md);
+      t2[m] = e1[m] < 0 ? md.q - (u64)(-e1[m]) : (u64)e1[m];
+    }
+  }
+}
+
+// c0 = v b + t0, c1 = v a + t1 (NTT domain), pk = [2][L][N]
+__global__ void k_enc_combine(const u64* __restrict__ tmp, int l, const u64* __restrict__ pk,
+                              int L, u64* __restrict__ out, int out_cap, size_t out_stride, int N,
+                              const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, idx = row / l, i = row - idx * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const DevMod m = mod[i];
+  const u64* t = tmp + (size_t)idx * 3 * l * N;
+  const u64 v = t[(size_t)i * N + k];
+  const u64 t0 = t[((size_t)l + i) * N + k];
+  const u64 t1 = t[((size_t)2 * l + i) * N + k];
+  const u64 b = pk[(size_t)i * N + k];
+  const u64 a = pk[((size_t)L + i) * N + k];
+  u64* o = out + idx * out_stride;
+  o[(size_t)i * N + k] = addmod(mulmod(v, b, m), t0, m.q);
+  o[((size_t)out_cap + i) * N + k] = addmod(mulmod(v, a, m), t1, m.q);
+}
+
+__global__ void k_ksk_combine(u64* b, const u64* __restrict__ a, const u64* __restrict__ e,
+                              const u64* __restrict__ s, const u64* __restrict__ t, u64 pmod, int u,
+                              int N, const DevMod* __restrict__ mod) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const DevMod m = mod[u];
+  u64 v = submod(e[k], mulmod(a[k], s[k], m), m.q);
+  if (t) v = addmod(v, mulmod(pmod, t[k], m), m.q);
+  b[k] = v;
+}
+
+__global__ void k_int_to_rns(const i64* __restrict__ in, int count, int l, u64* __restrict__ out,
+                             int N, const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, idx = row / l, i = row - idx * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  out[((size_t)idx * l + i) * N + k] = signed_to_res(in[(size_t)idx * N + k], mod[i]);
+}
+
+__global__ void k_decrypt(CPolyView ct, const u64* __restrict__ s, int l, u64* __restrict__ m,
+                          int N, const DevMod* __restrict__ mod) {
+  const int i = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const DevMod md = mod[i];
+  const u64 c0 = ct.d[(size_t)i * N + k];
+  const u64 c1 = ct.d[((size_t)ct.cap + i) * N + k];
+  m[(size_t)i * N + k] = addmod(c0, mulmod(c1, s[(size_t)i * N + k], md), md.q);
+}
+
+// ------------------------------------------------------------- encoding FFT
+// Complex arithmetic as separately rounded IEEE operations (no FMA), in the
+// order of the encoding procedure.
+__device__ __forceinline__ double2 cmul_exact(double2 a, double2 b) {
+  return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
+                      __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ void fft_bfly(double2& x, double2& y, double2 w) {
+  const double2 t = cmul_exact(y, w);
+  const double2 a = x;
+  x = make_double2(__dadd_rn(a.x, t.x), __dadd_rn(a.y, t.y));
+  y = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
+}
+
+// G[idx][pos[j]] = z[idx][j]
+__global__ void k_fft_scatter(const double2* __restrict__ z, const int* __restrict__ pos, int M,
+                              int count, double2* __restrict__ G) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * M) return;
+  const size_t idx = gid / M;
+  const int j = (int)(gid - idx * M);
+  G[idx * M + pos[j]] = z[gid];
+}
+
+// radix-2 stages len = 2 .. 2^a inside tiles of 2^a contiguous entries
+__global__ void k_fft_tile(double2* __restrict__ G, const double2* __restrict__ W, int logM, int a) {
+  extern __shared__ double2 sf[];
+  const int T = 1 << a;
+  const int M = 1 << logM;
+  double2* base = G + (size_t)blockIdx.x * T;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) sf[i] = base[i];
+  __syncthreads();
+  for (int ls = 1; ls <= a; ++ls) {
+    const int half = 1 << (ls - 1);
+    const int stride = M >> ls;
+    for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
+      const int blk = b >> (ls - 1), jj = b & (half - 1);
+      const int p = (blk << ls) + jj;
+      fft_bfly(sf[p], sf[p + half], W[jj * stride]);
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < T; i += blockDim.x) base[i] = sf[i];
+}
+
+// remaining stages len = 2^(a+1) .. M: thread per (transform, low index lo),
+// R = M / 2^a entries in registers
+template <int R>
+__global__ void k_fft_cols(double2* __restrict__ G, const double2* __restrict__ W, int logM, int a,
+                           int count) {
+  const int T = 1 << a, M = 1 << logM;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * T) return;
+  const size_t idx = gid / T;
+  const int lo = (int)(gid - idx * T);
+  double2* base = G + idx * M;
+  double2 x[R];
+#pragma unroll
+  for (int h = 0; h < R; ++h) x[h] = base[(size_t)h * T + lo];
+#pragma unroll
+  for (int s2 = 0; (1 << s2) < R; ++s2) {
+    const int hs = 1 << s2;
+    const int stride = M >> (a + 1 + s2);
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      if (h & hs) continue;
+      const int jj = ((h & (hs - 1)) << a) + lo;
+      fft_bfly(x[h], x[h + hs], W[jj * stride]);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < R; ++h) base[(size_t)h * T + lo] = x[h];
+}
+
+// c_k = G[k] T[k]; coefficient k = rint(Re c_k f), k + M = rint(Im c_k f)
+__global__ void k_fft_round(const double2* __restrict__ G, const double2* __restrict__ T, int M,
+                            int count, double f, i64* __restrict__ out) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * M) return;
+  const size_t idx = gid / M;
+  const int k = (int)(gid - idx * M);
+  const double2 c = cmul_exact(G[gid], T[k]);
+  i64* o = out + idx * 2 * M;
+  o[k] = __double2ll_rn(__dmul_rn(c.x, f));
+  o[k + M] = __double2ll_rn(__dmul_rn(c.y, f));
+}
+
+// decoding: centred residues mod q0 -> (m_k + i m_(k+M)) T[k] at bit-reversed k
+__global__ void k_decode_prep(const u64* __restrict__ m, const double2* __restrict__ T, int logM,
+                              int count, u64 q, double2* __restrict__ G) {
+  const int M = 1 << logM;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * M) return;
+  const size_t idx = gid / M;
+  const int k = (int)(gid - idx * M);
+  const u64* mp = m + idx * 2 * M;
+  const u64 a = mp[k], b = mp[k + M];
+  const double re = a > q / 2 ? -(double)(q - a) : (double)a;
+  const double im = b > q / 2 ? -(double)(q - b) : (double)b;
+  const int p = (int)(__brev((unsigned)k) >> (32 - logM));
+  G[idx * M + p] = cmul_exact(make_double2(re, im), T[k]);
+}
+
+__global__ void k_decode_gather(const double2* __restrict__ G, const int* __restrict__ u, int M,
+                                int count, double scale, double2* __restrict__ z) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * M) return;
+  const size_t idx = gid / M;
+  const int j = (int)(gid - idx * M);
+  const double2 g = G[idx * M + u[j]];
+  z[gid] = make_double2(g.x / scale, g.y / scale);
+}
+
+__global__ void k_build_snp_rep(const double* __restrict__ S, int n, long k, long k0, int nb,
+                                int B, int M, double2* __restrict__ z) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)n * M) return;
+  const size_t j = gid / M;
+  const int s = (int)(gid - j * M);
+  const int b = s / nb;
+  const long col = k0 + 2L * b;
+  double re = 0.0, im = 0.0;
+  if (b < B) {
+    if (col < k) re = S[j * (size_t)k + col];
+    if (col + 1 < k) im = S[j * (size_t)k + col + 1];
+  }
+  z[gid] = make_double2(re, im);
+}
+
+inline unsigned blocks_for(size_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ============================================================= wrappers
+void ew_addsub(Context* c, PolyView out, CPolyView a, CPolyView b, int npoly, int l, bool sub) {
+  ProfScope ps(c, PROF_ELEMWISE, 3.0 * npoly * l * 8.0 * c->N);
+  if (npoly * l == 0) return;
+  k_addsub<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, b, l, c->N, c->d_mod,
+                                                                   sub ? 1 : 0);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ew_negate(Context* c, PolyView out, CPolyView a, int npoly, int l) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
+  if (npoly * l == 0) return;
+  k_negate<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, l, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+static LimbVals make_vals(Context* c, int l, const u64* v) {
+  GWHE_REQUIRE(l <= kMaxRowLimbs, ST_EINVAL, "too many limbs");
+  LimbVals lv;
+  for (int i = 0; i < l; ++i) {
+    lv.v[i] = v[i] % c->mod[i];
+    lv.sh[i] = shoup_companion(lv.v[i], c->mod[i]);
+  }
+  return lv;
+}
+
+void ew_mul_scalar(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* v) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
+  if (npoly * l == 0) return;
+  k_mul_scalar<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, l, c->N, c->d_mod,
+                                                                       make_vals(c, l, v));
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ew_add_scalar_poly0(Context* c, PolyView ct, int l, const u64* v) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * l * 8.0 * c->N);
+  if (l == 0) return;
+  k_add_scalar0<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, c->N, c->d_mod,
+                                                                make_vals(c, l, v));
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ew_mul_plain(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* pt) {
+  ProfScope ps(c, PROF_ELEMWISE, (2.0 * npoly + 1) * l * 8.0 * c->N);
+  if (npoly * l == 0) return;
+  k_mul_plain<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, pt, l, c->N,
+                                                                      c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt) {
+  ProfScope ps(c, PROF_ELEMWISE, 3.0 * l * 8.0 * c->N);
+  if (l == 0) return;
+  k_add_plain0<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, pt, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void tensor_mac(Context* c, PolyView out3, const MacPair* d_pairs, int npairs, int l) {
+  ProfScope ps(c, PROF_TENSOR_MAC, (4.0 * npairs + 3.0) * l * 8.0 * c->N);
+  if (l == 0) return;
+  k_tensor_mac<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(out3, d_pairs, npairs, l, c->N,
+                                                               c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+static ConvArgs conv_args(const ConvTable& t, int in_mod0) {
+  GWHE_REQUIRE(t.n_in <= kMaxConvIn && t.n_out <= kMaxRowLimbs, ST_EINVAL, "conversion too large");
+  ConvArgs a;
+  a.tab = t.dev;
+  a.n_in = t.n_in;
+  a.n_out = t.n_out;
+  a.hm_stride = t.n_out;
+  a.in_mod0 = in_mod0;
+  for (int o = 0; o < t.n_out; ++o) {
+    a.out_pidx[o] = t.out_pidx[o];
+    a.out_row[o] = t.out_limb[o];
+  }
+  return a;
+}
+
+void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext) {
+  ProfScope ps(c, PROF_BASECONV, 0.0);
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  const int ne = l + c->P.K;
+  for (int j = 0; j < beta; ++j) {
+    const ConvTable& t = c->modup.at({l, j});
+    const ConvArgs a = conv_args(t, t.in_lo);
+    ps.bytes += 8.0 * (t.n_in + t.n_out) * c->N;
+    k_baseconv<<<dim3(blocks_for(c->N), 1), kThreads, 0, c->stream>>>(
+        x_coeff + (size_t)t.in_lo * c->N, 0, ext + (size_t)j * ne * c->N, 0, a, c->N, c->d_mod);
+    GWHE_LAUNCHED(c, 1);
+  }
+}
+
+void moddown_convert(Context* c, const u64* acc, int l, u64* conv) {
+  ProfScope ps(c, PROF_BASECONV, 2.0 * (c->P.K + l) * 8.0 * c->N);
+  GWHE_REQUIRE(l >= 1 && l <= c->P.L, ST_EINVAL, "bad level");
+  const int ne = l + c->P.K;
+  ConvArgs a = conv_args(c->moddown, c->P.L);  // table rows hold all L outputs
+  a.n_out = l;                                 // produce the first l of them
+  k_baseconv<<<dim3(blocks_for(c->N), 2), kThreads, 0, c->stream>>>(
+      acc + (size_t)l * c->N, (size_t)ne * c->N, conv, (size_t)l * c->N, a, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
+                     const u64* add0, const u64* add1) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * 3 * l * 8.0 * c->N);
+  k_moddown_combine<<<grid_rows(c->N, 2 * l), kThreads, 0, c->stream>>>(
+      acc, conv, l, c->P.K, out0, out1, add0, add1, c->d_pinv, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* key, u64* acc) {
+  const double ne_ = l + c->P.K, beta_ = (l + c->alpha - 1) / c->alpha;
+  ProfScope ps(c, PROF_KS_INNER, (3.0 * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N);
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  k_ks_inner<<<grid_rows(c->N, l + c->P.K), kThreads, 0, c->stream>>>(
+      c_ntt, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void rescale_prep(Context* c, const u64* last, int npoly, int l, u64* tmp) {
+  ProfScope ps(c, PROF_ELEMWISE, (npoly + npoly * (l - 1.0)) * 8.0 * c->N);
+  k_rescale_prep<<<grid_rows(c->N, npoly * (l - 1)), kThreads, 0, c->stream>>>(last, l, tmp, c->N,
+                                                                               c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void rescale_combine(Context* c, PolyView ct, const u64* tmp_ntt, int npoly, int l) {
+  ProfScope ps(c, PROF_ELEMWISE, 3.0 * npoly * (l - 1.0) * 8.0 * c->N);
+  const u64* qlinv = c->d_rescale + (size_t)l * c->P.L * 2;
+  k_rescale_combine<<<grid_rows(c->N, npoly * (l - 1)), kThreads, 0, c->stream>>>(
+      ct, tmp_ntt, l, c->N, c->d_mod, qlinv);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void automorph_ntt(Context* c, PolyView out, CPolyView in, int npoly, int l, u64 g) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
+  if (npoly * l == 0) return;
+  k_automorph<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, in, l, c->logN, g);
+  GWHE_LAUNCHED(c, 1);
+}
+
+static PidxList make_pl(const uint8_t* pidx, int nl) {
+  GWHE_REQUIRE(nl <= kMaxMod, ST_EINVAL, "too many limbs");
+  PidxList pl;
+  for (int i = 0; i < nl; ++i) pl.u[i] = pidx[i];
+  return pl;
+}
+
+void sample_ternary_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int nl) {
+  ProfScope ps(c, PROF_SAMPLE, 1.0 * nl * 8.0 * c->N);
+  k_sample_ternary<<<blocks_for(c->N / 16), kThreads, 0, c->stream>>>(
+      c->seed, obj, out, make_pl(pidx, nl), nl, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void sample_cbd_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int nl) {
+  ProfScope ps(c, PROF_SAMPLE, 1.0 * nl * 8.0 * c->N);
+  k_sample_cbd<<<blocks_for(c->N / 8), kThreads, 0, c->stream>>>(c->seed, obj, out,
+                                                                 make_pl(pidx, nl), nl, c->N,
+                                                                 c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void sample_uniform(Context* c, u64 obj, u32 tag, int u, u64* out) {
+  ProfScope ps(c, PROF_SAMPLE, 8.0 * c->N);
+  k_sample_uniform<<<blocks_for(c->N / 4), kThreads, 0, c->stream>>>(c->seed, obj, tag, u, out,
+                                                                     c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp) {
+  ProfScope ps(c, PROF_SAMPLE, (3.0 * l + 1.0) * count * 8.0 * c->N);
+  if (count == 0) return;
+  k_enc_sample<<<blocks_for((size_t)count * (c->N / 16)), kThreads, 0, c->stream>>>(
+      c->seed, id0, count, l, m_coeff, tmp, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void enc_combine(Context* c, const u64* tmp_ntt, int count, int l, u64* out, int out_cap,
+                 size_t out_stride) {
+  ProfScope ps(c, PROF_SAMPLE, 5.0 * count * l * 8.0 * c->N);
+  if (count == 0) return;
+  GWHE_REQUIRE((size_t)count * l < 65536, ST_EINVAL, "encryption batch too large");
+  k_enc_combine<<<grid_rows(c->N, count * l), kThreads, 0, c->stream>>>(
+      tmp_ntt, l, c->d_pk, c->P.L, out, out_cap, out_stride, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ksk_combine(Context* c, u64* b, const u64* a, const u64* e, const u64* s, const u64* t,
+                 u64 pmod, int u) {
+  ProfScope ps(c, PROF_ELEMWISE, 5.0 * 8.0 * c->N);
+  k_ksk_combine<<<blocks_for(c->N), kThreads, 0, c->stream>>>(b, a, e, s, t, pmod, u, c->N,
+                                                             c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void int_to_rns(Context* c, const i64* in, int count, int l, u64* out) {
+  ProfScope ps(c, PROF_ELEMWISE, (1.0 + l) * count * 8.0 * c->N);
+  if (count * l == 0) return;
+  GWHE_REQUIRE((size_t)count * l < 65536, ST_EINVAL, "batch too large");
+  k_int_to_rns<<<grid_rows(c->N, count * l), kThreads, 0, c->stream>>>(in, count, l, out, c->N,
+                                                                       c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m) {
+  ProfScope ps(c, PROF_ELEMWISE, 4.0 * l * 8.0 * c->N);
+  k_decrypt<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, c->d_sk, l, m, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+static void fft_stages(Context* c, double2* G, const double2* W, int count) {
+  const int logM = c->logN - 1, M = 1 << logM;
+  const int a = logM < 11 ? logM : 11;
+  const int T = 1 << a;
+  k_fft_tile<<<(unsigned)((size_t)count * (M / T)), 256, sizeof(double2) * T, c->stream>>>(G, W,
+                                                                                          logM, a);
+  GWHE_LAUNCHED(c, 1);
+  const int R = M / T;
+  const unsigned nb = blocks_for((size_t)count * T, 128);
+  switch (R) {
+    case 1: break;
+    case 2: k_fft_cols<2><<<nb, 128, 0, c->stream>>>(G, W, logM, a, count); break;
+    case 4: k_fft_cols<4><<<nb, 128, 0, c->stream>>>(G, W, logM, a, count); break;
+    case 8: k_fft_cols<8><<<nb, 128, 0, c->stream>>>(G, W, logM, a, count); break;
+    case 16: k_fft_cols<16><<<nb, 128, 0, c->stream>>>(G, W, logM, a, count); break;
+    default: throw Error(ST_EINVAL, "ring degree too large for the encoder");
+  }
+  GWHE_LAUNCHED(c, 1);
+}
+
+void encode_batch(Context* c, const double2* z, int count, double scale, i64* out, double2* work) {
+  ProfScope ps(c, PROF_ENCODE, 2.0 * count * 16.0 * (c->N / 2));
+  if (count == 0) return;
+  const int M = c->N / 2;
+  k_fft_scatter<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(z, c->d_slot_pos, M,
+                                                                          count, work);
+  GWHE_LAUNCHED(c, 1);
+  fft_stages(c, work, c->d_fftW_enc, count);
+  const double f = scale / (double)M;
+  k_fft_round<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(work, c->d_fftT_enc, M,
+                                                                        count, f, out);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void decode_batch(Context* c, const u64* m_coeff_q0, int count, double scale, double2* z,
+                  double2* work) {
+  ProfScope ps(c, PROF_ENCODE, 2.0 * count * 16.0 * (c->N / 2));
+  if (count == 0) return;
+  const int logM = c->logN - 1, M = 1 << logM;
+  k_decode_prep<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(
+      m_coeff_q0, c->d_fftT_dec, logM, count, c->mod[0], work);
+  GWHE_LAUNCHED(c, 1);
+  fft_stages(c, work, c->d_fftW_dec, count);
+  k_decode_gather<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(work, c->d_slot_u, M,
+                                                                            count, scale, z);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, int B, int M,
+                   double2* z) {
+  ProfScope ps(c, PROF_ELEMWISE, 16.0 * n * M);
+  k_build_snp_rep<<<blocks_for((size_t)n * M), kThreads, 0, c->stream>>>(S, n, k, k0, nb, B, M, z);
+  GWHE_LAUNCHED(c, 1);
+}
+
+}  // namespace gwhe

@@ -1,0 +1,83 @@
+// kernels.cuh -- launch wrappers of the element-wise, base-conversion,
+// sampling and encoding kernels (kernels.cu).  All work is enqueued on the
+// context's stream; buffers are device pointers.
+#pragma once
+
+#include "core.cuh"
+
+namespace gwhe {
+
+// A set of polynomials over the q-limbs: poly p, limb i at d + (p * cap + i) * N.
+struct PolyView {
+  u64* d;
+  int cap;
+};
+struct CPolyView {
+  const u64* d;
+  int cap;
+};
+
+// One term of a tensor sum: ciphertexts a, b (2 polys each).
+struct MacPair {
+  const u64* a;
+  const u64* b;
+  int capa, capb;
+};
+
+// element-wise (NTT or coefficient domain; limb i is modulo q_i)
+void ew_addsub(Context* c, PolyView out, CPolyView a, CPolyView b, int npoly, int l, bool sub);
+void ew_negate(Context* c, PolyView out, CPolyView a, int npoly, int l);
+// out = a * v_i for limb i (v[i] < q_i)
+void ew_mul_scalar(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* v);
+// c0 limb i += v[i] in every coefficient (a constant polynomial in the NTT domain)
+void ew_add_scalar_poly0(Context* c, PolyView ct, int l, const u64* v);
+// out_p = a_p * pt for p < npoly
+void ew_mul_plain(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* pt);
+// c0 += pt
+void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt);
+// out (3 polys) = sum over pairs of the tensor (a0 b0, a0 b1 + a1 b0, a1 b1)
+void tensor_mac(Context* c, PolyView out3, const MacPair* d_pairs, int npairs, int l);
+
+// key switching pieces
+// ext rows: for each digit j, ne = l + K limbs at ext + (j * ne + u) * N
+void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext);
+void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* key, u64* acc);
+void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
+                     const u64* add0, const u64* add1);
+void moddown_convert(Context* c, const u64* acc, int l, u64* conv);
+
+// rescale pieces: last = coefficient-domain last limbs [npoly][N]
+void rescale_prep(Context* c, const u64* last, int npoly, int l, u64* tmp);
+void rescale_combine(Context* c, PolyView ct, const u64* tmp_ntt, int npoly, int l);
+
+// Galois automorphism X -> X^g applied to NTT-domain limbs
+void automorph_ntt(Context* c, PolyView out, CPolyView in, int npoly, int l, u64 g);
+
+// sampling (ChaCha20, see the library header for the stream layout)
+void sample_ternary_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int nl);
+void sample_cbd_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int nl);
+void sample_uniform(Context* c, u64 obj, u32 tag, int u, u64* out);
+// batched encryption randomness: for ct idx < count (enc id = id0 + idx):
+// tmp[idx][0] = v, tmp[idx][1] = m + e0, tmp[idx][2] = e1 over l q-limbs
+void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp);
+void enc_combine(Context* c, const u64* tmp_ntt, int count, int l, u64* out, int out_cap,
+                 size_t out_stride);
+// key-switching key limb: b = -a s + e (+ Pt)
+void ksk_combine(Context* c, u64* b, const u64* a, const u64* e, const u64* s, const u64* t,
+                 u64 pmod, int u);
+
+// encoding procedure (see params / library header) and decoding
+void encode_batch(Context* c, const double2* z, int count, double scale, i64* out, double2* work);
+void int_to_rns(Context* c, const i64* in, int count, int l, u64* out);
+void decode_batch(Context* c, const u64* m_coeff_q0, int count, double scale, double2* z,
+                  double2* work);
+
+// decryption inner product m = c0 + c1 s over l limbs (NTT domain)
+void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m);
+
+// REP rows of a SNP batch as complex slots: rows j < n, slot b * nb + t =
+// S[j, k0 + 2b] + i S[j, k0 + 2b + 1] (zero beyond k)
+void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, int B, int M,
+                   double2* z);
+
+}  // namespace gwhe

@@ -1,0 +1,258 @@
+// ntt.cu -- batched negacyclic NTT / inverse NTT over RNS limbs.
+//
+// Forward transform (merged psi twist, Cooley-Tukey): for stage s = 0..logN-1
+// with m = 2^s blocks of half-size t = N / 2m, block i pairs (a[j], a[j+t]) with
+// twiddle psi^brv(m+i); the output slot j holds a(psi^(2 brv(j) + 1)).  The
+// inverse runs the Gentleman-Sande butterflies in reverse stage order with the
+// inverse twiddles and multiplies by N^-1.  Both keep Harvey's lazy ranges
+// ([0, 4q) forward, [0, 2q) inverse) and return canonical residues in [0, q).
+//
+// Layout for N = 2^12..2^16: the row is viewed as a 2^LA x 2^LB matrix
+// (element h * 2^LB + c).  Pass A runs the first LA stages as independent
+// 2^LA-point transforms down the columns, pass B the last LB stages along the
+// rows.  In each pass a 256-thread CTA owns 4096 residues: 16 per thread, the
+// first four local stages in registers in a strided layout (coalesced global
+// loads), a shared-memory transpose to a contiguous layout for the remaining
+// stages, and a transpose back for coalesced stores.  Each residue is read and
+// written once per pass.  Smaller rings use one CTA per row in shared memory.
+#include "core.cuh"
+
+namespace gwhe {
+
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q, u64 twoq) {
+  const u64 a = csub(x, twoq);
+  const u64 t = shoup_lazy(y, w, wsh, q);
+  x = a + t;
+  y = a - t + twoq;
+}
+
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q, u64 twoq) {
+  const u64 s = x + y;
+  const u64 d = x - y + twoq;
+  x = csub(s, twoq);
+  y = shoup_lazy(d, w, wsh, q);
+}
+
+// One pass of the two-pass transform.  LS = log2 of this pass's sub-transform
+// size; the other dimension has 2^(LOGN-LS) entries.  PASSA: sub-transforms
+// are columns (stride 2^(LOGN-LS)), global stages 0..LS-1; otherwise rows
+// (contiguous), global stages LOGN-LS..LOGN-1.
+template <int LOGN, int LS, bool PASSA, bool FWD>
+__global__ void __launch_bounds__(256) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
+                                                  const NttTables tb, const int groups_per_row) {
+  constexpr int S = 1 << LS;
+  constexpr int TPS = S / 16;         // threads per sub-transform
+  constexpr int G = 256 / TPS;        // sub-transforms per CTA
+  constexpr int LC = LOGN - LS;       // log2 of the other dimension
+  constexpr int PADS = PASSA ? (S + 1) : (S + S / 16);
+  constexpr int S0 = PASSA ? 0 : LC;  // global index of local stage 0
+  __shared__ u64 sm[G * PADS];
+
+  const int row = blockIdx.x / groups_per_row;
+  const int grp = blockIdx.x - row * groups_per_row;
+  const int poly = row / rm.nl;
+  const int limb = row - poly * rm.nl;
+  const int u = rm.pidx[limb];
+  u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * ((size_t)1 << LOGN);
+  const u64 q = tb.mod[u].q, twoq = 2 * q;
+  const u64* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << LOGN);
+  const u64* Wsh = (FWD ? tb.psi_sh : tb.ipsi_sh) + ((size_t)u << LOGN);
+
+  const int t = threadIdx.x;
+  const int lg = PASSA ? (t % G) : (t / TPS);
+  const int r = PASSA ? (t / G) : (t % TPS);
+  const int g = grp * G + lg;
+
+  auto gaddr = [&](int e) -> size_t {
+    return PASSA ? (((size_t)e << LC) + g) : (((size_t)g << LS) + e);
+  };
+  auto sidx = [&](int e) -> int { return PASSA ? (lg * PADS + e) : (lg * PADS + e + (e >> 4)); };
+  auto tw = [&](int s_local, int e) -> int {  // twiddle index for the pair led by e
+    const int s = S0 + s_local;
+    return (1 << s) + (PASSA ? 0 : (g << s_local)) + (e >> (LS - s_local));
+  };
+
+  u64 x[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) x[m] = base[gaddr(r + TPS * m)];
+
+  if (FWD) {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int st = 8 >> sp;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & st) continue;
+        const int idx = tw(sp, TPS * m);
+        ct_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[sidx(r + TPS * m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(16 * r + m)];
+#pragma unroll
+    for (int sp = 4; sp < LS; ++sp) {
+      const int st = S >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & st) continue;
+        const int idx = tw(sp, 16 * r + m);
+        ct_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[sidx(16 * r + m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(r + TPS * m)];
+    if (!PASSA) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = csub(csub(x[m], twoq), q);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[sidx(r + TPS * m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(16 * r + m)];
+#pragma unroll
+    for (int sp = LS - 1; sp >= 4; --sp) {
+      const int st = S >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & st) continue;
+        const int idx = tw(sp, 16 * r + m);
+        gs_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[sidx(16 * r + m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(r + TPS * m)];
+#pragma unroll
+    for (int sp = 3; sp >= 0; --sp) {
+      const int st = 8 >> sp;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & st) continue;
+        const int idx = tw(sp, TPS * m);
+        gs_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+      }
+    }
+    if (PASSA) {
+      const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = shoup(x[m], ni, nish, q);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 16; ++m) base[gaddr(r + TPS * m)] = x[m];
+}
+
+// Whole row in shared memory (N <= 2^11), one CTA per row.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const RowMap rm,
+                                                   const NttTables tb, const int logN) {
+  extern __shared__ u64 sh[];
+  const int N = 1 << logN;
+  const int row = blockIdx.x;
+  const int poly = row / rm.nl;
+  const int limb = row - poly * rm.nl;
+  const int u = rm.pidx[limb];
+  u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * (size_t)N;
+  const u64 q = tb.mod[u].q, twoq = 2 * q;
+  const u64* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << logN);
+  const u64* Wsh = (FWD ? tb.psi_sh : tb.ipsi_sh) + ((size_t)u << logN);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = base[i];
+  __syncthreads();
+  const int half = N >> 1;
+  if (FWD) {
+    for (int s = 0; s < logN; ++s) {
+      const int lt = logN - 1 - s;  // log2 of t
+      for (int b = threadIdx.x; b < half; b += blockDim.x) {
+        const int i = b >> lt;
+        const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
+        const int idx = (1 << s) + i;
+        ct_bfly(sh[j], sh[j + (1 << lt)], W[idx], Wsh[idx], q, twoq);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) base[i] = csub(csub(sh[i], twoq), q);
+  } else {
+    for (int s = logN - 1; s >= 0; --s) {
+      const int lt = logN - 1 - s;
+      for (int b = threadIdx.x; b < half; b += blockDim.x) {
+        const int i = b >> lt;
+        const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
+        const int idx = (1 << s) + i;
+        gs_bfly(sh[j], sh[j + (1 << lt)], W[idx], Wsh[idx], q, twoq);
+      }
+      __syncthreads();
+    }
+    const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) base[i] = shoup(sh[i], ni, nish, q);
+  }
+}
+
+template <int LOGN, int LA, int LB>
+static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
+  const NttTables tb = c->tables();
+  const int rows = rm.npoly * rm.nl;
+  const int gA = (1 << (LOGN - LA)) / (256 / ((1 << LA) / 16));
+  const int gB = (1 << (LOGN - LB)) / (256 / ((1 << LB) / 16));
+  if (fwd) {
+    k_ntt_pass<LOGN, LA, true, true><<<rows * gA, 256, 0, c->stream>>>(data, rm, tb, gA);
+    k_ntt_pass<LOGN, LB, false, true><<<rows * gB, 256, 0, c->stream>>>(data, rm, tb, gB);
+  } else {
+    k_ntt_pass<LOGN, LB, false, false><<<rows * gB, 256, 0, c->stream>>>(data, rm, tb, gB);
+    k_ntt_pass<LOGN, LA, true, false><<<rows * gA, 256, 0, c->stream>>>(data, rm, tb, gA);
+  }
+  GWHE_LAUNCHED(c, 2);
+}
+
+static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
+  const int rows = rm.npoly * rm.nl;
+  if (rows <= 0) return;
+  // algorithmic traffic: every residue read once and written once
+  ProfScope ps(c, PROF_NTT, 16.0 * rows * c->N);
+  GWHE_REQUIRE(rm.nl <= kMaxRowLimbs, ST_EINVAL, "too many limbs in a row map");
+  switch (c->logN) {
+    case 16: ntt_two_pass<16, 8, 8>(c, data, rm, fwd); return;
+    case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd); return;
+    case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd); return;
+    case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd); return;
+    case 12: ntt_two_pass<12, 6, 6>(c, data, rm, fwd); return;
+    default: break;
+  }
+  GWHE_REQUIRE(c->logN >= 2 && c->logN <= 11, ST_EINVAL, "unsupported ring degree");
+  const NttTables tb = c->tables();
+  const size_t shm = sizeof(u64) << c->logN;
+  if (fwd)
+    k_ntt_small<true><<<rows, 256, shm, c->stream>>>(data, rm, tb, c->logN);
+  else
+    k_ntt_small<false><<<rows, 256, shm, c->stream>>>(data, rm, tb, c->logN);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ntt_forward(Context* c, u64* data, const RowMap& rm) { ntt_dispatch(c, data, rm, true); }
+void ntt_inverse(Context* c, u64* data, const RowMap& rm) { ntt_dispatch(c, data, rm, false); }
+
+RowMap rows_q(int npoly, int l, int poly_stride) {
+  GWHE_REQUIRE(l >= 0 && l <= kMaxRowLimbs, ST_EINVAL, "too many limbs");
+  RowMap rm;
+  rm.npoly = npoly;
+  rm.nl = l;
+  rm.poly_stride = poly_stride;
+  for (int i = 0; i < l; ++i) {
+    rm.off[i] = (uint16_t)i;
+    rm.pidx[i] = (uint8_t)i;
+  }
+  return rm;
+}
+
+}  // namespace gwhe

@@ -61,10 +61,10 @@ WORKLOADS = {
     # small plain job: N = 2^13, 4 q-limbs (60 + 3 x 40 bits), 1 special prime
     "small-n64": dict(logN=13, L=4, q0_bits=60, scale_bits=40, K=1, sp_bits=60, dnum=4,
                       n=64, d=4, k=256, seed=1001, split=True),
-    # paper-shaped job: N = 2^16, 24 q-limbs (60 + 23 x 40), 8 special primes, dnum 3
-    "paper-n245": dict(logN=16, L=24, q0_bits=60, scale_bits=40, K=8, sp_bits=60, dnum=3,
+    # paper-shaped job: N = 2^16, 24 q-limbs (60 + 23 x 45), 8 special primes, dnum 3
+    "paper-n245": dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3,
                        n=245, d=5, k=10643, seed=1002, split=False),
     # kernel microbench: 64 ciphertexts x 2 polys x 24 limbs at N = 2^16
-    "ntt-ks-micro": dict(logN=16, L=24, q0_bits=60, scale_bits=40, K=8, sp_bits=60, dnum=3,
+    "ntt-ks-micro": dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3,
                          n_ct=64, seed=1003),
 }

@@ -1,0 +1,502 @@
+"""Thin Python binding of the gwhe C ABI (include/gwhe.h).
+
+Argument marshalling only: every step of the encrypted path runs in the CUDA
+library.  Host arrays are numpy; device buffers may be torch CUDA tensors (or
+raw device pointers) where the ABI accepts device memory.  If the compiled
+library is missing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgwhe.so")
+
+GWHE_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ELEVEL", -4: "ESCALE", -5: "ENOKEY",
+          -6: "ETIMEOUT", -7: "ECUDA"}
+
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_l = ctypes.c_long
+_d = ctypes.c_double
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("logN", _i), ("L", _i), ("q0_bits", _i), ("scale_bits", _i), ("K", _i),
+                ("sp_bits", _i), ("dnum", _i)]
+
+
+class GwheError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_SIGS = {
+    "gwhe_gen_primes": [ctypes.POINTER(Params), _u64p, _u64p],
+    "gwhe_fft_twiddles": [_i, _i, _f64p, _f64p],
+    "gwhe_layout": [_i, _i, _l, ctypes.POINTER(_l)],
+    "gwhe_ctx_create": [ctypes.POINTER(Params), _u64, _vp, ctypes.POINTER(_vp)],
+    "gwhe_ctx_destroy": [_vp],
+    "gwhe_ctx_moduli": [_vp, _u64p],
+    "gwhe_sync": [_vp],
+    "gwhe_keygen": [_vp, _i32p, _sz, _i],
+    "gwhe_export_secret": [_vp, _i64p],
+    "gwhe_export_pk": [_vp, _u64p],
+    "gwhe_export_ksk": [_vp, _u32, _u64p],
+    "gwhe_ct_create": [_vp, _i, _i, ctypes.POINTER(_vp)],
+    "gwhe_ct_destroy": [_vp],
+    "gwhe_ct_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
+    "gwhe_ct_import": [_vp, _u64p, _i, _i, _d],
+    "gwhe_ct_export": [_vp, _u64p],
+    "gwhe_encode": [_vp, _f64p, _d, _i64p],
+    "gwhe_encrypt": [_vp, _f64p, _d, _i, _u64, _vp],
+    "gwhe_encrypt_coeffs": [_vp, _i64p, _d, _i, _u64, _vp],
+    "gwhe_decrypt": [_vp, _vp, _u64p],
+    "gwhe_decrypt_decode": [_vp, _vp, _f64p],
+    "gwhe_add": [_vp, _vp, _vp, _vp],
+    "gwhe_sub": [_vp, _vp, _vp, _vp],
+    "gwhe_negate": [_vp, _vp, _vp],
+    "gwhe_add_const": [_vp, _vp, _d],
+    "gwhe_mul_int": [_vp, _vp, ctypes.c_int64],
+    "gwhe_mul_const": [_vp, _vp, _d],
+    "gwhe_mul_mask": [_vp, _vp, _f64p, _vp],
+    "gwhe_tensor": [_vp, _vp, _vp, _vp],
+    "gwhe_tensor_sum": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _sz, _vp],
+    "gwhe_relin": [_vp, _vp, _vp],
+    "gwhe_rescale": [_vp, _vp],
+    "gwhe_mult": [_vp, _vp, _vp, _vp],
+    "gwhe_rotate": [_vp, _vp, _i, _vp],
+    "gwhe_conjugate": [_vp, _vp, _vp],
+    "gwhe_drop": [_vp, _i],
+    "gwhe_keyswitch": [_vp, _u64p, _i, _u32, _u64p],
+    "gwhe_ntt_batch": [_vp, _vp, _i, _i, _i],
+    "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
+    "gwhe_job_destroy": [_vp],
+    "gwhe_encrypt_inputs": [_vp, _vp, _vp, _vp],
+    "gwhe_fit_covariates": [_vp, _i],
+    "gwhe_set_fit_state": [_vp, _vp, _vp, _vp],
+    "gwhe_snp_stats": [_vp, _vp, _l, _l, _i],
+    "gwhe_decrypt_results": [_vp, _f64p, _f64p],
+    "gwhe_job_ct": [_vp, _i, _l, ctypes.POINTER(_vp)],
+    "gwhe_prof_enable": [_vp, _i],
+    "gwhe_ks_histogram": [_vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS"), _i],
+    "gwhe_prof_read": [_vp, _f64p, _f64p, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")],
+}
+
+PROF_CLASSES = ("ntt", "ks_inner", "tensor_mac", "baseconv", "elementwise", "encode", "sample")
+
+_LIB = None
+
+
+def lib():
+    """The loaded libgwhe.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgwhe.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _i
+        L.gwhe_last_error.argtypes = [_vp]
+        L.gwhe_last_error.restype = ctypes.c_char_p
+        L.gwhe_job_keyswitches.argtypes = [_vp]
+        L.gwhe_job_keyswitches.restype = _l
+        L.gwhe_launch_count.argtypes = [_vp]
+        L.gwhe_launch_count.restype = _l
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(list(_SIGS) + ["gwhe_last_error", "gwhe_job_keyswitches", "gwhe_launch_count"])
+
+
+def _check(rc, ctx=None):
+    if rc != GWHE_OK:
+        msg = ""
+        if ctx is not None:
+            m = lib().gwhe_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise GwheError(rc, msg)
+
+
+def _ptr(x):
+    """device pointer of a torch tensor / integer, or a host array's address."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(x))
+
+
+def _slots(z, M):
+    z = np.asarray(z, dtype=complex)
+    full = np.zeros(M, complex)
+    full[: z.shape[0]] = z
+    return np.ascontiguousarray(np.stack([full.real, full.imag], axis=1).reshape(-1))
+
+
+# ----------------------------------------------------------------- host only
+def params(logN, L, q0_bits=60, scale_bits=40, K=1, sp_bits=60, dnum=None):
+    return Params(logN, L, q0_bits, scale_bits, K, sp_bits, L if dnum is None else dnum)
+
+
+def gen_primes(prm: Params):
+    q = np.zeros(prm.L, np.uint64)
+    p = np.zeros(prm.K, np.uint64)
+    _check(lib().gwhe_gen_primes(ctypes.byref(prm), q, p))
+    return q, p
+
+
+def fft_twiddles(logN, sign):
+    M = 1 << (logN - 1)
+    W = np.zeros(M, np.float64)  # M/2 complex
+    T = np.zeros(2 * M, np.float64)
+    _check(lib().gwhe_fft_twiddles(logN, sign, W, T))
+    return W, T
+
+
+def layout(logN, n, k):
+    out = (_l * 5)()
+    _check(lib().gwhe_layout(logN, n, k, out))
+    return dict(zip(("nb", "B", "tau", "batches", "H"), list(out)))
+
+
+# ----------------------------------------------------------------- objects
+class Ciphertext:
+    def __init__(self, ctx: "Context", handle):
+        self.ctx = ctx
+        self.h = handle
+        ctx._children.add(self)
+
+    def close(self):
+        # a handle must not outlive its context (the context closes it first)
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
+            lib().gwhe_ct_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        npoly, l, sc = _i(), _i(), _d()
+        _check(lib().gwhe_ct_info(self.h, ctypes.byref(npoly), ctypes.byref(l), ctypes.byref(sc)))
+        return npoly.value, l.value, sc.value
+
+    @property
+    def level(self):
+        return self.info()[1]
+
+    @property
+    def scale(self):
+        return self.info()[2]
+
+    def export(self):
+        npoly, l, _ = self.info()
+        out = np.zeros((npoly, l, self.ctx.N), np.uint64)
+        _check(lib().gwhe_ct_export(self.h, out), self.ctx.h)
+        return out
+
+    def import_(self, coeffs, scale):
+        coeffs = np.ascontiguousarray(coeffs, np.uint64)
+        _check(lib().gwhe_ct_import(self.h, coeffs, coeffs.shape[0], coeffs.shape[1], scale),
+               self.ctx.h)
+
+    def drop(self, l):
+        _check(lib().gwhe_drop(self.h, l), self.ctx.h)
+        return self
+
+
+class Context:
+    def __init__(self, logN, L, q0_bits=60, scale_bits=40, K=1, sp_bits=60, dnum=None, seed=0,
+                 stream=None):
+        self.prm = params(logN, L, q0_bits, scale_bits, K, sp_bits, dnum)
+        self.logN, self.L, self.K = logN, L, K
+        self.N = 1 << logN
+        self.M = self.N // 2
+        self.dnum = self.prm.dnum
+        self.delta = float(2 ** scale_bits)
+        self._children = weakref.WeakSet()
+        h = _vp()
+        _check(lib().gwhe_ctx_create(ctypes.byref(self.prm), seed, _ptr(stream), ctypes.byref(h)))
+        self.h = h
+        mods = np.zeros(L + K, np.uint64)
+        _check(lib().gwhe_ctx_moduli(self.h, mods))
+        self.mods = mods
+        self.q = [int(x) for x in mods[:L]]
+        self.p = [int(x) for x in mods[L:]]
+
+    def close(self):
+        if getattr(self, "h", None):
+            # jobs first (they own ciphertexts), then ciphertext handles
+            kids = sorted(list(self._children), key=lambda x: 0 if isinstance(x, Job) else 1)
+            for kid in kids:
+                kid.close()
+            lib().gwhe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self.h)
+
+    def sync(self):
+        self._c(lib().gwhe_sync(self.h))
+
+    # keys
+    def keygen(self, rot_steps=(), conj=False):
+        steps = np.ascontiguousarray(np.array(list(rot_steps), dtype=np.int32).reshape(-1))
+        self._c(lib().gwhe_keygen(self.h, steps, len(steps), 1 if conj else 0))
+
+    def export_secret(self):
+        s = np.zeros(self.N, np.int64)
+        self._c(lib().gwhe_export_secret(self.h, s))
+        return s
+
+    def export_pk(self):
+        pk = np.zeros((2, self.L, self.N), np.uint64)
+        self._c(lib().gwhe_export_pk(self.h, pk))
+        return pk
+
+    def export_ksk(self, key_id):
+        out = np.zeros((self.dnum, 2, self.L + self.K, self.N), np.uint64)
+        self._c(lib().gwhe_export_ksk(self.h, key_id, out))
+        return out
+
+    # ciphertexts
+    def ct(self, npoly=2, cap=None):
+        h = _vp()
+        self._c(lib().gwhe_ct_create(self.h, npoly, self.L if cap is None else cap,
+                                     ctypes.byref(h)))
+        return Ciphertext(self, h)
+
+    def import_ct(self, coeffs, scale):
+        coeffs = np.ascontiguousarray(coeffs, np.uint64)
+        c = self.ct(coeffs.shape[0], coeffs.shape[1])
+        c.import_(coeffs, scale)
+        return c
+
+    def encode(self, z, scale):
+        out = np.zeros(self.N, np.int64)
+        self._c(lib().gwhe_encode(self.h, _slots(z, self.M), scale, out))
+        return out
+
+    def encrypt(self, z, scale, level, enc_id):
+        c = self.ct(2, level)
+        self._c(lib().gwhe_encrypt(self.h, _slots(z, self.M), scale, level, enc_id, c.h))
+        return c
+
+    def encrypt_coeffs(self, m, scale, level, enc_id):
+        c = self.ct(2, level)
+        self._c(lib().gwhe_encrypt_coeffs(self.h, np.ascontiguousarray(m, np.int64), scale,
+                                          level, enc_id, c.h))
+        return c
+
+    def decrypt(self, ct):
+        out = np.zeros((ct.level, self.N), np.uint64)
+        self._c(lib().gwhe_decrypt(self.h, ct.h, out))
+        return out
+
+    def decrypt_decode(self, ct):
+        out = np.zeros(2 * self.M, np.float64)
+        self._c(lib().gwhe_decrypt_decode(self.h, ct.h, out))
+        return out[0::2] + 1j * out[1::2]
+
+    # arithmetic (results are new ciphertexts unless noted)
+    def _out(self, a, npoly=2):
+        return self.ct(npoly, a.level)
+
+    def add(self, a, b):
+        o = self._out(a)
+        self._c(lib().gwhe_add(self.h, a.h, b.h, o.h))
+        return o
+
+    def sub(self, a, b):
+        o = self._out(a)
+        self._c(lib().gwhe_sub(self.h, a.h, b.h, o.h))
+        return o
+
+    def negate(self, a):
+        o = self._out(a)
+        self._c(lib().gwhe_negate(self.h, a.h, o.h))
+        return o
+
+    def add_const(self, a, v):  # in place
+        self._c(lib().gwhe_add_const(self.h, a.h, v))
+        return a
+
+    def mul_int(self, a, k):  # in place
+        self._c(lib().gwhe_mul_int(self.h, a.h, k))
+        return a
+
+    def mul_const(self, a, v):  # in place
+        self._c(lib().gwhe_mul_const(self.h, a.h, v))
+        return a
+
+    def mul_mask(self, a, z):
+        o = self._out(a)
+        self._c(lib().gwhe_mul_mask(self.h, a.h, _slots(z, self.M), o.h))
+        return o
+
+    def tensor(self, a, b):
+        o = self._out(a, 3)
+        self._c(lib().gwhe_tensor(self.h, a.h, b.h, o.h))
+        return o
+
+    def tensor_sum(self, pairs):
+        a = (_vp * len(pairs))(*[p[0].h for p in pairs])
+        b = (_vp * len(pairs))(*[p[1].h for p in pairs])
+        o = self._out(pairs[0][0], 3)
+        self._c(lib().gwhe_tensor_sum(self.h, a, b, len(pairs), o.h))
+        return o
+
+    def relin(self, t3):
+        o = self._out(t3)
+        self._c(lib().gwhe_relin(self.h, t3.h, o.h))
+        return o
+
+    def rescale(self, a):  # in place
+        self._c(lib().gwhe_rescale(self.h, a.h))
+        return a
+
+    def mult(self, a, b):
+        o = self._out(a)
+        self._c(lib().gwhe_mult(self.h, a.h, b.h, o.h))
+        return o
+
+    def rotate(self, a, r):
+        o = self._out(a)
+        self._c(lib().gwhe_rotate(self.h, a.h, r, o.h))
+        return o
+
+    def conj(self, a):
+        o = self._out(a)
+        self._c(lib().gwhe_conjugate(self.h, a.h, o.h))
+        return o
+
+    def keyswitch(self, x, key_id):
+        x = np.ascontiguousarray(x, np.uint64)
+        l = x.shape[0]
+        out = np.zeros((2, l, self.N), np.uint64)
+        self._c(lib().gwhe_keyswitch(self.h, x, l, key_id, out))
+        return out
+
+    def ks_histogram(self):
+        out = np.zeros(65, np.int64)
+        self._c(lib().gwhe_ks_histogram(self.h, out, 65))
+        return out
+
+    def launches(self):
+        return lib().gwhe_launch_count(self.h)
+
+    def prof_enable(self, on=True):
+        self._c(lib().gwhe_prof_enable(self.h, 1 if on else 0))
+
+    def prof_read(self):
+        """{class: (ms, algorithmic bytes, launch groups)} since the last read."""
+        ms = np.zeros(len(PROF_CLASSES))
+        by = np.zeros(len(PROF_CLASSES))
+        n = np.zeros(len(PROF_CLASSES), np.int64)
+        self._c(lib().gwhe_prof_read(self.h, ms, by, n))
+        return {k: (float(ms[i]), float(by[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def ntt_batch(self, dev, npoly, nlimbs, inverse=False):
+        """in-place NTT of device rows dev[npoly][nlimbs][N] (torch tensor or pointer)."""
+        self._c(lib().gwhe_ntt_batch(self.h, _ptr(dev), npoly, nlimbs, 1 if inverse else 0))
+
+
+class Job:
+    """An encrypted semi-parallel GWAS job (Alg. 11) on a context."""
+
+    def __init__(self, ctx: Context, n, d, k):
+        self.ctx = ctx
+        self.n, self.d, self.k = n, d, k
+        h = _vp()
+        ctx._c(lib().gwhe_job_create(ctx.h, n, d, k, ctypes.byref(h)))
+        self.h = h
+        self.layout = layout(ctx.logN, n, k)
+        ctx._children.add(self)
+
+    def close(self):
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
+            # views taken from this job become invalid with it
+            for kid in list(self.ctx._children):
+                if isinstance(kid, Ciphertext) and getattr(kid, "job", None) is self:
+                    kid.close()
+            lib().gwhe_job_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _arr(x):
+        if hasattr(x, "data_ptr"):
+            return x, _ptr(x)
+        a = np.ascontiguousarray(x, np.float64)
+        return a, _ptr(a)
+
+    def encrypt_inputs(self, X, XtX_inv, y):
+        X, px = self._arr(X)
+        A, pa = self._arr(XtX_inv)
+        y, py = self._arr(y)
+        self.ctx._c(lib().gwhe_encrypt_inputs(self.h, px, pa, py))
+
+    def fit(self, kappa):
+        self.ctx._c(lib().gwhe_fit_covariates(self.h, kappa))
+
+    def set_fit_state(self, M, w, wz):
+        M, pm = self._arr(M)
+        w, pw = self._arr(w)
+        wz, pz = self._arr(wz)
+        self.ctx._c(lib().gwhe_set_fit_state(self.h, pm, pw, pz))
+
+    def snp_stats(self, S, b0=0, b1=None):
+        S, ps = self._arr(S)
+        b1 = self.layout["batches"] if b1 is None else b1
+        self.ctx._c(lib().gwhe_snp_stats(self.h, ps, b0, b1, 1))
+
+    def decrypt_results(self):
+        num = np.full(self.k, np.nan)
+        den = np.full(self.k, np.nan)
+        self.ctx._c(lib().gwhe_decrypt_results(self.h, num, den))
+        return num, den
+
+    def ct(self, which, index=0):
+        """a view of a job ciphertext (valid while the job lives)."""
+        h = _vp()
+        self.ctx._c(lib().gwhe_job_ct(self.h, which, index, ctypes.byref(h)))
+        v = Ciphertext(self.ctx, h)
+        v.job = self
+        return v
+
+    def keyswitches(self):
+        return lib().gwhe_job_keyswitches(self.h)

@@ -1,0 +1,134 @@
+"""GPU parity of the encrypted GWAS job (Algorithms 1-11) against the CPU oracle:
+ciphertexts bit for bit where the oracle can run the circuit, decrypted
+results within |d b'| <= 5e-3 and |d(-log10 p)| <= 0.05 of the FP64 reference
+at the paper's shape (245 samples, 5 covariates, 10643 SNPs, N = 2^16)."""
+import numpy as np
+import pytest
+
+from oracle import gwas_fp64
+from oracle.circuit import Circuit, Layout, rotation_steps
+from oracle.ckks import OracleCKKS, galois_conj, galois_rot
+from paper_1902_04303_gb300.datagen import WORKLOADS, make_gwas
+
+pytestmark = pytest.mark.gpu
+
+TOL_B = 5e-3
+TOL_LOGP = 0.05
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1902_04303_gb300 import build
+    build.build()
+    from paper_1902_04303_gb300 import gwhe
+    return gwhe
+
+
+def check_accuracy(num, den, ref, k):
+    assert np.all(np.isfinite(num[:k])) and np.all(np.isfinite(den[:k]))
+    ok = np.abs(ref["den"]) > 1e-6  # monomorphic SNPs: den = 0 (degenerate)
+    assert np.max(np.abs(den[~ok]), initial=0.0) < 1e-3
+    b = num[ok] / den[ok]
+    db = np.abs(b - ref["b"][ok])
+    assert np.max(db) <= TOL_B, np.max(db)
+    dl = np.abs(gwas_fp64.neglog10p(b, 1.0 / den[ok])
+                - gwas_fp64.neglog10p(ref["b"][ok], ref["err"][ok]))
+    assert np.max(dl) <= TOL_LOGP, np.max(dl)
+    return float(np.max(db)), float(np.max(dl))
+
+
+def test_job_circuit_bit_exact(g):
+    """Covariate fit + one ragged batch: every output ciphertext and the
+    intermediate z', beta, Dup(M_j), Dup(w), Dup(w z') equal the oracle's."""
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 11
+    n, d, k = 16, 3, 40
+    data = make_gwas(n, d, k, seed=5)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(logN, n, d, k)
+    steps = rotation_steps(lay)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    ctx.keygen(rot_steps=steps, conj=True)
+    job = g.Job(ctx, n, d, k)
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
+    o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
+    c = Circuit(o, lay)
+    c.encrypt_inputs(data.X, A, data.y)
+    c.fit(kappa=1)
+    assert np.array_equal(job.ct(7).export(), c.beta.c)
+    assert np.array_equal(job.ct(6).export(), c.zp.c)
+    assert np.array_equal(job.ct(4).export(), c.DupW.c)
+    assert np.array_equal(job.ct(5).export(), c.DupWZ.c)
+    for jj in (0, 7, n - 1):
+        assert np.array_equal(job.ct(3, jj).export(), c.DupM[jj].c), jj
+    want = c.snp_batch(c.encrypt_snp_batch(data.S, 0))
+    for which in range(3):
+        assert np.array_equal(job.ct(which, 0).export(), want[which].c), which
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, k)
+
+
+def test_job_split_mode_small_workload(g):
+    """The small plain job (N = 2^13, 4 limbs, 1 special prime, n = 64, d = 4,
+    k = 256, two batches): the client supplies M, w, w z' (split mode);
+    batch outputs bit-exact with the oracle, decrypted within tolerance."""
+    W = WORKLOADS["small-n64"]
+    data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"])
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1)
+    lay = Layout(W["logN"], W["n"], W["d"], W["k"])
+    steps = [1 << i for i in range(int(np.log2(lay.nb)))]  # colSum only
+    ctx = g.Context(W["logN"], W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
+    ctx.keygen(rot_steps=steps, conj=True)
+    job = g.Job(ctx, W["n"], W["d"], W["k"])
+    wz = ref["w"] * ref["zp"]
+    job.set_fit_state(ref["M"], ref["w"], wz)
+    job.snp_stats(data.S)
+    num, den = job.decrypt_results()
+    check_accuracy(num, den, ref, W["k"])
+    o = OracleCKKS(logN=W["logN"], L=W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
+    o.keygen(galois=[galois_rot(W["logN"], r) for r in steps] + [galois_conj(W["logN"])])
+    c = Circuit(o, lay)
+    c.load_split_state(ref["M"], ref["w"], wz)
+    want = c.snp_batch(c.encrypt_snp_batch(data.S, 1))
+    for which in range(3):
+        assert np.array_equal(job.ct(which, 1).export(), want[which].c), which
+
+
+def test_job_paper_shape_accuracy(g):
+    """245 x 5 x 10643 at N = 2^16 (42 batches, ragged last batch of 147 SNPs):
+    decrypted numerators/denominators against the FP64 reference; the
+    ciphertexts of this size are checked op by op in test_gpu_parity."""
+    W = WORKLOADS["paper-n245"]
+    data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"])
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                    W["dnum"], seed=W["seed"])
+    ctx.keygen(rot_steps=[1 << i for i in range(W["logN"] - 1)], conj=True)
+    job = g.Job(ctx, W["n"], W["d"], W["k"])
+    assert job.layout["tau"] == 256 and job.layout["batches"] == 42 and job.layout["H"] == 2
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    db, dl = check_accuracy(num, den, ref, W["k"])
+    print("paper shape: max |d b'| = %.3g, max |d -log10 p| = %.3g" % (db, dl))
+
+
+def test_job_rejects_missing_state_and_depth(g):
+    ctx = g.Context(10, 4, K=2, dnum=2, seed=1)
+    ctx.keygen(rot_steps=[1 << i for i in range(9)], conj=True)
+    job = g.Job(ctx, 16, 3, 40)
+    S = np.zeros((16, 40))
+    with pytest.raises(g.GwheError):
+        job.snp_stats(S)  # no covariate phase yet
+    data = make_gwas(16, 3, 40, seed=2)
+    job.encrypt_inputs(data.X, gwas_fp64.xtx_inv(data.X), data.y)
+    with pytest.raises(g.GwheError) as e:
+        job.fit(1)  # four limbs cannot hold the fit
+    assert e.value.code == -3
