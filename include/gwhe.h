@@ -170,6 +170,26 @@ int gwhe_keyswitch(gwhe_ctx* ctx, const uint64_t* x, int l, uint32_t key_id, uin
  * dev[npoly][nlimbs][N]; limb i of every poly is modulo q_i. */
 int gwhe_ntt_batch(gwhe_ctx* ctx, uint64_t* dev, int npoly, int nlimbs, int inverse);
 
+/* Key switch without any device allocation, for callers that cannot let the
+ * library allocate: a serving process whose device memory is already
+ * reserved by its own pool, or a request path where an allocator call could
+ * block or synchronise the device.  The paper has no counterpart; this is a
+ * deployment variant of gwhe_keyswitch.  x_ntt: device uint64[l][N], NTT
+ * domain; out_ntt: device uint64[2][l][N], NTT domain (same arithmetic,
+ * bit for bit, as gwhe_keyswitch).  Temporaries live in one static 32 MiB
+ * device array (2^22 words) that every GPU loading the library holds until
+ * exit; a switch at level l needs (3 l + (ceil(l/alpha) + 2)(l + K)) N words,
+ * larger requests return GWHE_EINVAL with the sizes in gwhe_last_error.  The
+ * first call on a device looks up the array's address with that device
+ * current: make that first call before any stream capture.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams,
+ * other contexts on the same device) race and must be serialised by the
+ * caller.  The array keeps the previous call's contents; nothing in it needs
+ * to start at zero.  Allocates nothing while the kernel timers
+ * (gwhe_prof_enable) are off. */
+int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int l, uint32_t key_id,
+                           uint64_t* out_ntt);
+
 /* ------------------------------------------------------------ GWAS job
  * The paper's problem statement (Alg. 11 inputs / outputs): n samples, d
  * covariates (column 0 = intercept), k SNPs.  Input arrays may be host or

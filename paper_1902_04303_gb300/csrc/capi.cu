@@ -3,22 +3,9 @@
 #include <algorithm>
 #include <cstring>
 
-#include "../../include/gwhe.h"
-#include "gwas.cuh"
+#include "capi_types.cuh"
 
 using namespace gwhe;
-
-struct gwhe_ctx {
-  Context* c;
-};
-struct gwhe_ct {
-  gwhe_ctx* owner;
-  CtPtr ct;
-};
-struct gwhe_job {
-  gwhe_ctx* owner;
-  std::unique_ptr<Job> job;
-};
 
 namespace {
 

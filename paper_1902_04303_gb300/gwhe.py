@@ -82,6 +82,7 @@ _SIGS = {
     "gwhe_conjugate": [_vp, _vp, _vp],
     "gwhe_drop": [_vp, _i],
     "gwhe_keyswitch": [_vp, _u64p, _i, _u32, _u64p],
+    "gwhe_keyswitch_noalloc": [_vp, _vp, _i, _u32, _vp],
     "gwhe_ntt_batch": [_vp, _vp, _i, _i, _i],
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
     "gwhe_job_destroy": [_vp],
@@ -424,6 +425,11 @@ class Context:
         n = np.zeros(len(PROF_CLASSES), np.int64)
         self._c(lib().gwhe_prof_read(self.h, ms, by, n))
         return {k: (float(ms[i]), float(by[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def keyswitch_noalloc(self, x_dev, l, key_id, out_dev):
+        """Key switch of device rows x_dev[l][N] (NTT domain) into out_dev
+        [2][l][N] using the library's static scratch (no device allocation)."""
+        self._c(lib().gwhe_keyswitch_noalloc(self.h, _ptr(x_dev), l, key_id, _ptr(out_dev)))
 
     def ntt_batch(self, dev, npoly, nlimbs, inverse=False):
         """in-place NTT of device rows dev[npoly][nlimbs][N] (torch tensor or pointer)."""
