@@ -225,6 +225,8 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if not args.no_micro:
+        out["micro"] = run_micro(stream)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(ks_hist, W)
     print(json.dumps(out))
@@ -232,6 +234,70 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+MICRO = dict(name="ntt-ks-micro", logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60,
+             dnum=3, n_ct=64, seed=1003)
+
+
+def run_micro(ctx_stream, reps=3):
+    """Kernel microbench: a batched negacyclic NTT + inverse NTT over 64
+    ciphertexts x 2 polys x 24 limbs (3072 limb transforms, N = 2^16), and 512
+    rotations (64 ciphertexts x steps 1, 2, ..., 128) at level 24, each
+    followed by a rescale.  Returns throughputs and algorithmic NTT GB/s."""
+    import torch
+    from paper_1902_04303_gb300 import gwhe
+    from paper_1902_04303_gb300.datagen import make_slots
+    W = MICRO
+    stream = ctx_stream
+    ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                       W["dnum"], seed=W["seed"], stream=stream.cuda_stream)
+    steps = [1 << i for i in range(8)]
+    N, L, nct = ctx.N, W["L"], W["n_ct"]
+    rows = nct * 2 * L
+    g = torch.Generator(device="cuda")
+    g.manual_seed(W["seed"])
+    x = torch.empty((nct * 2, L, N), dtype=torch.int64, device="cuda")
+    for i in range(L):
+        x[:, i, :] = torch.randint(0, ctx.q[i], (nct * 2, N), device="cuda", generator=g)
+    ref = x.clone()
+    ctx.ntt_batch(x, nct * 2, L)
+    ctx.ntt_batch(x, nct * 2, L, inverse=True)
+    torch.cuda.synchronize()
+    ok = bool(torch.equal(x, ref))
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.ntt_batch(x, nct * 2, L)
+        ctx.ntt_batch(x, nct * 2, L, inverse=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1) / 2)  # per transform direction
+    t_ntt = min(ms) / 1e3
+    del x, ref
+    ctx.keygen(rot_steps=steps, conj=False)
+    cts = [ctx.encrypt(make_slots(ctx.M, 7 + i), ctx.delta, L, 0x500 + i) for i in range(nct)]
+    torch.cuda.synchronize()
+    ks = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in cts:
+            for r in steps:
+                o = ctx.rotate(c, r)
+                ctx.rescale(o)
+        e1.record(stream)
+        e1.synchronize()
+        ks.append(e0.elapsed_time(e1))
+    t_ks = min(ks) / 1e3
+    return {"workload": W["name"], "ntt_roundtrip_exact": ok,
+            "ntt_limb_per_s": round(rows / t_ntt, 1),
+            "ntt_gbs_algorithmic": round(rows * N * 16 / t_ntt / 1e9, 1),
+            "ntt_ms_3072_limbs": round(t_ntt * 1e3, 3),
+            "rotations": nct * len(steps),
+            "keyswitch_per_s_level24": round(nct * len(steps) / t_ks, 1),
+            "rotate_rescale_ms_512": round(t_ks * 1e3, 2)}
 
 
 def oracle_sample(W):
@@ -351,7 +417,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwhe", choices=["gwhe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-micro", action="store_true")
+    ap.add_argument("--micro-only", action="store_true",
+                    help="only the kernel microbench (the controlled case for profiler captures)")
     args = ap.parse_args()
+    if args.micro_only:
+        import torch
+        from paper_1902_04303_gb300 import build as pkg_build
+        pkg_build.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_micro(torch.cuda.current_stream(), reps=max(1, args.steps))))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
