@@ -549,8 +549,8 @@ void op_rescale(Context* c, Ct& ct) {
   const int l = ct.l, np = ct.npoly, N = c->N;
   GWHE_REQUIRE(l >= 2, ST_ELEVEL, "no level left to rescale");
   Tmp last(c, sizeof(u64) * np * N);
-  for (int p = 0; p < np; ++p)
-    GWHE_CUDA(cudaMemcpyAsync(last.u() + (size_t)p * N, ct.limb(p, l - 1), sizeof(u64) * N,
+  GWHE_CUDA(cudaMemcpy2DAsync(last.p, sizeof(u64) * N, ct.limb(0, l - 1),
+                              sizeof(u64) * (size_t)ct.cap * N, sizeof(u64) * N, np,
                               cudaMemcpyDeviceToDevice, c->stream));
   RowMap rl;
   rl.npoly = np;
@@ -593,6 +593,202 @@ void op_conj(Context* c, const Ct& a, Ct& out) { op_galois(c, a, galois_conj(c),
 void op_drop(Ct& ct, int l) {
   GWHE_REQUIRE(l >= 1 && l <= ct.l, ST_ELEVEL, "cannot raise a level");
   ct.l = l;
+}
+
+// ---------------------------------------------------------------- sets
+CtSet::~CtSet() {
+  if (owned && d && ctx) dfree(ctx, d);
+}
+
+CtSet CtSet::slice(int first, int n, int lv) const {
+  GWHE_REQUIRE(first >= 0 && n >= 1 && first + n <= cnt && lv <= l, ST_EINVAL, "bad set slice");
+  CtSet v;
+  v.ctx = ctx;
+  v.d = item(first);
+  v.cnt = n;
+  v.npoly = npoly;
+  v.cap = cap;
+  v.l = lv;
+  v.scale = scale;
+  v.owned = false;
+  return v;
+}
+
+CtPtr CtSet::view(int i) const {
+  CtPtr v(new Ct());
+  v->ctx = ctx;
+  v->d = item(i);
+  v->npoly = npoly;
+  v->cap = cap;
+  v->l = l;
+  v->scale = scale;
+  v->owned = false;
+  return v;
+}
+
+Ct CtSet::all() const {
+  Ct v;
+  v.ctx = ctx;
+  v.d = d;
+  v.npoly = npoly * cnt;
+  v.cap = cap;
+  v.l = l;
+  v.scale = scale;
+  v.owned = false;
+  return v;
+}
+
+CtSetPtr set_new(Context* c, int cnt, int npoly, int cap, int l, double scale) {
+  GWHE_REQUIRE(cnt >= 1 && l <= cap, ST_EINVAL, "bad ciphertext set");
+  CtSetPtr s(new CtSet());
+  s->ctx = c;
+  s->cnt = cnt;
+  s->npoly = npoly;
+  s->cap = cap;
+  s->l = l;
+  s->scale = scale;
+  s->d = dalloc_u64(c, (size_t)cnt * npoly * cap * c->N);
+  return s;
+}
+
+template <class T>
+static T* upload_async(Context* c, Tmp& t, const std::vector<T>& v) {
+  GWHE_CUDA(cudaMemcpyAsync(t.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+  return t.as<T>();
+}
+
+void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const Ksk& key,
+                   u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                   size_t a0_stride, size_t a1_stride) {
+  const size_t N = c->N;
+  const int K = c->P.K, L = c->P.L, ne = l + K;
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  c->ks_count += cnt;
+  c->ks_by_level[l] += cnt;
+  Tmp xc(c, sizeof(u64) * cnt * l * N);
+  GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x, sizeof(u64) * x_stride,
+                              sizeof(u64) * l * N, cnt, cudaMemcpyDeviceToDevice, c->stream));
+  ntt_inverse(c, xc.u(), rows_q(cnt, l, l));
+  Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
+  modup_convert_set(c, xc.u(), l, ext.u(), cnt);
+  for (int j = 0; j < beta; ++j) {
+    const ConvTable& t = c->modup.at({l, j});
+    RowMap rm;
+    rm.npoly = cnt;
+    rm.nl = t.n_out;
+    rm.poly_stride = beta * ne;
+    for (int o = 0; o < t.n_out; ++o) {
+      rm.off[o] = (uint16_t)(j * ne + t.out_limb[o]);
+      rm.pidx[o] = t.out_pidx[o];
+    }
+    ntt_forward(c, ext.u(), rm);
+  }
+  Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
+  ks_inner_set(c, x, x_stride, l, ext.u(), key.d, acc.u(), cnt);
+  RowMap rk;
+  rk.npoly = 2 * cnt;
+  rk.nl = K;
+  rk.poly_stride = ne;
+  for (int k = 0; k < K; ++k) {
+    rk.off[k] = (uint16_t)(l + k);
+    rk.pidx[k] = (uint8_t)(L + k);
+  }
+  ntt_inverse(c, acc.u(), rk);
+  Tmp conv(c, sizeof(u64) * cnt * 2 * l * N);
+  moddown_convert_set(c, acc.u(), l, conv.u(), cnt);
+  ntt_forward(c, conv.u(), rows_q(2 * cnt, l, l));
+  moddown_combine_set(c, acc.u(), conv.u(), l, cnt, out0, out1, o_stride, add0, add1, a0_stride,
+                      a1_stride);
+}
+
+void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps) {
+  GWHE_REQUIRE(s.npoly == 2, ST_EINVAL, "ladder needs ciphertexts");
+  const size_t N = c->N;
+  const int l = s.l;
+  Tmp t(c, sizeof(u64) * s.cnt * 2 * l * N);
+  for (int step : steps) {
+    const u32 g = galois_for_rotation(c, step);
+    auto it = c->ksk.find(g);
+    GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "missing Galois key " + std::to_string(g));
+    // t = (sigma(s0) + s0, sigma(s1)); s = (t0 + KS(t1)_0, s1 + KS(t1)_1)
+    automorph_ladder_set(c, s.d, s.cap, s.stride(), t.u(), l, (size_t)2 * l * N, l, s.cnt, g);
+    keyswitch_set(c, t.u() + (size_t)l * N, (size_t)2 * l * N, s.cnt, l, it->second, s.d,
+                  s.d + (size_t)s.cap * N, s.stride(), t.u(), s.d + (size_t)s.cap * N,
+                  (size_t)2 * l * N, s.stride());
+  }
+}
+
+void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out) {
+  auto it = c->ksk.find(g);
+  GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "missing Galois key " + std::to_string(g));
+  GWHE_REQUIRE(out.cnt == a.cnt && out.cap >= a.l && a.d != out.d, ST_EINVAL, "bad galois set");
+  const size_t N = c->N;
+  const int l = a.l;
+  Ct ai = a.all(), oi = out.all();
+  automorph_ntt(c, PolyView{oi.d, oi.cap}, CPolyView{ai.d, ai.cap}, 2 * a.cnt, l, g);
+  keyswitch_set(c, out.d + (size_t)out.cap * N, out.stride(), a.cnt, l, it->second, out.d,
+                out.d + (size_t)out.cap * N, out.stride(), out.d, nullptr, out.stride(), 0);
+  out.l = l;
+  out.scale = a.scale;
+}
+
+void set_mask(Context* c, const std::vector<MaskItem>& items, double src_scale, double pt_scale,
+              CtSet& out, bool rescale) {
+  GWHE_REQUIRE((int)items.size() == out.cnt, ST_EINVAL, "mask set size");
+  Tmp d(c, sizeof(MaskItem) * items.size());
+  mask_set(c, upload_async(c, d, items), out.cnt, out.d, out.cap, out.stride(), out.l);
+  out.scale = src_scale * pt_scale;
+  if (rescale) set_rescale(c, out);
+}
+
+void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs,
+                    int npairs, CtSet& out3) {
+  GWHE_REQUIRE(out3.npoly == 3 && (int)pairs.size() == npairs * out3.cnt, ST_EINVAL,
+               "tensor set shape");
+  const int l = pairs[0].first->l;
+  std::vector<MacPair> hp;
+  const double sc = pairs[0].first->scale * pairs[0].second->scale;
+  for (auto& pr : pairs) {
+    GWHE_REQUIRE(pr.first->l == l && pr.second->l == l, ST_ELEVEL,
+                 "tensor operands at different levels");
+    check_scales(pr.first->scale * pr.second->scale, sc);
+    hp.push_back(MacPair{pr.first->d, pr.second->d, pr.first->cap, pr.second->cap});
+  }
+  GWHE_REQUIRE(out3.cap >= l, ST_EINVAL, "tensor output too small");
+  Tmp d(c, sizeof(MacPair) * hp.size());
+  tensor_mac_set(c, PolyView{out3.d, out3.cap}, out3.stride(), upload_async(c, d, hp), npairs,
+                 out3.cnt, l);
+  out3.l = l;
+  out3.scale = sc;
+}
+
+void set_relin(Context* c, const CtSet& t3, CtSet& out) {
+  GWHE_REQUIRE(t3.npoly == 3 && out.npoly == 2 && out.cnt == t3.cnt && out.cap >= t3.l,
+               ST_EINVAL, "relinearisation set shape");
+  auto it = c->ksk.find(0);
+  GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "no relinearisation key");
+  const size_t N = c->N;
+  keyswitch_set(c, t3.d + (size_t)2 * t3.cap * N, t3.stride(), t3.cnt, t3.l, it->second, out.d,
+                out.d + (size_t)out.cap * N, out.stride(), t3.d, t3.d + (size_t)t3.cap * N,
+                t3.stride(), t3.stride());
+  out.l = t3.l;
+  out.scale = t3.scale;
+}
+
+void set_rescale(Context* c, CtSet& s) {
+  Ct all = s.all();
+  op_rescale(c, all);
+  s.l = all.l;
+  s.scale = all.scale;
+}
+
+void set_mult(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs, CtSet& out) {
+  const int l = pairs[0].first->l;
+  CtSetPtr t3 = set_new(c, out.cnt, 3, l, l, 1.0);
+  set_tensor_mac(c, pairs, 1, *t3);
+  set_relin(c, *t3, out);
+  set_rescale(c, out);
 }
 
 // ---------------------------------------------------------------- encoding

@@ -69,6 +69,48 @@ void ct_import(Context* c, Ct& ct, const u64* host_coeff, int npoly, int l, doub
 void ct_export(Context* c, const Ct& ct, u64* host_coeff);
 void decrypt_coeff(Context* c, const Ct& ct, u64* dev_out);  // [l][N] coefficient domain
 
+// A set of cnt ciphertexts (npoly polys each, room for cap limbs) in one
+// allocation: item i, poly p, limb k at d + ((i * npoly + p) * cap + k) * N.
+// All items share a level and a scale.  Independent ciphertexts of the
+// circuit (the columns of M, the entries being replicated, the SNP batches)
+// are processed as one set so that every kernel launch covers all of them.
+struct CtSet {
+  Context* ctx = nullptr;
+  u64* d = nullptr;
+  int cnt = 0, npoly = 2, cap = 0, l = 0;
+  double scale = 1.0;
+  bool owned = true;
+  ~CtSet();
+  // non-owning set over items [first, first + n) at level lv (lv <= l)
+  CtSet slice(int first, int n, int lv) const;
+  size_t stride() const { return (size_t)npoly * cap * ctx->N; }
+  u64* item(int i) const { return d + (size_t)i * stride(); }
+  CtPtr view(int i) const;  // non-owning ciphertext of item i
+  Ct all() const;           // the whole set as one npoly*cnt-poly ciphertext (non-owning)
+};
+typedef std::unique_ptr<CtSet> CtSetPtr;
+CtSetPtr set_new(Context* c, int cnt, int npoly, int cap, int l, double scale);
+
+// batched key switch: item i reads x + i x_stride (l limbs, NTT domain) and
+// writes out0/out1 + i o_stride (+ add0 + i a0_stride, add1 + i a1_stride)
+void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const Ksk& key,
+                   u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                   size_t a0_stride, size_t a1_stride);
+// s[i] += Rotate(s[i], step) for each step in turn (Alg. 1/4/5/7 ladders)
+void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps);
+// out[i] = automorphism g of a[i] (rotation or conjugation)
+void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out);
+// out[i] = items[i].src * items[i].pt, scale = src scale * pt_scale (then rescale)
+void set_mask(Context* c, const std::vector<MaskItem>& items, double src_scale, double pt_scale,
+              CtSet& out, bool rescale);
+// out3[i] = sum_j tensor(pairs[i npairs + j]) (out3 has npoly = 3)
+void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs,
+                    int npairs, CtSet& out3);
+void set_relin(Context* c, const CtSet& t3, CtSet& out);
+void set_rescale(Context* c, CtSet& s);
+// out[i] = a_i * b_i (tensor, relinearise, rescale)
+void set_mult(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs, CtSet& out);
+
 // pool allocation of temporaries: freed at scope exit (stream-ordered)
 struct Tmp {
   Context* c;

@@ -120,52 +120,102 @@ struct Eval {
     return out;
   }
 
-  // Alg. 1 for one entry: mask slot cidx, then rotate-and-add over log2(M) steps
-  CtPtr replicate(const Ct& v, int cidx) {
-    CtPtr t = mul_mask(v, kMaskSlot, cidx, e_slot(cidx));
-    ladder(*t, pow2_steps(lay.logN - 1));
-    return t;
+  // Alg. 1 for several (source, entry) pairs at once: mask the entry's slot
+  // (plaintext at scale q_last, rescale), then a log2(M) rotate-and-add ladder.
+  CtSetPtr replicate_set(const std::vector<std::pair<const Ct*, int>>& items) {
+    const Ct& v0 = *items[0].first;
+    const int l = v0.l;
+    const double ql = (double)c->mod[l - 1];
+    std::vector<MaskItem> mi;
+    for (auto& it : items) {
+      GWHE_REQUIRE(it.first->l == l && it.first->scale == v0.scale, ST_ELEVEL,
+                   "replicated sources must share level and scale");
+      mi.push_back(MaskItem{it.first->d, it.first->cap,
+                            mask_pt(c, kMaskSlot, it.second, l, ql, e_slot(it.second))});
+    }
+    CtSetPtr set = set_new(c, (int)items.size(), 2, l, l, 1.0);
+    set_mask(c, mi, v0.scale, ql, *set, true);
+    set_ladder(c, *set, pow2_steps(lay.logN - 1));
+    return set;
   }
   // Alg. 2: sum_c A(c) * Replicate(v)(c)
   CtPtr cp_matvec(const std::vector<CtPtr>& cols, const Ct& v, int m) {
-    std::vector<CtPtr> reps, views;
-    for (int cidx = 0; cidx < m; ++cidx) reps.push_back(replicate(v, cidx));
-    const int lv = reps[0]->l;
+    std::vector<std::pair<const Ct*, int>> items;
+    for (int cidx = 0; cidx < m; ++cidx) items.push_back({&v, cidx});
+    CtSetPtr reps = replicate_set(items);
+    const int lv = reps->l;
+    std::vector<CtPtr> views, rv;
     std::vector<std::pair<const Ct*, const Ct*>> pairs;
     for (int cidx = 0; cidx < m; ++cidx) {
       views.push_back(view(*cols[cidx], lv));
-      pairs.push_back({views.back().get(), reps[cidx].get()});
+      rv.push_back(reps->view(cidx));
+      pairs.push_back({views.back().get(), rv.back().get()});
     }
     return mac_relin_rescale(pairs);
   }
-  // Alg. 5: C = A * B then C += Rotate(C, 2^i) for i < log2(M)
-  CtPtr dotprod(const Ct& a, const Ct& b) {
-    CtPtr t = mult(a, b);
-    ladder(*t, pow2_steps(lay.logN - 1));
-    return t;
+  // Alg. 3 (CP-MatMult): column r of X * A is CP-MatVecMult(X, A_r); all d x m
+  // replicates and the d tensor sums run as sets.
+  CtSetPtr cp_matmul(const std::vector<CtPtr>& X, const std::vector<CtPtr>& Acols, int m) {
+    const int d = (int)Acols.size();
+    std::vector<std::pair<const Ct*, int>> items;
+    for (int r = 0; r < d; ++r)
+      for (int cidx = 0; cidx < m; ++cidx) items.push_back({Acols[r].get(), cidx});
+    CtSetPtr reps = replicate_set(items);
+    const int lv = reps->l;
+    std::vector<CtPtr> views, rv;
+    for (int cidx = 0; cidx < m; ++cidx) views.push_back(view(*X[cidx], lv));
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
+    for (int r = 0; r < d; ++r)
+      for (int cidx = 0; cidx < m; ++cidx) {
+        rv.push_back(reps->view(r * m + cidx));
+        pairs.push_back({views[cidx].get(), rv.back().get()});
+      }
+    CtSetPtr t3 = set_new(c, d, 3, lv, lv, 1.0);
+    set_tensor_mac(c, pairs, m, *t3);
+    CtSetPtr out = set_new(c, d, 2, lv, lv, 1.0);
+    set_relin(c, *t3, *out);
+    set_rescale(c, *out);
+    return out;
   }
-  // Alg. 6: sum_c DotProd(A(c), v) * e_c, masks summed before one rescale
+  // Alg. 6 with Alg. 5 inside: every DotProd(A(c), v) (product, log2(M) ladder)
+  // as one set, then the masks e_c summed before one rescale.
   CtPtr rp_matvec(const std::vector<CtPtr>& rows, const Ct& v, int m) {
-    CtPtr acc;
+    std::vector<CtPtr> views;
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
     for (int cidx = 0; cidx < m; ++cidx) {
-      CtPtr rv = view(*rows[cidx], v.l);
-      CtPtr dp = dotprod(*rv, v);
-      const double ql = (double)c->mod[dp->l - 1];
-      const u64* pt = mask_pt(c, kMaskSlot, cidx, dp->l, ql, e_slot(cidx));
-      CtPtr t = fresh(dp->l);
-      op_mul_plain(c, *dp, pt, ql, *t);
-      if (!acc)
-        acc = std::move(t);
-      else
-        op_addsub(c, *acc, *t, *acc, false);
+      views.push_back(view(*rows[cidx], v.l));
+      pairs.push_back({views.back().get(), &v});
     }
+    CtSetPtr dp = set_new(c, m, 2, v.l, v.l, 1.0);
+    set_mult(c, pairs, *dp);
+    set_ladder(c, *dp, pow2_steps(lay.logN - 1));
+    const int l = dp->l;
+    const double ql = (double)c->mod[l - 1];
+    std::vector<MaskItem> mi;
+    for (int cidx = 0; cidx < m; ++cidx)
+      mi.push_back(MaskItem{dp->item(cidx), dp->cap,
+                            mask_pt(c, kMaskSlot, cidx, l, ql, e_slot(cidx))});
+    CtSetPtr masked = set_new(c, m, 2, l, l, 1.0);
+    set_mask(c, mi, dp->scale, ql, *masked, false);
+    CtPtr acc = fresh(l);
+    sum_set(c, masked->d, masked->cap, masked->stride(), m, acc->d, acc->cap, l);
+    acc->l = l;
+    acc->scale = masked->scale;
     op_rescale(c, *acc);
     return acc;
   }
   // Alg. 4: log2(nb) rotate-and-add steps; block sums land at slots c*nb
-  void colsum(Ct& v) { ladder(v, pow2_steps(ilog2(lay.nb))); }
+  std::vector<int> colsum_steps() { return pow2_steps(ilog2(lay.nb)); }
   // Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks
-  void duplicate(Ct& v) { ladder(v, pow2_steps(ilog2(lay.B), lay.nb)); }
+  std::vector<int> dup_steps() { return pow2_steps(ilog2(lay.B), lay.nb); }
+  // a one-ciphertext set holding a copy of a at level l (for the ladders)
+  CtSetPtr single(const Ct& a, int l) {
+    CtSetPtr s = set_new(c, 1, 2, l, l, a.scale);
+    for (int p = 0; p < 2; ++p)
+      GWHE_CUDA(cudaMemcpyAsync(s->d + (size_t)p * l * c->N, a.poly(p), sizeof(u64) * l * c->N,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    return s;
+  }
 
   // eq. sigma7 at depth 3
   CtPtr sigma7(const Ct& x) {
@@ -291,25 +341,37 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
 }
 
 static void make_dup_state(Job* j, Eval& ev) {
+  Context* c = j->c;
   const Layout& lay = j->lay;
   const int lb = kBatchLevel;
   GWHE_REQUIRE(j->wzp->l >= lb - 1, ST_ELEVEL, "depth exhausted before the SNP batches");
+  // Dup(M_j) for every column j: mask block (j mod B) of ciphertext j / B at
+  // lb + 1 limbs (plaintext at scale q_last, rescale), then Alg. 7's ladder
   std::vector<CtPtr> src;
   for (auto& m : j->Mct) src.push_back(ev.view(*m, lb + 1));
-  j->DupM.clear();
+  const double ql = (double)c->mod[lb];
+  std::vector<MaskItem> mi;
   for (int jj = 0; jj < lay.n; ++jj) {
     const int h = jj / lay.B, b = jj % lay.B;
     auto z = ev.slots_zero();
     for (int t = 0; t < lay.n; ++t) z[b * lay.nb + t] = make_double2(1, 0);
-    CtPtr mj = ev.mul_mask(*src[h], kMaskBlock, ((long)lay.n << 32) | ((long)lay.nb << 16) | b, z);
-    ev.duplicate(*mj);
-    j->DupM.push_back(std::move(mj));
+    const long key = ((long)lay.n << 32) | ((long)lay.nb << 16) | b;
+    mi.push_back(MaskItem{src[h]->d, src[h]->cap, mask_pt(c, kMaskBlock, key, lb + 1, ql, z)});
   }
-  j->DupW = ev.clone_at(*j->w_m, lb - 1);
-  ev.duplicate(*j->DupW);
-  j->DupWZ = ev.clone_at(*j->wzp, lb - 1);
-  ev.duplicate(*j->DupWZ);
-
+  CtSetPtr dm = set_new(c, lay.n, 2, lb + 1, lb + 1, 1.0);
+  set_mask(c, mi, src[0]->scale, ql, *dm, true);
+  set_ladder(c, *dm, ev.dup_steps());
+  j->DupM.clear();
+  for (int jj = 0; jj < lay.n; ++jj) j->DupM.push_back(dm->view(jj));
+  j->sets.push_back(std::move(dm));
+  CtSetPtr dw = ev.single(*j->w_m, lb - 1);
+  set_ladder(c, *dw, ev.dup_steps());
+  j->DupW = dw->view(0);
+  j->sets.push_back(std::move(dw));
+  CtSetPtr dwz = ev.single(*j->wzp, lb - 1);
+  set_ladder(c, *dwz, ev.dup_steps());
+  j->DupWZ = dwz->view(0);
+  j->sets.push_back(std::move(dwz));
 }
 
 void job_fit(Job* j, int kappa) {
@@ -378,23 +440,26 @@ void job_fit(Job* j, int kappa) {
   CtPtr wmv = ev.view(*j->w_m, j->zp->l);
   j->wzp = ev.mult(*wmv, *j->zp);
   // eq. M = I - X A X^T: Alg. 3 (CP-MatMult) then Alg. 8 (CP-REP-MatMult)
-  std::vector<CtPtr> dupXA;
-  for (int rr = 0; rr < d; ++rr) {
-    CtPtr xa = ev.cp_matvec(j->X, *j->A[rr], d);
-    ev.duplicate(*xa);
-    dupXA.push_back(std::move(xa));
-  }
+  CtSetPtr xa = ev.cp_matmul(j->X, j->A, d);
+  set_ladder(c, *xa, ev.dup_steps());  // Duplicate(XA_r) for every r
+  const int l0 = xa->l;
+  std::vector<CtPtr> dv, xv;
+  for (int rr = 0; rr < d; ++rr) dv.push_back(xa->view(rr));
+  std::vector<std::pair<const Ct*, const Ct*>> pairs;
+  for (int h = 0; h < lay.H; ++h)
+    for (int rr = 0; rr < d; ++rr) {
+      xv.push_back(ev.view(*j->XtREP[rr][h], l0));
+      pairs.push_back({dv[rr].get(), xv.back().get()});
+    }
+  CtSetPtr t3 = set_new(c, lay.H, 3, l0, l0, 1.0);
+  set_tensor_mac(c, pairs, d, *t3);
+  CtSetPtr acc = set_new(c, lay.H, 2, l0, l0, 1.0);
+  set_relin(c, *t3, *acc);
+  set_rescale(c, *acc);
   j->Mct.clear();
   for (int h = 0; h < lay.H; ++h) {
-    const int l0 = dupXA[0]->l;
-    std::vector<CtPtr> views;
-    std::vector<std::pair<const Ct*, const Ct*>> pairs;
-    for (int rr = 0; rr < d; ++rr) {
-      views.push_back(ev.view(*j->XtREP[rr][h], l0));
-      pairs.push_back({dupXA[rr].get(), views.back().get()});
-    }
-    CtPtr acc = ev.mac_relin_rescale(pairs);
-    CtPtr m = ev.negate(*acc);
+    CtPtr ah = acc->view(h);
+    CtPtr m = ev.negate(*ah);
     auto z = ev.slots_zero();
     for (int b = 0; b < lay.B; ++b) {
       const int col = h * lay.B + b;
@@ -437,6 +502,7 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
   GWHE_REQUIRE((int)j->DupM.size() == n && j->DupW && j->DupWZ, ST_EINVAL,
                "covariate phase not done (fit or set the fit state first)");
   GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
+  if (b0 == b1) return;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const bool dev = is_device_ptr(S);
   const double* Sd = S;
@@ -448,44 +514,89 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
     Sd = Sbuf->as<double>();
   }
   if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
-  Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
-  Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
-  std::vector<Ct> srow(n);
-  for (int jj = 0; jj < n; ++jj) {
-    srow[jj].ctx = c;
-    srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
-    srow[jj].cap = lb;
-    srow[jj].l = lb;
-    srow[jj].scale = delta;
-    srow[jj].owned = false;
-  }
-  for (long bi = b0; bi < b1; ++bi) {
-    // Alg. 11 input: the REP rows of batch bi, encoded and encrypted on the device
-    build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
-    encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
-    // S' = sum_j Dup(M_j) S_ij (Alg. 8), one relinearisation and rescale
+  const int nbt = (int)(b1 - b0);
+  // per batch: encode + encrypt the n REP rows, then the tensor sum of Alg. 8
+  CtSetPtr T3 = set_new(c, nbt, 3, lb, lb, 1.0);
+  {
+    Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
+    Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
+    std::vector<Ct> srow(n);
+    for (int jj = 0; jj < n; ++jj) {
+      srow[jj].ctx = c;
+      srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
+      srow[jj].cap = lb;
+      srow[jj].l = lb;
+      srow[jj].scale = delta;
+      srow[jj].owned = false;
+    }
     std::vector<std::pair<const Ct*, const Ct*>> pairs;
     for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
-    CtPtr Sp = ev.mac_relin_rescale(pairs);
-    // numerator = colSum(Dup(w z') S')
-    CtPtr num = ev.mult(*j->DupWZ, *Sp);
-    ev.colsum(*num);
-    // WS' = Dup(w) S'; WSS = WS' S'; WSC = WS' conj(S')
-    CtPtr ws = ev.mult(*j->DupW, *Sp);
-    CtPtr s1 = ev.view(*Sp, lb - 2);
-    CtPtr wss = ev.mult(*ws, *s1);
-    CtPtr cj = ev.fresh(s1->l);
-    op_conj(c, *s1, *cj);
-    CtPtr wsc = ev.mult(*ws, *cj);
-    // denEven / denOdd; the 1/2 is kept as scale metadata
-    CtPtr de = ev.add(*wsc, *wss);
-    de->scale *= 2.0;
-    CtPtr dO = ev.sub(*wsc, *wss);
-    dO->scale *= 2.0;
-    ev.colsum(*de);
-    ev.colsum(*dO);
-    j->out[bi] = {std::move(num), std::move(de), std::move(dO)};
+    for (long bi = b0; bi < b1; ++bi) {
+      build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
+      encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
+      CtSet t = T3->slice((int)(bi - b0), 1, lb);
+      set_tensor_mac(c, pairs, n, t);
+      T3->scale = t.scale;
+    }
   }
+  // the rest of the Alg. 11 loop body for all batches as sets
+  CtSetPtr Sp = set_new(c, nbt, 2, lb, lb, 1.0);
+  set_relin(c, *T3, *Sp);
+  set_rescale(c, *Sp);  // S' at lb - 1
+  T3.reset();
+  std::vector<CtPtr> spv;
+  for (int i = 0; i < nbt; ++i) spv.push_back(Sp->view(i));
+  // numerator = colSum(Dup(w z') S')
+  CtSetPtr num = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
+  {
+    std::vector<std::pair<const Ct*, const Ct*>> pr;
+    for (int i = 0; i < nbt; ++i) pr.push_back({j->DupWZ.get(), spv[i].get()});
+    set_mult(c, pr, *num);
+  }
+  set_ladder(c, *num, ev.colsum_steps());
+  // WS' = Dup(w) S'
+  CtSetPtr ws = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
+  {
+    std::vector<std::pair<const Ct*, const Ct*>> pr;
+    for (int i = 0; i < nbt; ++i) pr.push_back({j->DupW.get(), spv[i].get()});
+    set_mult(c, pr, *ws);
+  }
+  // conj(S') at lb - 2; WSS = WS' S', WSC = WS' conj(S') as one set of 2 nbt
+  CtSet s1 = Sp->slice(0, nbt, lb - 2);
+  CtSetPtr cj = set_new(c, nbt, 2, lb - 2, lb - 2, 1.0);
+  set_galois(c, s1, galois_conj(c), *cj);
+  CtSetPtr W2 = set_new(c, 2 * nbt, 2, lb - 2, lb - 2, 1.0);
+  {
+    std::vector<CtPtr> keep;
+    std::vector<std::pair<const Ct*, const Ct*>> pr;
+    for (int i = 0; i < nbt; ++i) {
+      keep.push_back(ws->view(i));
+      keep.push_back(s1.view(i));
+      pr.push_back({keep[keep.size() - 2].get(), keep.back().get()});
+    }
+    for (int i = 0; i < nbt; ++i) {
+      keep.push_back(ws->view(i));
+      keep.push_back(cj->view(i));
+      pr.push_back({keep[keep.size() - 2].get(), keep.back().get()});
+    }
+    set_mult(c, pr, *W2);
+  }
+  // denEven = WSC + WSS, denOdd = WSC - WSS (the 1/2 as scale metadata), colSum
+  CtSetPtr D = set_new(c, 2 * nbt, 2, lb - 3, lb - 3, 1.0);
+  {
+    const int l = W2->l;
+    Ct wss = W2->slice(0, nbt, l).all(), wsc = W2->slice(nbt, nbt, l).all();
+    Ct de = D->slice(0, nbt, l).all(), dO = D->slice(nbt, nbt, l).all();
+    op_addsub(c, wsc, wss, de, false);
+    op_addsub(c, wsc, wss, dO, true);
+    D->l = l;
+    D->scale = W2->scale * 2.0;
+  }
+  set_ladder(c, *D, ev.colsum_steps());
+  for (int i = 0; i < nbt; ++i)
+    j->out[b0 + i] = {num->view(i), D->view(i), D->view(nbt + i)};
+  j->sets.push_back(std::move(num));
+  j->sets.push_back(std::move(D));
 }
 
 void job_decrypt(Job* j, double* num, double* den) {

@@ -31,8 +31,9 @@ struct Job {
   std::vector<CtPtr> Mct;                 // [H]
   std::vector<CtPtr> DupM;                // [n]
   CtPtr DupW, DupWZ;
-  std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd
-  u64* DupM_store = nullptr;              // contiguous storage of DupM (split mode)
+  std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd (views)
+  std::vector<CtSetPtr> sets;             // storage behind the views above
+  u64* DupM_store = nullptr;              // unused (kept zero)
   ~Job();
 };
 

@@ -117,13 +117,16 @@ struct ConvArgs {
 };
 constexpr int kMaxConvIn = 16;
 
-// y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o
+// y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o.
+// Grid: x = coefficients, y = groups of kConvOG outputs, z = items (polynomials).
+constexpr int kConvOG = 8;
 __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __restrict__ out,
                            size_t out_pstride, const ConvArgs a, int N,
                            const DevMod* __restrict__ mod) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
-  const int p = blockIdx.y;
+  const int o0 = blockIdx.y * kConvOG;
+  const size_t p = blockIdx.z;
   const u64* xp = x + p * x_pstride;
   u64* op = out + p * out_pstride;
   u64 y[kMaxConvIn];
@@ -135,24 +138,30 @@ __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __r
     }
   }
   const u64* hm = a.tab + 2 * a.n_in;
-  for (int o = 0; o < a.n_out; ++o) {
+  const int o1 = min(o0 + kConvOG, a.n_out);
+  for (int o = o0; o < o1; ++o) {
     Acc128 s{0, 0};
 #pragma unroll
     for (int i = 0; i < kMaxConvIn; ++i)
-      if (i < a.n_in) mac128(s, y[i], hm[i * a.hm_stride + o]);
+      if (i < a.n_in) mac128(s, y[i], __ldg(hm + i * a.hm_stride + o));
     op[(size_t)a.out_row[o] * N + k] = reduce128(s.lo, s.hi, mod[a.out_pidx[o]]);
   }
 }
 
 // acc_p[u] = sum_j x_j[u] * key_j[p][u] over digits, for the l + K extended limbs;
 // x_j[u] is the input limb itself when u lies in digit j, else the converted limb.
-__global__ void k_ks_inner(const u64* __restrict__ c_ntt, const u64* __restrict__ ext,
-                           const u64* __restrict__ key, u64* __restrict__ acc, int l, int K, int L,
-                           int alpha, int beta, int N, const DevMod* __restrict__ mod) {
+__global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
+                           const u64* __restrict__ ext, const u64* __restrict__ key,
+                           u64* __restrict__ acc, int l, int K, int L, int alpha, int beta, int N,
+                           const DevMod* __restrict__ mod) {
   const int u = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
+  const size_t item = blockIdx.z;
+  c_ntt += item * c_stride;
+  ext += item * (size_t)beta * ne * N;
+  acc += item * (size_t)2 * ne * N;
   const int mi = u < l ? u : L + (u - l);
   const size_t LK = (size_t)(L + K);
   Acc128 s0{0, 0}, s1{0, 0};
@@ -171,7 +180,8 @@ __global__ void k_ks_inner(const u64* __restrict__ c_ntt, const u64* __restrict_
 
 // out_p[i] = (acc_p[i] - conv_p[i]) P^-1 mod q_i (+ add_p[i])
 __global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __restrict__ conv, int l,
-                                  int K, u64* out0, u64* out1, const u64* add0, const u64* add1,
+                                  int K, u64* out0, u64* out1, size_t o_stride, const u64* add0,
+                                  const u64* add1, size_t a0_stride, size_t a1_stride,
                                   const u64* __restrict__ pinv, int N,
                                   const DevMod* __restrict__ mod) {
   const int row = blockIdx.y, p = row / l, i = row - p * l;
@@ -179,6 +189,13 @@ __global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __rest
   if (k >= N) return;
   const u64 q = mod[i].q;
   const int ne = l + K;
+  const size_t item = blockIdx.z;
+  acc += item * (size_t)2 * ne * N;
+  conv += item * (size_t)2 * l * N;
+  out0 += item * o_stride;
+  out1 += item * o_stride;
+  if (add0) add0 += item * a0_stride;
+  if (add1) add1 += item * a1_stride;
   const u64 a = acc[((size_t)p * ne + i) * N + k];
   const u64 cv = conv[((size_t)p * l + i) * N + k];
   u64 v = shoup(submod(a, cv, q), pinv[2 * i], pinv[2 * i + 1], q);
@@ -231,6 +248,91 @@ __global__ void k_automorph(PolyView out, CPolyView in, int l, int logN, u64 g) 
   const u64 f = (g * e) & twoN_mask;
   const unsigned src = __brev((unsigned)((f - 1) >> 1)) >> (32 - logN);
   out.d[((size_t)p * out.cap + i) * N + j] = in.d[((size_t)p * in.cap + i) * N + src];
+}
+
+// ------------------------------------------------------------- ciphertext sets
+// Ladder step input: out[item] = (sigma(in0) + in0, sigma(in1)) for items laid
+// out at in_stride / out_stride words, cap limbs per poly.
+__global__ void k_automorph_ladder(const u64* __restrict__ in, int in_cap, size_t in_stride,
+                                   u64* __restrict__ out, int out_cap, size_t out_stride, int l,
+                                   int logN, u64 g, const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int N = 1 << logN;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const size_t item = blockIdx.z;
+  const u64* src = in + item * in_stride + ((size_t)p * in_cap + i) * N;
+  const u64 twoN_mask = ((u64)2 << logN) - 1;
+  const u64 e = 2 * (u64)(__brev((unsigned)j) >> (32 - logN)) + 1;
+  const u64 f = (g * e) & twoN_mask;
+  const unsigned srcj = __brev((unsigned)((f - 1) >> 1)) >> (32 - logN);
+  u64 v = src[srcj];
+  if (p == 0) v = addmod(v, src[j], mod[i].q);
+  out[item * out_stride + ((size_t)p * out_cap + i) * N + j] = v;
+}
+
+// out[item] = src_item * pt_item (both polys), items listed in an array
+__global__ void k_mask_set(const MaskItem* __restrict__ items, u64* __restrict__ out, int out_cap,
+                           size_t out_stride, int l, int N, const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const MaskItem it = items[blockIdx.z];
+  const u64 x = it.src[((size_t)p * it.src_cap + i) * N + k];
+  out[blockIdx.z * out_stride + ((size_t)p * out_cap + i) * N + k] =
+      mulmod(x, it.pt[(size_t)i * N + k], mod[i]);
+}
+
+// out[item] = sum over the item's npairs pairs of the tensor products
+__global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair* __restrict__ pairs,
+                                 int npairs, int l, int N, const DevMod* __restrict__ mod) {
+  const int i = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const DevMod m = mod[i];
+  const size_t item = blockIdx.z;
+  pairs += item * npairs;
+  Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
+  u64 r0 = 0, r1 = 0, r2 = 0;
+  const size_t off = (size_t)i * N + k;
+  for (int j = 0; j < npairs; ++j) {
+    const MacPair P = pairs[j];
+    const u64 a0 = P.a[off], a1 = P.a[(size_t)P.capa * N + off];
+    const u64 b0 = P.b[off], b1 = P.b[(size_t)P.capb * N + off];
+    mac128(s0, a0, b0);
+    mac128(s1, a0, b1);
+    mac128(s1, a1, b0);
+    mac128(s2, a1, b1);
+    if ((j & 31) == 31) {
+      r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
+      r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
+      r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
+      s0 = Acc128{0, 0};
+      s1 = Acc128{0, 0};
+      s2 = Acc128{0, 0};
+    }
+  }
+  r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
+  r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
+  r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
+  u64* o = out.d + item * out_stride;
+  o[off] = r0;
+  o[(size_t)out.cap * N + off] = r1;
+  o[(size_t)2 * out.cap * N + off] = r2;
+}
+
+// out = sum over items of the set (both polys)
+__global__ void k_sum_set(const u64* __restrict__ in, int in_cap, size_t in_stride, int cnt,
+                          u64* __restrict__ out, int out_cap, int l, int N,
+                          const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, p = row / l, i = row - p * l;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const u64 q = mod[i].q;
+  const size_t off = ((size_t)p * in_cap + i) * N + k;
+  u64 acc = 0;
+  for (int it = 0; it < cnt; ++it) acc = addmod(acc, in[it * in_stride + off], q);
+  out[((size_t)p * out_cap + i) * N + k] = acc;
 }
 
 // ------------------------------------------------------------- ChaCha20
@@ -638,45 +740,110 @@ static ConvArgs conv_args(const ConvTable& t, int in_mod0) {
   return a;
 }
 
-void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext) {
+static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_t os, int cnt,
+                            const ConvArgs& a) {
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "conversion batch too large");
+  const dim3 grid(blocks_for(c->N), (a.n_out + kConvOG - 1) / kConvOG, cnt);
+  k_baseconv<<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt) {
   ProfScope ps(c, PROF_BASECONV, 0.0);
   const int beta = (l + c->alpha - 1) / c->alpha;
   const int ne = l + c->P.K;
+  const size_t N = c->N;
   for (int j = 0; j < beta; ++j) {
     const ConvTable& t = c->modup.at({l, j});
     const ConvArgs a = conv_args(t, t.in_lo);
-    ps.bytes += 8.0 * (t.n_in + t.n_out) * c->N;
-    k_baseconv<<<dim3(blocks_for(c->N), 1), kThreads, 0, c->stream>>>(
-        x_coeff + (size_t)t.in_lo * c->N, 0, ext + (size_t)j * ne * c->N, 0, a, c->N, c->d_mod);
-    GWHE_LAUNCHED(c, 1);
+    ps.bytes += 8.0 * (t.n_in + t.n_out) * N * cnt;
+    launch_baseconv(c, x_coeff + (size_t)t.in_lo * N, (size_t)l * N, ext + (size_t)j * ne * N,
+                    (size_t)beta * ne * N, cnt, a);
   }
 }
 
-void moddown_convert(Context* c, const u64* acc, int l, u64* conv) {
-  ProfScope ps(c, PROF_BASECONV, 2.0 * (c->P.K + l) * 8.0 * c->N);
+void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext) {
+  modup_convert_set(c, x_coeff, l, ext, 1);
+}
+
+void moddown_convert_set(Context* c, const u64* acc, int l, u64* conv, int cnt) {
   GWHE_REQUIRE(l >= 1 && l <= c->P.L, ST_EINVAL, "bad level");
+  ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (c->P.K + l) * 8.0 * c->N);
   const int ne = l + c->P.K;
   ConvArgs a = conv_args(c->moddown, c->P.L);  // table rows hold all L outputs
   a.n_out = l;                                 // produce the first l of them
-  k_baseconv<<<dim3(blocks_for(c->N), 2), kThreads, 0, c->stream>>>(
-      acc + (size_t)l * c->N, (size_t)ne * c->N, conv, (size_t)l * c->N, a, c->N, c->d_mod);
+  // items: the 2 cnt polynomials of acc ([cnt][2][ne][N]) -> conv ([cnt][2][l][N])
+  launch_baseconv(c, acc + (size_t)l * c->N, (size_t)ne * c->N, conv, (size_t)l * c->N, 2 * cnt, a);
+}
+
+void moddown_convert(Context* c, const u64* acc, int l, u64* conv) {
+  moddown_convert_set(c, acc, l, conv, 1);
+}
+
+void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int cnt, u64* out0,
+                         u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                         size_t a0_stride, size_t a1_stride) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * 3 * l * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  k_moddown_combine<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
+      acc, conv, l, c->P.K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv,
+      c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
                      const u64* add0, const u64* add1) {
-  ProfScope ps(c, PROF_ELEMWISE, 2.0 * 3 * l * 8.0 * c->N);
-  k_moddown_combine<<<grid_rows(c->N, 2 * l), kThreads, 0, c->stream>>>(
-      acc, conv, l, c->P.K, out0, out1, add0, add1, c->d_pinv, c->N, c->d_mod);
+  moddown_combine_set(c, acc, conv, l, 1, out0, out1, 0, add0, add1, 0, 0);
+}
+
+void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
+                  const u64* key, u64* acc, int cnt) {
+  const double ne_ = l + c->P.K, beta_ = (l + c->alpha - 1) / c->alpha;
+  ProfScope ps(c, PROF_KS_INNER, (3.0 * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N * cnt);
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  k_ks_inner<<<dim3(blocks_for(c->N), l + c->P.K, cnt), kThreads, 0, c->stream>>>(
+      c_ntt, c_stride, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta, c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* key, u64* acc) {
-  const double ne_ = l + c->P.K, beta_ = (l + c->alpha - 1) / c->alpha;
-  ProfScope ps(c, PROF_KS_INNER, (3.0 * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N);
-  const int beta = (l + c->alpha - 1) / c->alpha;
-  k_ks_inner<<<grid_rows(c->N, l + c->P.K), kThreads, 0, c->stream>>>(
-      c_ntt, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta, c->N, c->d_mod);
+  ks_inner_set(c, c_ntt, 0, l, ext, key, acc, 1);
+}
+
+void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out,
+                          int out_cap, size_t out_stride, int l, int cnt, u64 g) {
+  ProfScope ps(c, PROF_ELEMWISE, 2.0 * 2 * l * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  k_automorph_ladder<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
+      in, in_cap, in_stride, out, out_cap, out_stride, l, c->logN, g, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void mask_set(Context* c, const MaskItem* d_items, int cnt, u64* out, int out_cap,
+              size_t out_stride, int l) {
+  ProfScope ps(c, PROF_ELEMWISE, 5.0 * l * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  k_mask_set<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
+      d_items, out, out_cap, out_stride, l, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void tensor_mac_set(Context* c, PolyView out3, size_t out_stride, const MacPair* d_pairs,
+                    int npairs, int cnt, int l) {
+  ProfScope ps(c, PROF_TENSOR_MAC, (4.0 * npairs + 3.0) * l * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  k_tensor_mac_set<<<dim3(blocks_for(c->N), l, cnt), kThreads, 0, c->stream>>>(
+      out3, out_stride, d_pairs, npairs, l, c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, int cnt, u64* out,
+             int out_cap, int l) {
+  ProfScope ps(c, PROF_ELEMWISE, (2.0 * cnt + 2.0) * l * 8.0 * c->N);
+  k_sum_set<<<dim3(blocks_for(c->N), 2 * l), kThreads, 0, c->stream>>>(in, in_cap, in_stride, cnt,
+                                                                      out, out_cap, l, c->N,
+                                                                      c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 

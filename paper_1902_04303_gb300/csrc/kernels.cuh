@@ -24,6 +24,13 @@ struct MacPair {
   int capa, capb;
 };
 
+// One item of a batched mask product: out = src (2 polys, src_cap) * pt.
+struct MaskItem {
+  const u64* src;
+  int src_cap;
+  const u64* pt;
+};
+
 // element-wise (NTT or coefficient domain; limb i is modulo q_i)
 void ew_addsub(Context* c, PolyView out, CPolyView a, CPolyView b, int npoly, int l, bool sub);
 void ew_negate(Context* c, PolyView out, CPolyView a, int npoly, int l);
@@ -45,6 +52,24 @@ void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* ke
 void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
                      const u64* add0, const u64* add1);
 void moddown_convert(Context* c, const u64* acc, int l, u64* conv);
+
+// batched forms over cnt items (strides in words)
+void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt);
+void moddown_convert_set(Context* c, const u64* acc, int l, u64* conv, int cnt);
+void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
+                  const u64* key, u64* acc, int cnt);
+void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int cnt, u64* out0,
+                         u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                         size_t a0_stride, size_t a1_stride);
+// out[item] = (sigma_g(in0) + in0, sigma_g(in1)): the automorphism of a ladder step
+void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out,
+                          int out_cap, size_t out_stride, int l, int cnt, u64 g);
+void mask_set(Context* c, const MaskItem* d_items, int cnt, u64* out, int out_cap,
+              size_t out_stride, int l);
+void tensor_mac_set(Context* c, PolyView out3, size_t out_stride, const MacPair* d_pairs,
+                    int npairs, int cnt, int l);
+void sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, int cnt, u64* out,
+             int out_cap, int l);
 
 // rescale pieces: last = coefficient-domain last limbs [npoly][N]
 void rescale_prep(Context* c, const u64* last, int npoly, int l, u64* tmp);
