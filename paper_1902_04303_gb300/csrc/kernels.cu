@@ -432,48 +432,57 @@ __global__ void k_sample_uniform(u64 seed, u64 obj, u32 tag, int u, u64* out, in
   }
 }
 
-// encryption randomness for ct idx (enc id id0 + idx), 16 coefficients per thread
-__global__ void k_enc_sample(u64 seed, u64 id0, int count, int l, const i64* __restrict__ m_coeff,
-                             u64* __restrict__ tmp, int N, const DevMod* __restrict__ mod) {
-  const int per = N / 16;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= count * per) return;
-  const int idx = gid / per, b = gid - idx * per;
+// encryption randomness for ct idx (enc id id0 + idx): a CTA of 256 threads
+// covers 4096 coefficients; each thread draws the ChaCha20 blocks of its 16
+// coefficients into shared memory, then the residues are written coalesced.
+__global__ void __launch_bounds__(256) k_enc_sample(u64 seed, u64 id0, int count, int l,
+                                                    const i64* __restrict__ m_coeff,
+                                                    u64* __restrict__ tmp, int N,
+                                                    const DevMod* __restrict__ mod) {
+  __shared__ int8_t sv[4096], se1[4096];
+  __shared__ i64 sme[4096];
+  const int tiles = (N + 4095) / 4096;
+  const int idx = blockIdx.x / tiles;
+  const int tile = blockIdx.x - idx * tiles;
+  if (idx >= count) return;
+  const int base = tile * 4096;
+  const int tcoef = min(4096, N - base);
   const u64 id = id0 + (u64)idx;
-  u32 wv[16], wa[16], wb[16];
-  chacha_block(seed, (3ull << 48) | id, 0, (u32)b, wv);
-  int v[16], e0[16], e1[16];
+  const int tid = threadIdx.x;
+  if (tid * 16 < tcoef) {
+    const int b = (base >> 4) + tid;  // ternary block of coefficients 16b..16b+15
+    u32 wv[16], wa[16], wb[16];
+    chacha_block(seed, (3ull << 48) | id, 0, (u32)b, wv);
 #pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = (int)(wv[m] % 3u) - 1;
-  chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b), wa);
-  chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b + 1), wb);
+    for (int m = 0; m < 16; ++m) sv[tid * 16 + m] = (int8_t)((int)(wv[m] % 3u) - 1);
+    chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b), wa);
+    chacha_block(seed, (4ull << 48) | id, 0, (u32)(2 * b + 1), wb);
+    const i64* mc = m_coeff + (size_t)idx * N + base + tid * 16;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    e0[m] = cbd21(wa[2 * m], wa[2 * m + 1]);
-    e0[m + 8] = cbd21(wb[2 * m], wb[2 * m + 1]);
+    for (int m = 0; m < 8; ++m) {
+      sme[tid * 16 + m] = mc[m] + (i64)cbd21(wa[2 * m], wa[2 * m + 1]);
+      sme[tid * 16 + 8 + m] = mc[8 + m] + (i64)cbd21(wb[2 * m], wb[2 * m + 1]);
+    }
+    chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b), wa);
+    chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b + 1), wb);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      se1[tid * 16 + m] = (int8_t)cbd21(wa[2 * m], wa[2 * m + 1]);
+      se1[tid * 16 + 8 + m] = (int8_t)cbd21(wb[2 * m], wb[2 * m + 1]);
+    }
   }
-  chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b), wa);
-  chacha_block(seed, (5ull << 48) | id, 0, (u32)(2 * b + 1), wb);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    e1[m] = cbd21(wa[2 * m], wa[2 * m + 1]);
-    e1[m + 8] = cbd21(wb[2 * m], wb[2 * m + 1]);
-  }
-  const i64* mc = m_coeff + (size_t)idx * N + (size_t)b * 16;
-  i64 me[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) me[m] = mc[m] + (i64)e0[m];
-  u64* t = tmp + (size_t)idx * 3 * l * N + (size_t)b * 16;
+  __syncthreads();
+  u64* t = tmp + (size_t)idx * 3 * l * N + base;
   for (int i = 0; i < l; ++i) {
     const DevMod md = mod[i];
     u64* t0 = t + (size_t)i * N;
     u64* t1 = t + ((size_t)l + i) * N;
     u64* t2 = t + ((size_t)2 * l + i) * N;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      t0[m] = v[m] < 0 ? md.q - 1 : (u64)v[m];
-      t1[m] = signed_to_res(me[m], md);
-      t2[m] = e1[m] < 0 ? md.q - (u64)(-e1[m]) : (u64)e1[m];
+    for (int k = tid; k < tcoef; k += 256) {
+      const int v = sv[k], e1 = se1[k];
+      t0[k] = v < 0 ? md.q - 1 : (u64)v;
+      t1[k] = signed_to_res(sme[k], md);
+      t2[k] = e1 < 0 ? md.q - (u64)(-e1) : (u64)e1;
     }
   }
 }
@@ -901,8 +910,10 @@ void sample_uniform(Context* c, u64 obj, u32 tag, int u, u64* out) {
 void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp) {
   ProfScope ps(c, PROF_SAMPLE, (3.0 * l + 1.0) * count * 8.0 * c->N);
   if (count == 0) return;
-  k_enc_sample<<<blocks_for((size_t)count * (c->N / 16)), kThreads, 0, c->stream>>>(
-      c->seed, id0, count, l, m_coeff, tmp, c->N, c->d_mod);
+  const int tiles = (c->N + 4095) / 4096;
+  k_enc_sample<<<(unsigned)((size_t)count * tiles), 256, 0, c->stream>>>(c->seed, id0, count, l,
+                                                                        m_coeff, tmp, c->N,
+                                                                        c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 

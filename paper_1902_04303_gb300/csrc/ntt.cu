@@ -38,7 +38,7 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q, u
 // are columns (stride 2^(LOGN-LS)), global stages 0..LS-1; otherwise rows
 // (contiguous), global stages LOGN-LS..LOGN-1.
 template <int LOGN, int LS, bool PASSA, bool FWD>
-__global__ void __launch_bounds__(256) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
+__global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
                                                   const NttTables tb, const int groups_per_row) {
   constexpr int S = 1 << LS;
   constexpr int TPS = S / 16;         // threads per sub-transform
