@@ -228,7 +228,7 @@ def run_gpu(args):
     if not args.no_micro:
         out["micro"] = run_micro(stream)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(ks_hist, W)
+        out["cpu_baseline"] = cpu_baseline(W)
     print(json.dumps(out))
     sys.stdout.flush()
     if world > 1:
@@ -276,6 +276,20 @@ def run_micro(ctx_stream, reps=3):
         ms.append(e0.elapsed_time(e1) / 2)  # per transform direction
     t_ntt = min(ms) / 1e3
     del x, ref
+    # batched encoding of 245 REP-like slot vectors (one SNP batch)
+    zb = torch.randint(0, 3, (245, ctx.M, 2), device="cuda", generator=g).to(torch.float64)
+    ob = torch.empty((245, N), dtype=torch.int64, device="cuda")
+    ctx.encode_batch(zb, 245, ctx.delta, ob)
+    ems = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.encode_batch(zb, 245, ctx.delta, ob)
+        e1.record(stream)
+        e1.synchronize()
+        ems.append(e0.elapsed_time(e1))
+    t_enc = min(ems) / 1e3
+    del zb, ob
     ctx.keygen(rot_steps=steps, conj=False)
     cts = [ctx.encrypt(make_slots(ctx.M, 7 + i), ctx.delta, L, 0x500 + i) for i in range(nct)]
     torch.cuda.synchronize()
@@ -295,6 +309,7 @@ def run_micro(ctx_stream, reps=3):
             "ntt_limb_per_s": round(rows / t_ntt, 1),
             "ntt_gbs_algorithmic": round(rows * N * 16 / t_ntt / 1e9, 1),
             "ntt_ms_3072_limbs": round(t_ntt * 1e3, 3),
+            "encode_ms_245": round(t_enc * 1e3, 3),
             "rotations": nct * len(steps),
             "keyswitch_per_s_level24": round(nct * len(steps) / t_ks, 1),
             "rotate_rescale_ms_512": round(t_ks * 1e3, 2)}
@@ -351,13 +366,15 @@ def extrapolate(sample, ks_hist, W):
     return t
 
 
-def cpu_baseline(ks_hist, W):
+def cpu_baseline(W):
+    from oracle.trace import job_ks_histogram
+    ks_hist, _, _ = job_ks_histogram(W, W["kappa"])
     s = oracle_sample(W)
     t_job = extrapolate(s, ks_hist, W)
     return {"value": round(W["k"] / t_job, 4), "unit": "SNPs/s", "cores": 1, "kind": "oracle",
             "sample": ("oracle (1 thread) timed on one key switch (%.2f s), one tensor (%.2f s) and "
                        "one encryption (%.2f s) at 4 limbs, N=2^16; extrapolated to the job with "
-                       "the GPU run's key-switch histogram (%d switches) and %d batch "
+                       "the oracle circuit's level trace (%d key switches) and %d batch "
                        "tensors/encryptions: %.0f s per job"
                        % (s["t_ks4"], s["t_tensor4"], s["t_enc4"], int(np.sum(ks_hist)),
                           W["n"] * -(-W["k"] // 256), t_job))}
@@ -372,11 +389,9 @@ def run_reference(args):
     W = WORKLOAD
     from oracle import build_oracle
     build_oracle.build()
-    # key-switch histogram of the job (levels follow from the circuit; from a
-    # GPU run of the same workload: stored with the profiles)
-    hist = np.zeros(65, np.int64)
-    for l, c in REFERENCE_KS_HIST.items():
-        hist[l] = c
+    from oracle.trace import job_ks_histogram
+    # key switches per level of the job, from a level trace of the oracle circuit
+    hist, _, _ = job_ks_histogram(W, W["kappa"])
     for _ in range(args.warmup):
         oracle_sample(W)
     times = []
@@ -404,10 +419,6 @@ def run_reference(args):
            "e2e": {"value": round(value, 4), "unit": "SNPs/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
-
-
-# key switches per level of one paper-n245 job (kappa = 1), from the circuit
-REFERENCE_KS_HIST = {}
 
 
 def main():

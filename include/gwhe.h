@@ -38,12 +38,15 @@
  *               ModUp by fast base conversion (no overflow correction), key
  *               digit j = (-a s + e + P [limb in digit j] s', a), ModDown
  *               (x - Conv([x]_P)) P^-1.
- *   encoding    m(zeta^(5^j)) = scale z_j (zeta = exp(i pi/N)) computed by the
- *               radix-2 procedure: G[bitrev(u_j)] = z_j with u_j = ((5^j mod 2N)
- *               - 1)/4; decimation-in-time stages len = 2..M with twiddles
- *               exp(-2 pi i t/M); c_k = G[k] exp(-pi i k/N); coefficients k and
- *               k+M = rint(Re, Im of c_k * (scale/M)); every product and sum
- *               separately rounded (no fused multiply-add).
+ *   encoding    m(zeta^(5^j)) = scale z_j (zeta = exp(i pi/N)) computed by a
+ *               fixed-point radix-2 procedure in exact integer arithmetic:
+ *               e = least e >= 0 with 2^e >= max |Re|, |Im| of z (<= 40), F =
+ *               61 - log2 M - e; G[bitrev(u_j)] = rint(z_j 2^F) with u_j =
+ *               ((5^j mod 2N) - 1)/4; decimation-in-time stages len = 2..M
+ *               with twiddles rint(2^62 exp(-2 pi i t/M)); c_k = G[k]
+ *               rint(2^62 exp(-pi i k/N)); each complex product formed on 128
+ *               bits and rounded as (v + 2^61) >> 62; coefficients k and k+M =
+ *               rint((double)Re, Im of c_k * scale / 2^(log2 M + F)).
  *   scales      product -> product of scales; rescale -> / (double)q_last; sums
  *               keep the first operand's scale (relative mismatch > 2^-10 is
  *               GWHE_ESCALE); a real constant c multiplies as rint(c q_last)
@@ -76,7 +79,8 @@ typedef struct gwhe_job gwhe_job;
 
 /* CKKS parameter set (paper section "Homomorphic Encryption": N, L, p; here in
  * RNS form).  logN in [4, 16]; L q-limbs (1 base prime of q0_bits, L-1 scale
- * primes near 2^scale_bits); K special primes of sp_bits; dnum key digits. */
+ * primes near 2^scale_bits); K special primes of sp_bits; dnum key digits
+ * (1..4, each of ceil(L/dnum) <= 16 limbs). */
 typedef struct {
   int logN, L, q0_bits, scale_bits, K, sp_bits, dnum;
 } gwhe_params;
@@ -128,6 +132,10 @@ int gwhe_ct_export(const gwhe_ct* ct, uint64_t* coeffs);
 /* Encode (section "Homomorphic Encryption", phi^-1): z = M complex slots
  * (host, interleaved) -> signed coefficients int64[N] (host). */
 int gwhe_encode(gwhe_ctx* ctx, const double* z, double scale, int64_t* coeffs);
+/* Encode a batch on the device: z_dev = count x M complex slots (interleaved
+ * doubles, device), coeffs_dev = count x N signed coefficients (device). */
+int gwhe_encode_batch(gwhe_ctx* ctx, const double* z_dev, int count, double scale,
+                      int64_t* coeffs_dev);
 /* Encrypt(pk, Encode(z)) at level l with randomness of encryption id enc_id. */
 int gwhe_encrypt(gwhe_ctx* ctx, const double* z, double scale, int l, uint64_t enc_id,
                  gwhe_ct* out);

@@ -34,6 +34,9 @@ ENC_S = 0x1000000
 SIGMA7_A = (-1.73496 / 8.0, 4.19407 / 8.0 ** 3, -5.43402 / 8.0 ** 5, 2.50739 / 8.0 ** 7)
 
 BATCH_LEVEL = 4  # level at which a SNP batch enters (S', num, WS', WSS/WSC)
+# M = I - X A X^T is only needed at BATCH_LEVEL + 1 limbs (the source of the
+# Dup(M_j) masks); it is computed from X and A dropped to this level
+M_LEVEL = BATCH_LEVEL + 4
 
 
 @dataclass
@@ -276,8 +279,9 @@ class Circuit:
         zp = ev.sub(ev.drop(z, xaxtz.level), xaxtz)
         wzp = ev.mult(ev.drop(w_m, zp.level), zp)
         self.z, self.zp, self.w_m, self.wzp = z, zp, w_m, wzp
-        # eq. M: M = I - X A X^T via Alg. 3 (CP-MatMult) and Alg. 8 (CP-REP)
-        XA = [self.cp_matvec(self.X, self.A[r], d) for r in range(d)]
+        # eq. M: M = I - X A X^T via Alg. 3 (CP-MatMult) and Alg. 8 (CP-REP),
+        # from X and A dropped to M_LEVEL limbs
+        XA = [self.cp_matvec(self.X, ev.drop(self.A[r], M_LEVEL), d) for r in range(d)]
         dupXA = [self.duplicate(XA[r]) for r in range(d)]
         self.Mct = []
         for h in range(lay.H):

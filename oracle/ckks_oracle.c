@@ -26,7 +26,7 @@
  *   - hybrid key switching: digits of alpha consecutive q-limbs; ModUp by
  *     fast base conversion without overflow correction; ModDown as
  *     (x - Conv([x]_P)) * P^-1.
- *   - encoding: the radix-2 FFT procedure documented at or_encode().
+ *   - encoding: the fixed-point radix-2 FFT procedure documented at or_encode().
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -706,51 +706,81 @@ static int bitrev(int x, int bits)
     return r;
 }
 
-/* Encoding procedure (exact in IEEE double, no fused multiply-add):
- *   G[bitrev(u_j)] = z_j                                   (j < M)
- *   for len = 2, 4, ..., M, every block b, jj < len/2:
- *       w = W[jj * (M/len)];  y = G[b+jj+len/2] * w  (re = yr*wr - yi*wi,
- *       im = yr*wi + yi*wr);  G[b+jj] = x + y;  G[b+jj+len/2] = x - y
- *   c_k = G[k] * T[k] (same complex product), then re, im each * (scale / M)
- *   coefficient k = llrint(re), coefficient k + M = llrint(im)
+/* Encoding procedure, exact fixed-point integer arithmetic:
+ *   e  = smallest integer >= 0 with 2^e >= max_j max(|Re z_j|, |Im z_j|), capped at 40
+ *   F  = 61 - log2(M) - e fractional bits;  Z_j = (llrint(Re z_j 2^F), llrint(Im z_j 2^F))
+ *   twiddles Wq[t] = llrint(W[t] 2^62), Tq[k] = llrint(T[k] 2^62) (W, T as above)
+ *   complex product a * w = (ar wr - ai wi, ar wi + ai wr) computed exactly on
+ *   128 bits, each part rounded to (v + 2^61) >> 62 (arithmetic shift)
+ *   G[bitrev(u_j)] = Z_j;  for len = 2, 4, ..., M, block b, jj < len/2:
+ *       y = G[b+jj+len/2] * Wq[jj (M/len)];  G[b+jj] = x + y;  G[b+jj+len/2] = x - y
+ *   c_k = G[k] * Tq[k];  f = scale / 2^(log2 M + F) (a double, exact power-of-two
+ *   scaling); coefficient k = llrint((double)Re c_k * f), k + M = llrint((double)Im c_k * f)
  * This inverts the canonical embedding m(zeta^(5^j)) = scale * z_j with
- * zeta = exp(i pi / N).  z is [M][2] (re, im); out is [N] signed integers. */
+ * zeta = exp(i pi / N).  Every value stays below 2^61.5 (inputs <= 2^(61-logM)
+ * grow at most 2^logM * sqrt 2); |z| <= 2^40 is required.  The result differs
+ * from the exact embedding's rounding by at most about scale * 2^-F.
+ * z is [M][2] (re, im); out is [N] signed integers. */
+typedef __int128 i128;
+static i64 rshift62(i128 v) { return (i64)((v + ((i128)1 << 61)) >> 62); }
+static void cmul_fx(i64 ar, i64 ai, i64 wr, i64 wi, i64 *rr, i64 *ri)
+{
+    *rr = rshift62((i128)ar * wr - (i128)ai * wi);
+    *ri = rshift62((i128)ar * wi + (i128)ai * wr);
+}
+
+int or_encode_exponent(const double *z, int M)
+{
+    double mx = 0.0;
+    for (int j = 0; j < 2 * M; j++) {
+        double a = fabs(z[j]);
+        if (a > mx) mx = a;
+    }
+    int e = 0;
+    while (e < 40 && ldexp(1.0, e) < mx) e++;
+    return e;
+}
+
 void or_encode(int logN, const double *z, double scale, i64 *out)
 {
     const int N = 1 << logN, M = N / 2, logM = logN - 1;
     double *W = (double *)malloc(sizeof(double) * M);
     double *T = (double *)malloc(sizeof(double) * 2 * M);
-    double *G = (double *)malloc(sizeof(double) * 2 * M);
+    i64 *Wq = (i64 *)malloc(sizeof(i64) * M);
+    i64 *Tq = (i64 *)malloc(sizeof(i64) * 2 * M);
+    i64 *G = (i64 *)malloc(sizeof(i64) * 2 * M);
     int *u = (int *)malloc(sizeof(int) * M);
     or_fft_twiddles(logN, -1, W, T);
+    for (int t = 0; t < M; t++) Wq[t] = llrint(ldexp(W[t], 62));
+    for (int k = 0; k < 2 * M; k++) Tq[k] = llrint(ldexp(T[k], 62));
     slot_index(logN, u);
+    const int e = or_encode_exponent(z, M);
+    const int F = 61 - logM - e;
     for (int j = 0; j < M; j++) {
         int p = bitrev(u[j], logM);
-        G[2 * p] = z[2 * j];
-        G[2 * p + 1] = z[2 * j + 1];
+        G[2 * p] = llrint(ldexp(z[2 * j], F));
+        G[2 * p + 1] = llrint(ldexp(z[2 * j + 1], F));
     }
     for (int len = 2; len <= M; len <<= 1) {
         int half = len / 2, stride = M / len;
         for (int b = 0; b < M; b += len)
             for (int jj = 0; jj < half; jj++) {
-                double wr = W[2 * (jj * stride)], wi = W[2 * (jj * stride) + 1];
-                double *x = G + 2 * (b + jj), *y = G + 2 * (b + jj + half);
-                double yr = y[0] * wr - y[1] * wi;
-                double yi = y[0] * wi + y[1] * wr;
-                double xr = x[0], xi = x[1];
-                x[0] = xr + yr; x[1] = xi + yi;
-                y[0] = xr - yr; y[1] = xi - yi;
+                i64 *x = G + 2 * (b + jj), *y = G + 2 * (b + jj + half);
+                i64 tr, ti;
+                cmul_fx(y[0], y[1], Wq[2 * (jj * stride)], Wq[2 * (jj * stride) + 1], &tr, &ti);
+                i64 xr = x[0], xi = x[1];
+                x[0] = xr + tr; x[1] = xi + ti;
+                y[0] = xr - tr; y[1] = xi - ti;
             }
     }
-    double f = scale / (double)M;
+    const double f = ldexp(scale, -(logM + F));
     for (int k = 0; k < M; k++) {
-        double gr = G[2 * k], gi = G[2 * k + 1], tr = T[2 * k], ti = T[2 * k + 1];
-        double cr = gr * tr - gi * ti;
-        double ci = gr * ti + gi * tr;
-        out[k] = llrint(cr * f);
-        out[k + M] = llrint(ci * f);
+        i64 cr, ci;
+        cmul_fx(G[2 * k], G[2 * k + 1], Tq[2 * k], Tq[2 * k + 1], &cr, &ci);
+        out[k] = llrint((double)cr * f);
+        out[k + M] = llrint((double)ci * f);
     }
-    free(W); free(T); free(G); free(u);
+    free(W); free(T); free(Wq); free(Tq); free(G); free(u);
 }
 
 /* signed coefficients -> residues over q_0..q_{l-1} ([l][N]) */

@@ -24,7 +24,6 @@ int guard(Context* c, F&& f) {
 }
 
 Context* C(gwhe_ctx* x) { return x ? x->c : nullptr; }
-Context* C(const gwhe_ctx* x) { return x ? x->c : nullptr; }
 
 void need(bool cond, const char* msg) {
   if (!cond) throw Error(ST_EINVAL, msg);
@@ -208,6 +207,16 @@ int gwhe_encode(gwhe_ctx* ctx, const double* z, double scale, int64_t* coeffs) {
     encode_batch(c, dz.as<double2>(), 1, scale, out.as<i64>(), work.as<double2>());
     GWHE_CUDA(cudaMemcpyAsync(coeffs, out.p, sizeof(i64) * c->N, cudaMemcpyDeviceToHost, c->stream));
     sync(c);
+  });
+}
+
+int gwhe_encode_batch(gwhe_ctx* ctx, const double* z_dev, int count, double scale,
+                      int64_t* coeffs_dev) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    need(z_dev && coeffs_dev && count >= 1, "bad arguments");
+    Tmp work(c, sizeof(double2) * (size_t)count * (c->N / 2));
+    encode_batch(c, (const double2*)z_dev, count, scale, coeffs_dev, work.as<double2>());
   });
 }
 

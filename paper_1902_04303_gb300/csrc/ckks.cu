@@ -118,6 +118,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   GWHE_REQUIRE(P.L >= 1 && P.L <= kMaxRowLimbs && P.K >= 1 && P.K <= 16, ST_EINVAL,
                "need 1 <= L <= 64 and 1 <= K <= 16");
   GWHE_REQUIRE(P.dnum >= 1 && P.dnum <= P.L, ST_EINVAL, "need 1 <= dnum <= L");
+  GWHE_REQUIRE(P.dnum <= 4, ST_EINVAL, "at most 4 key-switching digits are supported");
   GWHE_REQUIRE(P.L + P.K <= kMaxMod, ST_EINVAL, "too many moduli");
   GWHE_REQUIRE(P.q0_bits <= 60 && P.sp_bits <= 60 && P.scale_bits <= 60, ST_EINVAL,
                "moduli must stay below 2^60");
@@ -154,8 +155,8 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
 
   // NTT tables
   {
-    std::vector<u64> psi((size_t)nm * N), psi_sh((size_t)nm * N), ipsi((size_t)nm * N),
-        ipsi_sh((size_t)nm * N), ninv(nm), ninv_sh(nm), pw(N), ipw(N);
+    std::vector<ulonglong2> psi((size_t)nm * N), ipsi((size_t)nm * N);
+    std::vector<u64> ninv(nm), ninv_sh(nm), pw(N), ipw(N);
     for (int u = 0; u < nm; ++u) {
       const u64 q = c->mod[u];
       const u64 r = find_psi(q, P.logN), ri = host_inv(r, q);
@@ -167,18 +168,14 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       for (int i = 0; i < N; ++i) {
         const int b = bitrev_host(i, P.logN);
         const size_t o = (size_t)u * N + i;
-        psi[o] = pw[b];
-        psi_sh[o] = shoup_companion(psi[o], q);
-        ipsi[o] = ipw[b];
-        ipsi_sh[o] = shoup_companion(ipsi[o], q);
+        psi[o] = make_ulonglong2(pw[b], shoup_companion(pw[b], q));
+        ipsi[o] = make_ulonglong2(ipw[b], shoup_companion(ipw[b], q));
       }
       ninv[u] = host_inv((u64)N % q, q);
       ninv_sh[u] = shoup_companion(ninv[u], q);
     }
     c->d_psi = upload(c.get(), psi);
-    c->d_psi_sh = upload(c.get(), psi_sh);
     c->d_ipsi = upload(c.get(), ipsi);
-    c->d_ipsi_sh = upload(c.get(), ipsi_sh);
     c->d_ninv = upload(c.get(), ninv);
     c->d_ninv_sh = upload(c.get(), ninv_sh);
   }
@@ -276,9 +273,17 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       for (int k = 0; k < M; ++k) t2[k] = make_double2(T[2 * k], T[2 * k + 1]);
     };
     fft_twiddles(P.logN, -1, W.data(), T.data());
-    pack();
-    c->d_fftW_enc = upload(c.get(), w2);
-    c->d_fftT_enc = upload(c.get(), t2);
+    {
+      std::vector<longlong2> wq(M / 2), tq(M);
+      for (int t = 0; t < M / 2; ++t)
+        wq[t] = make_longlong2(std::llrint(std::ldexp(W[2 * t], 62)),
+                               std::llrint(std::ldexp(W[2 * t + 1], 62)));
+      for (int k = 0; k < M; ++k)
+        tq[k] = make_longlong2(std::llrint(std::ldexp(T[2 * k], 62)),
+                               std::llrint(std::ldexp(T[2 * k + 1], 62)));
+      c->d_fftWq = upload(c.get(), wq);
+      c->d_fftTq = upload(c.get(), tq);
+    }
     fft_twiddles(P.logN, +1, W.data(), T.data());
     pack();
     c->d_fftW_dec = upload(c.get(), w2);
@@ -291,8 +296,10 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       pos[j] = bitrev_host(uu[j], logM);
       g = (g * 5) % twoN;
     }
-    c->d_slot_pos = upload(c.get(), pos);
     c->d_slot_u = upload(c.get(), uu);
+    std::vector<int> inv(M);
+    for (int j = 0; j < M; ++j) inv[pos[j]] = j;
+    c->d_slot_inv = upload(c.get(), inv);
   }
   return c.release();
 }
@@ -300,11 +307,10 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
 void ctx_destroy(Context* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_psi_sh, (void*)c->d_ipsi,
-                  (void*)c->d_ipsi_sh, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
-                  (void*)c->d_pinv, (void*)c->d_conv_store, (void*)c->d_fftW_enc,
-                  (void*)c->d_fftT_enc, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
-                  (void*)c->d_slot_pos, (void*)c->d_slot_u})
+  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
+                  (void*)c->d_pinv, (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
+                  (void*)c->d_fftWq, (void*)c->d_fftTq,
+                  (void*)c->d_slot_u, (void*)c->d_slot_inv})
     if (p) cudaFree(p);
   for (auto& kv : c->masks) cudaFree(kv.second);
   for (auto& r : c->prof.recs) {
@@ -819,22 +825,23 @@ const u64* mask_pt(Context* c, int kind, long index, int l, double scale,
   return pt;
 }
 
-void encrypt_coeffs(Context* c, const i64* m, int count, int l, u64 id0, u64* out, int out_cap) {
+void encrypt_coeffs(Context* c, const i64* m, int count, int l, u64 id0, u64* out, int out_cap,
+                    const u64* d_ids) {
   GWHE_REQUIRE(c->d_pk, ST_ENOKEY, "no public key");
   const int N = c->N;
   Tmp tmp(c, sizeof(u64) * count * 3 * l * N);
-  enc_sample(c, id0, count, l, m, tmp.u());
+  enc_sample(c, id0, count, l, m, tmp.u(), d_ids);
   ntt_forward(c, tmp.u(), rows_q(count * 3, l, l));
   enc_combine(c, tmp.u(), count, l, out, out_cap, (size_t)2 * out_cap * N);
 }
 
 void encrypt_slots(Context* c, const double2* z, int count, double scale, int l, u64 id0, u64* out,
-                   int out_cap) {
+                   int out_cap, const u64* d_ids) {
   const int N = c->N;
   Tmp work(c, sizeof(double2) * count * (N / 2));
   Tmp ints(c, sizeof(i64) * count * N);
   encode_batch(c, z, count, scale, ints.as<i64>(), work.as<double2>());
-  encrypt_coeffs(c, ints.as<i64>(), count, l, id0, out, out_cap);
+  encrypt_coeffs(c, ints.as<i64>(), count, l, id0, out, out_cap, d_ids);
 }
 
 // ---------------------------------------------------------------- transfers

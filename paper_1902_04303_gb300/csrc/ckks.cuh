@@ -61,8 +61,9 @@ const u64* mask_pt(Context* c, int kind, long index, int l, double scale,
 // ciphertexts [count][2][out_cap][N] (level l <= out_cap); enc id of ct idx =
 // id0 + idx
 void encrypt_slots(Context* c, const double2* z, int count, double scale, int l, u64 id0,
-                   u64* out, int out_cap);
-void encrypt_coeffs(Context* c, const i64* m, int count, int l, u64 id0, u64* out, int out_cap);
+                   u64* out, int out_cap, const u64* d_ids = nullptr);
+void encrypt_coeffs(Context* c, const i64* m, int count, int l, u64 id0, u64* out, int out_cap,
+                    const u64* d_ids = nullptr);
 
 // host transfers in the coefficient domain
 void ct_import(Context* c, Ct& ct, const u64* host_coeff, int npoly, int l, double scale);

@@ -107,10 +107,28 @@ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a -
 struct Acc128 {
   u64 lo, hi;
 };
+// a += x * y on 128 bits, as a schoolbook product of 32-bit halves with
+// multiply-add carry chains: the x0 y0 and x1 y1 partial products go to words
+// 0-1 and 2-3, the two cross products to words 1-2.
 __device__ __forceinline__ void mac128(Acc128& a, u64 x, u64 y) {
-  u64 l = x * y, h = __umul64hi(x, y);
-  a.lo += l;
-  a.hi += h + (a.lo < l ? 1 : 0);
+  const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  uint32_t r0 = (uint32_t)a.lo, r1 = (uint32_t)(a.lo >> 32);
+  uint32_t r2 = (uint32_t)a.hi, r3 = (uint32_t)(a.hi >> 32);
+  asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.u32 %3, %5, %7, %3;\n\t"
+      "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32 %3, %3, 0;"
+      : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+      : "r"(x0), "r"(x1), "r"(y0), "r"(y1));
+  a.lo = ((u64)r1 << 32) | r0;
+  a.hi = ((u64)r3 << 32) | r2;
 }
 
 #endif  // __CUDACC__
@@ -127,12 +145,11 @@ struct RowMap {
 };
 
 // Tables of the negacyclic NTT for one modulus index u, each of length N:
-// psi[i] = psi^brv(i), ipsi[i] = psi^-brv(i), plus Shoup companions.
+// psi[i] = (psi^brv(i), Shoup companion), ipsi[i] = (psi^-brv(i), companion),
+// interleaved so that one 16-byte load fetches a twiddle and its companion.
 struct NttTables {
-  const u64* psi;
-  const u64* psi_sh;
-  const u64* ipsi;
-  const u64* ipsi_sh;
+  const ulonglong2* psi;
+  const ulonglong2* ipsi;
   const u64* ninv;     // [nmod] N^-1 mod q_u
   const u64* ninv_sh;  // [nmod]
   const DevMod* mod;   // [nmod]
@@ -203,7 +220,7 @@ struct Context {
   std::vector<u64> mod;        // [L + K]: q_0..q_{L-1}, p_0..p_{K-1}
   std::vector<DevMod> hmod;
   DevMod* d_mod = nullptr;
-  u64 *d_psi = nullptr, *d_psi_sh = nullptr, *d_ipsi = nullptr, *d_ipsi_sh = nullptr;
+  ulonglong2 *d_psi = nullptr, *d_ipsi = nullptr;
   u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l - 1 (value, Shoup)
   u64* d_rescale = nullptr;    // [L][L][2]
@@ -213,12 +230,12 @@ struct Context {
   u64* d_pinv = nullptr;       // [L][2] P^-1 mod q_i (value, Shoup)
   u64* d_conv_store = nullptr; // backing store of all conversion tables
   // encoding procedure tables
-  double2* d_fftW_enc = nullptr;  // [M/2]
-  double2* d_fftT_enc = nullptr;  // [M]
   double2* d_fftW_dec = nullptr;
+  longlong2* d_fftWq = nullptr;   // [M/2] encoding twiddles, 62 fractional bits
+  longlong2* d_fftTq = nullptr;   // [M]
   double2* d_fftT_dec = nullptr;
-  int* d_slot_pos = nullptr;      // [M] bitrev(u_j) for slot j
   int* d_slot_u = nullptr;        // [M] u_j
+  int* d_slot_inv = nullptr;      // [M] slot j with bitrev(u_j) = p, for each p
   // keys
   u64* d_sk = nullptr;            // [L+K][N] NTT domain
   u64* d_pk = nullptr;            // [2][L][N] NTT domain (b, a)
@@ -232,7 +249,7 @@ struct Context {
   Prof prof;
   std::string last_error;
   NttTables tables() const {
-    return NttTables{d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh, d_mod};
+    return NttTables{d_psi, d_ipsi, d_ninv, d_ninv_sh, d_mod};
   }
   size_t ksk_words() const { return (size_t)P.dnum * 2 * (P.L + P.K) * N; }
 };

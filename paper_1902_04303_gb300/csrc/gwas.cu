@@ -76,14 +76,6 @@ struct Eval {
     return z;
   }
 
-  // t += Rotate(t, step) for step in steps, in place
-  void ladder(Ct& t, const std::vector<int>& steps) {
-    CtPtr r = fresh(t.l);
-    for (int s : steps) {
-      op_rotate(c, t, s, *r);
-      op_addsub(c, t, *r, t, false);
-    }
-  }
   std::vector<int> pow2_steps(int count, int base = 1) {
     std::vector<int> s;
     for (int i = 0; i < count; ++i) s.push_back(base << i);
@@ -303,41 +295,59 @@ Job* job_create(Context* c, int n, int d, long k) {
 void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double* yp) {
   Context* c = j->c;
   const Layout& lay = j->lay;
-  Eval ev{c, lay};
-  const int n = lay.n, d = lay.d, L = c->P.L;
+  const int n = lay.n, d = lay.d, L = c->P.L, M = lay.M;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const std::vector<double> X = to_host(c, Xp, (size_t)n * d), A = to_host(c, Ap, (size_t)d * d),
                             y = to_host(c, yp, n);
+  // all inputs (X as CP, (X^T X)^-1 as CP, y, beta0 = 0, X^T as REP) in one
+  // batched encryption at the top level; encryption ids as in the spec
+  const int cnt = 2 * d + 2 + d * lay.H;
+  std::vector<double2> z((size_t)cnt * M, make_double2(0, 0));
+  std::vector<u64> ids(cnt);
+  int it = 0;
+  for (int col = 0; col < d; ++col, ++it) {
+    ids[it] = kEncX + col;
+    for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(X[(size_t)t * d + col], 0);
+  }
+  for (int col = 0; col < d; ++col, ++it) {
+    ids[it] = kEncA + col;
+    for (int r = 0; r < d; ++r) z[(size_t)it * M + r] = make_double2(A[(size_t)r * d + col], 0);
+  }
+  ids[it] = kEncY;
+  for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(y[t], 0);
+  ++it;
+  ids[it++] = kEncBeta0;
+  for (int col = 0; col < d; ++col)
+    for (int h = 0; h < lay.H; ++h, ++it) {
+      ids[it] = kEncXtRep + (u64)col * 4096 + h;
+      for (int b = 0; b < lay.B; ++b) {
+        const int s = h * lay.B + b;
+        if (s >= n) continue;
+        for (int t = 0; t < lay.nb; ++t)
+          z[(size_t)it * M + b * lay.nb + t] = make_double2(X[(size_t)s * d + col], 0);
+      }
+    }
+  CtSetPtr in = set_new(c, cnt, 2, L, L, delta);
+  {
+    Tmp dz(c, sizeof(double2) * z.size()), did(c, sizeof(u64) * cnt);
+    GWHE_CUDA(cudaMemcpyAsync(dz.p, z.data(), sizeof(double2) * z.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    GWHE_CUDA(cudaMemcpyAsync(did.p, ids.data(), sizeof(u64) * cnt, cudaMemcpyHostToDevice,
+                              c->stream));
+    encrypt_slots(c, dz.as<double2>(), cnt, delta, L, 0, in->d, L, did.u());
+  }
   j->X.clear();
   j->A.clear();
   j->XtREP.clear();
   j->XtREP.resize(d);
-  for (int col = 0; col < d; ++col) {
-    auto z = ev.slots_zero();
-    for (int t = 0; t < n; ++t) z[t] = make_double2(X[(size_t)t * d + col], 0);
-    j->X.push_back(ev.encrypt_vec(z, kEncX + col, L, delta));
-  }
-  for (int col = 0; col < d; ++col) {
-    auto z = ev.slots_zero();
-    for (int r = 0; r < d; ++r) z[r] = make_double2(A[(size_t)r * d + col], 0);
-    j->A.push_back(ev.encrypt_vec(z, kEncA + col, L, delta));
-  }
-  {
-    auto z = ev.slots_zero();
-    for (int t = 0; t < n; ++t) z[t] = make_double2(y[t], 0);
-    j->y = ev.encrypt_vec(z, kEncY, L, delta);
-    j->beta0 = ev.encrypt_vec(ev.slots_zero(), kEncBeta0, L, delta);
-  }
+  it = 0;
+  for (int col = 0; col < d; ++col) j->X.push_back(in->view(it++));
+  for (int col = 0; col < d; ++col) j->A.push_back(in->view(it++));
+  j->y = in->view(it++);
+  j->beta0 = in->view(it++);
   for (int col = 0; col < d; ++col)
-    for (int h = 0; h < lay.H; ++h) {
-      auto z = ev.slots_zero();
-      for (int b = 0; b < lay.B; ++b) {
-        const int s = h * lay.B + b;
-        if (s >= n) continue;
-        for (int t = 0; t < lay.nb; ++t) z[b * lay.nb + t] = make_double2(X[(size_t)s * d + col], 0);
-      }
-      j->XtREP[col].push_back(ev.encrypt_vec(z, kEncXtRep + (u64)col * 4096 + h, L, delta));
-    }
+    for (int h = 0; h < lay.H; ++h) j->XtREP[col].push_back(in->view(it++));
+  j->sets.push_back(std::move(in));
 }
 
 static void make_dup_state(Job* j, Eval& ev) {
@@ -439,8 +449,11 @@ void job_fit(Job* j, int kappa) {
   j->zp = ev.sub(*zv, *xaxtz);
   CtPtr wmv = ev.view(*j->w_m, j->zp->l);
   j->wzp = ev.mult(*wmv, *j->zp);
-  // eq. M = I - X A X^T: Alg. 3 (CP-MatMult) then Alg. 8 (CP-REP-MatMult)
-  CtSetPtr xa = ev.cp_matmul(j->X, j->A, d);
+  // eq. M = I - X A X^T: Alg. 3 (CP-MatMult) then Alg. 8 (CP-REP-MatMult),
+  // from X and A dropped to kMLevel limbs
+  std::vector<CtPtr> Alow;
+  for (int rr = 0; rr < d; ++rr) Alow.push_back(ev.view(*j->A[rr], kMLevel));
+  CtSetPtr xa = ev.cp_matmul(j->X, Alow, d);
   set_ladder(c, *xa, ev.dup_steps());  // Duplicate(XA_r) for every r
   const int l0 = xa->l;
   std::vector<CtPtr> dv, xv;

@@ -21,6 +21,9 @@ struct Layout {
 Layout make_layout(int logN, int n, int d, long k);
 
 constexpr int kBatchLevel = 4;  // limbs with which a SNP batch enters the loop
+// M = I - X A X^T is needed only at kBatchLevel + 1 limbs (the Dup(M_j) source):
+// it is computed from X and A dropped to this level
+constexpr int kMLevel = kBatchLevel + 4;
 
 struct Job {
   Context* c = nullptr;

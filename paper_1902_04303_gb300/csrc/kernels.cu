@@ -139,43 +139,67 @@ __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __r
   }
   const u64* hm = a.tab + 2 * a.n_in;
   const int o1 = min(o0 + kConvOG, a.n_out);
-  for (int o = o0; o < o1; ++o) {
-    Acc128 s{0, 0};
+  // four outputs at a time: independent accumulation chains
+  for (int o = o0; o < o1; o += 4) {
+    Acc128 s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 #pragma unroll
-    for (int i = 0; i < kMaxConvIn; ++i)
-      if (i < a.n_in) mac128(s, y[i], __ldg(hm + i * a.hm_stride + o));
-    op[(size_t)a.out_row[o] * N + k] = reduce128(s.lo, s.hi, mod[a.out_pidx[o]]);
+    for (int i = 0; i < kMaxConvIn; ++i) {
+      if (i < a.n_in) {
+        const u64* h = hm + i * a.hm_stride + o;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (o + t < o1) mac128(s[t], y[i], __ldg(h + t));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (o + t < o1)
+        op[(size_t)a.out_row[o + t] * N + k] = reduce128(s[t].lo, s[t].hi, mod[a.out_pidx[o + t]]);
   }
 }
 
 // acc_p[u] = sum_j x_j[u] * key_j[p][u] over digits, for the l + K extended limbs;
 // x_j[u] is the input limb itself when u lies in digit j, else the converted limb.
+// Each thread keeps its key words in registers and applies them to up to IB
+// items of the set, so the key is read once per IB ciphertexts.
+constexpr int kKsMaxBeta = 4;
+template <int IB>
 __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
                            const u64* __restrict__ ext, const u64* __restrict__ key,
                            u64* __restrict__ acc, int l, int K, int L, int alpha, int beta, int N,
-                           const DevMod* __restrict__ mod) {
+                           int cnt, const DevMod* __restrict__ mod) {
   const int u = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
-  const size_t item = blockIdx.z;
-  c_ntt += item * c_stride;
-  ext += item * (size_t)beta * ne * N;
-  acc += item * (size_t)2 * ne * N;
   const int mi = u < l ? u : L + (u - l);
   const size_t LK = (size_t)(L + K);
-  Acc128 s0{0, 0}, s1{0, 0};
-  for (int j = 0; j < beta; ++j) {
-    const int lo = j * alpha, hi = min(lo + alpha, l);
-    const u64 x = (u >= lo && u < hi) ? c_ntt[(size_t)u * N + k] : ext[((size_t)j * ne + u) * N + k];
-    const u64 b = key[(((size_t)j * 2 + 0) * LK + mi) * N + k];
-    const u64 a = key[(((size_t)j * 2 + 1) * LK + mi) * N + k];
-    mac128(s0, x, b);
-    mac128(s1, x, a);
-  }
+  u64 kb[kKsMaxBeta], ka[kKsMaxBeta];
+#pragma unroll
+  for (int j = 0; j < kKsMaxBeta; ++j)
+    if (j < beta) {
+      kb[j] = key[(((size_t)j * 2 + 0) * LK + mi) * N + k];
+      ka[j] = key[(((size_t)j * 2 + 1) * LK + mi) * N + k];
+    }
   const DevMod m = mod[mi];
-  acc[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
-  acc[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+  const int it0 = blockIdx.z * IB;
+  const int it1 = min(it0 + IB, cnt);
+  for (int item = it0; item < it1; ++item) {
+    const u64* cx = c_ntt + (size_t)item * c_stride;
+    const u64* ex = ext + (size_t)item * beta * ne * N;
+    Acc128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+    for (int j = 0; j < kKsMaxBeta; ++j) {
+      if (j >= beta) break;
+      const int lo = j * alpha, hi = min(lo + alpha, l);
+      const u64 x = (u >= lo && u < hi) ? cx[(size_t)u * N + k] : ex[((size_t)j * ne + u) * N + k];
+      mac128(s0, x, kb[j]);
+      mac128(s1, x, ka[j]);
+    }
+    u64* ac = acc + (size_t)item * 2 * ne * N;
+    ac[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
+    ac[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+  }
 }
 
 // out_p[i] = (acc_p[i] - conv_p[i]) P^-1 mod q_i (+ add_p[i])
@@ -435,7 +459,8 @@ __global__ void k_sample_uniform(u64 seed, u64 obj, u32 tag, int u, u64* out, in
 // encryption randomness for ct idx (enc id id0 + idx): a CTA of 256 threads
 // covers 4096 coefficients; each thread draws the ChaCha20 blocks of its 16
 // coefficients into shared memory, then the residues are written coalesced.
-__global__ void __launch_bounds__(256) k_enc_sample(u64 seed, u64 id0, int count, int l,
+__global__ void __launch_bounds__(256) k_enc_sample(u64 seed, u64 id0, const u64* __restrict__ ids,
+                                                    int count, int l,
                                                     const i64* __restrict__ m_coeff,
                                                     u64* __restrict__ tmp, int N,
                                                     const DevMod* __restrict__ mod) {
@@ -447,7 +472,7 @@ __global__ void __launch_bounds__(256) k_enc_sample(u64 seed, u64 id0, int count
   if (idx >= count) return;
   const int base = tile * 4096;
   const int tcoef = min(4096, N - base);
-  const u64 id = id0 + (u64)idx;
+  const u64 id = ids ? ids[idx] : id0 + (u64)idx;
   const int tid = threadIdx.x;
   if (tid * 16 < tcoef) {
     const int b = (base >> 4) + tid;  // ternary block of coefficients 16b..16b+15
@@ -550,16 +575,6 @@ __device__ __forceinline__ void fft_bfly(double2& x, double2& y, double2 w) {
   y = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
 }
 
-// G[idx][pos[j]] = z[idx][j]
-__global__ void k_fft_scatter(const double2* __restrict__ z, const int* __restrict__ pos, int M,
-                              int count, double2* __restrict__ G) {
-  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)count * M) return;
-  const size_t idx = gid / M;
-  const int j = (int)(gid - idx * M);
-  G[idx * M + pos[j]] = z[gid];
-}
-
 // radix-2 stages len = 2 .. 2^a inside tiles of 2^a contiguous entries
 __global__ void k_fft_tile(double2* __restrict__ G, const double2* __restrict__ W, int logM, int a) {
   extern __shared__ double2 sf[];
@@ -610,17 +625,154 @@ __global__ void k_fft_cols(double2* __restrict__ G, const double2* __restrict__ 
   for (int h = 0; h < R; ++h) base[(size_t)h * T + lo] = x[h];
 }
 
-// c_k = G[k] T[k]; coefficient k = rint(Re c_k f), k + M = rint(Im c_k f)
-__global__ void k_fft_round(const double2* __restrict__ G, const double2* __restrict__ T, int M,
-                            int count, double f, i64* __restrict__ out) {
+// ------------------------------------------------------------- fixed-point encoding
+// The encoding procedure in exact integer arithmetic (the same statement as
+// the library header): values are int64 fixed-point with F = 61 - log2 M - e
+// fractional bits, twiddles carry 62 fractional bits, every complex product is
+// formed on 128 bits and rounded as (v + 2^61) >> 62.
+// (p1 - p2 + 2^61) >> 62 for exact signed 128-bit products p1 = a1 b1, p2 =
+// a2 b2, sign +1 (or p1 + p2 for sign -1), from 64-bit low/high halves; the
+// result fits in 64 bits.
+__device__ __forceinline__ i64 fx_dot(i64 a1, i64 b1, i64 a2, i64 b2, bool sub) {
+  const u64 l1 = (u64)a1 * (u64)b1, l2 = (u64)a2 * (u64)b2;
+  const i64 h1 = __mul64hi(a1, b1), h2 = __mul64hi(a2, b2);
+  u64 lo;
+  i64 hi;
+  if (sub) {
+    lo = l1 - l2;
+    hi = h1 - h2 - (l1 < l2 ? 1 : 0);
+  } else {
+    lo = l1 + l2;
+    hi = h1 + h2 + (lo < l1 ? 1 : 0);
+  }
+  const u64 r = lo + ((u64)1 << 61);
+  hi += (r < lo ? 1 : 0);
+  return (i64)(((u64)hi << 2) | (r >> 62));
+}
+__device__ __forceinline__ longlong2 cmul_fx(longlong2 a, longlong2 w) {
+  return make_longlong2(fx_dot(a.x, w.x, a.y, w.y, true), fx_dot(a.x, w.y, a.y, w.x, false));
+}
+__device__ __forceinline__ void fx_bfly(longlong2& x, longlong2& y, longlong2 w) {
+  const longlong2 t = cmul_fx(y, w);
+  const longlong2 a = x;
+  x = make_longlong2(a.x + t.x, a.y + t.y);
+  y = make_longlong2(a.x - t.x, a.y - t.y);
+}
+
+// e[idx] = smallest e in [0, 40] with 2^e >= max |Re|, |Im| of plaintext idx.
+// Pass 1: per block, the maximum magnitude as the bit pattern of a
+// non-negative double (ordered like the value), atomically maxed per plaintext.
+__global__ void k_enc_maxabs(const double2* __restrict__ z, int M, int blocks_per,
+                             unsigned long long* __restrict__ mx) {
+  __shared__ double red[256];
+  const int idx = blockIdx.x / blocks_per, part = blockIdx.x - idx * blocks_per;
+  const int chunk = (M + blocks_per - 1) / blocks_per;
+  const double2* zz = z + (size_t)idx * M;
+  double m = 0.0;
+  for (int j = part * chunk + threadIdx.x; j < min(M, (part + 1) * chunk); j += blockDim.x) {
+    const double2 v = zz[j];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(mx + idx, (unsigned long long)__double_as_longlong(red[0]));
+}
+// pass 2: the exponent from the maximum
+__global__ void k_enc_exponent(const unsigned long long* __restrict__ mx, int count,
+                               int* __restrict__ e) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const double m = __longlong_as_double((long long)mx[idx]);
+  int ex = 0;
+  while (ex < 40 && scalbn(1.0, ex) < m) ++ex;
+  e[idx] = ex;
+}
+
+// Twist and round one entry k of transform idx: c = G Tq[k], coefficient
+// k = rint((double)Re c * f), k + M = rint((double)Im c * f).
+__device__ __forceinline__ void fx_emit(longlong2 g, const longlong2* __restrict__ T, int k,
+                                        int M, double f, i64* o) {
+  const longlong2 c = cmul_fx(g, T[k]);
+  o[k] = __double2ll_rn(__dmul_rn(__ll2double_rn(c.x), f));
+  o[k + M] = __double2ll_rn(__dmul_rn(__ll2double_rn(c.y), f));
+}
+
+// Radix-2 stages len = 2 .. 2^a inside tiles of 2^a contiguous entries of the
+// bit-reversed input: entry p of transform idx is loaded as the fixed-point
+// value of slot inv[p] (F = 61 - logM - e[idx]).  When the tile is the whole
+// transform (a = logM) the twist and rounding are applied here.
+__global__ void k_fx_tile(const double2* __restrict__ z, const int* __restrict__ inv,
+                          const int* __restrict__ e, longlong2* __restrict__ G,
+                          const longlong2* __restrict__ W, const longlong2* __restrict__ Tq,
+                          int logM, int a, double scale, i64* __restrict__ out) {
+  extern __shared__ longlong2 sfx[];
+  const int T = 1 << a;
+  const int M = 1 << logM;
+  const int tiles = M >> a;
+  const size_t idx = blockIdx.x / tiles;
+  const int t0 = (blockIdx.x - (int)(idx * tiles)) * T;
+  const int F = 61 - logM - e[idx];
+  const double2* zz = z + idx * M;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    const double2 v = zz[inv[t0 + i]];
+    sfx[i] = make_longlong2(__double2ll_rn(scalbn(v.x, F)), __double2ll_rn(scalbn(v.y, F)));
+  }
+  __syncthreads();
+  for (int ls = 1; ls <= a; ++ls) {
+    const int half = 1 << (ls - 1);
+    const int stride = M >> ls;
+    for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
+      const int blk = b >> (ls - 1), jj = b & (half - 1);
+      const int p = (blk << ls) + jj;
+      fx_bfly(sfx[p], sfx[p + half], W[jj * stride]);
+    }
+    __syncthreads();
+  }
+  if (a == logM) {
+    const double f = scalbn(scale, -(logM + F));
+    i64* o = out + idx * 2 * M;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) fx_emit(sfx[i], Tq, i, M, f, o);
+  } else {
+    longlong2* base = G + idx * M + t0;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) base[i] = sfx[i];
+  }
+}
+
+// remaining stages len = 2^(a+1) .. M, R entries per thread in registers,
+// then the twist and rounding of those R entries
+template <int R>
+__global__ void k_fx_cols(const longlong2* __restrict__ G, const longlong2* __restrict__ W,
+                          const longlong2* __restrict__ Tq, const int* __restrict__ e, int logM,
+                          int a, int count, double scale, i64* __restrict__ out) {
+  const int T = 1 << a, M = 1 << logM;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (size_t)count * M) return;
-  const size_t idx = gid / M;
-  const int k = (int)(gid - idx * M);
-  const double2 c = cmul_exact(G[gid], T[k]);
+  if (gid >= (size_t)count * T) return;
+  const size_t idx = gid / T;
+  const int lo = (int)(gid - idx * T);
+  const longlong2* base = G + idx * M;
+  longlong2 x[R];
+#pragma unroll
+  for (int h = 0; h < R; ++h) x[h] = base[(size_t)h * T + lo];
+#pragma unroll
+  for (int s2 = 0; (1 << s2) < R; ++s2) {
+    const int hs = 1 << s2;
+    const int stride = M >> (a + 1 + s2);
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      if (h & hs) continue;
+      const int jj = ((h & (hs - 1)) << a) + lo;
+      fx_bfly(x[h], x[h + hs], W[jj * stride]);
+    }
+  }
+  const int F = 61 - logM - e[idx];
+  const double f = scalbn(scale, -(logM + F));
   i64* o = out + idx * 2 * M;
-  o[k] = __double2ll_rn(__dmul_rn(c.x, f));
-  o[k + M] = __double2ll_rn(__dmul_rn(c.y, f));
+#pragma unroll
+  for (int h = 0; h < R; ++h) fx_emit(x[h], Tq, h * T + lo, M, f, o);
 }
 
 // decoding: centred residues mod q0 -> (m_k + i m_(k+M)) T[k] at bit-reversed k
@@ -811,8 +963,11 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
   ProfScope ps(c, PROF_KS_INNER, (3.0 * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N * cnt);
   const int beta = (l + c->alpha - 1) / c->alpha;
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
-  k_ks_inner<<<dim3(blocks_for(c->N), l + c->P.K, cnt), kThreads, 0, c->stream>>>(
-      c_ntt, c_stride, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta, c->N, c->d_mod);
+  GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
+  constexpr int IB = 8;
+  k_ks_inner<IB><<<dim3(blocks_for(c->N), l + c->P.K, (cnt + IB - 1) / IB), kThreads, 0,
+                   c->stream>>>(c_ntt, c_stride, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta,
+                                c->N, cnt, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -907,13 +1062,13 @@ void sample_uniform(Context* c, u64 obj, u32 tag, int u, u64* out) {
   GWHE_LAUNCHED(c, 1);
 }
 
-void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp) {
+void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp,
+                const u64* d_ids) {
   ProfScope ps(c, PROF_SAMPLE, (3.0 * l + 1.0) * count * 8.0 * c->N);
   if (count == 0) return;
   const int tiles = (c->N + 4095) / 4096;
-  k_enc_sample<<<(unsigned)((size_t)count * tiles), 256, 0, c->stream>>>(c->seed, id0, count, l,
-                                                                        m_coeff, tmp, c->N,
-                                                                        c->d_mod);
+  k_enc_sample<<<(unsigned)((size_t)count * tiles), 256, 0, c->stream>>>(
+      c->seed, id0, d_ids, count, l, m_coeff, tmp, c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -973,15 +1128,36 @@ static void fft_stages(Context* c, double2* G, const double2* W, int count) {
 void encode_batch(Context* c, const double2* z, int count, double scale, i64* out, double2* work) {
   ProfScope ps(c, PROF_ENCODE, 2.0 * count * 16.0 * (c->N / 2));
   if (count == 0) return;
-  const int M = c->N / 2;
-  k_fft_scatter<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(z, c->d_slot_pos, M,
-                                                                          count, work);
-  GWHE_LAUNCHED(c, 1);
-  fft_stages(c, work, c->d_fftW_enc, count);
-  const double f = scale / (double)M;
-  k_fft_round<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(work, c->d_fftT_enc, M,
-                                                                        count, f, out);
-  GWHE_LAUNCHED(c, 1);
+  const int logM = c->logN - 1, M = 1 << logM;
+  const int a = logM < 12 ? logM : 12;  // 4096-entry tiles: 64 KiB of shared memory
+  const int T = 1 << a;
+  static bool smem_opt_in = false;
+  if (!smem_opt_in) {
+    GWHE_CUDA(cudaFuncSetAttribute(k_fx_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(longlong2) * 4096));
+    smem_opt_in = true;
+  }
+  longlong2* G = (longlong2*)work;  // same size as count * M double2
+  int* e = (int*)dalloc_bytes(c, (sizeof(int) + sizeof(unsigned long long)) * count + 8);
+  unsigned long long* mx = (unsigned long long*)(e + count + (count & 1));
+  GWHE_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * count, c->stream));
+  const int blocks_per = M >= 8192 ? 16 : 1;
+  k_enc_maxabs<<<count * blocks_per, 256, 0, c->stream>>>(z, M, blocks_per, mx);
+  k_enc_exponent<<<blocks_for(count), kThreads, 0, c->stream>>>(mx, count, e);
+  k_fx_tile<<<(unsigned)((size_t)count * (M / T)), 256, sizeof(longlong2) * T, c->stream>>>(
+      z, c->d_slot_inv, e, G, c->d_fftWq, c->d_fftTq, logM, a, scale, out);
+  const int R = M / T;
+  const unsigned nb = blocks_for((size_t)count * T, 128);
+  switch (R) {
+    case 1: break;
+    case 2: k_fx_cols<2><<<nb, 128, 0, c->stream>>>(G, c->d_fftWq, c->d_fftTq, e, logM, a, count, scale, out); break;
+    case 4: k_fx_cols<4><<<nb, 128, 0, c->stream>>>(G, c->d_fftWq, c->d_fftTq, e, logM, a, count, scale, out); break;
+    case 8: k_fx_cols<8><<<nb, 128, 0, c->stream>>>(G, c->d_fftWq, c->d_fftTq, e, logM, a, count, scale, out); break;
+    case 16: k_fx_cols<16><<<nb, 128, 0, c->stream>>>(G, c->d_fftWq, c->d_fftTq, e, logM, a, count, scale, out); break;
+    default: throw Error(ST_EINVAL, "ring degree too large for the encoder");
+  }
+  dfree(c, e);
+  GWHE_LAUNCHED(c, R > 1 ? 4 : 3);
 }
 
 void decode_batch(Context* c, const u64* m_coeff_q0, int count, double scale, double2* z,

@@ -83,8 +83,10 @@ void sample_ternary_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int 
 void sample_cbd_rns(Context* c, u64 obj, u64* out, const uint8_t* pidx, int nl);
 void sample_uniform(Context* c, u64 obj, u32 tag, int u, u64* out);
 // batched encryption randomness: for ct idx < count (enc id = id0 + idx):
-// tmp[idx][0] = v, tmp[idx][1] = m + e0, tmp[idx][2] = e1 over l q-limbs
-void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp);
+// tmp[idx][0] = v, tmp[idx][1] = m + e0, tmp[idx][2] = e1 over l q-limbs;
+// with d_ids (device array) the enc id of ct idx is d_ids[idx]
+void enc_sample(Context* c, u64 id0, int count, int l, const i64* m_coeff, u64* tmp,
+                const u64* d_ids = nullptr);
 void enc_combine(Context* c, const u64* tmp_ntt, int count, int l, u64* out, int out_cap,
                  size_t out_stride);
 // key-switching key limb: b = -a s + e (+ Pt)

@@ -55,8 +55,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
   const int u = rm.pidx[limb];
   u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * ((size_t)1 << LOGN);
   const u64 q = tb.mod[u].q, twoq = 2 * q;
-  const u64* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << LOGN);
-  const u64* Wsh = (FWD ? tb.psi_sh : tb.ipsi_sh) + ((size_t)u << LOGN);
+  const ulonglong2* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << LOGN);
 
   const int t = threadIdx.x;
   const int lg = PASSA ? (t % G) : (t / TPS);
@@ -84,7 +83,8 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
       for (int m = 0; m < 16; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
-        ct_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+        const ulonglong2 w = __ldg(W + idx);
+        ct_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
       }
     }
 #pragma unroll
@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
       for (int m = 0; m < 16; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, 16 * r + m);
-        ct_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+        const ulonglong2 w = __ldg(W + idx);
+        ct_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
       }
     }
     __syncthreads();
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
       for (int m = 0; m < 16; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, 16 * r + m);
-        gs_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+        const ulonglong2 w = __ldg(W + idx);
+        gs_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
       }
     }
     __syncthreads();
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
       for (int m = 0; m < 16; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
-        gs_bfly(x[m], x[m + st], __ldg(W + idx), __ldg(Wsh + idx), q, twoq);
+        const ulonglong2 w = __ldg(W + idx);
+        gs_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
       }
     }
     if (PASSA) {
@@ -166,8 +169,7 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
   const int u = rm.pidx[limb];
   u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * (size_t)N;
   const u64 q = tb.mod[u].q, twoq = 2 * q;
-  const u64* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << logN);
-  const u64* Wsh = (FWD ? tb.psi_sh : tb.ipsi_sh) + ((size_t)u << logN);
+  const ulonglong2* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << logN);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = base[i];
   __syncthreads();
   const int half = N >> 1;
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
         const int i = b >> lt;
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
         const int idx = (1 << s) + i;
-        ct_bfly(sh[j], sh[j + (1 << lt)], W[idx], Wsh[idx], q, twoq);
+        const ulonglong2 w = W[idx];
+        ct_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q, twoq);
       }
       __syncthreads();
     }
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
         const int i = b >> lt;
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
         const int idx = (1 << s) + i;
-        gs_bfly(sh[j], sh[j + (1 << lt)], W[idx], Wsh[idx], q, twoq);
+        const ulonglong2 w = W[idx];
+        gs_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q, twoq);
       }
       __syncthreads();
     }

@@ -62,6 +62,7 @@ _SIGS = {
     "gwhe_ct_import": [_vp, _u64p, _i, _i, _d],
     "gwhe_ct_export": [_vp, _u64p],
     "gwhe_encode": [_vp, _f64p, _d, _i64p],
+    "gwhe_encode_batch": [_vp, _vp, _i, _d, _vp],
     "gwhe_encrypt": [_vp, _f64p, _d, _i, _u64, _vp],
     "gwhe_encrypt_coeffs": [_vp, _i64p, _d, _i, _u64, _vp],
     "gwhe_decrypt": [_vp, _vp, _u64p],
@@ -306,6 +307,10 @@ class Context:
         out = np.zeros(self.N, np.int64)
         self._c(lib().gwhe_encode(self.h, _slots(z, self.M), scale, out))
         return out
+
+    def encode_batch(self, z_dev, count, scale, out_dev):
+        """device-side encode of count x M complex slots (torch float64 [count, M, 2])."""
+        self._c(lib().gwhe_encode_batch(self.h, _ptr(z_dev), count, scale, _ptr(out_dev)))
 
     def encrypt(self, z, scale, level, enc_id):
         c = self.ct(2, level)

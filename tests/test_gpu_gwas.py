@@ -8,6 +8,7 @@ import pytest
 from oracle import gwas_fp64
 from oracle.circuit import Circuit, Layout, rotation_steps
 from oracle.ckks import OracleCKKS, galois_conj, galois_rot
+from oracle.trace import job_ks_histogram
 from paper_1902_04303_gb300.datagen import WORKLOADS, make_gwas
 
 pytestmark = pytest.mark.gpu
@@ -51,9 +52,15 @@ def test_job_circuit_bit_exact(g):
     ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
     ctx.keygen(rot_steps=steps, conj=True)
     job = g.Job(ctx, n, d, k)
+    ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
     job.fit(1)
     job.snp_stats(data.S)
+    # same key switches at the same levels as the oracle circuit's level trace
+    W = dict(logN=logN, L=L, q0_bits=60, scale_bits=40, K=K, sp_bits=60, dnum=dnum, n=n, d=d,
+             k=k)
+    want, _, _ = job_ks_histogram(W, 1)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want)
     o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
     o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
     c = Circuit(o, lay)
@@ -111,9 +118,12 @@ def test_job_paper_shape_accuracy(g):
     ctx.keygen(rot_steps=[1 << i for i in range(W["logN"] - 1)], conj=True)
     job = g.Job(ctx, W["n"], W["d"], W["k"])
     assert job.layout["tau"] == 256 and job.layout["batches"] == 42 and job.layout["H"] == 2
+    ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
     job.fit(1)
     job.snp_stats(data.S)
+    want, _, _ = job_ks_histogram(W, 1)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want)
     num, den = job.decrypt_results()
     ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
     db, dl = check_accuracy(num, den, ref, W["k"])

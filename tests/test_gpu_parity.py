@@ -45,7 +45,7 @@ def rand_ct(o, l, seed, npoly=2):
 @pytest.mark.parametrize("logN", [4, 7, 10, 12, 13, 14, 15, 16])
 def test_ntt_roundtrip_and_negacyclic_product(g, logN):
     import torch
-    L = 5
+    L = 4  # one-limb digits with one 60-bit special prime
     ctx, o = pair(g, logN, L, 1, L, keys=False)
     npoly = 3
     x = make_residues(npoly * L, ctx.N, [ctx.q[i % L] for i in range(npoly * L)], seed=logN)

@@ -162,8 +162,11 @@ def test_encode_matches_definition(logN):
     buf = np.ascontiguousarray(np.stack([z.real, z.imag], 1).reshape(-1))
     L.or_encode(logN, buf, delta, m)
     exact = encode_naive_real(z, logN, delta)
-    # rounding of a value within FP error of the definition
-    assert np.max(np.abs(m - exact)) <= 0.5 + 1e-3
+    # rounding of a value within the fixed-point procedure's error bound of the
+    # definition: 0.5 plus scale * 2^-F, F = 61 - log2(M) - e fractional bits
+    e = int(np.ceil(np.log2(max(np.max(np.abs(z.real)), np.max(np.abs(z.imag)), 1.0))))
+    F = 61 - (logN - 1) - e
+    assert np.max(np.abs(m - exact)) <= 0.5 + delta * 2.0 ** -F
     # decode by the definition recovers z within the rounding bound
     back = decode_naive(m, logN, delta)
     bound = (1 << logN) * 0.5 / delta

@@ -11,6 +11,7 @@ import pytest
 from oracle import gwas_exact, gwas_fp64
 from oracle.circuit import Circuit, Layout, rotation_steps
 from oracle.ckks import OracleCKKS, galois_conj, galois_rot
+from oracle.trace import job_ks_histogram
 from paper_1902_04303_gb300.datagen import make_gwas
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
@@ -123,6 +124,14 @@ def test_encrypted_circuit_matches_o2():
     o = OracleCKKS(logN=logN, L=21, K=7, dnum=3, seed=11)
     lay = Layout(logN, n, d, k)
     o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay)] + [galois_conj(logN)])
+    hist = np.zeros(65, np.int64)
+    real_ks = o.keyswitch
+
+    def counting_ks(x, key_id):
+        hist[x.shape[0]] += 1
+        return real_ks(x, key_id)
+
+    o.keyswitch = counting_ks
     c = Circuit(o, lay)
     c.encrypt_inputs(dat.X, A, dat.y)
     c.fit(kappa=1)
@@ -134,6 +143,10 @@ def test_encrypted_circuit_matches_o2():
         dens.append(b)
     num = np.concatenate(nums)
     den = np.concatenate(dens)
+    # the level tracer issues the same key switches at the same levels
+    W = dict(logN=logN, L=21, q0_bits=60, scale_bits=40, K=7, sp_bits=60, dnum=3, n=n, d=d, k=k)
+    want, _, _ = job_ks_histogram(W, 1)
+    assert np.array_equal(hist, want)
     ref = gwas_fp64.semi_parallel_fp64(dat.X, dat.y, dat.S, kappa=1, A=A)
     ok = np.abs(ref["den"]) > 1e-6  # monomorphic SNPs have den = 0 (degenerate)
     assert np.max(np.abs(den[~ok])) < 1e-4
@@ -142,3 +155,17 @@ def test_encrypted_circuit_matches_o2():
     dl = np.abs(gwas_fp64.neglog10p(b, 1 / den[ok]) - gwas_fp64.neglog10p(ref["b"][ok],
                                                                           ref["err"][ok]))
     assert np.max(dl) < 0.05
+
+
+@pytest.mark.parametrize("n", [16, 64, 245])
+def test_batch_key_switch_count_closed_form(n):
+    """One SNP batch (Alg. 11 loop body) switches keys 6 + 3 log2(nb) times:
+    relinearisations of S', Dup(w z') S', Dup(w) S', WSS, WSC (5), the
+    conjugation (1), and three column sums of log2(nb) rotations (Alg. 5)."""
+    W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=5,
+             k=10643)
+    _, _, batch = job_ks_histogram(W, 1)
+    nb = 1 << math.ceil(math.log2(n))
+    assert batch.sum() == 6 + 3 * int(math.log2(nb))
+    # every batch switch happens at or below the batch entry level
+    assert batch[5:].sum() == 0
