@@ -124,7 +124,9 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
                        W["dnum"], seed=W["seed"] + 7919 * rank, stream=stream.cuda_stream)
-    steps_rot = [1 << i for i in range(W["logN"] - 1)]
+    probe = gwhe.Job(ctx, W["n"], W["d"], W["k"], layout=args.layout)
+    steps_rot, layout_used = probe.rotation_steps(), "factored" if probe.factored else "mccp"
+    probe.close()
     ctx.keygen(rot_steps=steps_rot, conj=True)
     data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"] + rank)
     A = client_preprocess(data.X)
@@ -135,7 +137,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(src):
-        job = gwhe.Job(ctx, W["n"], W["d"], W["k"])
+        job = gwhe.Job(ctx, W["n"], W["d"], W["k"], layout=args.layout)
         job.encrypt_inputs(src["X"], src["A"], src["y"])
         job.fit(W["kappa"])
         job.snp_stats(src["S"])
@@ -215,7 +217,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": W["name"], "N": 1 << W["logN"], "q_limbs": W["L"],
                    "special_primes": W["K"], "dnum": W["dnum"], "n": W["n"], "d": W["d"],
-                   "k": W["k"], "kappa": W["kappa"], "parallelism": "independent jobs per GPU",
+                   "k": W["k"], "kappa": W["kappa"], "layout": layout_used,
+                   "parallelism": "independent jobs per GPU",
                    "l2": "flushed between steps (256 MiB write)"},
         "keyswitch_per_s": round(ks_per_job * world / (step_ms / 1e3), 1),
         "keyswitches_per_job": ks_per_job,
@@ -228,7 +231,7 @@ def run_gpu(args):
     if not args.no_micro:
         out["micro"] = run_micro(stream)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(W)
+        out["cpu_baseline"] = cpu_baseline(W, layout_used == "factored")
     print(json.dumps(out))
     sys.stdout.flush()
     if world > 1:
@@ -347,10 +350,12 @@ def oracle_sample(W):
     return dict(t_ks4=t_ks, t_tensor4=t_tensor, t_enc4=t_enc, t_setup=t_setup, alpha=o.alpha)
 
 
-def extrapolate(sample, ks_hist, W):
+def extrapolate(sample, ks_hist, W, factored=False):
     """Oracle job time: key switches scaled by their polynomial-product count
     (2 beta (l + K) per switch at level l) from the measured level-4 switch,
-    plus the batches' tensor sums and SNP encryptions at level 4."""
+    plus the batches' tensor products and SNP encryptions (M-CCP: n of each
+    at 4 limbs; factored: one encryption at 6 limbs, d tensors at 6 and d at
+    4 limbs, scaled by limbs)."""
     alpha, K = sample["alpha"], W["K"]
 
     def work(l):
@@ -362,22 +367,26 @@ def extrapolate(sample, ks_hist, W):
             t += cnt * sample["t_ks4"] * work(l) / work(4)
     tau = 2 * ((1 << (W["logN"] - 1)) // (1 << math.ceil(math.log2(W["n"]))))
     batches = -(-W["k"] // tau)
-    t += batches * W["n"] * (sample["t_tensor4"] + sample["t_enc4"])
+    if factored:
+        t += batches * (sample["t_enc4"] * 6 / 4
+                        + W["d"] * sample["t_tensor4"] * (6 / 4 + 1))
+    else:
+        t += batches * W["n"] * (sample["t_tensor4"] + sample["t_enc4"])
     return t
 
 
-def cpu_baseline(W):
+def cpu_baseline(W, factored=False):
     from oracle.trace import job_ks_histogram
-    ks_hist, _, _ = job_ks_histogram(W, W["kappa"])
+    ks_hist, _, _ = job_ks_histogram(W, W["kappa"], factored)
     s = oracle_sample(W)
-    t_job = extrapolate(s, ks_hist, W)
+    t_job = extrapolate(s, ks_hist, W, factored)
     return {"value": round(W["k"] / t_job, 4), "unit": "SNPs/s", "cores": 1, "kind": "oracle",
             "sample": ("oracle (1 thread) timed on one key switch (%.2f s), one tensor (%.2f s) and "
                        "one encryption (%.2f s) at 4 limbs, N=2^16; extrapolated to the job with "
-                       "the oracle circuit's level trace (%d key switches) and %d batch "
-                       "tensors/encryptions: %.0f s per job"
+                       "the oracle circuit's level trace (%d key switches, %s layout) and the "
+                       "batches' tensors/encryptions: %.0f s per job"
                        % (s["t_ks4"], s["t_tensor4"], s["t_enc4"], int(np.sum(ks_hist)),
-                          W["n"] * -(-W["k"] // 256), t_job))}
+                          "factored" if factored else "M-CCP", t_job))}
 
 
 def run_reference(args):
@@ -390,8 +399,11 @@ def run_reference(args):
     from oracle import build_oracle
     build_oracle.build()
     from oracle.trace import job_ks_histogram
+    # the same SNP-phase layout as the library arm (auto: factored when the
+    # ring has more than 8 limbs)
+    factored = args.layout == "factored" or (args.layout == "auto" and W["L"] > 8)
     # key switches per level of the job, from a level trace of the oracle circuit
-    hist, _, _ = job_ks_histogram(W, W["kappa"])
+    hist, _, _ = job_ks_histogram(W, W["kappa"], factored)
     for _ in range(args.warmup):
         oracle_sample(W)
     times = []
@@ -400,7 +412,7 @@ def run_reference(args):
     for _ in range(args.steps):
         s = oracle_sample(W)
         samples.append(s)
-        times.append(extrapolate(s, hist, W))
+        times.append(extrapolate(s, hist, W, factored))
     wall = time.perf_counter() - t_all
     t_job = float(np.mean(times))
     value = W["k"] / t_job
@@ -410,7 +422,8 @@ def run_reference(args):
            "data": "synthetic", "impl": "reference",
            "config": {"workload": W["name"], "N": 1 << W["logN"], "q_limbs": W["L"],
                       "special_primes": W["K"], "dnum": W["dnum"], "n": W["n"], "d": W["d"],
-                      "k": W["k"], "kappa": W["kappa"]},
+                      "k": W["k"], "kappa": W["kappa"],
+                      "layout": "factored" if factored else "mccp"},
            "cpu_baseline": {"value": round(value, 4), "unit": "SNPs/s", "cores": 1,
                             "kind": "oracle",
                             "sample": "per step: one key switch, one tensor, one encryption at "
@@ -427,6 +440,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwhe", choices=["gwhe", "reference"])
+    ap.add_argument("--layout", default="auto", choices=["auto", "mccp", "factored"],
+                    help="SNP-phase layout: S' = M S with M as a CCP matrix, or the "
+                         "factored S' = S - XA(X^T S) with S in CCP")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--micro-only", action="store_true",

@@ -203,7 +203,36 @@ int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int l, uint32_t
  * covariates (column 0 = intercept), k SNPs.  Input arrays may be host or
  * device pointers (detected per call). */
 int gwhe_job_create(gwhe_ctx* ctx, int n, int d, long k, gwhe_job** out);
+/* SNP-phase layout, both from eq. Sprime (section "Semi-Parallel GWAS with
+ * Homomorphic Encryption"):
+ *   GWHE_LAYOUT_MCCP      S' = M S, M = I - X (X^T X)^-1 X^T held as a CCP
+ *                         matrix (ceil(n / B) ciphertexts), S as n REP rows
+ *                         per batch at 4 limbs (Alg. 8, Alg. 11)
+ *   GWHE_LAYOUT_FACTORED  S' = S - (X (X^T X)^-1)(X^T S), the equation's second
+ *                         form: S as ONE CCP ciphertext per batch at 6 limbs,
+ *                         no n x n matrix; needs the right-rotation keys
+ *                         -2^i for 2^i < nb (see gwhe_job_rotation_steps)
+ *   GWHE_LAYOUT_AUTO      factored on rings with more than 8 limbs (deep
+ *                         enough for the fit), M-CCP below (split mode);
+ *                         M-CCP is bounded by the paper's 256-subject limit
+ *                         in spirit (section "Discussion"): its CCP matrix
+ *                         and n REP rows per batch grow with n^2
+ * Both layouts give the same tau = 2 M / nb SNPs per batch and the same
+ * outputs; the factored one needs the fit (no split mode). */
+#define GWHE_LAYOUT_AUTO 0
+#define GWHE_LAYOUT_MCCP 1
+#define GWHE_LAYOUT_FACTORED 2
+int gwhe_job_create_ex(gwhe_ctx* ctx, int n, int d, long k, int layout, gwhe_job** out);
 int gwhe_job_destroy(gwhe_job* job);
+/* out[8] = {M slots, nb, B blocks, tau SNPs per batch, H (CCP ciphertexts of
+ * M, 0 when factored), batches, layout (GWHE_LAYOUT_MCCP or _FACTORED), limbs
+ * with which a SNP batch is encrypted}. */
+int gwhe_job_info(const gwhe_job* job, long out[8]);
+/* The rotation steps whose Galois keys the job needs (pass them to
+ * gwhe_keygen, with conj = 1): 2^i for i < log2(M), plus -2^i for 2^i < nb in
+ * the factored layout.  *count = number of steps; steps may be NULL to query
+ * the count, else it must hold cap >= *count entries. */
+int gwhe_job_rotation_steps(const gwhe_job* job, int32_t* steps, int cap, int* count);
 /* X (n x d, row-major) as CP, (X^T X)^-1 (d x d, row-major; client
  * pre-processing, section "Hessian Matrix Approximation") as CP, X^T as REP,
  * y (n) and beta0 = Enc(0), all at the top level (Alg. 9 / Alg. 11 inputs). */
@@ -222,7 +251,8 @@ int gwhe_snp_stats(gwhe_job* job, const double* S, long b0, long b1, int keep);
 int gwhe_decrypt_results(gwhe_job* job, double* num, double* den);
 /* Job ciphertexts for parity checks: which = 0 num, 1 denEven, 2 denOdd (index
  * = batch); 3 Dup(M_j) (index j); 4 Dup(w); 5 Dup(w z'); 6 z'; 7 beta; 8 the
- * CCP matrix M (index = ciphertext h); 9 z; 10 the masked weights w.  *view
+ * CCP matrix M (index = ciphertext h); 9 z; 10 the masked weights w;
+ * factored layout: 11 Dup(X_c), 12 Dup((X (X^T X)^-1)_c) (index c).  *view
  * is a new handle that does not own the device memory: destroy it with
  * gwhe_ct_destroy, and do not use it after the job is destroyed. */
 int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view);

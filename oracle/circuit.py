@@ -10,6 +10,13 @@ Slot layouts (M = N/2 slots, nb = next power of two >= n, B = M/nb blocks):
   REP row (section REP)      entry c repeated nb times: slot c*nb + t
   CCP matrix (Alg. 4)        column c in slots c*nb .. c*nb + nb - 1
   S batch (REP, complex)     row j of S_i: slot b*nb + t = S[j, 2b] + i S[j, 2b+1]
+  S batch (CCP, complex)     one ciphertext: slot b*nb + t = S[t, 2b] + i S[t, 2b+1]
+
+Two layouts of the SNP phase, both from eq. Sprime:
+  M-CCP     S' = M S with M = I - X A X^T held as a CCP matrix and S in REP rows
+            (Alg. 8; the first form of eq. Sprime, as in Alg. 11)
+  factored  S' = S - (X A)(X^T S) with S in CCP (the second form of eq. Sprime):
+            no n x n matrix, one SNP ciphertext per batch
 """
 from __future__ import annotations
 
@@ -30,6 +37,7 @@ ENC_DUPWZ = 0x303
 ENC_XTREP = 0x10000
 ENC_DUPM = 0x20000
 ENC_S = 0x1000000
+ENC_SCCP = 0x100000000
 
 SIGMA7_A = (-1.73496 / 8.0, 4.19407 / 8.0 ** 3, -5.43402 / 8.0 ** 5, 2.50739 / 8.0 ** 7)
 
@@ -37,6 +45,9 @@ BATCH_LEVEL = 4  # level at which a SNP batch enters (S', num, WS', WSS/WSC)
 # M = I - X A X^T is only needed at BATCH_LEVEL + 1 limbs (the source of the
 # Dup(M_j) masks); it is computed from X and A dropped to this level
 M_LEVEL = BATCH_LEVEL + 4
+# factored layout: a CCP SNP batch enters here and S' = S - (XA)(X^T S) leaves
+# at BATCH_LEVEL - 1, where the M-CCP layout's S' is (product, mask, product)
+FACT_LEVEL = BATCH_LEVEL + 2
 
 
 @dataclass
@@ -79,16 +90,21 @@ class Layout:
             raise ValueError("a column of nb slots does not fit one ciphertext")
 
 
-def rotation_steps(layout: Layout):
+def rotation_steps(layout: Layout, factored: bool = False):
     """All rotations the circuit uses: 2^i for i < log2(M) (ladders of Alg. 1,
-    4, 5, 7 all rotate by powers of two)."""
-    return [1 << i for i in range(layout.logN - 1)]
+    4, 5, 7 all rotate by powers of two); the factored layout's in-block
+    broadcast adds the right rotations -2^i for 2^i < nb."""
+    steps = [1 << i for i in range(layout.logN - 1)]
+    if factored:
+        steps += [-(1 << i) for i in range(int(math.log2(layout.nb)))]
+    return steps
 
 
 class Circuit:
-    def __init__(self, ev: OracleCKKS, layout: Layout):
+    def __init__(self, ev: OracleCKKS, layout: Layout, factored: bool = False):
         self.ev = ev
         self.lay = layout
+        self.factored = factored
         layout.check()
 
     # --------------------------------------------------------- primitives
@@ -204,6 +220,8 @@ class Circuit:
         self.y = self.encrypt_vector(y, ENC_Y)
         self.beta0 = self.encrypt_vector(np.zeros(1), ENC_BETA0)
         self.XtREP = []
+        if self.factored:
+            return  # X^T in REP only feeds the CCP matrix M
         for c in range(d):
             row = []
             for h in range(lay.H):
@@ -234,6 +252,23 @@ class Circuit:
         lay = self.lay
         return [self.encrypt_vector(z, ENC_S + i * lay.n + j, level=BATCH_LEVEL)
                 for j, z in enumerate(self.snp_batch_slots(S, i))]
+
+    def snp_batch_ccp_slots(self, S, i):
+        """CCP batch i (factored layout): slot b*nb + t = S[t, 2c] + i S[t, 2c+1]
+        with c = i*B + b the complex column (section "Complex Space")."""
+        lay = self.lay
+        n, k = S.shape
+        z = np.zeros(lay.M, complex)
+        for b in range(lay.B):
+            c0 = i * lay.tau + 2 * b
+            re = S[:, c0] if c0 < k else np.zeros(n)
+            im = S[:, c0 + 1] if c0 + 1 < k else np.zeros(n)
+            z[b * lay.nb:b * lay.nb + n] = re + 1j * im
+        return z
+
+    def encrypt_snp_batch_ccp(self, S, i):
+        return self.encrypt_vector(self.snp_batch_ccp_slots(S, i), ENC_SCCP + i,
+                                   level=FACT_LEVEL)
 
     # --------------------------------------------------------- covariate phase
     def fit(self, kappa: int):
@@ -279,10 +314,17 @@ class Circuit:
         zp = ev.sub(ev.drop(z, xaxtz.level), xaxtz)
         wzp = ev.mult(ev.drop(w_m, zp.level), zp)
         self.z, self.zp, self.w_m, self.wzp = z, zp, w_m, wzp
-        # eq. M: M = I - X A X^T via Alg. 3 (CP-MatMult) and Alg. 8 (CP-REP),
-        # from X and A dropped to M_LEVEL limbs
+        # X A via Alg. 3 (CP-MatMult) from X and A dropped to M_LEVEL limbs,
+        # each column duplicated into every block (Alg. 7)
         XA = [self.cp_matvec(self.X, ev.drop(self.A[r], M_LEVEL), d) for r in range(d)]
         dupXA = [self.duplicate(XA[r]) for r in range(d)]
+        if self.factored:
+            # second form of eq. Sprime: keep Dup((XA)_c) and Dup(X_c)
+            self.DupB = dupXA
+            self.DupX = [self.duplicate(ev.drop(self.X[c], FACT_LEVEL)) for c in range(d)]
+            self.make_dup_state()
+            return
+        # eq. M: M = I - X A X^T via Alg. 8 (CP-REP) on the duplicated columns
         self.Mct = []
         for h in range(lay.H):
             lv = dupXA[0].level
@@ -302,9 +344,9 @@ class Circuit:
         lb = BATCH_LEVEL
         if self.wzp.level < lb - 1:
             raise ValueError("depth exhausted before the SNP batches")
-        src = [ev.drop(m, lb + 1) for m in self.Mct]
         self.DupM = []
-        for j in range(lay.n):
+        src = [] if self.factored else [ev.drop(m, lb + 1) for m in self.Mct]
+        for j in range(0 if self.factored else lay.n):
             h, b = divmod(j, lay.B)
             mask = np.zeros(lay.M)
             mask[b * lay.nb:b * lay.nb + lay.n] = 1.0
@@ -332,12 +374,42 @@ class Circuit:
 
     # --------------------------------------------------------- per batch
     def snp_batch(self, Srow):
-        """Alg. 11 loop body for one batch: S' = sum_j Dup(M_j) S_ij (Alg. 8),
-        numerator = colSum(Dup(w z') S'), WSS, WSC, denEven/denOdd (the 1/2
+        """Alg. 11 loop body for one batch of the M-CCP layout:
+        S' = sum_j Dup(M_j) S_ij (Alg. 8), then the common body."""
+        Sp = self.mac_relin_rescale([(self.DupM[j], Srow[j]) for j in range(len(Srow))])
+        return self.batch_body(Sp)
+
+    def factored_sprime(self, Sct: Ct) -> Ct:
+        """Second form of eq. Sprime for one CCP batch at FACT_LEVEL:
+          U_c = Dup(X_c) S                       (product, one level)
+          T_c = colSum(U_c) masked to the block heads b*nb   (Alg. 5, one level)
+          R_c = T_c broadcast down its block: R += Rotate(R, -2^i), i < log2(nb)
+          S'  = S - sum_c Dup((XA)_c) R_c        (tensor sum, relin, rescale)
+        so slot b*nb + t of S' is S[t, .] - sum_c (XA)[t, c] (X^T S)[c, .]."""
+        ev, lay = self.ev, self.lay
+        d = len(self.DupX)
+        heads = np.zeros(lay.M)
+        heads[::lay.nb] = 1.0
+        R = []
+        for c in range(d):
+            u = self.colsum(ev.mult(self.DupX[c], Sct))
+            r = ev.mul_mask(u, heads)
+            for i in range(int(math.log2(lay.nb))):
+                r = ev.add(r, ev.rotate(r, -(1 << i)))
+            R.append(r)
+        lv = R[0].level
+        P = self.mac_relin_rescale([(ev.drop(self.DupB[c], lv), R[c]) for c in range(d)])
+        return ev.sub(ev.drop(Sct, P.level), P)
+
+    def snp_batch_factored(self, Sct: Ct):
+        """Alg. 11 loop body for one CCP batch of the factored layout."""
+        return self.batch_body(self.factored_sprime(Sct))
+
+    def batch_body(self, Sp: Ct):
+        """numerator = colSum(Dup(w z') S'), WSS, WSC, denEven/denOdd (the 1/2
         kept as scale metadata), colSum of each."""
         ev = self.ev
         lb = BATCH_LEVEL
-        Sp = self.mac_relin_rescale([(self.DupM[j], Srow[j]) for j in range(len(Srow))])
         num = self.colsum(ev.mult(self.DupWZ, Sp))
         ws = ev.mult(self.DupW, Sp)
         s1 = ev.drop(Sp, lb - 2)

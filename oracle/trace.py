@@ -65,26 +65,31 @@ class LevelTrace(OracleCKKS):
         return Ct(np.zeros_like(a.c), a.scale)
 
 
-def job_ks_histogram(W, kappa: int = 1):
+def job_ks_histogram(W, kappa: int = 1, factored: bool = False):
     """Key switches per level of one job of workload W (dict with logN, L,
     q0_bits, scale_bits, K, sp_bits, dnum, n, d, k): the covariate phase once,
     then the SNP-batch body once per batch (every batch issues the same
-    switches at the same levels).  Returns (histogram[65], fit_part, batch_part)."""
-    from .circuit import BATCH_LEVEL, Circuit, Layout
+    switches at the same levels), for the M-CCP or the factored layout.
+    Returns (histogram[65], fit_part, batch_part)."""
+    from .circuit import BATCH_LEVEL, FACT_LEVEL, Circuit, Layout
 
     ev = LevelTrace(logN=W["logN"], L=W["L"], q0_bits=W["q0_bits"],
                     scale_bits=W["scale_bits"], K=W["K"], sp_bits=W["sp_bits"],
                     dnum=W["dnum"], seed=0)
     lay = Layout(logN=W["logN"], n=W["n"], d=W["d"], k=W["k"])
     lay.check()
-    circ = Circuit(ev, lay)
+    circ = Circuit(ev, lay, factored=factored)
     n, d = W["n"], W["d"]
     X = np.zeros((n, d))
     X[:, 0] = 1.0
     circ.encrypt_inputs(X, np.eye(d), np.zeros(n))
     circ.fit(kappa)
     fit = ev.ks_hist.copy()
-    Srow = [ev.encrypt(np.zeros((BATCH_LEVEL, 1), np.uint64), 0, ev.delta) for _ in range(n)]
-    circ.snp_batch(Srow)
+    if factored:
+        circ.snp_batch_factored(ev.encrypt(np.zeros((FACT_LEVEL, 1), np.uint64), 0, ev.delta))
+    else:
+        Srow = [ev.encrypt(np.zeros((BATCH_LEVEL, 1), np.uint64), 0, ev.delta)
+                for _ in range(n)]
+        circ.snp_batch(Srow)
     batch = ev.ks_hist - fit
     return fit + batch * lay.batches, fit, batch

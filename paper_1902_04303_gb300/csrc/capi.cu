@@ -373,15 +373,41 @@ int gwhe_ntt_batch(gwhe_ctx* ctx, uint64_t* dev, int npoly, int nlimbs, int inve
   });
 }
 
-int gwhe_job_create(gwhe_ctx* ctx, int n, int d, long k, gwhe_job** out) {
+int gwhe_job_create_ex(gwhe_ctx* ctx, int n, int d, long k, int layout, gwhe_job** out) {
   if (!out) return GWHE_EINVAL;
   *out = nullptr;
   return guard(C(ctx), [&] {
     std::unique_ptr<gwhe_job> j(new gwhe_job());
     j->owner = ctx;
-    j->job.reset(job_create(C(ctx), n, d, k));
+    j->job.reset(job_create(C(ctx), n, d, k, layout));
     *out = j.release();
   });
+}
+
+int gwhe_job_create(gwhe_ctx* ctx, int n, int d, long k, gwhe_job** out) {
+  return gwhe_job_create_ex(ctx, n, d, k, GWHE_LAYOUT_AUTO, out);
+}
+
+int gwhe_job_info(const gwhe_job* job, long out[8]) {
+  if (!job || !out || !job->job) return GWHE_EINVAL;
+  const Job* j = job->job.get();
+  const Layout& L = j->lay;
+  const long v[8] = {L.M, L.nb, L.B, L.tau, j->factored ? 0 : L.H, L.batches,
+                     j->factored ? GWHE_LAYOUT_FACTORED : GWHE_LAYOUT_MCCP,
+                     j->factored ? kFactLevel : kBatchLevel};
+  for (int i = 0; i < 8; ++i) out[i] = v[i];
+  return GWHE_OK;
+}
+
+int gwhe_job_rotation_steps(const gwhe_job* job, int32_t* steps, int cap, int* count) {
+  if (!job || !count || !job->job) return GWHE_EINVAL;
+  const std::vector<int> s = job_rotation_steps(job->job.get());
+  *count = (int)s.size();
+  if (steps) {
+    if (cap < (int)s.size()) return GWHE_EINVAL;
+    for (size_t i = 0; i < s.size(); ++i) steps[i] = s[i];
+  }
+  return GWHE_OK;
 }
 
 int gwhe_job_destroy(gwhe_job* job) {
@@ -457,6 +483,14 @@ int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view) {
         break;
       case 9: src = j->z.get(); break;
       case 10: src = j->w_m.get(); break;
+      case 11:
+        need(index >= 0 && index < (long)j->DupX.size(), "no such Dup(X_c)");
+        src = j->DupX[index].get();
+        break;
+      case 12:
+        need(index >= 0 && index < (long)j->DupB.size(), "no such Dup((XA)_c)");
+        src = j->DupB[index].get();
+        break;
       default: break;
     }
     need(src != nullptr, "no such ciphertext");

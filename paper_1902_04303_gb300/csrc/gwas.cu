@@ -8,6 +8,7 @@
 //   REP row               entry c repeated nb times: slots c*nb .. c*nb+nb-1
 //   CCP matrix            column c in slots c*nb .. (Alg. 4)
 //   S batch (REP)         row j: slot b*nb + t = S[j, 2b] + i S[j, 2b+1]
+//   S batch (CCP)         one ciphertext: slot b*nb + t = S[t, 2b] + i S[t, 2b+1]
 // The op order below is the specification that the CPU oracle's circuit
 // follows as well; ciphertext bits depend on it (every key switch and rescale
 // rounds).
@@ -21,10 +22,15 @@ namespace gwhe {
 namespace {
 
 constexpr u64 kEncX = 0x100, kEncA = 0x200, kEncY = 0x300, kEncBeta0 = 0x301, kEncDupW = 0x302,
-              kEncDupWZ = 0x303, kEncXtRep = 0x10000, kEncDupM = 0x20000, kEncS = 0x1000000;
+              kEncDupWZ = 0x303, kEncXtRep = 0x10000, kEncDupM = 0x20000, kEncS = 0x1000000,
+              kEncSccp = 0x100000000ull;
 
 // mask kinds for the plaintext cache
-enum MaskKind { kMaskSlot = 1, kMaskPrefix = 2, kMaskBlock = 3, kMaskEye = 4 };
+enum MaskKind { kMaskSlot = 1, kMaskPrefix = 2, kMaskBlock = 3, kMaskEye = 4, kMaskHeads = 5 };
+
+// batches of the factored layout processed together (bounds the temporaries:
+// d products per batch at kFactLevel limbs)
+constexpr int kFactChunk = 64;
 
 // eq. sigma7 coefficients of x^1, x^3, x^5, x^7 (the printed c_k / 8^k)
 const double kSig[4] = {-1.73496 / 8.0, 4.19407 / 512.0, -5.43402 / 32768.0,
@@ -201,11 +207,23 @@ struct Eval {
   // Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks
   std::vector<int> dup_steps() { return pow2_steps(ilog2(lay.B), lay.nb); }
   // a one-ciphertext set holding a copy of a at level l (for the ladders)
-  CtSetPtr single(const Ct& a, int l) {
-    CtSetPtr s = set_new(c, 1, 2, l, l, a.scale);
-    for (int p = 0; p < 2; ++p)
-      GWHE_CUDA(cudaMemcpyAsync(s->d + (size_t)p * l * c->N, a.poly(p), sizeof(u64) * l * c->N,
-                                cudaMemcpyDeviceToDevice, c->stream));
+  CtSetPtr single(const Ct& a, int l) { return gather({&a}, l); }
+  // a set holding copies of the given ciphertexts (same scale) at level l
+  CtSetPtr gather(const std::vector<const Ct*>& src, int l) {
+    CtSetPtr s = set_new(c, (int)src.size(), 2, l, l, src[0]->scale);
+    for (size_t i = 0; i < src.size(); ++i) {
+      GWHE_REQUIRE(src[i]->l >= l && src[i]->scale == src[0]->scale, ST_ELEVEL,
+                   "gathered ciphertexts must reach the level and share the scale");
+      for (int p = 0; p < 2; ++p)
+        GWHE_CUDA(cudaMemcpyAsync(s->item((int)i) + (size_t)p * l * c->N, src[i]->poly(p),
+                                  sizeof(u64) * l * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return s;
+  }
+  // in-block broadcast from the block heads: v += Rotate(v, -2^i), i < log2(nb)
+  std::vector<int> bcast_steps() {
+    std::vector<int> s;
+    for (int i = 0; i < ilog2(lay.nb); ++i) s.push_back(-(1 << i));
     return s;
   }
 
@@ -284,12 +302,26 @@ Job::~Job() {
   if (DupM_store && c) dfree(c, DupM_store);
 }
 
-Job* job_create(Context* c, int n, int d, long k) {
+Job* job_create(Context* c, int n, int d, long k, int mode) {
   GWHE_REQUIRE(d >= 1 && d <= 64 && k >= 1, ST_EINVAL, "bad job shape");
+  GWHE_REQUIRE(mode == kLayoutAuto || mode == kLayoutMccp || mode == kLayoutFactored, ST_EINVAL,
+               "bad layout mode");
   Job* j = new Job();
   j->c = c;
   j->lay = make_layout(c->logN, n, d, k);
+  // auto: the factored layout whenever the ring can run the fit (it is the
+  // faster one at every cohort size measured and the only one past n = 256);
+  // M-CCP on rings without the fit's depth (split mode)
+  j->factored = mode == kLayoutFactored || (mode == kLayoutAuto && c->P.L > kMLevel);
   return j;
+}
+
+std::vector<int> job_rotation_steps(const Job* j) {
+  std::vector<int> s;
+  for (int i = 0; i < j->lay.logN - 1; ++i) s.push_back(1 << i);
+  if (j->factored)
+    for (int i = 0; i < ilog2(j->lay.nb); ++i) s.push_back(-(1 << i));
+  return s;
 }
 
 void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double* yp) {
@@ -300,8 +332,10 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
   const std::vector<double> X = to_host(c, Xp, (size_t)n * d), A = to_host(c, Ap, (size_t)d * d),
                             y = to_host(c, yp, n);
   // all inputs (X as CP, (X^T X)^-1 as CP, y, beta0 = 0, X^T as REP) in one
-  // batched encryption at the top level; encryption ids as in the spec
-  const int cnt = 2 * d + 2 + d * lay.H;
+  // batched encryption at the top level; encryption ids as in the spec.  The
+  // factored layout has no CCP matrix M and needs no X^T.
+  const int H = j->factored ? 0 : lay.H;
+  const int cnt = 2 * d + 2 + d * H;
   std::vector<double2> z((size_t)cnt * M, make_double2(0, 0));
   std::vector<u64> ids(cnt);
   int it = 0;
@@ -318,7 +352,7 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
   ++it;
   ids[it++] = kEncBeta0;
   for (int col = 0; col < d; ++col)
-    for (int h = 0; h < lay.H; ++h, ++it) {
+    for (int h = 0; h < H; ++h, ++it) {
       ids[it] = kEncXtRep + (u64)col * 4096 + h;
       for (int b = 0; b < lay.B; ++b) {
         const int s = h * lay.B + b;
@@ -346,7 +380,7 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
   j->y = in->view(it++);
   j->beta0 = in->view(it++);
   for (int col = 0; col < d; ++col)
-    for (int h = 0; h < lay.H; ++h) j->XtREP[col].push_back(in->view(it++));
+    for (int h = 0; h < H; ++h) j->XtREP[col].push_back(in->view(it++));
   j->sets.push_back(std::move(in));
 }
 
@@ -355,6 +389,8 @@ static void make_dup_state(Job* j, Eval& ev) {
   const Layout& lay = j->lay;
   const int lb = kBatchLevel;
   GWHE_REQUIRE(j->wzp->l >= lb - 1, ST_ELEVEL, "depth exhausted before the SNP batches");
+  j->DupM.clear();
+  if (!j->factored) {
   // Dup(M_j) for every column j: mask block (j mod B) of ciphertext j / B at
   // lb + 1 limbs (plaintext at scale q_last, rescale), then Alg. 7's ladder
   std::vector<CtPtr> src;
@@ -371,9 +407,9 @@ static void make_dup_state(Job* j, Eval& ev) {
   CtSetPtr dm = set_new(c, lay.n, 2, lb + 1, lb + 1, 1.0);
   set_mask(c, mi, src[0]->scale, ql, *dm, true);
   set_ladder(c, *dm, ev.dup_steps());
-  j->DupM.clear();
   for (int jj = 0; jj < lay.n; ++jj) j->DupM.push_back(dm->view(jj));
   j->sets.push_back(std::move(dm));
+  }
   CtSetPtr dw = ev.single(*j->w_m, lb - 1);
   set_ladder(c, *dw, ev.dup_steps());
   j->DupW = dw->view(0);
@@ -449,12 +485,29 @@ void job_fit(Job* j, int kappa) {
   j->zp = ev.sub(*zv, *xaxtz);
   CtPtr wmv = ev.view(*j->w_m, j->zp->l);
   j->wzp = ev.mult(*wmv, *j->zp);
-  // eq. M = I - X A X^T: Alg. 3 (CP-MatMult) then Alg. 8 (CP-REP-MatMult),
-  // from X and A dropped to kMLevel limbs
+  // X A: Alg. 3 (CP-MatMult) from X and A dropped to kMLevel limbs, every
+  // column duplicated into all blocks (Alg. 7)
   std::vector<CtPtr> Alow;
   for (int rr = 0; rr < d; ++rr) Alow.push_back(ev.view(*j->A[rr], kMLevel));
   CtSetPtr xa = ev.cp_matmul(j->X, Alow, d);
   set_ladder(c, *xa, ev.dup_steps());  // Duplicate(XA_r) for every r
+  if (j->factored) {
+    // second form of eq. Sprime: keep Dup((XA)_c) and Dup(X_c) at kFactLevel
+    GWHE_REQUIRE(j->X[0]->l >= kFactLevel, ST_ELEVEL, "need kFactLevel limbs for Dup(X_c)");
+    j->DupB.clear();
+    j->DupX.clear();
+    for (int rr = 0; rr < d; ++rr) j->DupB.push_back(xa->view(rr));
+    j->sets.push_back(std::move(xa));
+    std::vector<const Ct*> xs;
+    for (int cc = 0; cc < d; ++cc) xs.push_back(j->X[cc].get());
+    CtSetPtr dx = ev.gather(xs, kFactLevel);
+    set_ladder(c, *dx, ev.dup_steps());
+    for (int cc = 0; cc < d; ++cc) j->DupX.push_back(dx->view(cc));
+    j->sets.push_back(std::move(dx));
+    make_dup_state(j, ev);
+    return;
+  }
+  // eq. M = I - X A X^T: Alg. 8 (CP-REP-MatMult) on the duplicated columns
   const int l0 = xa->l;
   std::vector<CtPtr> dv, xv;
   for (int rr = 0; rr < d; ++rr) dv.push_back(xa->view(rr));
@@ -491,6 +544,7 @@ void job_set_fit_state(Job* j, const double* Mp, const double* wp, const double*
   const Layout& lay = j->lay;
   Eval ev{c, lay};
   const int n = lay.n, lb = kBatchLevel;
+  GWHE_REQUIRE(!j->factored, ST_EINVAL, "split mode needs the M-CCP layout");
   GWHE_REQUIRE(c->P.L >= lb, ST_ELEVEL, "need at least 4 limbs for the SNP batches");
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const std::vector<double> M = to_host(c, Mp, (size_t)n * n), w = to_host(c, wp, n),
@@ -507,56 +561,15 @@ void job_set_fit_state(Job* j, const double* Mp, const double* wp, const double*
   j->DupWZ = ev.encrypt_vec(dup(wz, 1, 0), kEncDupWZ, lb - 1, delta);
 }
 
-void job_snp_stats(Job* j, const double* S, long b0, long b1) {
+namespace {
+
+// the Alg. 11 loop body after S' (at kBatchLevel - 1 limbs) for batches
+// [b0, b0 + nbt): numerator = colSum(Dup(w z') S'), WS' = Dup(w) S',
+// WSS = WS' S', WSC = WS' conj(S'), denEven/denOdd (the 1/2 as scale
+// metadata), colSum of each; the outputs become the job's kept results
+void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
   Context* c = j->c;
-  const Layout& lay = j->lay;
-  Eval ev{c, lay};
-  const int n = lay.n, lb = kBatchLevel, N = c->N;
-  GWHE_REQUIRE((int)j->DupM.size() == n && j->DupW && j->DupWZ, ST_EINVAL,
-               "covariate phase not done (fit or set the fit state first)");
-  GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
-  if (b0 == b1) return;
-  const double delta = std::ldexp(1.0, c->P.scale_bits);
-  const bool dev = is_device_ptr(S);
-  const double* Sd = S;
-  std::unique_ptr<Tmp> Sbuf;
-  if (!dev) {
-    Sbuf.reset(new Tmp(c, sizeof(double) * (size_t)n * lay.k));
-    GWHE_CUDA(cudaMemcpyAsync(Sbuf->p, S, sizeof(double) * (size_t)n * lay.k,
-                              cudaMemcpyHostToDevice, c->stream));
-    Sd = Sbuf->as<double>();
-  }
-  if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
-  const int nbt = (int)(b1 - b0);
-  // per batch: encode + encrypt the n REP rows, then the tensor sum of Alg. 8
-  CtSetPtr T3 = set_new(c, nbt, 3, lb, lb, 1.0);
-  {
-    Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
-    Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
-    std::vector<Ct> srow(n);
-    for (int jj = 0; jj < n; ++jj) {
-      srow[jj].ctx = c;
-      srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
-      srow[jj].cap = lb;
-      srow[jj].l = lb;
-      srow[jj].scale = delta;
-      srow[jj].owned = false;
-    }
-    std::vector<std::pair<const Ct*, const Ct*>> pairs;
-    for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
-    for (long bi = b0; bi < b1; ++bi) {
-      build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
-      encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
-      CtSet t = T3->slice((int)(bi - b0), 1, lb);
-      set_tensor_mac(c, pairs, n, t);
-      T3->scale = t.scale;
-    }
-  }
-  // the rest of the Alg. 11 loop body for all batches as sets
-  CtSetPtr Sp = set_new(c, nbt, 2, lb, lb, 1.0);
-  set_relin(c, *T3, *Sp);
-  set_rescale(c, *Sp);  // S' at lb - 1
-  T3.reset();
+  const int lb = kBatchLevel, nbt = Sp->cnt;
   std::vector<CtPtr> spv;
   for (int i = 0; i < nbt; ++i) spv.push_back(Sp->view(i));
   // numerator = colSum(Dup(w z') S')
@@ -610,6 +623,145 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
     j->out[b0 + i] = {num->view(i), D->view(i), D->view(nbt + i)};
   j->sets.push_back(std::move(num));
   j->sets.push_back(std::move(D));
+}
+
+// M-CCP layout: per batch encode + encrypt the n REP rows, then the tensor
+// sum of Alg. 8 (S' = sum_j Dup(M_j) S_ij), relinearise and rescale
+CtSetPtr sprime_mccp(Job* j, const double* Sd, long b0, long b1) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  const int n = lay.n, lb = kBatchLevel, N = c->N;
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  const int nbt = (int)(b1 - b0);
+  CtSetPtr T3 = set_new(c, nbt, 3, lb, lb, 1.0);
+  {
+    Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
+    Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
+    std::vector<Ct> srow(n);
+    for (int jj = 0; jj < n; ++jj) {
+      srow[jj].ctx = c;
+      srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
+      srow[jj].cap = lb;
+      srow[jj].l = lb;
+      srow[jj].scale = delta;
+      srow[jj].owned = false;
+    }
+    std::vector<std::pair<const Ct*, const Ct*>> pairs;
+    for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
+    for (long bi = b0; bi < b1; ++bi) {
+      build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
+      encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
+      CtSet t = T3->slice((int)(bi - b0), 1, lb);
+      set_tensor_mac(c, pairs, n, t);
+      T3->scale = t.scale;
+    }
+  }
+  CtSetPtr Sp = set_new(c, nbt, 2, lb, lb, 1.0);
+  set_relin(c, *T3, *Sp);
+  set_rescale(c, *Sp);  // S' at lb - 1
+  return Sp;
+}
+
+// factored layout (second form of eq. Sprime) for batches [b0, b1):
+//   S_i = Enc(CCP batch i) at kFactLevel limbs
+//   U_ic = Dup(X_c) S_i; colSum (Alg. 5) puts (X^T S_i)[c, .] at the block heads
+//   R_ic = U_ic masked to the heads, broadcast down the block (right ladder)
+//   S'_i = S_i - sum_c Dup((XA)_c) R_ic   (tensor sum, relinearise, rescale)
+CtSetPtr sprime_factored(Job* j, Eval& ev, const double* Sd, long b0, long b1) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  const int d = lay.d, lf = kFactLevel, lb = kBatchLevel;
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  const int nbt = (int)(b1 - b0);
+  CtSetPtr Sset = set_new(c, nbt, 2, lf, lf, delta);
+  {
+    Tmp z(c, sizeof(double2) * (size_t)nbt * lay.M);
+    build_snp_ccp(c, Sd, lay.n, lay.k, b0 * lay.tau, nbt, lay.tau, lay.nb, lay.B, lay.M,
+                  z.as<double2>());
+    encrypt_slots(c, z.as<double2>(), nbt, delta, lf, kEncSccp + (u64)b0, Sset->d, lf);
+  }
+  std::vector<CtPtr> sv;
+  for (int i = 0; i < nbt; ++i) sv.push_back(Sset->view(i));
+  // U = Dup(X_c) S_i for all (i, c), item i d + c
+  CtSetPtr U = set_new(c, nbt * d, 2, lf, lf, 1.0);
+  {
+    std::vector<std::pair<const Ct*, const Ct*>> pr;
+    for (int i = 0; i < nbt; ++i)
+      for (int cc = 0; cc < d; ++cc) pr.push_back({j->DupX[cc].get(), sv[i].get()});
+    set_mult(c, pr, *U);
+  }
+  set_ladder(c, *U, ev.colsum_steps());
+  // keep the block heads, then broadcast them down their blocks
+  const int lu = U->l;
+  const double ql = (double)c->mod[lu - 1];
+  auto heads = ev.slots_zero();
+  for (int b = 0; b < lay.B; ++b) heads[b * lay.nb] = make_double2(1, 0);
+  const u64* hp = mask_pt(c, kMaskHeads, lay.nb, lu, ql, heads);
+  std::vector<MaskItem> mi;
+  for (int it = 0; it < nbt * d; ++it) mi.push_back(MaskItem{U->item(it), U->cap, hp});
+  CtSetPtr R = set_new(c, nbt * d, 2, lu, lu, 1.0);
+  set_mask(c, mi, U->scale, ql, *R, true);
+  U.reset();
+  set_ladder(c, *R, ev.bcast_steps());
+  // S'_i = S_i - sum_c Dup((XA)_c) R_ic
+  const int lr = R->l;
+  std::vector<CtPtr> bv, rv;
+  for (int cc = 0; cc < d; ++cc) bv.push_back(ev.view(*j->DupB[cc], lr));
+  std::vector<std::pair<const Ct*, const Ct*>> pairs;
+  for (int i = 0; i < nbt; ++i)
+    for (int cc = 0; cc < d; ++cc) {
+      rv.push_back(R->view(i * d + cc));
+      pairs.push_back({bv[cc].get(), rv.back().get()});
+    }
+  CtSetPtr T3 = set_new(c, nbt, 3, lr, lr, 1.0);
+  set_tensor_mac(c, pairs, d, *T3);
+  R.reset();
+  CtSetPtr P = set_new(c, nbt, 2, lr, lr, 1.0);
+  set_relin(c, *T3, *P);
+  T3.reset();
+  set_rescale(c, *P);
+  GWHE_REQUIRE(P->l == lb - 1, ST_ELEVEL, "factored S' must leave at kBatchLevel - 1 limbs");
+  CtSetPtr Sp = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
+  Ct sa = Sset->slice(0, nbt, lb - 1).all(), pa = P->all(), oa = Sp->all();
+  op_addsub(c, sa, pa, oa, true);
+  Sp->scale = Sset->scale;
+  return Sp;
+}
+
+}  // namespace
+
+void job_snp_stats(Job* j, const double* S, long b0, long b1) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  Eval ev{c, lay};
+  const int n = lay.n;
+  if (j->factored)
+    GWHE_REQUIRE((int)j->DupX.size() == lay.d && (int)j->DupB.size() == lay.d && j->DupW &&
+                     j->DupWZ,
+                 ST_EINVAL, "covariate phase not done (fit first)");
+  else
+    GWHE_REQUIRE((int)j->DupM.size() == n && j->DupW && j->DupWZ, ST_EINVAL,
+                 "covariate phase not done (fit or set the fit state first)");
+  GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
+  if (b0 == b1) return;
+  const bool dev = is_device_ptr(S);
+  const double* Sd = S;
+  std::unique_ptr<Tmp> Sbuf;
+  if (!dev) {
+    Sbuf.reset(new Tmp(c, sizeof(double) * (size_t)n * lay.k));
+    GWHE_CUDA(cudaMemcpyAsync(Sbuf->p, S, sizeof(double) * (size_t)n * lay.k,
+                              cudaMemcpyHostToDevice, c->stream));
+    Sd = Sbuf->as<double>();
+  }
+  if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
+  if (!j->factored) {
+    batch_body(j, ev, sprime_mccp(j, Sd, b0, b1), b0);
+    return;
+  }
+  for (long c0 = b0; c0 < b1; c0 += kFactChunk) {
+    const long c1 = std::min(b1, c0 + kFactChunk);
+    batch_body(j, ev, sprime_factored(j, ev, Sd, c0, c1), c0);
+  }
 }
 
 void job_decrypt(Job* j, double* num, double* den) {

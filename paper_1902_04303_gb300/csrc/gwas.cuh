@@ -24,6 +24,16 @@ constexpr int kBatchLevel = 4;  // limbs with which a SNP batch enters the loop
 // M = I - X A X^T is needed only at kBatchLevel + 1 limbs (the Dup(M_j) source):
 // it is computed from X and A dropped to this level
 constexpr int kMLevel = kBatchLevel + 4;
+// factored layout: a CCP SNP batch enters with this many limbs; S' = S - (XA)(X^T S)
+// (product, mask, product) leaves at kBatchLevel - 1 like the M-CCP layout's S'
+constexpr int kFactLevel = kBatchLevel + 2;
+
+// SNP-phase layouts (both from eq. Sprime): M-CCP = S' = M S with M held as a
+// CCP matrix and S as n REP rows per batch; factored = S' = S - (XA)(X^T S)
+// with one CCP ciphertext per batch and no n x n matrix.  Auto picks the
+// factored layout on rings deep enough for the fit (more than kMLevel limbs)
+// and M-CCP otherwise (split mode).
+enum LayoutMode { kLayoutAuto = 0, kLayoutMccp = 1, kLayoutFactored = 2 };
 
 struct Job {
   Context* c = nullptr;
@@ -32,15 +42,19 @@ struct Job {
   std::vector<std::vector<CtPtr>> XtREP;  // [d][H]
   CtPtr y, beta0, beta, z, zp, w_m, wzp;
   std::vector<CtPtr> Mct;                 // [H]
-  std::vector<CtPtr> DupM;                // [n]
+  std::vector<CtPtr> DupM;                // [n]      (M-CCP)
+  std::vector<CtPtr> DupX, DupB;          // [d] Dup(X_c), Dup((XA)_c) (factored)
   CtPtr DupW, DupWZ;
+  bool factored = false;
   std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd (views)
   std::vector<CtSetPtr> sets;             // storage behind the views above
   u64* DupM_store = nullptr;              // unused (kept zero)
   ~Job();
 };
 
-Job* job_create(Context* c, int n, int d, long k);
+Job* job_create(Context* c, int n, int d, long k, int mode = kLayoutAuto);
+// rotation steps whose keys the job needs
+std::vector<int> job_rotation_steps(const Job* j);
 void job_encrypt_inputs(Job* j, const double* X, const double* A, const double* y);
 void job_fit(Job* j, int kappa);
 void job_set_fit_state(Job* j, const double* M, const double* w, const double* wz);

@@ -817,6 +817,24 @@ __global__ void k_build_snp_rep(const double* __restrict__ S, int n, long k, lon
   z[gid] = make_double2(re, im);
 }
 
+// CCP SNP batches (factored layout): batch i of count, slot b*nb + t =
+// S[t, c] + i S[t, c + 1] with c = k0 + i*tau + 2b, zero for t >= n or c >= k
+__global__ void k_build_snp_ccp(const double* __restrict__ S, int n, long k, long k0, int count,
+                                int tau, int nb, int B, int M, double2* __restrict__ z) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (size_t)count * M) return;
+  const size_t i = gid / M;
+  const int s = (int)(gid - i * M);
+  const int b = s / nb, t = s - b * nb;
+  const long col = k0 + (long)i * tau + 2L * b;
+  double re = 0.0, im = 0.0;
+  if (b < B && t < n) {
+    if (col < k) re = S[(size_t)t * k + col];
+    if (col + 1 < k) im = S[(size_t)t * k + col + 1];
+  }
+  z[gid] = make_double2(re, im);
+}
+
 inline unsigned blocks_for(size_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -1178,6 +1196,15 @@ void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, 
                    double2* z) {
   ProfScope ps(c, PROF_ELEMWISE, 16.0 * n * M);
   k_build_snp_rep<<<blocks_for((size_t)n * M), kThreads, 0, c->stream>>>(S, n, k, k0, nb, B, M, z);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void build_snp_ccp(Context* c, const double* S, int n, long k, long k0, int count, int tau, int nb,
+                   int B, int M, double2* z) {
+  ProfScope ps(c, PROF_ELEMWISE, 16.0 * (double)count * M);
+  if (count == 0) return;
+  k_build_snp_ccp<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(S, n, k, k0, count,
+                                                                             tau, nb, B, M, z);
   GWHE_LAUNCHED(c, 1);
 }
 

@@ -106,5 +106,9 @@ void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m);
 // S[j, k0 + 2b] + i S[j, k0 + 2b + 1] (zero beyond k)
 void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, int B, int M,
                    double2* z);
+// count CCP SNP batches from k0 (tau SNPs each): slot b*nb + t of batch i =
+// S[t, k0 + i tau + 2b] + i S[t, k0 + i tau + 2b + 1]
+void build_snp_ccp(Context* c, const double* S, int n, long k, long k0, int count, int tau, int nb,
+                   int B, int M, double2* z);
 
 }  // namespace gwhe

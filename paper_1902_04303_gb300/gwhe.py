@@ -86,6 +86,9 @@ _SIGS = {
     "gwhe_keyswitch_noalloc": [_vp, _vp, _i, _u32, _vp],
     "gwhe_ntt_batch": [_vp, _vp, _i, _i, _i],
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
+    "gwhe_job_create_ex": [_vp, _i, _i, _l, _i, ctypes.POINTER(_vp)],
+    "gwhe_job_info": [_vp, ctypes.POINTER(_l)],
+    "gwhe_job_rotation_steps": [_vp, ctypes.POINTER(ctypes.c_int32), _i, ctypes.POINTER(_i)],
     "gwhe_job_destroy": [_vp],
     "gwhe_encrypt_inputs": [_vp, _vp, _vp, _vp],
     "gwhe_fit_covariates": [_vp, _i],
@@ -441,17 +444,35 @@ class Context:
         self._c(lib().gwhe_ntt_batch(self.h, _ptr(dev), npoly, nlimbs, 1 if inverse else 0))
 
 
-class Job:
-    """An encrypted semi-parallel GWAS job (Alg. 11) on a context."""
+LAYOUTS = {"auto": 0, "mccp": 1, "factored": 2}
 
-    def __init__(self, ctx: Context, n, d, k):
+
+class Job:
+    """An encrypted semi-parallel GWAS job (Alg. 11) on a context.  layout:
+    "mccp" (S' = M S, M as a CCP matrix, S in REP rows), "factored"
+    (S' = S - XA(X^T S), S in CCP) or "auto" (factored on rings deep enough
+    for the fit, M-CCP otherwise)."""
+
+    def __init__(self, ctx: Context, n, d, k, layout="auto"):
         self.ctx = ctx
         self.n, self.d, self.k = n, d, k
         h = _vp()
-        ctx._c(lib().gwhe_job_create(ctx.h, n, d, k, ctypes.byref(h)))
+        ctx._c(lib().gwhe_job_create_ex(ctx.h, n, d, k, LAYOUTS[layout], ctypes.byref(h)))
         self.h = h
-        self.layout = layout(ctx.logN, n, k)
+        info = (_l * 8)()
+        ctx._c(lib().gwhe_job_info(h, info))
+        keys = ["M", "nb", "B", "tau", "H", "batches", "layout", "batch_limbs"]
+        self.layout = {kk: int(v) for kk, v in zip(keys, info)}
+        self.factored = self.layout["layout"] == LAYOUTS["factored"]
         ctx._children.add(self)
+
+    def rotation_steps(self):
+        """rotation steps whose Galois keys the job needs (with conjugation)."""
+        cnt = _i(0)
+        self.ctx._c(lib().gwhe_job_rotation_steps(self.h, None, 0, ctypes.byref(cnt)))
+        out = (ctypes.c_int32 * cnt.value)()
+        self.ctx._c(lib().gwhe_job_rotation_steps(self.h, out, cnt.value, ctypes.byref(cnt)))
+        return [int(v) for v in out]
 
     def close(self):
         if getattr(self, "h", None) and getattr(self.ctx, "h", None):

@@ -51,7 +51,7 @@ def test_job_circuit_bit_exact(g):
     steps = rotation_steps(lay)
     ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
     ctx.keygen(rot_steps=steps, conj=True)
-    job = g.Job(ctx, n, d, k)
+    job = g.Job(ctx, n, d, k, layout="mccp")
     ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
     job.fit(1)
@@ -116,7 +116,7 @@ def test_job_paper_shape_accuracy(g):
     ctx = g.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
                     W["dnum"], seed=W["seed"])
     ctx.keygen(rot_steps=[1 << i for i in range(W["logN"] - 1)], conj=True)
-    job = g.Job(ctx, W["n"], W["d"], W["k"])
+    job = g.Job(ctx, W["n"], W["d"], W["k"], layout="mccp")
     assert job.layout["tau"] == 256 and job.layout["batches"] == 42 and job.layout["H"] == 2
     ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
@@ -134,6 +134,7 @@ def test_job_rejects_missing_state_and_depth(g):
     ctx = g.Context(10, 4, K=2, dnum=2, seed=1)
     ctx.keygen(rot_steps=[1 << i for i in range(9)], conj=True)
     job = g.Job(ctx, 16, 3, 40)
+    assert not job.factored  # four limbs: split-mode layout
     S = np.zeros((16, 40))
     with pytest.raises(g.GwheError):
         job.snp_stats(S)  # no covariate phase yet
@@ -142,3 +143,87 @@ def test_job_rejects_missing_state_and_depth(g):
     with pytest.raises(g.GwheError) as e:
         job.fit(1)  # four limbs cannot hold the fit
     assert e.value.code == -3
+
+
+def test_factored_layout_bit_exact(g):
+    """Factored layout (second form of eq. Sprime, S as one CCP ciphertext per
+    batch): Dup(X_c), Dup((XA)_c) and every batch output equal the oracle's
+    factored circuit bit for bit, with the key switches of its level trace."""
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 12
+    n, d, k = 16, 3, 100  # two batches of 64 SNPs, the second ragged
+    data = make_gwas(n, d, k, seed=6)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(logN, n, d, k)
+    steps = rotation_steps(lay, factored=True)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    job = g.Job(ctx, n, d, k, layout="factored")
+    assert job.factored and sorted(job.rotation_steps()) == sorted(steps)
+    assert job.layout["H"] == 0 and job.layout["batch_limbs"] == 6
+    ctx.keygen(rot_steps=steps, conj=True)
+    ks0 = ctx.ks_histogram().copy()
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    W = dict(logN=logN, L=L, q0_bits=60, scale_bits=40, K=K, sp_bits=60, dnum=dnum, n=n, d=d,
+             k=k)
+    want, _, _ = job_ks_histogram(W, 1, factored=True)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want)
+    o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
+    o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
+    c = Circuit(o, lay, factored=True)
+    c.encrypt_inputs(data.X, A, data.y)
+    c.fit(kappa=1)
+    for cc in range(d):
+        assert np.array_equal(job.ct(11, cc).export(), c.DupX[cc].c), cc
+        assert np.array_equal(job.ct(12, cc).export(), c.DupB[cc].c), cc
+    assert np.array_equal(job.ct(4).export(), c.DupW.c)
+    assert np.array_equal(job.ct(5).export(), c.DupWZ.c)
+    for bi in range(lay.batches):
+        want = c.snp_batch_factored(c.encrypt_snp_batch_ccp(data.S, bi))
+        for which in range(3):
+            assert np.array_equal(job.ct(which, bi).export(), want[which].c), (bi, which)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, k)
+
+
+def test_factored_layout_paper_shape(g):
+    """The paper's shape through the factored layout: 42 CCP batches, the same
+    decrypted statistics within tolerance, key switches as the trace says."""
+    W = WORKLOADS["paper-n245"]
+    data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"])
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                    W["dnum"], seed=W["seed"])
+    job = g.Job(ctx, W["n"], W["d"], W["k"], layout="factored")
+    ctx.keygen(rot_steps=job.rotation_steps(), conj=True)
+    ks0 = ctx.ks_histogram().copy()
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    want, _, _ = job_ks_histogram(W, 1, factored=True)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, W["k"])
+
+
+def test_large_cohort_auto_factored(g):
+    """A cohort beyond the paper's 256-subject limit (n = 600, nb = 1024,
+    tau = 64 at N = 2^16): the automatic layout is the factored one and the
+    results meet the tolerances."""
+    W = dict(WORKLOADS["paper-n245"])
+    n, d, k = 600, 4, 1500
+    data = make_gwas(n, d, k, seed=77)
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                    W["dnum"], seed=78)
+    job = g.Job(ctx, n, d, k)
+    assert job.factored and job.layout["tau"] == 64 and job.layout["batches"] == 24
+    ctx.keygen(rot_steps=job.rotation_steps(), conj=True)
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, k)

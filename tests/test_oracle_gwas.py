@@ -169,3 +169,78 @@ def test_batch_key_switch_count_closed_form(n):
     assert batch.sum() == 6 + 3 * int(math.log2(nb))
     # every batch switch happens at or below the batch entry level
     assert batch[5:].sum() == 0
+
+
+@pytest.mark.parametrize("n,d", [(16, 3), (245, 5), (1000, 6)])
+def test_factored_batch_key_switch_count_closed_form(n, d):
+    """The factored layout adds, per batch, d products, d column sums and d
+    in-block broadcasts of log2(nb) rotations each, and one relinearised
+    tensor sum: d + 2 d log2(nb) + 1 switches, then the body shared with the
+    M-CCP layout (5 + 3 log2(nb): four relinearisations, the conjugation,
+    three column sums); per level d at 6 limbs, d log2(nb) at 5, d log2(nb)
+    + 1 at 4."""
+    W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=d,
+             k=50000)
+    _, fit_f, batch_f = job_ks_histogram(W, 1, factored=True)
+    lg = int(math.log2(1 << math.ceil(math.log2(n))))
+    assert batch_f.sum() == (d + 2 * d * lg + 1) + (5 + 3 * lg)
+    assert batch_f[6] == d and batch_f[5] == d * lg and batch_f[4] == d * lg + 1
+    assert batch_f[7:].sum() == 0  # the CCP batch enters at 6 limbs
+
+
+def test_sprime_forms_agree(data):
+    """eq. Sprime: M S = S - X (X^T X)^-1 X^T S, and the packed complex batch
+    of the factored layout carries two SNP columns per slot unchanged."""
+    X, y, S = data.X, data.y, data.S
+    A = gwas_fp64.xtx_inv(X)
+    Mm = np.eye(X.shape[0]) - X @ A @ X.T
+    assert np.max(np.abs(Mm @ S - (S - (X @ A) @ (X.T @ S)))) < 1e-10
+    Sc = S[:, 0::2][:, : S.shape[1] // 2] + 1j * S[:, 1::2][:, : S.shape[1] // 2]
+    Pc = Mm @ Sc
+    assert np.allclose(Pc.real, Mm @ S[:, 0::2][:, : S.shape[1] // 2])
+    assert np.allclose(Pc.imag, Mm @ S[:, 1::2][:, : S.shape[1] // 2])
+
+
+def test_encrypted_factored_circuit_matches_o2():
+    """the factored layout (second form of eq. Sprime, S in CCP) over O1
+    decrypts to O2 within the acceptance tolerances, with the key switches
+    the level trace predicts."""
+    logN, n, d, k = 10, 16, 3, 100
+    dat = make_gwas(n, d, k, seed=6)
+    A = gwas_fp64.xtx_inv(dat.X)
+    o = OracleCKKS(logN=logN, L=21, K=7, dnum=3, seed=12)
+    lay = Layout(logN, n, d, k)
+    o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay, factored=True)]
+             + [galois_conj(logN)])
+    hist = np.zeros(65, np.int64)
+    real_ks = o.keyswitch
+
+    def counting_ks(x, key_id):
+        hist[x.shape[0]] += 1
+        return real_ks(x, key_id)
+
+    o.keyswitch = counting_ks
+    c = Circuit(o, lay, factored=True)
+    c.encrypt_inputs(dat.X, A, dat.y)
+    c.fit(kappa=1)
+    assert not c.XtREP and not c.DupM
+    nums, dens = [], []
+    for i in range(lay.batches):
+        Sct = c.encrypt_snp_batch_ccp(dat.S, i)
+        num, de, do = c.snp_batch_factored(Sct)
+        a, b = c.extract(num, de, do, i)
+        nums.append(a)
+        dens.append(b)
+    num = np.concatenate(nums)
+    den = np.concatenate(dens)
+    W = dict(logN=logN, L=21, q0_bits=60, scale_bits=40, K=7, sp_bits=60, dnum=3, n=n, d=d, k=k)
+    want, _, _ = job_ks_histogram(W, 1, factored=True)
+    assert np.array_equal(hist, want)
+    ref = gwas_fp64.semi_parallel_fp64(dat.X, dat.y, dat.S, kappa=1, A=A)
+    ok = np.abs(ref["den"]) > 1e-6
+    assert np.max(np.abs(den[~ok]), initial=0.0) < 1e-4
+    b = num[ok] / den[ok]
+    assert np.max(np.abs(b - ref["b"][ok])) < 5e-3
+    dl = np.abs(gwas_fp64.neglog10p(b, 1 / den[ok]) - gwas_fp64.neglog10p(ref["b"][ok],
+                                                                          ref["err"][ok]))
+    assert np.max(dl) < 0.05
