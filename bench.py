@@ -100,6 +100,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# GB300: 152 SMs, four warp schedulers each issuing one warp instruction per
+# clock.  The butterfly (Shoup product + Harvey corrections) takes
+# WARP_INSTR_PER_BFLY warp instructions per 32 butterflies (one per lane),
+# counted by ncu (smsp__inst_executed.sum) on the register-only probe.
+NUM_SMS = 152
+WARP_INSTR_PER_BFLY = 24.0
+
+
+def alu_peak_gbfly(sm_mhz):
+    """issue-limited butterfly rate (G/s) at the given SM clock."""
+    return NUM_SMS * 4 * sm_mhz * 1e6 * 32.0 / WARP_INSTR_PER_BFLY / 1e9
+
+
 def client_preprocess(X):
     """Client-side plaintext pre-processing of the paper (section 'Hessian
     Matrix Approximation'): (X^T X)^-1, computed before encryption."""
@@ -157,9 +170,13 @@ def run_gpu(args):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            # NVTX range around each timed job: profilers can select exactly
+            # these launches (ncu --nvtx --nvtx-include "gwas_job/")
+            torch.cuda.nvtx.range_push("gwas_job")
             e0.record(stream)
             out = step(src)
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         barrier()
@@ -208,6 +225,23 @@ def run_gpu(args):
             "launch_groups": cnt_d, "ms_per_step": round(ms_d, 3),
             "share_of_step": round(ms_d / sum(v[0] for v in prof.values()), 3),
             "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+    if dom == "ntt":
+        # the NTT is bound by 64-bit modular arithmetic: report it against the
+        # butterfly issue ceiling (unit counts x clock / instructions per
+        # butterfly), with the register-only probe and the HBM view beside it
+        bfly = by_d / 16.0 * (W["logN"] / 2.0)  # 16 B and N/2 log2 N butterflies per limb row
+        ach_b = bfly / (ms_d / 1e3) / 1e9
+        probe, _ = ctx.probe_butterflies()
+        clk_mhz = clk.summary().get("sm_max_mhz") or 2070.0
+        peak_b = alu_peak_gbfly(clk_mhz)
+        roof.update({"bound": "alu", "achieved": round(ach_b, 2), "unit": "Gbutterfly/s",
+                     "peak": round(peak_b, 2), "frac": round(ach_b / peak_b, 4),
+                     "peak_source": "derived: %d SMs x 4 schedulers x %.0f MHz / %.2f warp "
+                                    "instructions per 32 butterflies" %
+                                    (NUM_SMS, clk_mhz, WARP_INSTR_PER_BFLY),
+                     "probe_gbfly": round(probe / 1e9, 2),
+                     "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                                  "frac": round(achieved / hbm, 4)}})
     h2d = sum(host[nm].numel() * 8 for nm in host)
     d2h = 2 * W["k"] * 8
     out = {
@@ -279,6 +313,7 @@ def run_micro(ctx_stream, reps=3):
         ms.append(e0.elapsed_time(e1) / 2)  # per transform direction
     t_ntt = min(ms) / 1e3
     del x, ref
+    probe, probe_ms = ctx.probe_butterflies()
     # batched encoding of 245 REP-like slot vectors (one SNP batch)
     zb = torch.randint(0, 3, (245, ctx.M, 2), device="cuda", generator=g).to(torch.float64)
     ob = torch.empty((245, N), dtype=torch.int64, device="cuda")
@@ -312,6 +347,8 @@ def run_micro(ctx_stream, reps=3):
             "ntt_limb_per_s": round(rows / t_ntt, 1),
             "ntt_gbs_algorithmic": round(rows * N * 16 / t_ntt / 1e9, 1),
             "ntt_ms_3072_limbs": round(t_ntt * 1e3, 3),
+            "ntt_gbfly_per_s": round(rows * (N // 2) * W["logN"] / t_ntt / 1e9, 2),
+            "probe_gbfly_per_s": round(probe / 1e9, 2), "probe_ms": round(probe_ms, 3),
             "encode_ms_245": round(t_enc * 1e3, 3),
             "rotations": nct * len(steps),
             "keyswitch_per_s_level24": round(nct * len(steps) / t_ks, 1),

@@ -275,6 +275,14 @@ int gwhe_prof_enable(gwhe_ctx* ctx, int on);
  * Synchronises the stream. */
 int gwhe_prof_read(gwhe_ctx* ctx, double* ms, double* bytes, long* count);
 
+/* Arithmetic ceiling of the NTT butterfly: runs the transform's Cooley-Tukey
+ * butterfly (Shoup product + Harvey lazy corrections, section "Homomorphic
+ * Encryption" ring arithmetic) on register-resident residues on every SM, no
+ * memory traffic, rounds x 32 butterflies per thread.  *per_s = butterflies
+ * per second, *ms (optional) = the timed launch.  Measurement only; the
+ * paper has no counterpart. */
+int gwhe_probe_butterflies(gwhe_ctx* ctx, int rounds, double* per_s, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

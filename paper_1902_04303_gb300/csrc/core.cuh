@@ -84,6 +84,67 @@ __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wsh, u64 q) {
   return csub(shoup_lazy(x, w, wsh, q), q);
 }
 
+// Shoup product with an estimated quotient, for the NTT butterflies.  With
+// y = y1 2^32 + y0 and w' = s1 2^32 + s0 (w' = floor(w 2^64 / q)), the
+// quotient floor(y w' / 2^64) is estimated by e = y1 s1 + hi32(y1 s0) +
+// hi32(y0 s1): the dropped terms (the low words of the cross products and
+// y0 s0) sum to less than 3 * 2^64, so e is at most 2 below the exact quotient
+// and never above it.  The Shoup remainder y w - quotient q lies in [0, 2q)
+// for any y < 2^64, hence r = y w - e q lies in [0, 4q).  The low word is
+// formed as y w + e (2^64 - q) mod 2^64 with nq = 2^64 - q, from 32-bit
+// multiply-adds.
+__device__ __forceinline__ u64 shoup_est(u64 y, u64 w, u64 wsh, u64 nq) {
+  u64 r;
+  asm("{\n\t"
+      ".reg .u32 y0, y1, w0, w1, s0, s1, h1, h2, cy, e0, e1, n0, n1, r0, r1;\n\t"
+      ".reg .u64 e, t;\n\t"
+      "mov.b64 {y0, y1}, %1;\n\t"
+      "mov.b64 {w0, w1}, %2;\n\t"
+      "mov.b64 {s0, s1}, %3;\n\t"
+      "mov.b64 {n0, n1}, %4;\n\t"
+      "mul.hi.u32 h1, y1, s0;\n\t"
+      "mul.hi.u32 h2, y0, s1;\n\t"
+      "add.cc.u32 h1, h1, h2;\n\t"
+      "addc.u32 cy, 0, 0;\n\t"
+      "mov.b64 t, {h1, cy};\n\t"
+      "mad.wide.u32 e, y1, s1, t;\n\t"
+      "mov.b64 {e0, e1}, e;\n\t"
+      "mul.wide.u32 t, y0, w0;\n\t"
+      "mad.wide.u32 t, e0, n0, t;\n\t"
+      "mov.b64 {r0, r1}, t;\n\t"
+      "mad.lo.u32 r1, y0, w1, r1;\n\t"
+      "mad.lo.u32 r1, y1, w0, r1;\n\t"
+      "mad.lo.u32 r1, e0, n1, r1;\n\t"
+      "mad.lo.u32 r1, e1, n0, r1;\n\t"
+      "mov.b64 %0, {r0, r1};\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(y), "l"(w), "l"(wsh), "l"(nq));
+  return r;
+}
+
+// Harvey-style lazy butterflies on [0, 8q) (q < 2^60, so 8q < 2^63), with the
+// estimated Shoup product t in [0, 4q) and q4 = 4q:
+//   Cooley-Tukey:     a = x mod' 4q in [0, 4q); x = a + t, y = a - t + 4q
+//   Gentleman-Sande:  x = (x + y) mod' 4q; y = Shoup(x - y + 4q) in [0, 4q)
+// (mod' = one conditional subtraction).  Both keep every value below 8q.
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q4, u64 nq) {
+  const u64 a = csub(x, q4);
+  const u64 t = shoup_est(y, w, wsh, nq);
+  x = a + t;
+  y = a - t + q4;
+}
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q4, u64 nq) {
+  const u64 s = x + y;
+  const u64 d = x - y + q4;
+  x = csub(s, q4);
+  y = shoup_est(d, w, wsh, nq);
+}
+// [0, 8q) -> [0, q)
+__device__ __forceinline__ u64 reduce_8q(u64 x, u64 q) {
+  return csub(csub(csub(x, 4 * q), 2 * q), q);
+}
+
 // (hi 2^64 + lo) mod q: hi 2^64 = hi R (mod q) by a Shoup product, lo by a
 // 64-bit Barrett step (quotient estimate off by at most one).
 __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const DevMod& m) {

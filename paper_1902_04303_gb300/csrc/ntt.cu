@@ -4,8 +4,9 @@
 // with m = 2^s blocks of half-size t = N / 2m, block i pairs (a[j], a[j+t]) with
 // twiddle psi^brv(m+i); the output slot j holds a(psi^(2 brv(j) + 1)).  The
 // inverse runs the Gentleman-Sande butterflies in reverse stage order with the
-// inverse twiddles and multiplies by N^-1.  Both keep Harvey's lazy ranges
-// ([0, 4q) forward, [0, 2q) inverse) and return canonical residues in [0, q).
+// inverse twiddles and multiplies by N^-1.  Both keep lazy ranges below 8q
+// between stages (and between the two passes) and return canonical residues
+// in [0, q).
 //
 // Layout for N = 2^12..2^16: the row is viewed as a 2^LA x 2^LB matrix
 // (element h * 2^LB + c).  Pass A runs the first LA stages as independent
@@ -18,20 +19,6 @@
 #include "core.cuh"
 
 namespace gwhe {
-
-__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q, u64 twoq) {
-  const u64 a = csub(x, twoq);
-  const u64 t = shoup_lazy(y, w, wsh, q);
-  x = a + t;
-  y = a - t + twoq;
-}
-
-__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q, u64 twoq) {
-  const u64 s = x + y;
-  const u64 d = x - y + twoq;
-  x = csub(s, twoq);
-  y = shoup_lazy(d, w, wsh, q);
-}
 
 // One pass of the two-pass transform.  LS = log2 of this pass's sub-transform
 // size; the other dimension has 2^(LOGN-LS) entries.  PASSA: sub-transforms
@@ -54,7 +41,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
   const int limb = row - poly * rm.nl;
   const int u = rm.pidx[limb];
   u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * ((size_t)1 << LOGN);
-  const u64 q = tb.mod[u].q, twoq = 2 * q;
+  const u64 q = tb.mod[u].q, q4 = 4 * q, nq = 0 - q;
   const ulonglong2* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << LOGN);
 
   const int t = threadIdx.x;
@@ -84,7 +71,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
         const ulonglong2 w = __ldg(W + idx);
-        ct_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
 #pragma unroll
@@ -100,7 +87,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
         if (m & st) continue;
         const int idx = tw(sp, 16 * r + m);
         const ulonglong2 w = __ldg(W + idx);
-        ct_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
     __syncthreads();
@@ -111,7 +98,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
     for (int m = 0; m < 16; ++m) x[m] = sm[sidx(r + TPS * m)];
     if (!PASSA) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = csub(csub(x[m], twoq), q);
+      for (int m = 0; m < 16; ++m) x[m] = reduce_8q(x[m], q);
     }
   } else {
 #pragma unroll
@@ -127,7 +114,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
         if (m & st) continue;
         const int idx = tw(sp, 16 * r + m);
         const ulonglong2 w = __ldg(W + idx);
-        gs_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
     __syncthreads();
@@ -144,7 +131,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
         const ulonglong2 w = __ldg(W + idx);
-        gs_bfly(x[m], x[m + st], w.x, w.y, q, twoq);
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
     if (PASSA) {
@@ -168,7 +155,7 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
   const int limb = row - poly * rm.nl;
   const int u = rm.pidx[limb];
   u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * (size_t)N;
-  const u64 q = tb.mod[u].q, twoq = 2 * q;
+  const u64 q = tb.mod[u].q, q4 = 4 * q, nq = 0 - q;
   const ulonglong2* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << logN);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = base[i];
   __syncthreads();
@@ -181,11 +168,11 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
         const int idx = (1 << s) + i;
         const ulonglong2 w = W[idx];
-        ct_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q, twoq);
+        ct_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q4, nq);
       }
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) base[i] = csub(csub(sh[i], twoq), q);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) base[i] = reduce_8q(sh[i], q);
   } else {
     for (int s = logN - 1; s >= 0; --s) {
       const int lt = logN - 1 - s;
@@ -194,7 +181,7 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
         const int idx = (1 << s) + i;
         const ulonglong2 w = W[idx];
-        gs_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q, twoq);
+        gs_bfly(sh[j], sh[j + (1 << lt)], w.x, w.y, q4, nq);
       }
       __syncthreads();
     }

@@ -88,6 +88,8 @@ _SIGS = {
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
     "gwhe_job_create_ex": [_vp, _i, _i, _l, _i, ctypes.POINTER(_vp)],
     "gwhe_job_info": [_vp, ctypes.POINTER(_l)],
+    "gwhe_probe_butterflies": [_vp, _i, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)],
     "gwhe_job_rotation_steps": [_vp, ctypes.POINTER(ctypes.c_int32), _i, ctypes.POINTER(_i)],
     "gwhe_job_destroy": [_vp],
     "gwhe_encrypt_inputs": [_vp, _vp, _vp, _vp],
@@ -414,6 +416,13 @@ class Context:
         out = np.zeros((2, l, self.N), np.uint64)
         self._c(lib().gwhe_keyswitch(self.h, x, l, key_id, out))
         return out
+
+    def probe_butterflies(self, rounds=2048):
+        """butterflies/s of the NTT butterfly on register-resident data (the
+        arithmetic ceiling of a butterfly kernel) and the launch's ms."""
+        r, ms = ctypes.c_double(), ctypes.c_double()
+        self._c(lib().gwhe_probe_butterflies(self.h, rounds, ctypes.byref(r), ctypes.byref(ms)))
+        return r.value, ms.value
 
     def ks_histogram(self):
         out = np.zeros(65, np.int64)
