@@ -100,17 +100,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# GB300: 152 SMs, four warp schedulers each issuing one warp instruction per
-# clock.  The butterfly (Shoup product + Harvey corrections) takes
-# WARP_INSTR_PER_BFLY warp instructions per 32 butterflies (one per lane),
-# counted by ncu (smsp__inst_executed.sum) on the register-only probe.
+# GB300: 152 SMs of four sub-partitions, each with one fmaheavy pipe (the
+# only pipe that executes integer multiply-adds).  The butterfly (estimated
+# Shoup product + lazy corrections) occupies that pipe for
+# FMAHEAVY_CYCLES_PER_WARP_BFLY cycles per 32 butterflies (one per lane):
+# measured by ncu on the register-only probe (sm__pipe_fmaheavy_cycles_active
+# 95.05% of 38.3 M cycles per sub-partition for 1.05 M warp-butterflies each).
+# The probe's 23.8 warp instructions per warp-butterfly would allow more, so
+# the multiply-add pipe, not issue, bounds the transform.
 NUM_SMS = 152
-WARP_INSTR_PER_BFLY = 24.0
+FMAHEAVY_CYCLES_PER_WARP_BFLY = 34.7
 
 
 def alu_peak_gbfly(sm_mhz):
-    """issue-limited butterfly rate (G/s) at the given SM clock."""
-    return NUM_SMS * 4 * sm_mhz * 1e6 * 32.0 / WARP_INSTR_PER_BFLY / 1e9
+    """multiply-add-pipe bound of the butterfly rate (G/s) at the given SM clock."""
+    return NUM_SMS * 4 * sm_mhz * 1e6 * 32.0 / FMAHEAVY_CYCLES_PER_WARP_BFLY / 1e9
 
 
 def client_preprocess(X):
@@ -236,9 +240,9 @@ def run_gpu(args):
         peak_b = alu_peak_gbfly(clk_mhz)
         roof.update({"bound": "alu", "achieved": round(ach_b, 2), "unit": "Gbutterfly/s",
                      "peak": round(peak_b, 2), "frac": round(ach_b / peak_b, 4),
-                     "peak_source": "derived: %d SMs x 4 schedulers x %.0f MHz / %.2f warp "
-                                    "instructions per 32 butterflies" %
-                                    (NUM_SMS, clk_mhz, WARP_INSTR_PER_BFLY),
+                     "peak_source": "derived: %d SMs x 4 fmaheavy pipes x %.0f MHz x 32 / "
+                                    "%.1f pipe cycles per warp-butterfly (ncu, probe)" %
+                                    (NUM_SMS, clk_mhz, FMAHEAVY_CYCLES_PER_WARP_BFLY),
                      "probe_gbfly": round(probe / 1e9, 2),
                      "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                                   "frac": round(achieved / hbm, 4)}})
