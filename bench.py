@@ -376,7 +376,10 @@ def oracle_sample(W):
     t0 = time.perf_counter()
     o.pk_b = rnd(W["L"], 1).c[0]
     o.pk_a = rnd(W["L"], 1).c[0]
-    o.keys[0] = rng.integers(0, 2 ** 59, size=(W["dnum"], 2, W["L"] + W["K"], N), dtype=np.uint64)
+    k4 = o.ks_k[l]  # the key family that a switch at the batch level uses
+    lmax = o.key_lmax[k4]
+    o.keys[0] = {k4: rng.integers(0, 2 ** 59, size=(-(-lmax // o.alpha), 2, lmax + k4, N),
+                                  dtype=np.uint64)}
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     o.keyswitch(rnd(l, 1).c[0], 0)
@@ -388,19 +391,21 @@ def oracle_sample(W):
     t0 = time.perf_counter()
     o.encrypt(rnd(l, 1).c[0], 1, o.delta)
     t_enc = time.perf_counter() - t0
-    return dict(t_ks4=t_ks, t_tensor4=t_tensor, t_enc4=t_enc, t_setup=t_setup, alpha=o.alpha)
+    return dict(t_ks4=t_ks, t_tensor4=t_tensor, t_enc4=t_enc, t_setup=t_setup, alpha=o.alpha,
+                ks_k=list(o.ks_k))
 
 
 def extrapolate(sample, ks_hist, W, factored=False):
     """Oracle job time: key switches scaled by their polynomial-product count
-    (2 beta (l + K) per switch at level l) from the measured level-4 switch,
+    (2 beta (l + K_l) per switch at level l, K_l special primes) from the
+    measured level-4 switch,
     plus the batches' tensor products and SNP encryptions (M-CCP: n of each
     at 4 limbs; factored: one encryption at 6 limbs, d tensors at 6 and d at
     4 limbs, scaled by limbs)."""
-    alpha, K = sample["alpha"], W["K"]
+    alpha, ks_k = sample["alpha"], sample["ks_k"]
 
     def work(l):
-        return math.ceil(l / alpha) * (l + K)
+        return math.ceil(l / alpha) * (l + ks_k[l])
 
     t = 0.0
     for l, cnt in enumerate(ks_hist):

@@ -112,11 +112,20 @@ int gwhe_sync(gwhe_ctx* ctx);
  * and, if conj, for complex conjugation.  Keys stay resident on the device. */
 int gwhe_keygen(gwhe_ctx* ctx, const int32_t* rot_steps, size_t nrot, int conj);
 /* Key material in the coefficient domain for parity checks: the secret as
- * signed coefficients int64[N]; pk as uint64[2][L][N] (b, a); a switching key
- * as uint64[dnum][2][L+K][N]. */
+ * signed coefficients int64[N]; pk as uint64[2][L][N] (b, a); one family of a
+ * switching key (the part used by the switches with k special primes, see
+ * gwhe_ks_special) as uint64[dk][2][lmax + k][N], dk = ceil(lmax / alpha),
+ * rows q_0..q_{lmax-1} then p_0..p_{k-1}. */
 int gwhe_export_secret(gwhe_ctx* ctx, int64_t* s);
 int gwhe_export_pk(gwhe_ctx* ctx, uint64_t* pk);
-int gwhe_export_ksk(gwhe_ctx* ctx, uint32_t key_id, uint64_t* out);
+int gwhe_export_ksk(gwhe_ctx* ctx, uint32_t key_id, int k, uint64_t* out);
+/* Special primes of a key switch at level l (hybrid key switching is not in
+ * the paper; this is the library's reading): *k = the fewest leading special
+ * primes p_0..p_{k-1} whose bits (sum of bit lengths minus one) exceed the
+ * level's widest digit (sum of its q bit lengths) by 24, or all K when none
+ * does; *key_lmax (optional) = the highest level with that count, the levels
+ * the key family covers. */
+int gwhe_ks_special(const gwhe_ctx* ctx, int l, int* k, int* key_lmax);
 
 /* ------------------------------------------------------------ ciphertexts
  * A handle holds npoly (2, or 3 for a tensor) polynomials with room for cap

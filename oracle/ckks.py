@@ -59,7 +59,8 @@ def lib():
         "or_ctx_moduli": (None, [vp, _u64p]),
         "or_keygen_sk": (None, [vp, _i64p]),
         "or_keygen_pk": (None, [vp, _u64p, _u64p]),
-        "or_keygen_ksk": (None, [vp, u32, _u64p, _u64p]),
+        "or_keygen_ksk": (None, [vp, u32, i32, i32, _u64p, _u64p]),
+        "or_ks_special": (i32, [vp, i32]),
         "or_sk_square": (None, [vp, _u64p]),
         "or_sk_galois": (None, [vp, u64, _u64p]),
         "or_automorphism": (None, [_u64p, _u64p, i32, u64, u64]),
@@ -68,7 +69,7 @@ def lib():
         "or_mul_plain": (None, [vp, _u64p, i32, _u64p, i32, _u64p]),
         "or_tensor": (None, [vp, _u64p, _u64p, i32, _u64p]),
         "or_rescale": (None, [vp, _u64p, i32, i32, _u64p]),
-        "or_keyswitch": (None, [vp, _u64p, i32, _u64p, _u64p]),
+        "or_keyswitch": (None, [vp, _u64p, i32, _u64p, i32, _u64p]),
         "or_fft_twiddles": (None, [i32, i32, _f64p, _f64p]),
         "or_encode": (None, [i32, _f64p, dbl, _i64p]),
         "or_to_rns": (None, [vp, _i64p, i32, _u64p]),
@@ -177,6 +178,12 @@ class OracleCKKS:
         self.q = [int(x) for x in mods[:L]]
         self.p = [int(x) for x in mods[L:]]
         self.alpha = lib().or_ctx_alpha(self._ctx)
+        # key switches at level l use the first ks_k[l] special primes; one key
+        # family per count k covers the levels up to key_lmax[k]
+        self.ks_k = [0] + [lib().or_ks_special(self._ctx, l) for l in range(1, L + 1)]
+        self.key_lmax = {}
+        for l in range(1, L + 1):
+            self.key_lmax[self.ks_k[l]] = l
         self.keys = {}
 
     def __del__(self):
@@ -211,9 +218,15 @@ class OracleCKKS:
         self.keys[int(g)] = self._ksk(int(g), t)
 
     def _ksk(self, key_id, target):
-        out = np.zeros((self.dnum, 2, self.L + self.K, self.N), np.uint64)
-        lib().or_keygen_ksk(self._ctx, key_id, np.ascontiguousarray(target), out)
-        return out
+        """{k: array [ceil(lmax/alpha)][2][lmax + k][N]} for every special-prime
+        count k in use (target: residues over all L + K moduli)."""
+        fam = {}
+        for k, lmax in sorted(self.key_lmax.items()):
+            dk = -(-lmax // self.alpha)
+            out = np.zeros((dk, 2, lmax + k, self.N), np.uint64)
+            lib().or_keygen_ksk(self._ctx, key_id, k, lmax, np.ascontiguousarray(target), out)
+            fam[k] = out
+        return fam
 
     # ----------------------------------------------------------- encoding
     def encode_int(self, z, scale: float) -> np.ndarray:
@@ -387,8 +400,10 @@ class OracleCKKS:
 
     def keyswitch(self, x: np.ndarray, key_id: int) -> np.ndarray:
         l = x.shape[0]
+        k = self.ks_k[l]
         out = np.zeros((2, l, self.N), np.uint64)
-        lib().or_keyswitch(self._ctx, np.ascontiguousarray(x), l, self.keys[key_id], out)
+        lib().or_keyswitch(self._ctx, np.ascontiguousarray(x), l,
+                           np.ascontiguousarray(self.keys[key_id][k]), self.key_lmax[k], out)
         return out
 
     def relin(self, t: Ct) -> Ct:

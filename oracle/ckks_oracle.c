@@ -316,7 +316,40 @@ typedef struct {
     u64 seed;
     u64 mod[OR_MAXMOD]; /* mod[0..L) = q_i, mod[L..L+K) = p_k */
     u64 psi[OR_MAXMOD];
+    int ks_k[OR_MAXMOD + 1]; /* special primes used by a key switch at level l */
 } or_ctx;
+
+static int bitlen(u64 x)
+{
+    int b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+
+/* Special primes of a key switch at level l (hybrid key switching, a reading
+ * of the paper's relinearisation/rotation keys): the fewest leading special
+ * primes p_0..p_{k-1} whose product P_k has at least OR_KS_MARGIN more bits
+ * than the widest digit at that level, or all K when no count reaches the
+ * margin.  Bit counts are bounded from below for P_k (sum of bitlen(p) - 1)
+ * and from above for the digits (sum of bitlen(q)), so the rule is
+ * integer-only. */
+#define OR_KS_MARGIN 24
+static int ks_special_rule(const or_ctx *c, int l)
+{
+    int need = 0;
+    for (int lo = 0; lo < l; lo += c->alpha) {
+        int hi = lo + c->alpha < l ? lo + c->alpha : l, bits = 0;
+        for (int i = lo; i < hi; i++) bits += bitlen(c->mod[i]);
+        if (bits > need) need = bits;
+    }
+    need += OR_KS_MARGIN;
+    int have = 0;
+    for (int k = 1; k <= c->K; k++) {
+        have += bitlen(c->mod[c->L + k - 1]) - 1;
+        if (have >= need) return k;
+    }
+    return c->K;
+}
 
 void *or_ctx_create(int logN, int L, int q0_bits, int scale_bits, int K, int sp_bits,
                     int dnum, u64 seed)
@@ -331,7 +364,13 @@ void *or_ctx_create(int logN, int L, int q0_bits, int scale_bits, int K, int sp_
         return NULL;
     }
     for (int i = 0; i < L + K; i++) c->psi[i] = or_primitive_root_2n(c->mod[i], logN);
+    for (int l = 1; l <= L; l++) c->ks_k[l] = ks_special_rule(c, l);
     return c;
+}
+int or_ks_special(const void *ctx, int l)
+{
+    const or_ctx *c = (const or_ctx *)ctx;
+    return (l >= 1 && l <= c->L) ? c->ks_k[l] : 0;
 }
 void or_ctx_destroy(void *ctx) { free(ctx); }
 int or_ctx_alpha(const void *ctx) { return ((const or_ctx *)ctx)->alpha; }
@@ -345,8 +384,8 @@ void or_ctx_moduli(const void *ctx, u64 *out)
 #define OBJ_SK 1ull
 #define OBJ_PK_A 2ull
 #define OBJ_PK_E 3ull
-#define OBJ_KSK_A(key, j) ((1ull << 40) | ((u64)(key) << 8) | (u64)(j))
-#define OBJ_KSK_E(key, j) ((2ull << 40) | ((u64)(key) << 8) | (u64)(j))
+#define OBJ_KSK_A(key, k, j) ((1ull << 40) | ((u64)(k) << 32) | ((u64)(key) << 8) | (u64)(j))
+#define OBJ_KSK_E(key, k, j) ((2ull << 40) | ((u64)(k) << 32) | ((u64)(key) << 8) | (u64)(j))
 #define OBJ_ENC_V(id) ((3ull << 48) | (u64)(id))
 #define OBJ_ENC_E0(id) ((4ull << 48) | (u64)(id))
 #define OBJ_ENC_E1(id) ((5ull << 48) | (u64)(id))
@@ -385,33 +424,38 @@ void or_keygen_pk(const void *ctx, u64 *b, u64 *a)
     free(s); free(e); free(sr); free(t);
 }
 
-/* switching key from target t (residues over all L+K moduli, [L+K][N]) to s.
- * out is [dnum][2][L+K][N]; digit j holds b_j = -a_j s + e_j + [u in digit j] P t
- * and a_j (uniform). key_id 0 = relinearisation, otherwise the Galois element. */
-void or_keygen_ksk(const void *ctx, u32 key_id, const u64 *target, u64 *out)
+/* Switching key from target t (residues over all L+K moduli, [L+K][N]) to s,
+ * for the key switches that use k special primes, up to level lmax.  Its
+ * moduli are q_0..q_{lmax-1} then p_0..p_{k-1} (nm = lmax + k rows) and its
+ * digits are the alpha-limb groups of [0, lmax):  out is [dk][2][nm][N],
+ * dk = ceil(lmax / alpha); digit j holds b_j = -a_j s + e_j + [u in digit j]
+ * P_k t and a_j (uniform).  key_id 0 = relinearisation, otherwise the Galois
+ * element. */
+void or_keygen_ksk(const void *ctx, u32 key_id, int k, int lmax, const u64 *target, u64 *out)
 {
     const or_ctx *c = (const or_ctx *)ctx;
-    const int N = c->N, nm = c->L + c->K;
+    const int N = c->N, nm = lmax + k, dk = (lmax + c->alpha - 1) / c->alpha;
     i64 *s = (i64 *)malloc(sizeof(i64) * N), *e = (i64 *)malloc(sizeof(i64) * N);
     u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
-    for (int j = 0; j < c->dnum; j++) {
-        or_sample_cbd(c->seed, OBJ_KSK_E(key_id, j), c->logN, e);
-        int lo = j * c->alpha, hi = lo + c->alpha < c->L ? lo + c->alpha : c->L;
+    for (int j = 0; j < dk; j++) {
+        or_sample_cbd(c->seed, OBJ_KSK_E(key_id, k, j), c->logN, e);
+        int lo = j * c->alpha, hi = lo + c->alpha < lmax ? lo + c->alpha : lmax;
         for (int u = 0; u < nm; u++) {
-            u64 m = c->mod[u];
+            int gm = u < lmax ? u : c->L + (u - lmax); /* index into mod[] */
+            u64 m = c->mod[gm];
             u64 *bj = out + (((size_t)j * 2 + 0) * nm + u) * N;
             u64 *aj = out + (((size_t)j * 2 + 1) * nm + u) * N;
-            or_sample_uniform(c->seed, OBJ_KSK_A(key_id, j), (u32)u, m, c->logN, aj);
-            for (int k = 0; k < N; k++) sr[k] = mred_i64(s[k], m);
-            or_polymul(aj, sr, t, c->logN, m, c->psi[u]);
+            or_sample_uniform(c->seed, OBJ_KSK_A(key_id, k, j), (u32)gm, m, c->logN, aj);
+            for (int kk = 0; kk < N; kk++) sr[kk] = mred_i64(s[kk], m);
+            or_polymul(aj, sr, t, c->logN, m, c->psi[gm]);
             u64 Pm = 1;
-            for (int kk = 0; kk < c->K; kk++) Pm = mmul(Pm, c->mod[c->L + kk] % m, m);
+            for (int kk = 0; kk < k; kk++) Pm = mmul(Pm, c->mod[c->L + kk] % m, m);
             int in_digit = (u >= lo && u < hi);
-            for (int k = 0; k < N; k++) {
-                u64 v = madd(msub(0, t[k], m), mred_i64(e[k], m), m);
-                if (in_digit) v = madd(v, mmul(Pm, target[(size_t)u * N + k], m), m);
-                bj[k] = v;
+            for (int kk = 0; kk < N; kk++) {
+                u64 v = madd(msub(0, t[kk], m), mred_i64(e[kk], m), m);
+                if (in_digit) v = madd(v, mmul(Pm, target[(size_t)gm * N + kk], m), m);
+                bj[kk] = v;
             }
         }
     }
@@ -575,16 +619,19 @@ void or_rescale(const void *ctx, const u64 *in, int npoly, int l, u64 *out)
  *   inner   : acc_t = sum_j ext_{j,t} * ksk_j,t (negacyclic products)
  *   ModDown : z_k = [acc_{p_k} (P/p_k)^-1]_{p_k};  conv_i = sum_k z_k (P/p_k) mod q_i;
  *             out_i = (acc_i - conv_i) P^-1 mod q_i                                */
-void or_keyswitch(const void *ctx, const u64 *x, int l, const u64 *ksk, u64 *out)
+/* Hybrid key switch of x (coefficient domain, l limbs) with the key family of
+ * K_l = or_ks_special(l) special primes (built by or_keygen_ksk with that k
+ * and key_lmax >= l): ModUp per digit, inner product, ModDown by P_{K_l}. */
+void or_keyswitch(const void *ctx, const u64 *x, int l, const u64 *ksk, int key_lmax, u64 *out)
 {
     const or_ctx *c = (const or_ctx *)ctx;
-    const int N = c->N, L = c->L, K = c->K, nm = L + K, ne = l + K;
+    const int N = c->N, L = c->L, K = c->ks_k[l], nm = key_lmax + K, ne = l + K;
     const int beta = (l + c->alpha - 1) / c->alpha;
     u64 emod[OR_MAXMOD];
-    int ekey[OR_MAXMOD]; /* limb index of the key for extended limb u */
+    int ekey[OR_MAXMOD]; /* row of the key for extended limb u */
     for (int u = 0; u < ne; u++) {
         emod[u] = u < l ? c->mod[u] : c->mod[L + (u - l)];
-        ekey[u] = u < l ? u : L + (u - l);
+        ekey[u] = u < l ? u : key_lmax + (u - l);
     }
     u64 *ext = (u64 *)malloc(sizeof(u64) * (size_t)beta * ne * N);
     u64 *acc = (u64 *)calloc((size_t)2 * ne * N, sizeof(u64));

@@ -112,7 +112,10 @@ int gwhe_keygen(gwhe_ctx* ctx, const int32_t* rot_steps, size_t nrot, int conj) 
   });
 }
 
-static void export_rows(Context* c, const u64* dev, int npoly, int nl, int first_mod, u64* host) {
+// npoly polynomials of nl NTT-domain rows (row i modulo mod[pidx[i]], or
+// mod[first_mod + i] without pidx) -> coefficient domain, host
+static void export_rows(Context* c, const u64* dev, int npoly, int nl, int first_mod, u64* host,
+                        const int* pidx = nullptr) {
   const size_t N = c->N, words = (size_t)npoly * nl * N;
   Tmp t(c, sizeof(u64) * words);
   GWHE_CUDA(cudaMemcpyAsync(t.p, dev, sizeof(u64) * words, cudaMemcpyDeviceToDevice, c->stream));
@@ -122,7 +125,7 @@ static void export_rows(Context* c, const u64* dev, int npoly, int nl, int first
   rm.poly_stride = nl;
   for (int i = 0; i < nl; ++i) {
     rm.off[i] = (uint16_t)i;
-    rm.pidx[i] = (uint8_t)(first_mod + i);
+    rm.pidx[i] = (uint8_t)(pidx ? pidx[i] : first_mod + i);
   }
   ntt_inverse(c, t.u(), rm);
   GWHE_CUDA(cudaMemcpyAsync(host, t.p, sizeof(u64) * words, cudaMemcpyDeviceToHost, c->stream));
@@ -148,13 +151,26 @@ int gwhe_export_pk(gwhe_ctx* ctx, uint64_t* pk) {
   });
 }
 
-int gwhe_export_ksk(gwhe_ctx* ctx, uint32_t key_id, uint64_t* out) {
+int gwhe_export_ksk(gwhe_ctx* ctx, uint32_t key_id, int k, uint64_t* out) {
   return guard(C(ctx), [&] {
     Context* c = C(ctx);
     auto it = c->ksk.find(key_id);
     if (it == c->ksk.end()) throw Error(ST_ENOKEY, "no such key");
-    export_rows(c, it->second.d, 2 * c->P.dnum, c->nmod, 0, out);
+    need(k >= 1 && k <= kMaxSpecial && it->second.fam[k].d, "no key family with that count");
+    const Ksk& f = it->second.fam[k];
+    std::vector<int> pidx(f.rows());
+    for (int u = 0; u < f.rows(); ++u) pidx[u] = u < f.lmax ? u : c->P.L + (u - f.lmax);
+    export_rows(c, f.d, 2 * f.dk, f.rows(), 0, out, pidx.data());
   });
+}
+
+int gwhe_ks_special(const gwhe_ctx* ctx, int l, int* k, int* key_lmax) {
+  if (!ctx || !ctx->c || !k) return GWHE_EINVAL;
+  const Context* c = ctx->c;
+  if (l < 1 || l > c->P.L) return GWHE_EINVAL;
+  *k = c->ks_k[l];
+  if (key_lmax) *key_lmax = c->key_lmax[*k];
+  return GWHE_OK;
 }
 
 int gwhe_ct_create(gwhe_ctx* ctx, int npoly, int cap, gwhe_ct** out) {

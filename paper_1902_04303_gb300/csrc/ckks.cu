@@ -192,6 +192,28 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
     c->d_rescale = upload(c.get(), t);
   }
   // base conversion tables
+  // special primes per level (see Context::ks_k): the widest digit's bits
+  // (upper bound: sum of bit lengths) plus a 24-bit margin against the
+  // special product's bits (lower bound: sum of bit lengths minus one)
+  for (int l = 1; l <= L; ++l) {
+    int need = 0;
+    for (int lo = 0; lo < l; lo += alpha) {
+      int bits = 0;
+      for (int i = lo; i < std::min(lo + alpha, l); ++i) bits += 64 - __builtin_clzll(c->mod[i]);
+      need = std::max(need, bits);
+    }
+    need += 24;
+    int k = K, have = 0;
+    for (int kk = 1; kk <= K; ++kk) {
+      have += 63 - __builtin_clzll(c->mod[L + kk - 1]);
+      if (have >= need) {
+        k = kk;
+        break;
+      }
+    }
+    c->ks_k[l] = k;
+    c->key_lmax[k] = l;
+  }
   {
     std::vector<u64> store;
     std::vector<std::pair<ConvTable*, size_t>> fix;
@@ -231,7 +253,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
             out_mod.push_back(i);
             t.out_limb.push_back((uint16_t)i);
           }
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < c->ks_k[l]; ++k) {
           out_mod.push_back(L + k);
           t.out_limb.push_back((uint16_t)(l + k));
         }
@@ -239,11 +261,13 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
         add_table(t, in_mod, out_mod);
       }
     }
-    {
-      ConvTable& t = c->moddown;
+    // ModDown from the first k special primes to the q-limbs, per k in use
+    for (int k = 1; k <= K; ++k) {
+      if (!c->key_lmax[k]) continue;
+      ConvTable& t = c->moddown[k];
       t.in_lo = L;
       std::vector<int> in_mod, out_mod;
-      for (int k = 0; k < K; ++k) in_mod.push_back(L + k);
+      for (int kk = 0; kk < k; ++kk) in_mod.push_back(L + kk);
       for (int i = 0; i < L; ++i) {
         out_mod.push_back(i);
         t.out_limb.push_back((uint16_t)i);
@@ -253,15 +277,18 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
     }
     c->d_conv_store = upload(c.get(), store);
     for (auto& f : fix) f.first->dev = c->d_conv_store + f.second;
-    std::vector<u64> pinv((size_t)L * 2);
-    for (int i = 0; i < L; ++i) {
-      const u64 q = c->mod[i];
-      u64 Pm = 1;
-      for (int k = 0; k < K; ++k) Pm = host_mulmod(Pm, c->mod[L + k] % q, q);
-      pinv[2 * i] = host_inv(Pm, q);
-      pinv[2 * i + 1] = shoup_companion(pinv[2 * i], q);
+    for (int k = 1; k <= K; ++k) {
+      if (!c->key_lmax[k]) continue;
+      std::vector<u64> pinv((size_t)L * 2);
+      for (int i = 0; i < L; ++i) {
+        const u64 q = c->mod[i];
+        u64 Pm = 1;
+        for (int kk = 0; kk < k; ++kk) Pm = host_mulmod(Pm, c->mod[L + kk] % q, q);
+        pinv[2 * i] = host_inv(Pm, q);
+        pinv[2 * i + 1] = shoup_companion(pinv[2 * i], q);
+      }
+      c->d_pinv[k] = upload(c.get(), pinv);
     }
-    c->d_pinv = upload(c.get(), pinv);
   }
   // encoding tables
   {
@@ -308,11 +335,13 @@ void ctx_destroy(Context* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
-                  (void*)c->d_pinv, (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
+                  (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
                   (void*)c->d_slot_u, (void*)c->d_slot_inv})
     if (p) cudaFree(p);
   for (auto& kv : c->masks) cudaFree(kv.second);
+  for (u64* p : c->d_pinv)
+    if (p) cudaFree(p);
   for (auto& r : c->prof.recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -321,7 +350,8 @@ void ctx_destroy(Context* c) {
   if (c->d_sk) cudaFreeAsync(c->d_sk, c->stream);
   if (c->d_pk) cudaFreeAsync(c->d_pk, c->stream);
   for (auto& kv : c->ksk)
-    if (kv.second.d) cudaFreeAsync(kv.second.d, c->stream);
+    for (const Ksk& f : kv.second.fam)
+      if (f.d) cudaFreeAsync(f.d, c->stream);
   cudaStreamSynchronize(c->stream);
   delete c;
 }
@@ -339,36 +369,76 @@ static RowMap rows_all(const Context* c, int first, int count, int poly_stride, 
   return rm;
 }
 
+const Ksk& key_family(const Context* c, u32 key_id, int l) {
+  auto it = c->ksk.find(key_id);
+  GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "missing switching key " + std::to_string(key_id));
+  GWHE_REQUIRE(l >= 1 && l <= c->P.L, ST_EINVAL, "bad level for a key switch");
+  const Ksk& f = it->second.fam[c->ks_k[l]];
+  GWHE_REQUIRE(f.d && f.lmax >= l, ST_ENOKEY, "switching key family missing");
+  return f;
+}
+
+// target: residues of the key's target over all L + K moduli ([L+K][N], NTT
+// domain).  One family per special-prime count k in use: digit j of family k
+// holds b_j = -a_j s + e_j + [u in digit j] P_k t and a_j, rows q_0..q_{lmax-1},
+// p_0..p_{k-1}; the random streams are keyed by (key id, k, j) and the uniform
+// rows by the global modulus index.
 static void make_ksk(Context* c, u32 key_id, const u64* target) {
-  const int N = c->N, L = c->P.L, K = c->P.K, nm = L + K;
-  Ksk k;
-  k.d = dalloc_u64(c, c->ksk_words());
-  Tmp e(c, sizeof(u64) * nm * N);
-  std::vector<uint8_t> pidx(nm);
-  for (int u = 0; u < nm; ++u) pidx[u] = (uint8_t)u;
-  for (int j = 0; j < c->P.dnum; ++j) {
-    u64* bj = k.d + ((size_t)j * 2 + 0) * nm * N;
-    u64* aj = k.d + ((size_t)j * 2 + 1) * nm * N;
-    sample_cbd_rns(c, obj_ksk_e(key_id, j), e.u(), pidx.data(), nm);
-    ntt_forward(c, e.u(), rows_all(c, 0, nm, nm, 1));
-    for (int u = 0; u < nm; ++u) sample_uniform(c, obj_ksk_a(key_id, j), (u32)u, u, aj + (size_t)u * N);
-    ntt_forward(c, aj, rows_all(c, 0, nm, nm, 1));
-    const int lo = j * c->alpha, hi = std::min(lo + c->alpha, L);
+  const int N = c->N, L = c->P.L, K = c->P.K;
+  KeySet ks;
+  for (int k = 1; k <= K; ++k) {
+    const int lmax = c->key_lmax[k];
+    if (!lmax) continue;
+    Ksk f;
+    f.k = k;
+    f.lmax = lmax;
+    f.dk = (lmax + c->alpha - 1) / c->alpha;
+    const int nm = f.rows();
+    f.d = dalloc_u64(c, (size_t)f.dk * 2 * nm * N);
+    std::vector<uint8_t> pidx(nm);
+    std::vector<int> gm(nm);
     for (int u = 0; u < nm; ++u) {
-      u64 pm = 0;
-      const u64* t = nullptr;
-      if (u >= lo && u < hi) {
-        pm = 1;
-        for (int kk = 0; kk < K; ++kk) pm = host_mulmod(pm, c->mod[L + kk] % c->mod[u], c->mod[u]);
-        t = target + (size_t)u * N;
-      }
-      ksk_combine(c, bj + (size_t)u * N, aj + (size_t)u * N, e.u() + (size_t)u * N,
-                  c->d_sk + (size_t)u * N, t, pm, u);
+      gm[u] = u < lmax ? u : L + (u - lmax);
+      pidx[u] = (uint8_t)gm[u];
     }
+    RowMap rm;
+    rm.npoly = 1;
+    rm.nl = nm;
+    rm.poly_stride = nm;
+    for (int u = 0; u < nm; ++u) {
+      rm.off[u] = (uint16_t)u;
+      rm.pidx[u] = pidx[u];
+    }
+    Tmp e(c, sizeof(u64) * nm * N);
+    for (int j = 0; j < f.dk; ++j) {
+      u64* bj = f.d + ((size_t)j * 2 + 0) * nm * N;
+      u64* aj = f.d + ((size_t)j * 2 + 1) * nm * N;
+      sample_cbd_rns(c, obj_ksk_e(key_id, k, j), e.u(), pidx.data(), nm);
+      ntt_forward(c, e.u(), rm);
+      for (int u = 0; u < nm; ++u)
+        sample_uniform(c, obj_ksk_a(key_id, k, j), (u32)gm[u], gm[u], aj + (size_t)u * N);
+      ntt_forward(c, aj, rm);
+      const int lo = j * c->alpha, hi = std::min(lo + c->alpha, lmax);
+      for (int u = 0; u < nm; ++u) {
+        u64 pm = 0;
+        const u64* t = nullptr;
+        const u64 m = c->mod[gm[u]];
+        if (u >= lo && u < hi) {
+          pm = 1;
+          for (int kk = 0; kk < k; ++kk) pm = host_mulmod(pm, c->mod[L + kk] % m, m);
+          t = target + (size_t)gm[u] * N;
+        }
+        ksk_combine(c, bj + (size_t)u * N, aj + (size_t)u * N, e.u() + (size_t)u * N,
+                    c->d_sk + (size_t)gm[u] * N, t, pm, gm[u]);
+      }
+    }
+    ks.fam[k] = f;
   }
   auto it = c->ksk.find(key_id);
-  if (it != c->ksk.end() && it->second.d) dfree(c, it->second.d);
-  c->ksk[key_id] = k;
+  if (it != c->ksk.end())
+    for (const Ksk& f : it->second.fam)
+      if (f.d) dfree(c, f.d);
+  c->ksk[key_id] = ks;
 }
 
 void add_galois_key(Context* c, u32 g) {
@@ -500,44 +570,9 @@ void op_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>
   out3.scale = terms[0].first->scale * terms[0].second->scale;
 }
 
-void keyswitch(Context* c, const u64* x_ntt, int l, const Ksk& key, u64* out0, u64* out1,
+void keyswitch(Context* c, const u64* x_ntt, int l, const KeySet& key, u64* out0, u64* out1,
                const u64* add0, const u64* add1) {
-  const int N = c->N, K = c->P.K, L = c->P.L, ne = l + K;
-  const int beta = (l + c->alpha - 1) / c->alpha;
-  ++c->ks_count;
-  ++c->ks_by_level[l];
-  Tmp xc(c, sizeof(u64) * l * N);
-  GWHE_CUDA(cudaMemcpyAsync(xc.p, x_ntt, sizeof(u64) * l * N, cudaMemcpyDeviceToDevice, c->stream));
-  ntt_inverse(c, xc.u(), rows_q(1, l, l));
-  Tmp ext(c, sizeof(u64) * beta * ne * N);
-  modup_convert(c, xc.u(), l, ext.u());
-  for (int j = 0; j < beta; ++j) {
-    const ConvTable& t = c->modup.at({l, j});
-    RowMap rm;
-    rm.npoly = 1;
-    rm.nl = t.n_out;
-    rm.poly_stride = ne;
-    for (int o = 0; o < t.n_out; ++o) {
-      rm.off[o] = t.out_limb[o];
-      rm.pidx[o] = t.out_pidx[o];
-    }
-    ntt_forward(c, ext.u() + (size_t)j * ne * N, rm);
-  }
-  Tmp acc(c, sizeof(u64) * 2 * ne * N);
-  ks_inner(c, x_ntt, l, ext.u(), key.d, acc.u());
-  RowMap rk;
-  rk.npoly = 2;
-  rk.nl = K;
-  rk.poly_stride = ne;
-  for (int k = 0; k < K; ++k) {
-    rk.off[k] = (uint16_t)(l + k);
-    rk.pidx[k] = (uint8_t)(L + k);
-  }
-  ntt_inverse(c, acc.u(), rk);
-  Tmp conv(c, sizeof(u64) * 2 * l * N);
-  moddown_convert(c, acc.u(), l, conv.u());
-  ntt_forward(c, conv.u(), rows_q(2, l, l));
-  moddown_combine(c, acc.u(), conv.u(), l, out0, out1, add0, add1);
+  keyswitch_set(c, x_ntt, 0, 1, l, key, out0, out1, 0, add0, add1, 0, 0);
 }
 
 void op_relin(Context* c, const Ct& t3, Ct& out) {
@@ -664,16 +699,22 @@ static T* upload_async(Context* c, Tmp& t, const std::vector<T>& v) {
   return t.as<T>();
 }
 
-void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const Ksk& key,
+// Hybrid key switch of cnt ciphertext parts at level l with the key family of
+// K_l special primes: ModUp (iNTT, fast base conversion per digit, NTT of the
+// new limbs), the inner product with the key digits, ModDown (iNTT of the
+// special limbs, conversion to the q-limbs, NTT, (x - conv) P_{K_l}^-1).
+void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const KeySet& key,
                    u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                    size_t a0_stride, size_t a1_stride) {
   const size_t N = c->N;
-  const int K = c->P.K, L = c->P.L, ne = l + K;
+  const Ksk& fam = key.fam[c->ks_k[l]];
+  GWHE_REQUIRE(fam.d && fam.lmax >= l, ST_ENOKEY, "switching key family missing");
+  const int K = fam.k, L = c->P.L, ne = l + K;
   const int beta = (l + c->alpha - 1) / c->alpha;
   c->ks_count += cnt;
   c->ks_by_level[l] += cnt;
   Tmp xc(c, sizeof(u64) * cnt * l * N);
-  GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x, sizeof(u64) * x_stride,
+  GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x, sizeof(u64) * std::max<size_t>(x_stride, l * N),
                               sizeof(u64) * l * N, cnt, cudaMemcpyDeviceToDevice, c->stream));
   ntt_inverse(c, xc.u(), rows_q(cnt, l, l));
   Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
@@ -691,7 +732,7 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
     ntt_forward(c, ext.u(), rm);
   }
   Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
-  ks_inner_set(c, x, x_stride, l, ext.u(), key.d, acc.u(), cnt);
+  ks_inner_set(c, x, x_stride, l, ext.u(), fam, acc.u(), cnt);
   RowMap rk;
   rk.npoly = 2 * cnt;
   rk.nl = K;
@@ -702,10 +743,10 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
   }
   ntt_inverse(c, acc.u(), rk);
   Tmp conv(c, sizeof(u64) * cnt * 2 * l * N);
-  moddown_convert_set(c, acc.u(), l, conv.u(), cnt);
+  moddown_convert_set(c, acc.u(), l, K, conv.u(), cnt);
   ntt_forward(c, conv.u(), rows_q(2 * cnt, l, l));
-  moddown_combine_set(c, acc.u(), conv.u(), l, cnt, out0, out1, o_stride, add0, add1, a0_stride,
-                      a1_stride);
+  moddown_combine_set(c, acc.u(), conv.u(), l, K, cnt, out0, out1, o_stride, add0, add1,
+                      a0_stride, a1_stride);
 }
 
 void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps) {

@@ -16,8 +16,12 @@ namespace gwhe {
 constexpr u64 kObjSk = 1;
 constexpr u64 kObjPkA = 2;
 constexpr u64 kObjPkE = 3;
-inline u64 obj_ksk_a(u32 key, int j) { return (1ull << 40) | ((u64)key << 8) | (u64)j; }
-inline u64 obj_ksk_e(u32 key, int j) { return (2ull << 40) | ((u64)key << 8) | (u64)j; }
+inline u64 obj_ksk_a(u32 key, int k, int j) {
+  return (1ull << 40) | ((u64)k << 32) | ((u64)key << 8) | (u64)j;
+}
+inline u64 obj_ksk_e(u32 key, int k, int j) {
+  return (2ull << 40) | ((u64)k << 32) | ((u64)key << 8) | (u64)j;
+}
 
 Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream);
 void ctx_destroy(Context* c);
@@ -48,7 +52,7 @@ void op_conj(Context* c, const Ct& a, Ct& out);
 void op_drop(Ct& ct, int l);
 
 // key switch of the NTT-domain l-limb polynomial x: out_p = KS(x)_p (+ add_p)
-void keyswitch(Context* c, const u64* x_ntt, int l, const Ksk& key, u64* out0, u64* out1,
+void keyswitch(Context* c, const u64* x_ntt, int l, const KeySet& key, u64* out0, u64* out1,
                const u64* add0, const u64* add1);
 
 // encoding: z (device, count x M complex) -> plaintexts (device, NTT domain,
@@ -94,7 +98,7 @@ CtSetPtr set_new(Context* c, int cnt, int npoly, int cap, int l, double scale);
 
 // batched key switch: item i reads x + i x_stride (l limbs, NTT domain) and
 // writes out0/out1 + i o_stride (+ add0 + i a0_stride, add1 + i a1_stride)
-void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const Ksk& key,
+void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const KeySet& key,
                    u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                    size_t a0_stride, size_t a1_stride);
 // s[i] += Rotate(s[i], step) for each step in turn (Alg. 1/4/5/7 ladders)

@@ -234,9 +234,19 @@ struct Ct {
 };
 typedef std::unique_ptr<Ct> CtPtr;
 
-// Switching key in the NTT domain: [dnum][2][L+K][N].
+// One family of a switching key, for the key switches that use k special
+// primes (the levels l with K_l = k, up to lmax): NTT domain,
+// [dk][2][lmax + k][N] with dk = ceil(lmax / alpha) digits; rows are
+// q_0..q_{lmax-1} then p_0..p_{k-1}.
+constexpr int kMaxSpecial = 16;
 struct Ksk {
   u64* d = nullptr;
+  int k = 0, lmax = 0, dk = 0;
+  int rows() const { return lmax + k; }
+};
+// A switching key: its families, indexed by the special-prime count k.
+struct KeySet {
+  Ksk fam[kMaxSpecial + 1];
 };
 
 struct Params {
@@ -285,10 +295,15 @@ struct Context {
   u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l - 1 (value, Shoup)
   u64* d_rescale = nullptr;    // [L][L][2]
-  // ModUp tables per (level l, digit j) and the ModDown table
+  // key switches at level l use the first ks_k[l] special primes (fewest
+  // whose product exceeds the level's widest digit by 24 bits, else all K);
+  // key_lmax[k] = the highest level using k (0 if none)
+  int ks_k[kMaxRowLimbs + 1] = {};
+  int key_lmax[kMaxSpecial + 1] = {};
+  // ModUp tables per (level l, digit j); ModDown tables and P_k^-1 per k
   std::map<std::pair<int, int>, ConvTable> modup;
-  ConvTable moddown;
-  u64* d_pinv = nullptr;       // [L][2] P^-1 mod q_i (value, Shoup)
+  ConvTable moddown[kMaxSpecial + 1];
+  u64* d_pinv[kMaxSpecial + 1] = {};  // [L][2] P_k^-1 mod q_i (value, Shoup)
   u64* d_conv_store = nullptr; // backing store of all conversion tables
   // encoding procedure tables
   double2* d_fftW_dec = nullptr;
@@ -300,7 +315,7 @@ struct Context {
   // keys
   u64* d_sk = nullptr;            // [L+K][N] NTT domain
   u64* d_pk = nullptr;            // [2][L][N] NTT domain (b, a)
-  std::map<u32, Ksk> ksk;         // key id -> switching key
+  std::map<u32, KeySet> ksk;      // key id -> switching key
   bool have_keys = false;
   // encoded public plaintexts (masks), keyed by (kind, index, level, scale)
   std::map<std::tuple<int, long, int, double>, u64*> masks;
@@ -312,8 +327,10 @@ struct Context {
   NttTables tables() const {
     return NttTables{d_psi, d_ipsi, d_ninv, d_ninv_sh, d_mod};
   }
-  size_t ksk_words() const { return (size_t)P.dnum * 2 * (P.L + P.K) * N; }
 };
+
+// the family of key id that a switch at level l uses (ST_ENOKEY if absent)
+const Ksk& key_family(const Context* c, u32 key_id, int l);
 
 // ---------------------------------------------------------------- host helpers
 // params.cpp

@@ -164,22 +164,24 @@ __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __r
 // items of the set, so the key is read once per IB ciphertexts.
 constexpr int kKsMaxBeta = 4;
 template <int IB>
+// The key family has rows q_0..q_{key_lmax-1}, p_0..p_{K-1} per digit and poly.
 __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
                            const u64* __restrict__ ext, const u64* __restrict__ key,
-                           u64* __restrict__ acc, int l, int K, int L, int alpha, int beta, int N,
-                           int cnt, const DevMod* __restrict__ mod) {
+                           u64* __restrict__ acc, int l, int K, int L, int key_lmax, int alpha,
+                           int beta, int N, int cnt, const DevMod* __restrict__ mod) {
   const int u = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
-  const int mi = u < l ? u : L + (u - l);
-  const size_t LK = (size_t)(L + K);
+  const int mi = u < l ? u : L + (u - l);        // modulus of extended limb u
+  const int kr = u < l ? u : key_lmax + (u - l);  // its row in the key family
+  const size_t KR = (size_t)(key_lmax + K);
   u64 kb[kKsMaxBeta], ka[kKsMaxBeta];
 #pragma unroll
   for (int j = 0; j < kKsMaxBeta; ++j)
     if (j < beta) {
-      kb[j] = key[(((size_t)j * 2 + 0) * LK + mi) * N + k];
-      ka[j] = key[(((size_t)j * 2 + 1) * LK + mi) * N + k];
+      kb[j] = key[(((size_t)j * 2 + 0) * KR + kr) * N + k];
+      ka[j] = key[(((size_t)j * 2 + 1) * KR + kr) * N + k];
     }
   const DevMod m = mod[mi];
   const int it0 = blockIdx.z * IB;
@@ -930,7 +932,7 @@ static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_
 void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt) {
   ProfScope ps(c, PROF_BASECONV, 0.0);
   const int beta = (l + c->alpha - 1) / c->alpha;
-  const int ne = l + c->P.K;
+  const int ne = l + c->ks_k[l];
   const size_t N = c->N;
   for (int j = 0; j < beta; ++j) {
     const ConvTable& t = c->modup.at({l, j});
@@ -941,56 +943,42 @@ void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt)
   }
 }
 
-void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext) {
-  modup_convert_set(c, x_coeff, l, ext, 1);
-}
-
-void moddown_convert_set(Context* c, const u64* acc, int l, u64* conv, int cnt) {
-  GWHE_REQUIRE(l >= 1 && l <= c->P.L, ST_EINVAL, "bad level");
-  ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (c->P.K + l) * 8.0 * c->N);
-  const int ne = l + c->P.K;
-  ConvArgs a = conv_args(c->moddown, c->P.L);  // table rows hold all L outputs
-  a.n_out = l;                                 // produce the first l of them
+void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt) {
+  GWHE_REQUIRE(l >= 1 && l <= c->P.L && K >= 1 && K <= c->P.K && c->d_pinv[K], ST_EINVAL,
+               "bad level or special-prime count");
+  ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (K + l) * 8.0 * c->N);
+  const int ne = l + K;
+  ConvArgs a = conv_args(c->moddown[K], c->P.L);  // table rows hold all L outputs
+  a.n_out = l;                                    // produce the first l of them
   // items: the 2 cnt polynomials of acc ([cnt][2][ne][N]) -> conv ([cnt][2][l][N])
   launch_baseconv(c, acc + (size_t)l * c->N, (size_t)ne * c->N, conv, (size_t)l * c->N, 2 * cnt, a);
 }
 
-void moddown_convert(Context* c, const u64* acc, int l, u64* conv) {
-  moddown_convert_set(c, acc, l, conv, 1);
-}
-
-void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int cnt, u64* out0,
-                         u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int K, int cnt,
+                         u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                          size_t a0_stride, size_t a1_stride) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * 3 * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   k_moddown_combine<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
-      acc, conv, l, c->P.K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv,
+      acc, conv, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv[K],
       c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
-void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
-                     const u64* add0, const u64* add1) {
-  moddown_combine_set(c, acc, conv, l, 1, out0, out1, 0, add0, add1, 0, 0);
-}
-
 void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
-                  const u64* key, u64* acc, int cnt) {
-  const double ne_ = l + c->P.K, beta_ = (l + c->alpha - 1) / c->alpha;
+                  const Ksk& key, u64* acc, int cnt) {
+  const int K = key.k;
+  const double ne_ = l + K, beta_ = (l + c->alpha - 1) / c->alpha;
   ProfScope ps(c, PROF_KS_INNER, (3.0 * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N * cnt);
   const int beta = (l + c->alpha - 1) / c->alpha;
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
+  GWHE_REQUIRE(key.d && key.lmax >= l && beta <= key.dk, ST_ENOKEY, "key family does not reach the level");
   constexpr int IB = 8;
-  k_ks_inner<IB><<<dim3(blocks_for(c->N), l + c->P.K, (cnt + IB - 1) / IB), kThreads, 0,
-                   c->stream>>>(c_ntt, c_stride, ext, key, acc, l, c->P.K, c->P.L, c->alpha, beta,
-                                c->N, cnt, c->d_mod);
+  k_ks_inner<IB><<<dim3(blocks_for(c->N), l + K, (cnt + IB - 1) / IB), kThreads, 0,
+                   c->stream>>>(c_ntt, c_stride, ext, key.d, acc, l, K, c->P.L, key.lmax,
+                                c->alpha, beta, c->N, cnt, c->d_mod);
   GWHE_LAUNCHED(c, 1);
-}
-
-void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* key, u64* acc) {
-  ks_inner_set(c, c_ntt, 0, l, ext, key, acc, 1);
 }
 
 void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out,

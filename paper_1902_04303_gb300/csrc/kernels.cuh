@@ -45,21 +45,15 @@ void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt);
 // out (3 polys) = sum over pairs of the tensor (a0 b0, a0 b1 + a1 b0, a1 b1)
 void tensor_mac(Context* c, PolyView out3, const MacPair* d_pairs, int npairs, int l);
 
-// key switching pieces
-// ext rows: for each digit j, ne = l + K limbs at ext + (j * ne + u) * N
-void modup_convert(Context* c, const u64* x_coeff, int l, u64* ext);
-void ks_inner(Context* c, const u64* c_ntt, int l, const u64* ext, const u64* key, u64* acc);
-void moddown_combine(Context* c, const u64* acc, const u64* conv, int l, u64* out0, u64* out1,
-                     const u64* add0, const u64* add1);
-void moddown_convert(Context* c, const u64* acc, int l, u64* conv);
-
-// batched forms over cnt items (strides in words)
+// key switching pieces, over cnt items (strides in words).  A switch at level
+// l uses K = ks_k[l] special primes; ext rows: for each digit j, ne = l + K
+// limbs at ext + (j * ne + u) * N.
 void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt);
-void moddown_convert_set(Context* c, const u64* acc, int l, u64* conv, int cnt);
+void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt);
 void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
-                  const u64* key, u64* acc, int cnt);
-void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int cnt, u64* out0,
-                         u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                  const Ksk& key, u64* acc, int cnt);
+void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int K, int cnt,
+                         u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                          size_t a0_stride, size_t a1_stride);
 // out[item] = (sigma_g(in0) + in0, sigma_g(in1)): the automorphism of a ladder step
 void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out,

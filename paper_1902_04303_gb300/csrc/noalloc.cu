@@ -23,7 +23,8 @@ using namespace gwhe;
 namespace {
 
 // 32 MiB of scratch (2^22 words).  A key switch at level l needs
-// (3 l + (beta + 2) (l + K)) N words with beta = ceil(l / alpha) digits.
+// (3 l + (beta + 2) (l + K_l)) N words with beta = ceil(l / alpha) digits and
+// K_l the special primes that level uses.
 constexpr size_t kScratchWords = (size_t)1 << 22;
 static __device__ __align__(256) u64 g_ks_scratch[kScratchWords];
 
@@ -54,10 +55,9 @@ extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int 
   try {
     if (!x_ntt || !out_ntt || l < 1 || l > c->P.L)
       throw Error(ST_EINVAL, "keyswitch_noalloc: bad arguments");
-    auto it = c->ksk.find(key_id);
-    if (it == c->ksk.end()) throw Error(ST_ENOKEY, "keyswitch_noalloc: no such key");
+    const Ksk& fam = key_family(c, key_id, l);
     const size_t N = c->N;
-    const int K = c->P.K, L = c->P.L, ne = l + K;
+    const int K = fam.k, L = c->P.L, ne = l + K;
     const int beta = (l + c->alpha - 1) / c->alpha;
     const size_t need = ((size_t)3 * l + (size_t)(beta + 2) * ne) * N;
     if (need > kScratchWords)
@@ -75,7 +75,7 @@ extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int 
     ++c->ks_by_level[l];
     GWHE_CUDA(cudaMemcpyAsync(xc, x_ntt, sizeof(u64) * l * N, cudaMemcpyDeviceToDevice, c->stream));
     ntt_inverse(c, xc, rows_q(1, l, l));
-    modup_convert(c, xc, l, ext);
+    modup_convert_set(c, xc, l, ext, 1);
     for (int j = 0; j < beta; ++j) {
       const ConvTable& t = c->modup.at({l, j});
       RowMap rm;
@@ -88,7 +88,7 @@ extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int 
       }
       ntt_forward(c, ext + (size_t)j * ne * N, rm);
     }
-    ks_inner(c, x_ntt, l, ext, it->second.d, acc);
+    ks_inner_set(c, x_ntt, 0, l, ext, fam, acc, 1);
     RowMap rk;
     rk.npoly = 2;
     rk.nl = K;
@@ -98,9 +98,10 @@ extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int 
       rk.pidx[k] = (uint8_t)(L + k);
     }
     ntt_inverse(c, acc, rk);
-    moddown_convert(c, acc, l, conv);
+    moddown_convert_set(c, acc, l, K, conv, 1);
     ntt_forward(c, conv, rows_q(2, l, l));
-    moddown_combine(c, acc, conv, l, out_ntt, out_ntt + (size_t)l * N, nullptr, nullptr);
+    moddown_combine_set(c, acc, conv, l, K, 1, out_ntt, out_ntt + (size_t)l * N, 0, nullptr,
+                        nullptr, 0, 0);
     return GWHE_OK;
   } catch (const Error& e) {
     c->last_error = e.what();

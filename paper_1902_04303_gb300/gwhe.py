@@ -55,7 +55,8 @@ _SIGS = {
     "gwhe_keygen": [_vp, _i32p, _sz, _i],
     "gwhe_export_secret": [_vp, _i64p],
     "gwhe_export_pk": [_vp, _u64p],
-    "gwhe_export_ksk": [_vp, _u32, _u64p],
+    "gwhe_export_ksk": [_vp, _u32, _i, _u64p],
+    "gwhe_ks_special": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "gwhe_ct_create": [_vp, _i, _i, ctypes.POINTER(_vp)],
     "gwhe_ct_destroy": [_vp],
     "gwhe_ct_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
@@ -290,9 +291,24 @@ class Context:
         self._c(lib().gwhe_export_pk(self.h, pk))
         return pk
 
+    def ks_special(self, l):
+        """(special primes a switch at level l uses, highest level of that count)."""
+        k, lmax = _i(0), _i(0)
+        self._c(lib().gwhe_ks_special(self.h, l, ctypes.byref(k), ctypes.byref(lmax)))
+        return k.value, lmax.value
+
     def export_ksk(self, key_id):
-        out = np.zeros((self.dnum, 2, self.L + self.K, self.N), np.uint64)
-        self._c(lib().gwhe_export_ksk(self.h, key_id, out))
+        """{k: family [ceil(lmax/alpha)][2][lmax + k][N]} in the coefficient domain."""
+        alpha = -(-self.L // self.dnum)
+        fams = {}
+        for l in range(1, self.L + 1):
+            k, lmax = self.ks_special(l)
+            fams[k] = lmax
+        out = {}
+        for k, lmax in fams.items():
+            a = np.zeros((-(-lmax // alpha), 2, lmax + k, self.N), np.uint64)
+            self._c(lib().gwhe_export_ksk(self.h, key_id, k, a))
+            out[k] = a
         return out
 
     # ciphertexts

@@ -64,14 +64,19 @@ def test_ntt_roundtrip_and_negacyclic_product(g, logN):
 
 
 # ------------------------------------------------------------------ keys, encoding
-@pytest.mark.parametrize("logN,L,K,dnum", [(10, 6, 3, 3), (13, 4, 1, 4)])
+@pytest.mark.parametrize("logN,L,K,dnum", [(10, 6, 3, 3), (13, 4, 1, 4), (10, 9, 7, 2)])
 def test_keygen_bit_exact(g, logN, L, K, dnum):
     ctx, o = pair(g, logN, L, K, dnum)
     assert np.array_equal(ctx.export_secret(), o.secret_key())
     pk = ctx.export_pk()
     assert np.array_equal(pk[0], o.pk_b) and np.array_equal(pk[1], o.pk_a)
+    for l in range(1, L + 1):
+        assert ctx.ks_special(l) == (o.ks_k[l], o.key_lmax[o.ks_k[l]]), l
     for kid in [0, galois_rot(logN, 1), galois_rot(logN, -1), galois_conj(logN)]:
-        assert np.array_equal(ctx.export_ksk(kid), o.keys[kid]), kid
+        got, want = ctx.export_ksk(kid), o.keys[kid]
+        assert set(got) == set(want), kid
+        for k in want:
+            assert np.array_equal(got[k], want[k]), (kid, k)
 
 
 @pytest.mark.parametrize("logN", [5, 10, 13, 16])
@@ -173,6 +178,37 @@ def test_keyswitch_levels_bit_exact(g, small, l):
     x = rand_ct(o, l, 70 + l, npoly=1).c[0]
     for kid in (0, galois_conj(10)):
         assert np.array_equal(ctx.keyswitch(x, kid), o.keyswitch(x, kid))
+
+
+@pytest.fixture(scope="module")
+def wide(g):
+    # 7 special primes, digits of 5 limbs (two digits above level 5): levels
+    # 1..9 use 2..5 of them
+    return pair(g, 10, 9, 7, 2, seed=22)
+
+
+def test_wide_context_uses_several_special_prime_counts(wide):
+    ctx, o = wide
+    ks = [ctx.ks_special(l)[0] for l in range(1, 10)]
+    assert len(set(ks)) >= 3 and max(ks) < 7, ks
+
+
+@pytest.mark.parametrize("l", range(1, 10))
+def test_keyswitch_reduced_special_primes_bit_exact(g, wide, l):
+    """every level of a context whose switches use 2..5 of the 7 special
+    primes: relinearisation and rotation switches bit-exact, and a rotation
+    plus rescale through the set path."""
+    ctx, o = wide
+    x = rand_ct(o, l, 90 + l, npoly=1).c[0]
+    for kid in (0, galois_rot(10, 1)):
+        assert np.array_equal(ctx.keyswitch(x, kid), o.keyswitch(x, kid)), kid
+    if l >= 2:
+        a = rand_ct(o, l, 120 + l)
+        ga = ctx.import_ct(a.c, a.scale)
+        assert np.array_equal(ctx.rotate(ga, -1).export(), o.rotate(a, -1).c)
+        b = rand_ct(o, l, 140 + l)
+        gb = ctx.import_ct(b.c, b.scale)
+        assert np.array_equal(ctx.mult(ga, gb).export(), o.mult(a, b).c)
 
 
 def test_errors_are_status_codes(g, small):

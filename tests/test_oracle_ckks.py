@@ -280,6 +280,45 @@ def test_keyswitch_noise_invariant(small, l):
     assert _noise_of(o, u_bad, s2, x) > math.prod(o.q[:l]) // 2 ** 8
 
 
+@pytest.fixture(scope="module")
+def wide():
+    # K = 6 special primes, digits of 3 limbs: the switches at low levels use
+    # fewer special primes than those at the top
+    o = OracleCKKS(logN=9, L=6, K=6, dnum=2, seed=6)
+    o.keygen(galois=[galois_rot(9, 1)])
+    return o
+
+
+def test_special_prime_counts_shrink_with_the_level(wide):
+    """each level uses between one and K special primes, never fewer at a
+    higher level, and at least two counts occur in this context."""
+    o = wide
+    ks = o.ks_k[1:]
+    assert all(1 <= k <= o.K for k in ks)
+    assert all(a <= b for a, b in zip(ks, ks[1:]))
+    assert len(set(ks)) >= 2, ks
+    # one key family per count, each covering the levels that use it
+    assert set(o.keys[0]) == set(ks)
+    for k, fam in o.keys[0].items():
+        lmax = o.key_lmax[k]
+        assert fam.shape == (-(-lmax // o.alpha), 2, lmax + k, o.N)
+
+
+@pytest.mark.parametrize("l", [1, 2, 3, 4, 6])
+def test_keyswitch_noise_invariant_reduced_special_primes(wide, l):
+    """u0 + u1 s = x s^2 + e with |e| < 2^24 whatever the number of special
+    primes the level uses; a key for another target fails the identity."""
+    o = wide
+    rng = _rng(31 + l)
+    x = np.stack([rng.integers(0, o.q[i], size=o.N, dtype=np.uint64) for i in range(l)])
+    u = o.keyswitch(x, 0)
+    s2 = np.zeros((o.L + o.K, o.N), np.uint64)
+    L.or_sk_square(o._ctx, s2)
+    assert _noise_of(o, u, s2, x) < 2 ** 24
+    u_bad = o.keyswitch(x, galois_rot(9, 1))
+    assert _noise_of(o, u_bad, s2, x) > math.prod(o.q[:l]) // 2 ** 8
+
+
 def test_automorphism_rotates_slots():
     o = OracleCKKS(logN=8, L=2, K=1)
     rng = _rng(12)
