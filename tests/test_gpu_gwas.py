@@ -227,3 +227,34 @@ def test_large_cohort_auto_factored(g):
     num, den = job.decrypt_results()
     ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
     check_accuracy(num, den, ref, k)
+
+
+def test_sharded_batch_ranges_merge_into_one_job(g):
+    """The batch ranges two ranks would evaluate, run as two jobs here (one
+    GPU: no cross-rank waits), merge into exactly the one-job results."""
+    from paper_1902_04303_gb300.sharding import merge_shards, shard_batches, snp_range
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 13
+    n, d, k = 16, 3, 300  # five batches of 64 SNPs
+    data = make_gwas(n, d, k, seed=8)
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    full = g.Job(ctx, n, d, k)
+    ctx.keygen(rot_steps=full.rotation_steps(), conj=True)
+    full.encrypt_inputs(data.X, A, data.y)
+    full.fit(1)
+    full.snp_stats(data.S)
+    want_num, want_den = full.decrypt_results()
+    shards = []
+    for rank in range(2):
+        job = g.Job(ctx, n, d, k)
+        job.encrypt_inputs(data.X, A, data.y)
+        job.fit(1)
+        b0, b1 = shard_batches(job.layout["batches"], 2, rank)
+        job.snp_stats(data.S, b0, b1)
+        num, den = job.decrypt_results()
+        s0, s1 = snp_range(b0, b1, job.layout["tau"], k)
+        assert np.isnan(num[:s0]).all() and np.isnan(num[s1:]).all()
+        shards.append((s0, s1, num, den))
+    num, den, complete = merge_shards(shards, k)
+    assert complete
+    assert np.array_equal(num, want_num) and np.array_equal(den, want_den)
