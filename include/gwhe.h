@@ -179,6 +179,14 @@ int gwhe_rescale(gwhe_ctx* ctx, gwhe_ct* ct);                         /* drops q
 int gwhe_mult(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
 int gwhe_rotate(gwhe_ctx* ctx, const gwhe_ct* a, int steps, gwhe_ct* out); /* out != a */
 int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out);         /* out != a */
+/* out = a + sum_i Rotate(a, steps[i]) for 1 <= nsteps <= 3, the rotations'
+ * key switches hoisted: one ModUp of c1, each rotation's automorphism applied
+ * to the ModUp digits, the inner products with the rotations' keys summed in
+ * the extended basis, one ModDown.  Two steps r, 2r of a doubling
+ * rotate-and-add ladder (Alg. 1, 4, 5, 7) are the sum over {r, 2r, 3r}; the
+ * library's ladders run this way.  out != a; needs the rotations' keys. */
+int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int nsteps,
+                    gwhe_ct* out);
 int gwhe_drop(gwhe_ct* ct, int l);                                          /* keep l limbs */
 /* Hybrid key switch of one coefficient-domain polynomial x (uint64[l][N],
  * host) with key key_id: out = uint64[2][l][N] coefficient domain (host). */

@@ -90,13 +90,43 @@ class Layout:
             raise ValueError("a column of nb slots does not fit one ciphertext")
 
 
-def rotation_steps(layout: Layout, factored: bool = False):
-    """All rotations the circuit uses: 2^i for i < log2(M) (ladders of Alg. 1,
-    4, 5, 7 all rotate by powers of two); the factored layout's in-block
-    broadcast adds the right rotations -2^i for 2^i < nb."""
-    steps = [1 << i for i in range(layout.logN - 1)]
+def ladder_groups(steps):
+    """Hoisted evaluation of a doubling ladder v += Rotate(v, s) over steps:
+    consecutive steps r, 2r merge into one group {r, 2r, 3r} (the same sum of
+    rotations, v + Rot(v, r) + Rot(v, 2r) + Rot(v, 3r)); a step without a
+    partner stays alone."""
+    out, i = [], 0
+    while i < len(steps):
+        if i + 1 < len(steps) and steps[i + 1] == 2 * steps[i]:
+            out.append([steps[i], 2 * steps[i], 3 * steps[i]])
+            i += 2
+        else:
+            out.append([steps[i]])
+            i += 1
+    return out
+
+
+def circuit_ladders(layout: Layout, factored: bool = False):
+    """The step lists of the circuit's ladders: Replicate/DotProd over all
+    slots (Alg. 1, 5), colSum over nb (Alg. 4), Duplicate over the blocks
+    (Alg. 7), and the factored layout's in-block broadcast."""
+    lad = [[1 << i for i in range(layout.logN - 1)],
+           [1 << i for i in range(int(math.log2(layout.nb)))],
+           [layout.nb << i for i in range(int(math.log2(layout.B)))]]
     if factored:
-        steps += [-(1 << i) for i in range(int(math.log2(layout.nb)))]
+        lad.append([-(1 << i) for i in range(int(math.log2(layout.nb)))])
+    return lad
+
+
+def rotation_steps(layout: Layout, factored: bool = False):
+    """All rotations whose keys the circuit needs, as its hoisted ladder
+    groups use them."""
+    steps = []
+    for lad in circuit_ladders(layout, factored):
+        for g in ladder_groups(lad):
+            for r in g:
+                if r not in steps:
+                    steps.append(r)
     return steps
 
 
@@ -108,6 +138,13 @@ class Circuit:
         layout.check()
 
     # --------------------------------------------------------- primitives
+    def ladder(self, v: Ct, steps) -> Ct:
+        """v += Rotate(v, s) for s in steps (the doubling ladders of Alg. 1, 4,
+        5, 7), evaluated as hoisted rotation sums over ladder_groups(steps)."""
+        for g in ladder_groups(steps):
+            v = self.ev.rotate_sum(v, g)
+        return v
+
     def e_slot(self, c):
         z = np.zeros(self.lay.M)
         z[c] = 1.0
@@ -126,8 +163,7 @@ class Circuit:
         """Alg. 1 for entry c: mask slot c, then a log2(M) rotate-and-add ladder."""
         ev = self.ev
         t = ev.mul_mask(v, self.e_slot(c))
-        for i in range(self.lay.logN - 1):
-            t = ev.add(t, ev.rotate(t, 1 << i))
+        t = self.ladder(t, [1 << i for i in range(self.lay.logN - 1)])
         return t
 
     def cp_matvec(self, cols, v: Ct, m: int) -> Ct:
@@ -140,8 +176,7 @@ class Circuit:
         """Alg. 5: C = A * B, then C += Rotate(C, 2^i) for i < log2(M)."""
         ev = self.ev
         t = ev.mult(a, b)
-        for i in range(self.lay.logN - 1):
-            t = ev.add(t, ev.rotate(t, 1 << i))
+        t = self.ladder(t, [1 << i for i in range(self.lay.logN - 1)])
         return t
 
     def rp_matvec(self, rows, v: Ct, m: int) -> Ct:
@@ -157,16 +192,12 @@ class Circuit:
 
     def colsum(self, v: Ct) -> Ct:
         """Alg. 4: log2(nb) rotate-and-add steps; sums land at slots c*nb."""
-        ev = self.ev
-        for i in range(int(math.log2(self.lay.nb))):
-            v = ev.add(v, ev.rotate(v, 1 << i))
+        v = self.ladder(v, [1 << i for i in range(int(math.log2(self.lay.nb)))])
         return v
 
     def duplicate(self, v: Ct) -> Ct:
         """Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks."""
-        ev = self.ev
-        for i in range(int(math.log2(self.lay.B))):
-            v = ev.add(v, ev.rotate(v, self.lay.nb << i))
+        v = self.ladder(v, [self.lay.nb << i for i in range(int(math.log2(self.lay.B)))])
         return v
 
     def sigma7(self, x: Ct) -> Ct:
@@ -394,8 +425,7 @@ class Circuit:
         for c in range(d):
             u = self.colsum(ev.mult(self.DupX[c], Sct))
             r = ev.mul_mask(u, heads)
-            for i in range(int(math.log2(lay.nb))):
-                r = ev.add(r, ev.rotate(r, -(1 << i)))
+            r = self.ladder(r, [-(1 << i) for i in range(int(math.log2(lay.nb)))])
             R.append(r)
         lv = R[0].level
         P = self.mac_relin_rescale([(ev.drop(self.DupB[c], lv), R[c]) for c in range(d)])

@@ -70,6 +70,7 @@ def lib():
         "or_tensor": (None, [vp, _u64p, _u64p, i32, _u64p]),
         "or_rescale": (None, [vp, _u64p, i32, i32, _u64p]),
         "or_keyswitch": (None, [vp, _u64p, i32, _u64p, i32, _u64p]),
+        "or_keyswitch_hoisted": (None, [vp, _u64p, i32, i32, _u64p, _u64p, i32, _u64p]),
         "or_fft_twiddles": (None, [i32, i32, _f64p, _f64p]),
         "or_encode": (None, [i32, _f64p, dbl, _i64p]),
         "or_to_rns": (None, [vp, _i64p, i32, _u64p]),
@@ -450,3 +451,21 @@ class OracleCKKS:
 
     def conj(self, a: Ct) -> Ct:
         return self.apply_galois(a, galois_conj(self.logN))
+
+    def rotate_sum(self, a: Ct, rs) -> Ct:
+        """a + sum_r Rotate(a, r) with the rotations' key switches hoisted: one
+        ModUp of c1, each rotation's automorphism applied to the ModUp digits,
+        the inner products with the rotations' keys summed in the extended
+        basis, one ModDown; c0 + sum_r sigma_r(c0) is added exactly."""
+        l = a.level
+        k = self.ks_k[l]
+        gal = [galois_rot(self.logN, r) for r in rs]
+        keys = np.ascontiguousarray(np.stack([self.keys[g][k] for g in gal]))
+        ks = np.zeros((2, l, self.N), np.uint64)
+        lib().or_keyswitch_hoisted(self._ctx, np.ascontiguousarray(a.c[1]), l, len(gal),
+                                   np.array(gal, np.uint64), keys, self.key_lmax[k], ks)
+        acc = Ct(np.stack([a.c[0], a.c[1]]), a.scale)
+        for g in gal:
+            rot0 = self.automorphism(Ct(a.c[0:1].copy(), a.scale), g)
+            acc = self.add(acc, Ct(np.concatenate([rot0.c, np.zeros_like(rot0.c)]), a.scale))
+        return self.add(acc, Ct(ks, a.scale))

@@ -619,12 +619,33 @@ void or_rescale(const void *ctx, const u64 *in, int npoly, int l, u64 *out)
  *   inner   : acc_t = sum_j ext_{j,t} * ksk_j,t (negacyclic products)
  *   ModDown : z_k = [acc_{p_k} (P/p_k)^-1]_{p_k};  conv_i = sum_k z_k (P/p_k) mod q_i;
  *             out_i = (acc_i - conv_i) P^-1 mod q_i                                */
-/* Hybrid key switch of x (coefficient domain, l limbs) with the key family of
+/* Hybrid key switch of x (coefficient domain, l limbs) with key families of
  * K_l = or_ks_special(l) special primes (built by or_keygen_ksk with that k
- * and key_lmax >= l): ModUp per digit, inner product, ModDown by P_{K_l}. */
+ * and key_lmax >= l): ModUp per digit, inner product, ModDown by P_{K_l}.
+ *
+ * With ngal > 0 this is the hoisted sum over Galois elements gal[0..ngal):
+ * the ModUp digits are computed once, each element's automorphism is applied
+ * to them (limb by limb, modulo that limb's modulus), their inner products
+ * with the element's key (ksk holds ngal families back to back) are summed in
+ * the extended basis, and one ModDown follows.  ngal = 0 is the plain switch
+ * of x with the one key in ksk. */
+static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const u64 *gal,
+                          const u64 *ksk, int key_lmax, u64 *out);
+
 void or_keyswitch(const void *ctx, const u64 *x, int l, const u64 *ksk, int key_lmax, u64 *out)
 {
-    const or_ctx *c = (const or_ctx *)ctx;
+    keyswitch_sum((const or_ctx *)ctx, x, l, 0, NULL, ksk, key_lmax, out);
+}
+
+void or_keyswitch_hoisted(const void *ctx, const u64 *x, int l, int ngal, const u64 *gal,
+                          const u64 *ksk, int key_lmax, u64 *out)
+{
+    keyswitch_sum((const or_ctx *)ctx, x, l, ngal, gal, ksk, key_lmax, out);
+}
+
+static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const u64 *gal,
+                          const u64 *ksk, int key_lmax, u64 *out)
+{
     const int N = c->N, L = c->L, K = c->ks_k[l], nm = key_lmax + K, ne = l + K;
     const int beta = (l + c->alpha - 1) / c->alpha;
     u64 emod[OR_MAXMOD];
@@ -663,18 +684,30 @@ void or_keyswitch(const void *ctx, const u64 *x, int l, const u64 *ksk, int key_
             }
         }
     }
-    /* inner product with the key */
-    for (int pz = 0; pz < 2; pz++)
-        for (int u = 0; u < ne; u++) {
-            u64 m = emod[u];
-            u64 psi = u < l ? c->psi[u] : c->psi[L + (u - l)];
-            u64 *a = acc + ((size_t)pz * ne + u) * N;
-            for (int j = 0; j < beta; j++) {
-                const u64 *kj = ksk + (((size_t)j * 2 + pz) * nm + ekey[u]) * N;
-                or_polymul(ext + ((size_t)j * ne + u) * N, kj, t, c->logN, m, psi);
-                for (int k = 0; k < N; k++) a[k] = madd(a[k], t[k], m);
+    /* inner product with the key (or the sum over the automorphisms' keys) */
+    const int dk = (key_lmax + c->alpha - 1) / c->alpha;
+    const size_t fam_words = (size_t)dk * 2 * nm * N;
+    u64 *sg = (u64 *)malloc(sizeof(u64) * N);
+    for (int gi = 0; gi < (ngal > 0 ? ngal : 1); gi++) {
+        const u64 *key = ksk + (size_t)gi * fam_words;
+        for (int pz = 0; pz < 2; pz++)
+            for (int u = 0; u < ne; u++) {
+                u64 m = emod[u];
+                u64 psi = u < l ? c->psi[u] : c->psi[L + (u - l)];
+                u64 *a = acc + ((size_t)pz * ne + u) * N;
+                for (int j = 0; j < beta; j++) {
+                    const u64 *kj = key + (((size_t)j * 2 + pz) * nm + ekey[u]) * N;
+                    const u64 *ej = ext + ((size_t)j * ne + u) * N;
+                    if (ngal > 0) {
+                        or_automorphism(ej, sg, c->logN, gal[gi], m);
+                        ej = sg;
+                    }
+                    or_polymul(ej, kj, t, c->logN, m, psi);
+                    for (int k = 0; k < N; k++) a[k] = madd(a[k], t[k], m);
+                }
             }
-        }
+    }
+    free(sg);
     /* ModDown */
     u64 phinv[OR_MAXMOD];           /* (P/p_k)^-1 mod p_k */
     u64 phmod[OR_MAXMOD][OR_MAXMOD]; /* (P/p_k) mod q_i    */

@@ -5,7 +5,8 @@ oracle/circuit.py) on ciphertexts of ONE coefficient per limb, so that only
 the bookkeeping is real: the level of every ciphertext, its scale (product of
 the operands' scales, divided by the dropped prime on each rescale, sect. 2.2)
 and the number of key switches issued at each level (one per
-relinearisation and one per rotation or conjugation, sect. 2.3).  No
+relinearisation or conjugation, and one per hoisted group of ladder rotations,
+which shares one ModUp and one ModDown).  No
 ciphertext arithmetic is meaningful here; the tracer exists to count the
 work of a job at full size in a fraction of a second.
 
@@ -62,6 +63,10 @@ class LevelTrace(OracleCKKS):
         return Ct(self._z(a.c.shape[0], l - 1), a.scale / float(self.q[l - 1]))
 
     def automorphism(self, a: Ct, g: int) -> Ct:
+        return Ct(np.zeros_like(a.c), a.scale)
+
+    def rotate_sum(self, a: Ct, rs) -> Ct:
+        self.ks_hist[a.level] += 1
         return Ct(np.zeros_like(a.c), a.scale)
 
 

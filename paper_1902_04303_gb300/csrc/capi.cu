@@ -350,6 +350,27 @@ int gwhe_mult(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out) {
 int gwhe_rotate(gwhe_ctx* ctx, const gwhe_ct* a, int steps, gwhe_ct* out) {
   return guard(C(ctx), [&] { op_rotate(C(ctx), CT(a), steps, CT(out)); });
 }
+int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int nsteps,
+                    gwhe_ct* out) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    need(a && out && steps && nsteps >= 1 && nsteps <= 3, "bad rotation sum");
+    const Ct& x = *a->ct;
+    need(x.npoly == 2 && out->ct->npoly == 2 && out->ct->cap >= x.l, "bad ciphertexts");
+    CtSetPtr s = set_new(c, 1, 2, x.l, x.l, x.scale);
+    for (int p = 0; p < 2; ++p)
+      GWHE_CUDA(cudaMemcpyAsync(s->item(0) + (size_t)p * x.l * c->N, x.poly(p),
+                                sizeof(u64) * x.l * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    set_rotate_sum(c, *s, std::vector<int>(steps, steps + nsteps));
+    Ct& o = *out->ct;
+    for (int p = 0; p < 2; ++p)
+      GWHE_CUDA(cudaMemcpyAsync(o.poly(p), s->item(0) + (size_t)p * x.l * c->N,
+                                sizeof(u64) * x.l * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    o.l = x.l;
+    o.scale = x.scale;
+  });
+}
+
 int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out) {
   return guard(C(ctx), [&] { op_conj(C(ctx), CT(a), CT(out)); });
 }

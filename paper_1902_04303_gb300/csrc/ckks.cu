@@ -699,26 +699,20 @@ static T* upload_async(Context* c, Tmp& t, const std::vector<T>& v) {
   return t.as<T>();
 }
 
-// Hybrid key switch of cnt ciphertext parts at level l with the key family of
-// K_l special primes: ModUp (iNTT, fast base conversion per digit, NTT of the
-// new limbs), the inner product with the key digits, ModDown (iNTT of the
-// special limbs, conversion to the q-limbs, NTT, (x - conv) P_{K_l}^-1).
-void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const KeySet& key,
-                   u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
-                   size_t a0_stride, size_t a1_stride) {
+// ModUp of cnt inputs (NTT domain, item i at x + i x_stride, l limbs): the
+// coefficient form of each digit is converted to the other limbs of the
+// extended basis (K = ks_k[l] special primes) and transformed back; ext is
+// [cnt][beta][ne][N] and omits the digit's own limbs (read from x).
+static void modup_ext(Context* c, const u64* x, size_t x_stride, int cnt, int l, u64* ext) {
   const size_t N = c->N;
-  const Ksk& fam = key.fam[c->ks_k[l]];
-  GWHE_REQUIRE(fam.d && fam.lmax >= l, ST_ENOKEY, "switching key family missing");
-  const int K = fam.k, L = c->P.L, ne = l + K;
+  const int ne = l + c->ks_k[l];
   const int beta = (l + c->alpha - 1) / c->alpha;
-  c->ks_count += cnt;
-  c->ks_by_level[l] += cnt;
   Tmp xc(c, sizeof(u64) * cnt * l * N);
-  GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x, sizeof(u64) * std::max<size_t>(x_stride, l * N),
-                              sizeof(u64) * l * N, cnt, cudaMemcpyDeviceToDevice, c->stream));
+  GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x,
+                              sizeof(u64) * std::max<size_t>(x_stride, l * N), sizeof(u64) * l * N,
+                              cnt, cudaMemcpyDeviceToDevice, c->stream));
   ntt_inverse(c, xc.u(), rows_q(cnt, l, l));
-  Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
-  modup_convert_set(c, xc.u(), l, ext.u(), cnt);
+  modup_convert_set(c, xc.u(), l, ext, cnt);
   for (int j = 0; j < beta; ++j) {
     const ConvTable& t = c->modup.at({l, j});
     RowMap rm;
@@ -729,10 +723,17 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
       rm.off[o] = (uint16_t)(j * ne + t.out_limb[o]);
       rm.pidx[o] = t.out_pidx[o];
     }
-    ntt_forward(c, ext.u(), rm);
+    ntt_forward(c, ext, rm);
   }
-  Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
-  ks_inner_set(c, x, x_stride, l, ext.u(), fam, acc.u(), cnt);
+}
+
+// ModDown of cnt key products acc ([cnt][2][ne][N], NTT domain) by P_K into
+// out0/out1 (+ add0/add1), item strides as given.
+static void moddown_out(Context* c, u64* acc, int cnt, int l, int K, u64* out0, u64* out1,
+                        size_t o_stride, const u64* add0, const u64* add1, size_t a0_stride,
+                        size_t a1_stride) {
+  const size_t N = c->N;
+  const int L = c->P.L, ne = l + K;
   RowMap rk;
   rk.npoly = 2 * cnt;
   rk.nl = K;
@@ -741,29 +742,87 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
     rk.off[k] = (uint16_t)(l + k);
     rk.pidx[k] = (uint8_t)(L + k);
   }
-  ntt_inverse(c, acc.u(), rk);
+  ntt_inverse(c, acc, rk);
   Tmp conv(c, sizeof(u64) * cnt * 2 * l * N);
-  moddown_convert_set(c, acc.u(), l, K, conv.u(), cnt);
+  moddown_convert_set(c, acc, l, K, conv.u(), cnt);
   ntt_forward(c, conv.u(), rows_q(2 * cnt, l, l));
-  moddown_combine_set(c, acc.u(), conv.u(), l, K, cnt, out0, out1, o_stride, add0, add1,
-                      a0_stride, a1_stride);
+  moddown_combine_set(c, acc, conv.u(), l, K, cnt, out0, out1, o_stride, add0, add1, a0_stride,
+                      a1_stride);
+}
+
+// Hybrid key switch of cnt ciphertext parts at level l with the key family of
+// K_l special primes: ModUp (iNTT, fast base conversion per digit, NTT of the
+// new limbs), the inner product with the key digits, ModDown (iNTT of the
+// special limbs, conversion to the q-limbs, NTT, (x - conv) P_{K_l}^-1).
+void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const KeySet& key,
+                   u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
+                   size_t a0_stride, size_t a1_stride) {
+  const size_t N = c->N;
+  const Ksk& fam = key.fam[c->ks_k[l]];
+  GWHE_REQUIRE(fam.d && fam.lmax >= l, ST_ENOKEY, "switching key family missing");
+  const int K = fam.k, ne = l + K;
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  c->ks_count += cnt;
+  c->ks_by_level[l] += cnt;
+  Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
+  modup_ext(c, x, x_stride, cnt, l, ext.u());
+  Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
+  ks_inner_set(c, x, x_stride, l, ext.u(), fam, acc.u(), cnt);
+  moddown_out(c, acc.u(), cnt, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride);
+}
+
+// s[i] <- s[i] + sum_{r in rs} Rotate(s[i], r), the rotations' key switches
+// hoisted: one ModUp of each c1, the automorphisms applied to the ModUp
+// digits, the inner products with the rotations' keys summed in the extended
+// basis, one ModDown; c0 + sum_r sigma_r(c0) is added exactly.  Counts as one
+// key switch per item.
+void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs) {
+  const size_t N = c->N;
+  const int l = s.l, cnt = s.cnt;
+  GWHE_REQUIRE(!rs.empty() && (int)rs.size() <= kMaxHoist, ST_EINVAL, "bad hoisted rotation set");
+  const int K = c->ks_k[l], ne = l + K;
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  HoistKeys hk;
+  hk.G = (int)rs.size();
+  int key_lmax = 0;
+  for (int g = 0; g < hk.G; ++g) {
+    const u32 gal = galois_for_rotation(c, rs[g]);
+    const Ksk& fam = key_family(c, gal, l);
+    hk.key[g] = fam.d;
+    hk.g[g] = gal;
+    key_lmax = fam.lmax;
+  }
+  c->ks_count += cnt;
+  c->ks_by_level[l] += cnt;
+  u64* c1 = s.d + (size_t)s.cap * N;
+  Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
+  modup_ext(c, c1, s.stride(), cnt, l, ext.u());
+  Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
+  ks_inner_hoist_set(c, c1, s.stride(), l, ext.u(), hk, key_lmax, K, acc.u(), cnt);
+  Tmp t0(c, sizeof(u64) * cnt * l * N);
+  automorph_sum_set(c, s.d, s.cap, s.stride(), t0.u(), l, cnt, hk);
+  moddown_out(c, acc.u(), cnt, l, K, s.d, c1, s.stride(), t0.u(), c1, (size_t)l * N, s.stride());
+}
+
+std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps) {
+  // consecutive steps r, 2r of a doubling ladder merge into one hoisted step
+  // over the rotations r, 2r, 3r (the same sum of rotations)
+  std::vector<std::vector<int>> out;
+  for (size_t i = 0; i < steps.size();) {
+    if (i + 1 < steps.size() && steps[i + 1] == 2 * steps[i]) {
+      out.push_back({steps[i], 2 * steps[i], 3 * steps[i]});
+      i += 2;
+    } else {
+      out.push_back({steps[i]});
+      i += 1;
+    }
+  }
+  return out;
 }
 
 void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps) {
   GWHE_REQUIRE(s.npoly == 2, ST_EINVAL, "ladder needs ciphertexts");
-  const size_t N = c->N;
-  const int l = s.l;
-  Tmp t(c, sizeof(u64) * s.cnt * 2 * l * N);
-  for (int step : steps) {
-    const u32 g = galois_for_rotation(c, step);
-    auto it = c->ksk.find(g);
-    GWHE_REQUIRE(it != c->ksk.end(), ST_ENOKEY, "missing Galois key " + std::to_string(g));
-    // t = (sigma(s0) + s0, sigma(s1)); s = (t0 + KS(t1)_0, s1 + KS(t1)_1)
-    automorph_ladder_set(c, s.d, s.cap, s.stride(), t.u(), l, (size_t)2 * l * N, l, s.cnt, g);
-    keyswitch_set(c, t.u() + (size_t)l * N, (size_t)2 * l * N, s.cnt, l, it->second, s.d,
-                  s.d + (size_t)s.cap * N, s.stride(), t.u(), s.d + (size_t)s.cap * N,
-                  (size_t)2 * l * N, s.stride());
-  }
+  for (const auto& rs : ladder_groups(steps)) set_rotate_sum(c, s, rs);
 }
 
 void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out) {

@@ -101,8 +101,14 @@ CtSetPtr set_new(Context* c, int cnt, int npoly, int cap, int l, double scale);
 void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, const KeySet& key,
                    u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                    size_t a0_stride, size_t a1_stride);
-// s[i] += Rotate(s[i], step) for each step in turn (Alg. 1/4/5/7 ladders)
+// s[i] += Rotate(s[i], step) for each step in turn (Alg. 1/4/5/7 ladders),
+// evaluated as hoisted sums over the groups of ladder_groups(steps)
 void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps);
+// s[i] += sum_{r in rs} Rotate(s[i], r) with the key switches hoisted (one
+// ModUp, one ModDown; at most three rotations)
+void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs);
+// consecutive doubling steps (r, 2r) -> one group {r, 2r, 3r}; others alone
+std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps);
 // out[i] = automorphism g of a[i] (rotation or conjugation)
 void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out);
 // out[i] = items[i].src * items[i].pt, scale = src scale * pt_scale (then rescale)

@@ -317,10 +317,21 @@ Job* job_create(Context* c, int n, int d, long k, int mode) {
 }
 
 std::vector<int> job_rotation_steps(const Job* j) {
-  std::vector<int> s;
-  for (int i = 0; i < j->lay.logN - 1; ++i) s.push_back(1 << i);
+  // every rotation of the circuit's ladders (Replicate and DotProd over all
+  // slots, colSum over nb, Duplicate over the blocks, the factored layout's
+  // in-block broadcast), as the hoisted groups evaluate them
+  const Layout& lay = j->lay;
+  std::vector<std::vector<int>> ladders(4);
+  for (int i = 0; i < lay.logN - 1; ++i) ladders[0].push_back(1 << i);
+  for (int i = 0; i < ilog2(lay.nb); ++i) ladders[1].push_back(1 << i);
+  for (int i = 0; i < ilog2(lay.B); ++i) ladders[2].push_back(lay.nb << i);
   if (j->factored)
-    for (int i = 0; i < ilog2(j->lay.nb); ++i) s.push_back(-(1 << i));
+    for (int i = 0; i < ilog2(lay.nb); ++i) ladders[3].push_back(-(1 << i));
+  std::vector<int> s;
+  for (const auto& steps : ladders)
+    for (const auto& g : ladder_groups(steps))
+      for (int r : g)
+        if (std::find(s.begin(), s.end(), r) == s.end()) s.push_back(r);
   return s;
 }
 

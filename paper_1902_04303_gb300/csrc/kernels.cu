@@ -204,6 +204,90 @@ __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
   }
 }
 
+// NTT slot j holds a(psi^(2 brv(j) + 1)); X -> X^g maps it to slot
+// brv((g (2 brv(j) + 1) mod 2N - 1) / 2) of the input.
+__device__ __forceinline__ unsigned automorph_src(unsigned j, u64 g, int logN) {
+  const u64 twoN_mask = ((u64)2 << logN) - 1;
+  const u64 e = 2 * (u64)(__brev(j) >> (32 - logN)) + 1;
+  const u64 f = (g * e) & twoN_mask;
+  return __brev((unsigned)((f - 1) >> 1)) >> (32 - logN);
+}
+
+// Hoisted inner product for a sum of automorphisms: acc_p[u] = sum_g sum_j
+// sigma_g(x_j)[u] * key_g,j[p][u], x_j the ModUp digits of one c1 (the input
+// limb itself when u lies in digit j).  sigma_g is a permutation of NTT slots,
+// applied while reading; all G beta products are summed on 128 bits and
+// reduced once.  Each thread keeps its key words in registers for up to IB
+// items.
+template <int IB, int G>
+__global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
+                                 const u64* __restrict__ ext, HoistKeys hk,
+                                 u64* __restrict__ acc, int l, int K, int L, int key_lmax,
+                                 int alpha, int beta, int logN, int cnt,
+                                 const DevMod* __restrict__ mod) {
+  const int u = blockIdx.y;
+  const int N = 1 << logN;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int ne = l + K;
+  const int mi = u < l ? u : L + (u - l);
+  const int kr = u < l ? u : key_lmax + (u - l);
+  const size_t KR = (size_t)(key_lmax + K);
+  u64 kb[G][kKsMaxBeta], ka[G][kKsMaxBeta];
+  unsigned src[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    src[g] = automorph_src((unsigned)k, hk.g[g], logN);
+#pragma unroll
+    for (int j = 0; j < kKsMaxBeta; ++j)
+      if (j < beta) {
+        kb[g][j] = hk.key[g][(((size_t)j * 2 + 0) * KR + kr) * N + k];
+        ka[g][j] = hk.key[g][(((size_t)j * 2 + 1) * KR + kr) * N + k];
+      }
+  }
+  const DevMod m = mod[mi];
+  const int it0 = blockIdx.z * IB;
+  const int it1 = min(it0 + IB, cnt);
+  for (int item = it0; item < it1; ++item) {
+    const u64* cx = c_ntt + (size_t)item * c_stride + (size_t)u * N;
+    const u64* ex = ext + (size_t)item * beta * ne * N;
+    Acc128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+    for (int j = 0; j < kKsMaxBeta; ++j) {
+      if (j >= beta) break;
+      const int lo = j * alpha, hi = min(lo + alpha, l);
+      const u64* row = (u >= lo && u < hi) ? cx : ex + ((size_t)j * ne + u) * N;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const u64 x = row[src[g]];
+        mac128(s0, x, kb[g][j]);
+        mac128(s1, x, ka[g][j]);
+      }
+    }
+    u64* ac = acc + (size_t)item * 2 * ne * N;
+    ac[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
+    ac[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+  }
+}
+
+// out[item][i] = c0[item][i] + sum_g sigma_g(c0[item][i]) (NTT domain)
+template <int G>
+__global__ void k_automorph_sum(const u64* __restrict__ in, int in_cap, size_t in_stride,
+                                u64* __restrict__ out, int l, int logN, HoistKeys hk,
+                                const DevMod* __restrict__ mod) {
+  const int i = blockIdx.y;
+  const int N = 1 << logN;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const size_t item = blockIdx.z;
+  const u64* src = in + item * in_stride + (size_t)i * N;
+  const u64 q = mod[i].q;
+  u64 v = src[j];
+#pragma unroll
+  for (int g = 0; g < G; ++g) v = addmod(v, src[automorph_src((unsigned)j, hk.g[g], logN)], q);
+  out[(item * l + i) * N + j] = v;
+}
+
 // out_p[i] = (acc_p[i] - conv_p[i]) P^-1 mod q_i (+ add_p[i])
 __global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __restrict__ conv, int l,
                                   int K, u64* out0, u64* out1, size_t o_stride, const u64* add0,
@@ -978,6 +1062,50 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
   k_ks_inner<IB><<<dim3(blocks_for(c->N), l + K, (cnt + IB - 1) / IB), kThreads, 0,
                    c->stream>>>(c_ntt, c_stride, ext, key.d, acc, l, K, c->P.L, key.lmax,
                                 c->alpha, beta, c->N, cnt, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
+                        const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt) {
+  const double ne_ = l + K, beta_ = (l + c->alpha - 1) / c->alpha;
+  ProfScope ps(c, PROF_KS_INNER, ((1.0 + 2.0 * hk.G) * beta_ * ne_ + 2.0 * ne_) * 8.0 * c->N * cnt);
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
+  constexpr int IB = 8;
+  const dim3 grid(blocks_for(c->N), l + K, (cnt + IB - 1) / IB);
+  switch (hk.G) {
+    case 1:
+      k_ks_inner_hoist<IB, 1><<<grid, kThreads, 0, c->stream>>>(
+          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
+          c->d_mod);
+      break;
+    case 2:
+      k_ks_inner_hoist<IB, 2><<<grid, kThreads, 0, c->stream>>>(
+          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
+          c->d_mod);
+      break;
+    case 3:
+      k_ks_inner_hoist<IB, 3><<<grid, kThreads, 0, c->stream>>>(
+          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
+          c->d_mod);
+      break;
+    default: throw Error(ST_EINVAL, "at most three hoisted automorphisms");
+  }
+  GWHE_LAUNCHED(c, 1);
+}
+
+void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out, int l,
+                       int cnt, const HoistKeys& hk) {
+  ProfScope ps(c, PROF_ELEMWISE, (1.0 + hk.G) * l * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  const dim3 grid(blocks_for(c->N), l, cnt);
+  switch (hk.G) {
+    case 1: k_automorph_sum<1><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
+    case 2: k_automorph_sum<2><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
+    case 3: k_automorph_sum<3><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
+    default: throw Error(ST_EINVAL, "at most three hoisted automorphisms");
+  }
   GWHE_LAUNCHED(c, 1);
 }
 

@@ -55,6 +55,20 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
 void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int K, int cnt,
                          u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                          size_t a0_stride, size_t a1_stride);
+// Hoisted key switching of a sum of automorphisms (at most kMaxHoist): the
+// Galois elements and the key family each uses.
+constexpr int kMaxHoist = 3;
+struct HoistKeys {
+  const u64* key[kMaxHoist];
+  u64 g[kMaxHoist];
+  int G;
+};
+// acc = sum_g <sigma_g(ModUp digits), key_g> for cnt items (c_ntt: the items' c1)
+void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
+                        const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt);
+// out[item] ([cnt][l][N]) = c0 + sum_g sigma_g(c0), c0 = item poly 0
+void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out, int l,
+                       int cnt, const HoistKeys& hk);
 // out[item] = (sigma_g(in0) + in0, sigma_g(in1)): the automorphism of a ladder step
 void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out,
                           int out_cap, size_t out_stride, int l, int cnt, u64 g);

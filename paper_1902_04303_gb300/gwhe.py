@@ -89,6 +89,7 @@ _SIGS = {
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
     "gwhe_job_create_ex": [_vp, _i, _i, _l, _i, ctypes.POINTER(_vp)],
     "gwhe_job_info": [_vp, ctypes.POINTER(_l)],
+    "gwhe_rotate_sum": [_vp, _vp, ctypes.POINTER(ctypes.c_int32), _i, _vp],
     "gwhe_probe_butterflies": [_vp, _i, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)],
     "gwhe_job_rotation_steps": [_vp, ctypes.POINTER(ctypes.c_int32), _i, ctypes.POINTER(_i)],
@@ -424,6 +425,13 @@ class Context:
     def conj(self, a):
         o = self._out(a)
         self._c(lib().gwhe_conjugate(self.h, a.h, o.h))
+        return o
+
+    def rotate_sum(self, a, steps):
+        """a + sum_r Rotate(a, r) over at most three steps, key switches hoisted."""
+        o = self._out(a)
+        arr = (ctypes.c_int32 * len(steps))(*steps)
+        self._c(lib().gwhe_rotate_sum(self.h, a.h, arr, len(steps), o.h))
         return o
 
     def keyswitch(self, x, key_id):

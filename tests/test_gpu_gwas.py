@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import gwas_fp64
-from oracle.circuit import Circuit, Layout, rotation_steps
+from oracle.circuit import Circuit, Layout, ladder_groups, rotation_steps
 from oracle.ckks import OracleCKKS, galois_conj, galois_rot
 from oracle.trace import job_ks_histogram
 from paper_1902_04303_gb300.datagen import WORKLOADS, make_gwas
@@ -88,7 +88,8 @@ def test_job_split_mode_small_workload(g):
     data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"])
     ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1)
     lay = Layout(W["logN"], W["n"], W["d"], W["k"])
-    steps = [1 << i for i in range(int(np.log2(lay.nb)))]  # colSum only
+    # colSum only, as its hoisted groups use them
+    steps = [r for grp in ladder_groups([1 << i for i in range(int(np.log2(lay.nb)))]) for r in grp]
     ctx = g.Context(W["logN"], W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
     ctx.keygen(rot_steps=steps, conj=True)
     job = g.Job(ctx, W["n"], W["d"], W["k"])
@@ -115,8 +116,8 @@ def test_job_paper_shape_accuracy(g):
     A = gwas_fp64.xtx_inv(data.X)
     ctx = g.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
                     W["dnum"], seed=W["seed"])
-    ctx.keygen(rot_steps=[1 << i for i in range(W["logN"] - 1)], conj=True)
     job = g.Job(ctx, W["n"], W["d"], W["k"], layout="mccp")
+    ctx.keygen(rot_steps=job.rotation_steps(), conj=True)
     assert job.layout["tau"] == 256 and job.layout["batches"] == 42 and job.layout["H"] == 2
     ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
@@ -132,8 +133,8 @@ def test_job_paper_shape_accuracy(g):
 
 def test_job_rejects_missing_state_and_depth(g):
     ctx = g.Context(10, 4, K=2, dnum=2, seed=1)
-    ctx.keygen(rot_steps=[1 << i for i in range(9)], conj=True)
     job = g.Job(ctx, 16, 3, 40)
+    ctx.keygen(rot_steps=job.rotation_steps(), conj=True)
     assert not job.factored  # four limbs: split-mode layout
     S = np.zeros((16, 40))
     with pytest.raises(g.GwheError):

@@ -319,6 +319,54 @@ def test_keyswitch_noise_invariant_reduced_special_primes(wide, l):
     assert _noise_of(o, u_bad, s2, x) > math.prod(o.q[:l]) // 2 ** 8
 
 
+@pytest.mark.parametrize("l,rs", [(5, [1, 2, 3]), (3, [8, 16, 24]), (2, [-1, -2, -3]), (4, [2])])
+def test_hoisted_rotation_sum_is_the_sum_of_automorphisms(small_rot, l, rs):
+    """Dec(rotate_sum(a, rs)) = Dec(a) + sum_r sigma_r(Dec(a)) + e with |e|
+    < 2^24: the automorphism is exact on the decryption (sigma(c0 + c1 s) =
+    sigma(c0) + sigma(c1) sigma(s)), so the one shared ModUp / ModDown must
+    reproduce it up to switch noise; and a rotation set whose key is replaced
+    fails the identity."""
+    o = small_rot
+    rng = _rng(50 + l)
+    a = ckks.Ct(np.stack([np.stack([rng.integers(0, o.q[i], size=o.N, dtype=np.uint64)
+                                    for i in range(l)]) for _ in range(2)]), o.delta)
+    dec = o.decrypt(a)
+    want = dec.copy()
+    for r in rs:
+        g = galois_rot(o.logN, r)
+        for i in range(l):
+            t = np.zeros(o.N, np.uint64)
+            L.or_automorphism(np.ascontiguousarray(dec[i]), t, o.logN, g, o.q[i])
+            q = np.uint64(o.q[i])
+            ssum = want[i] + t
+            want[i] = np.where(ssum >= q, ssum - q, ssum)
+    got = o.decrypt(o.rotate_sum(a, rs))
+    diff = np.zeros_like(got)
+    for i in range(l):
+        q = np.uint64(o.q[i])
+        diff[i] = np.where(got[i] >= want[i], got[i] - want[i], got[i] + q - want[i])
+    assert max(abs(v) for v in o.crt_centered(diff)) < 2 ** 24
+    # swap in a wrong key for the first rotation: the identity breaks
+    g0 = galois_rot(o.logN, rs[0])
+    saved = o.keys[g0]
+    o.keys[g0] = o.keys[0]
+    try:
+        bad = o.decrypt(o.rotate_sum(a, rs))
+    finally:
+        o.keys[g0] = saved
+    for i in range(l):
+        q = np.uint64(o.q[i])
+        diff[i] = np.where(bad[i] >= want[i], bad[i] - want[i], bad[i] + q - want[i])
+    assert max(abs(v) for v in o.crt_centered(diff)) > math.prod(o.q[:l]) // 2 ** 8
+
+
+@pytest.fixture(scope="module")
+def small_rot():
+    o = OracleCKKS(logN=9, L=5, K=4, dnum=2, seed=7)
+    o.keygen(galois=[galois_rot(9, r) for r in (1, 2, 3, 8, 16, 24, -1, -2, -3)])
+    return o
+
+
 def test_automorphism_rotates_slots():
     o = OracleCKKS(logN=8, L=2, K=1)
     rng = _rng(12)

@@ -14,6 +14,29 @@ from oracle.ckks import OracleCKKS, galois_conj, galois_rot
 from oracle.trace import job_ks_histogram
 from paper_1902_04303_gb300.datagen import make_gwas
 
+def _count_switches(o):
+    """per-level key switches of the oracle evaluator o: one per switch and
+    one per hoisted rotation group (shared ModUp and ModDown)"""
+    hist = np.zeros(65, np.int64)
+    real_ks, real_sum = o.keyswitch, o.rotate_sum
+
+    def counting_ks(x, key_id):
+        hist[x.shape[0]] += 1
+        return real_ks(x, key_id)
+
+    def counting_sum(a, rs):
+        hist[a.level] += 1
+        old = o.keyswitch
+        o.keyswitch = real_ks
+        try:
+            return real_sum(a, rs)
+        finally:
+            o.keyswitch = old
+
+    o.keyswitch, o.rotate_sum = counting_ks, counting_sum
+    return hist
+
+
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
 
@@ -124,14 +147,7 @@ def test_encrypted_circuit_matches_o2():
     o = OracleCKKS(logN=logN, L=21, K=7, dnum=3, seed=11)
     lay = Layout(logN, n, d, k)
     o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay)] + [galois_conj(logN)])
-    hist = np.zeros(65, np.int64)
-    real_ks = o.keyswitch
-
-    def counting_ks(x, key_id):
-        hist[x.shape[0]] += 1
-        return real_ks(x, key_id)
-
-    o.keyswitch = counting_ks
+    hist = _count_switches(o)
     c = Circuit(o, lay)
     c.encrypt_inputs(dat.X, A, dat.y)
     c.fit(kappa=1)
@@ -159,14 +175,15 @@ def test_encrypted_circuit_matches_o2():
 
 @pytest.mark.parametrize("n", [16, 64, 245])
 def test_batch_key_switch_count_closed_form(n):
-    """One SNP batch (Alg. 11 loop body) switches keys 6 + 3 log2(nb) times:
-    relinearisations of S', Dup(w z') S', Dup(w) S', WSS, WSC (5), the
-    conjugation (1), and three column sums of log2(nb) rotations (Alg. 5)."""
+    """One SNP batch (Alg. 11 loop body) switches keys 6 + 3 ceil(log2(nb)/2)
+    times: relinearisations of S', Dup(w z') S', Dup(w) S', WSS, WSC (5), the
+    conjugation (1), and three column sums (Alg. 4) of log2(nb) rotation
+    steps, evaluated two steps per hoisted switch."""
     W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=5,
              k=10643)
     _, _, batch = job_ks_histogram(W, 1)
     nb = 1 << math.ceil(math.log2(n))
-    assert batch.sum() == 6 + 3 * int(math.log2(nb))
+    assert batch.sum() == 6 + 3 * math.ceil(math.log2(nb) / 2)
     # every batch switch happens at or below the batch entry level
     assert batch[5:].sum() == 0
 
@@ -174,17 +191,17 @@ def test_batch_key_switch_count_closed_form(n):
 @pytest.mark.parametrize("n,d", [(16, 3), (245, 5), (1000, 6)])
 def test_factored_batch_key_switch_count_closed_form(n, d):
     """The factored layout adds, per batch, d products, d column sums and d
-    in-block broadcasts of log2(nb) rotations each, and one relinearised
-    tensor sum: d + 2 d log2(nb) + 1 switches, then the body shared with the
-    M-CCP layout (5 + 3 log2(nb): four relinearisations, the conjugation,
-    three column sums); per level d at 6 limbs, d log2(nb) at 5, d log2(nb)
-    + 1 at 4."""
+    in-block broadcasts of log2(nb) rotation steps each (two steps per hoisted
+    switch, h = ceil(log2(nb)/2) switches), and one relinearised tensor sum:
+    d + 2 d h + 1 switches, then the body shared with the M-CCP layout
+    (5 + 3 h: four relinearisations, the conjugation, three column sums); per
+    level d at 6 limbs, d h at 5, d h + 1 at 4."""
     W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=d,
              k=50000)
     _, fit_f, batch_f = job_ks_histogram(W, 1, factored=True)
-    lg = int(math.log2(1 << math.ceil(math.log2(n))))
-    assert batch_f.sum() == (d + 2 * d * lg + 1) + (5 + 3 * lg)
-    assert batch_f[6] == d and batch_f[5] == d * lg and batch_f[4] == d * lg + 1
+    h = math.ceil(math.ceil(math.log2(n)) / 2)
+    assert batch_f.sum() == (d + 2 * d * h + 1) + (5 + 3 * h)
+    assert batch_f[6] == d and batch_f[5] == d * h and batch_f[4] == d * h + 1
     assert batch_f[7:].sum() == 0  # the CCP batch enters at 6 limbs
 
 
@@ -212,14 +229,7 @@ def test_encrypted_factored_circuit_matches_o2():
     lay = Layout(logN, n, d, k)
     o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay, factored=True)]
              + [galois_conj(logN)])
-    hist = np.zeros(65, np.int64)
-    real_ks = o.keyswitch
-
-    def counting_ks(x, key_id):
-        hist[x.shape[0]] += 1
-        return real_ks(x, key_id)
-
-    o.keyswitch = counting_ks
+    hist = _count_switches(o)
     c = Circuit(o, lay, factored=True)
     c.encrypt_inputs(dat.X, A, dat.y)
     c.fit(kappa=1)
