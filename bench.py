@@ -480,6 +480,180 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------ cohorts / serving
+COHORTS = dict(name="cohorts16", logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60,
+               dnum=3, jobs=16, seed=1004, kappa=1)
+SERVING = dict(name="serving", requests=200, big_fraction=0.05, big=(6000, 4, 100000), seed=1005)
+
+
+def cohort_shapes(count, seed):
+    """uneven cohorts: n ~ U{100..1000}, d ~ U{2..6} (with the intercept),
+    k ~ U{1000..50000}, seeded"""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [(int(rng.integers(100, 1001)), int(rng.integers(2, 7)), int(rng.integers(1000, 50001)))
+            for _ in range(count)]
+
+
+def _serving_ctx(gwhe, stream, shapes):
+    W = COHORTS
+    ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
+                       W["dnum"], seed=W["seed"], stream=stream.cuda_stream)
+    steps = []
+    for n, d, k in set(shapes):
+        job = gwhe.Job(ctx, n, d, k)
+        steps += [r for r in job.rotation_steps() if r not in steps]
+        job.close()
+    ctx.keygen(rot_steps=steps, conj=True)
+    return ctx
+
+
+def _cohort_inputs(shapes, seed):
+    from paper_1902_04303_gb300.datagen import make_gwas
+    out = []
+    for i, (n, d, k) in enumerate(shapes):
+        data = make_gwas(n, d, k, seed=seed + i)
+        out.append((data, client_preprocess(data.X)))
+    return out
+
+
+def _check_sample(num, den, data, A, kappa):
+    """|d b'| against the FP64 reference on the first 512 SNPs of a job."""
+    from oracle import gwas_fp64
+    m = min(512, data.S.shape[1])
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S[:, :m], kappa=kappa, A=A)
+    ok = np.abs(ref["den"]) > 1e-6
+    return float(np.max(np.abs(num[:m][ok] / den[:m][ok] - ref["b"][ok]), initial=0.0))
+
+
+def run_cohorts(args):
+    """Batched uneven cohorts: 16 jobs one at a time on one stream, then all
+    submitted at once to the serving engine (workers with their own streams
+    sharing the keys); total SNPs / wall time for both."""
+    import torch
+    from paper_1902_04303_gb300 import build as pkg_build
+    from paper_1902_04303_gb300 import gwhe
+    pkg_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    W = COHORTS
+    shapes = cohort_shapes(W["jobs"], W["seed"])
+    ctx = _serving_ctx(gwhe, stream, shapes)
+    inputs = _cohort_inputs(shapes, W["seed"] + 100)
+    snps = sum(k for _, _, k in shapes)
+
+    def one(i):
+        (data, A) = inputs[i]
+        n, d = data.X.shape
+        job = gwhe.Job(ctx, n, d, data.S.shape[1])
+        job.set_nonce(i + 1)
+        job.encrypt_inputs(data.X, A, data.y)
+        job.fit(W["kappa"])
+        job.snp_stats(data.S)
+        r = job.decrypt_results()
+        job.close()
+        return r
+
+    one(0)  # warm-up: tables, caches, the memory pool
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [one(i) for i in range(len(shapes))]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64)
+    t0 = time.perf_counter()
+    ids = [srv.submit(data.X, A, data.y, data.S, kappa=W["kappa"], nonce=i + 1)
+           for i, (data, A) in enumerate(inputs)]
+    res = [srv.wait(rid) for rid in ids]
+    t_srv = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(seq, res))
+    err = max(_check_sample(r[0], r[1], data, A, W["kappa"]) for r, (data, A) in zip(res, inputs))
+    out = {"metric": "batched uneven-cohort encrypted-GWAS SNPs/s (16 jobs, N=2^16)",
+           "value": round(snps / t_srv, 1), "unit": "SNPs/s", "n_gpus": 1, "steps": 1,
+           "warmup": 1, "ms_per_step": round(t_srv * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": W["name"], "jobs": [list(x) for x in shapes],
+                      "workers": args.workers, "snps": snps},
+           "one_at_a_time": {"value": round(snps / t_seq, 1), "ms": round(t_seq * 1e3, 1)},
+           "speedup_vs_one_at_a_time": round(t_seq / t_srv, 3),
+           "same_results_alone_and_batched": bool(same), "max_abs_db_sampled": err,
+           "peak_bytes_claimed": st["peak_bytes_claimed"]}
+    print(json.dumps(out))
+
+
+def run_serving(args):
+    """Serving: Poisson arrivals of GWAS requests (the cohort mix plus a few
+    6000 x 100000 jobs), admitted by HBM footprint as workers and memory
+    free up; p50/p99 latency beside SNPs/s."""
+    import threading
+
+    import torch
+    from paper_1902_04303_gb300 import build as pkg_build
+    from paper_1902_04303_gb300 import gwhe
+    pkg_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    S_ = SERVING
+    nreq = args.requests
+    rng = np.random.Generator(np.random.PCG64(S_["seed"]))
+    mix = cohort_shapes(nreq, S_["seed"] + 1)
+    shapes = [S_["big"] if rng.random() < S_["big_fraction"] else mix[i] for i in range(nreq)]
+    ctx = _serving_ctx(gwhe, stream, shapes)
+    inputs = _cohort_inputs(shapes, S_["seed"] + 1000)
+    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64)
+    # calibration: mean service time of the cohort mix alone (4 jobs, one at a time)
+    cal = []
+    for i in range(min(4, nreq)):
+        data, A = inputs[i]
+        t0 = time.perf_counter()
+        srv.wait(srv.submit(data.X, A, data.y, data.S, nonce=4000 + i))
+        cal.append(time.perf_counter() - t0)
+    rate = 0.8 / float(np.mean(cal)) if args.rate <= 0 else args.rate  # ~80% busy
+    gaps = rng.exponential(1.0 / rate, size=nreq)
+    lat = [None] * nreq
+    lock = threading.Lock()
+
+    def waiter(i, rid):
+        _, _, t = srv.wait(rid)
+        with lock:
+            lat[i] = t
+
+    threads = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for i in range(nreq):
+        t_next += gaps[i]
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        data, A = inputs[i]
+        rid = srv.submit(data.X, A, data.y, data.S, nonce=i + 1)
+        th = threading.Thread(target=waiter, args=(i, rid))
+        th.start()
+        threads.append(th)
+    for th in threads:
+        th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    tot = np.array([x["latency_ms"] for x in lat])
+    snps = sum(k for _, _, k in shapes)
+    out = {"metric": "served encrypted-GWAS SNPs/s with p50/p99 latency (Poisson arrivals, N=2^16)",
+           "value": round(snps / wall, 1), "unit": "SNPs/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+           "ms_per_step": round(wall * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "serving%d" % nreq, "requests": nreq,
+                      "big_jobs": sum(1 for x in shapes if x == S_["big"]),
+                      "arrival_rate_per_s": round(rate, 3), "workers": args.workers},
+           "latency_ms": {"p50": round(float(np.percentile(tot, 50)), 1),
+                          "p99": round(float(np.percentile(tot, 99)), 1),
+                          "max": round(float(tot.max()), 1)},
+           "queue_ms_p50": round(float(np.percentile([x["queue_ms"] for x in lat], 50)), 1),
+           "peak_bytes_claimed": st["peak_bytes_claimed"], "budget_bytes": st["budget"]}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -493,7 +667,20 @@ def main():
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--micro-only", action="store_true",
                     help="only the kernel microbench (the controlled case for profiler captures)")
+    ap.add_argument("--workload", default="paper-n245",
+                    choices=["paper-n245", "cohorts16", "serving"],
+                    help="paper-n245: the paper-shaped job; cohorts16: 16 uneven cohorts one at "
+                         "a time and batched; serving: Poisson request stream")
+    ap.add_argument("--workers", type=int, default=4, help="serving-engine workers")
+    ap.add_argument("--requests", type=int, default=SERVING["requests"])
+    ap.add_argument("--rate", type=float, default=0.0, help="arrivals/s (0: ~80%% busy)")
     args = ap.parse_args()
+    if args.impl != "reference" and args.workload == "cohorts16":
+        run_cohorts(args)
+        return
+    if args.impl != "reference" and args.workload == "serving":
+        run_serving(args)
+        return
     if args.micro_only:
         import torch
         from paper_1902_04303_gb300 import build as pkg_build

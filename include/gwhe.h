@@ -276,6 +276,55 @@ int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view);
 /* number of key switches issued on the job's context so far */
 long gwhe_job_keyswitches(const gwhe_job* job);
 
+/* Stop sharing randomness between jobs under one key: every encryption id of
+ * the job is offset by nonce << 36 (0 <= nonce < 4096).  Call before
+ * gwhe_encrypt_inputs; jobs that may both be live under one key need
+ * different nonces. */
+int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce);
+/* Drop the kept batch outputs (after gwhe_decrypt_results), so that a long
+ * job can evaluate and decrypt its SNP batches chunk by chunk. */
+int gwhe_job_release_results(gwhe_job* job);
+/* Estimated device bytes of one job beyond the shared keys (device copy of S,
+ * encrypted inputs, the covariate phase's temporaries, one chunk of
+ * chunk_batches SNP batches and its outputs); -1 on bad arguments. */
+long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, int chunk_batches);
+
+/* ------------------------------------------------------------ serving
+ * Continuous batching of GWAS jobs on one GPU (no counterpart in the paper,
+ * which runs one job).  `workers` threads each own a CUDA stream and a child
+ * context sharing ctx's tables and device-resident keys (generated first,
+ * with every rotation the jobs need), so jobs overlap on the device.  A free
+ * worker admits the first waiting job whose estimated footprint
+ * (gwhe_job_footprint) fits in hbm_budget bytes minus the running jobs'
+ * (hbm_budget 0 = 60% of the free device memory); a job runs the covariate
+ * phase, then its SNP batches chunk_batches at a time, decrypting and
+ * dropping each chunk.  Do not use ctx for other work while the server runs;
+ * destroy the server before ctx.
+ *   submit: copies the host inputs (X n x d row-major, (X^T X)^-1 d x d, y n,
+ *           S n x k row-major); ENOMEM if the footprint exceeds the budget.
+ *   wait:   blocks until the job is done; num[k], den[k] as
+ *           gwhe_decrypt_results; times_ms (optional) = {waiting for
+ *           admission, running, total}; the job's status is returned and the
+ *           job is forgotten.
+ *   stats:  {admitted, running, waiting, bytes claimed, peak bytes claimed,
+ *           budget}.
+ *   destroy: running jobs finish, waiting ones end with GWHE_EINVAL. */
+typedef struct gwhe_server gwhe_server;
+int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
+                       gwhe_server** out);
+int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
+                       const double* X, const double* XtX_inv, const double* y, const double* S,
+                       long* id);
+int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms);
+int gwhe_server_stats(gwhe_server* s, long out[6]);
+int gwhe_server_destroy(gwhe_server* s);
+
+/* Child context on another stream (void* = cudaStream_t) that shares ctx's
+ * tables and keys read-only: for callers that drive several jobs from
+ * several threads.  Keys must exist; no key generation on the child; destroy
+ * it before ctx. */
+int gwhe_ctx_create_child(gwhe_ctx* ctx, void* stream, gwhe_ctx** out);
+
 /* ------------------------------------------------------------ instrumentation */
 /* key switches issued so far per level: out[l] for l < n */
 int gwhe_ks_histogram(const gwhe_ctx* ctx, long* out, int n);

@@ -38,6 +38,10 @@ ENC_XTREP = 0x10000
 ENC_DUPM = 0x20000
 ENC_S = 0x1000000
 ENC_SCCP = 0x100000000
+# a job's nonce (distinct per job under one key, so that no two jobs share
+# encryption randomness) is added to every id above, shifted past them
+ENC_NONCE_SHIFT = 36
+MAX_NONCE = (1 << 12) - 1
 
 SIGMA7_A = (-1.73496 / 8.0, 4.19407 / 8.0 ** 3, -5.43402 / 8.0 ** 5, 2.50739 / 8.0 ** 7)
 
@@ -131,10 +135,13 @@ def rotation_steps(layout: Layout, factored: bool = False):
 
 
 class Circuit:
-    def __init__(self, ev: OracleCKKS, layout: Layout, factored: bool = False):
+    def __init__(self, ev: OracleCKKS, layout: Layout, factored: bool = False, nonce: int = 0):
+        if not 0 <= nonce <= MAX_NONCE:
+            raise ValueError("job nonce out of range")
         self.ev = ev
         self.lay = layout
         self.factored = factored
+        self.enc_base = nonce << ENC_NONCE_SHIFT
         layout.check()
 
     # --------------------------------------------------------- primitives
@@ -239,7 +246,7 @@ class Circuit:
         scale = ev.delta if scale is None else scale
         z = np.zeros(self.lay.M, complex)
         z[: len(v)] = v
-        return ev.encrypt(ev.encode(z, scale, level), enc_id, scale)
+        return ev.encrypt(ev.encode(z, scale, level), self.enc_base + enc_id, scale)
 
     def encrypt_inputs(self, X, A, y):
         """X as CP, (X^T X)^-1 as CP, y, beta0 = Enc(0), X^T as REP (Alg. 11

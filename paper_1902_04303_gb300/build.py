@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgwhe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["ntt.cu", "kernels.cu", "ckks.cu", "gwas.cu", "capi.cu", "noalloc.cu", "probe.cu", "params.cpp"]
+UNITS = ["ntt.cu", "kernels.cu", "ckks.cu", "gwas.cu", "capi.cu", "noalloc.cu", "probe.cu", "server.cu", "params.cpp"]
 
 
 def nvcc():

@@ -537,6 +537,26 @@ int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view) {
   });
 }
 
+int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] { job_set_nonce(job->job.get(), nonce); });
+}
+
+int gwhe_job_release_results(gwhe_job* job) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] { job_release_results(job->job.get()); });
+}
+
+int gwhe_ctx_create_child(gwhe_ctx* ctx, void* stream, gwhe_ctx** out) {
+  if (!out) return GWHE_EINVAL;
+  *out = nullptr;
+  return guard(C(ctx), [&] {
+    std::unique_ptr<gwhe_ctx> h(new gwhe_ctx());
+    h->c = ctx_child(C(ctx), (cudaStream_t)stream);
+    *out = h.release();
+  });
+}
+
 int gwhe_ks_histogram(const gwhe_ctx* ctx, long* out, int n) {
   if (!ctx || !out || n < 1) return GWHE_EINVAL;
   for (int l = 0; l < n; ++l) out[l] = l <= kMaxRowLimbs ? ctx->c->ks_by_level[l] : 0;

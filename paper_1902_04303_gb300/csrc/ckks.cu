@@ -331,9 +331,34 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   return c.release();
 }
 
+Context* ctx_child(const Context* base, cudaStream_t stream) {
+  GWHE_REQUIRE(base && !base->parent, ST_EINVAL, "a child needs a root context");
+  GWHE_REQUIRE(base->have_keys, ST_ENOKEY, "generate the keys before making child contexts");
+  std::unique_ptr<Context> c(new Context(*base));
+  c->parent = base;
+  c->stream = stream;
+  c->masks.clear();
+  c->ks_count = 0;
+  c->launches = 0;
+  for (long& v : c->ks_by_level) v = 0;
+  c->prof = Prof();
+  c->last_error.clear();
+  return c.release();
+}
+
 void ctx_destroy(Context* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->parent) {  // only the child's own state
+    for (auto& kv : c->masks) cudaFree(kv.second);
+    for (auto& r : c->prof.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    delete c;
+    return;
+  }
   for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
                   (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
@@ -442,6 +467,7 @@ static void make_ksk(Context* c, u32 key_id, const u64* target) {
 }
 
 void add_galois_key(Context* c, u32 g) {
+  GWHE_REQUIRE(!c->parent, ST_EINVAL, "keys are generated on the root context");
   const int N = c->N, nm = c->nmod;
   Tmp t(c, sizeof(u64) * nm * N);
   automorph_ntt(c, PolyView{t.u(), nm}, CPolyView{c->d_sk, nm}, 1, nm, g);
@@ -449,6 +475,7 @@ void add_galois_key(Context* c, u32 g) {
 }
 
 void keygen(Context* c, const std::vector<u32>& galois) {
+  GWHE_REQUIRE(!c->parent, ST_EINVAL, "keys are generated on the root context");
   const int N = c->N, L = c->P.L, nm = c->nmod;
   std::vector<uint8_t> pidx(nm);
   for (int u = 0; u < nm; ++u) pidx[u] = (uint8_t)u;

@@ -25,6 +25,9 @@ inline u64 obj_ksk_e(u32 key, int k, int j) {
 
 Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream);
 void ctx_destroy(Context* c);
+// a context on another stream sharing base's tables and keys (base must
+// outlive it and hold its keys; no key generation on the child)
+Context* ctx_child(const Context* base, cudaStream_t stream);
 
 void keygen(Context* c, const std::vector<u32>& galois);
 void add_galois_key(Context* c, u32 g);
@@ -85,6 +88,7 @@ struct CtSet {
   int cnt = 0, npoly = 2, cap = 0, l = 0;
   double scale = 1.0;
   bool owned = true;
+  bool is_output = false;  // holds a job's kept batch results
   ~CtSet();
   // non-owning set over items [first, first + n) at level lv (lv <= l)
   CtSet slice(int first, int n, int lv) const;

@@ -284,6 +284,9 @@ struct Prof {
 };
 
 struct Context {
+  // a child context (ctx_child) shares its parent's tables and keys
+  // read-only and owns only its stream, caches and counters
+  const Context* parent = nullptr;
   Params P;
   int N = 0, logN = 0, alpha = 0, nmod = 0;
   u64 seed = 0;

@@ -316,6 +316,24 @@ Job* job_create(Context* c, int n, int d, long k, int mode) {
   return j;
 }
 
+void job_set_nonce(Job* j, u32 nonce) {
+  GWHE_REQUIRE(nonce <= kMaxNonce, ST_EINVAL, "job nonce out of range");
+  GWHE_REQUIRE(j->X.empty(), ST_EINVAL, "set the nonce before encrypting the inputs");
+  j->enc_base = (u64)nonce << kNonceShift;
+}
+
+void job_release_results(Job* j) {
+  // the kept outputs are views into sets the job owns: drop both (the
+  // covariate state's sets stay)
+  for (auto& o : j->out)
+    for (auto& v : o) v.reset();
+  j->out.clear();
+  auto& sets = j->sets;
+  sets.erase(std::remove_if(sets.begin(), sets.end(),
+                            [&](const CtSetPtr& s) { return s->is_output; }),
+             sets.end());
+}
+
 std::vector<int> job_rotation_steps(const Job* j) {
   // every rotation of the circuit's ladders (Replicate and DotProd over all
   // slots, colSum over nb, Duplicate over the blocks, the factored layout's
@@ -351,20 +369,20 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
   std::vector<u64> ids(cnt);
   int it = 0;
   for (int col = 0; col < d; ++col, ++it) {
-    ids[it] = kEncX + col;
+    ids[it] = j->enc_base + kEncX + col;
     for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(X[(size_t)t * d + col], 0);
   }
   for (int col = 0; col < d; ++col, ++it) {
-    ids[it] = kEncA + col;
+    ids[it] = j->enc_base + kEncA + col;
     for (int r = 0; r < d; ++r) z[(size_t)it * M + r] = make_double2(A[(size_t)r * d + col], 0);
   }
-  ids[it] = kEncY;
+  ids[it] = j->enc_base + kEncY;
   for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(y[t], 0);
   ++it;
-  ids[it++] = kEncBeta0;
+  ids[it++] = j->enc_base + kEncBeta0;
   for (int col = 0; col < d; ++col)
     for (int h = 0; h < H; ++h, ++it) {
-      ids[it] = kEncXtRep + (u64)col * 4096 + h;
+      ids[it] = j->enc_base + kEncXtRep + (u64)col * 4096 + h;
       for (int b = 0; b < lay.B; ++b) {
         const int s = h * lay.B + b;
         if (s >= n) continue;
@@ -567,9 +585,10 @@ void job_set_fit_state(Job* j, const double* Mp, const double* wp, const double*
     return z;
   };
   j->DupM.clear();
-  for (int jj = 0; jj < n; ++jj) j->DupM.push_back(ev.encrypt_vec(dup(M, n, jj), kEncDupM + jj, lb, delta));
-  j->DupW = ev.encrypt_vec(dup(w, 1, 0), kEncDupW, lb - 1, delta);
-  j->DupWZ = ev.encrypt_vec(dup(wz, 1, 0), kEncDupWZ, lb - 1, delta);
+  for (int jj = 0; jj < n; ++jj)
+    j->DupM.push_back(ev.encrypt_vec(dup(M, n, jj), j->enc_base + kEncDupM + jj, lb, delta));
+  j->DupW = ev.encrypt_vec(dup(w, 1, 0), j->enc_base + kEncDupW, lb - 1, delta);
+  j->DupWZ = ev.encrypt_vec(dup(wz, 1, 0), j->enc_base + kEncDupWZ, lb - 1, delta);
 }
 
 namespace {
@@ -632,6 +651,8 @@ void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
   set_ladder(c, *D, ev.colsum_steps());
   for (int i = 0; i < nbt; ++i)
     j->out[b0 + i] = {num->view(i), D->view(i), D->view(nbt + i)};
+  num->is_output = true;
+  D->is_output = true;
   j->sets.push_back(std::move(num));
   j->sets.push_back(std::move(D));
 }
@@ -661,7 +682,8 @@ CtSetPtr sprime_mccp(Job* j, const double* Sd, long b0, long b1) {
     for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
     for (long bi = b0; bi < b1; ++bi) {
       build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
-      encrypt_slots(c, z.as<double2>(), n, delta, lb, kEncS + (u64)bi * n, sct.u(), lb);
+      encrypt_slots(c, z.as<double2>(), n, delta, lb, j->enc_base + kEncS + (u64)bi * n, sct.u(),
+                    lb);
       CtSet t = T3->slice((int)(bi - b0), 1, lb);
       set_tensor_mac(c, pairs, n, t);
       T3->scale = t.scale;
@@ -689,7 +711,8 @@ CtSetPtr sprime_factored(Job* j, Eval& ev, const double* Sd, long b0, long b1) {
     Tmp z(c, sizeof(double2) * (size_t)nbt * lay.M);
     build_snp_ccp(c, Sd, lay.n, lay.k, b0 * lay.tau, nbt, lay.tau, lay.nb, lay.B, lay.M,
                   z.as<double2>());
-    encrypt_slots(c, z.as<double2>(), nbt, delta, lf, kEncSccp + (u64)b0, Sset->d, lf);
+    encrypt_slots(c, z.as<double2>(), nbt, delta, lf, j->enc_base + kEncSccp + (u64)b0, Sset->d,
+                  lf);
   }
   std::vector<CtPtr> sv;
   for (int i = 0; i < nbt; ++i) sv.push_back(Sset->view(i));

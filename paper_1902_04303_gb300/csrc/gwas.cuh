@@ -46,6 +46,7 @@ struct Job {
   std::vector<CtPtr> DupX, DupB;          // [d] Dup(X_c), Dup((XA)_c) (factored)
   CtPtr DupW, DupWZ;
   bool factored = false;
+  u64 enc_base = 0;  // job nonce << 36, added to every encryption id
   std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd (views)
   std::vector<CtSetPtr> sets;             // storage behind the views above
   u64* DupM_store = nullptr;              // unused (kept zero)
@@ -53,6 +54,12 @@ struct Job {
 };
 
 Job* job_create(Context* c, int n, int d, long k, int mode = kLayoutAuto);
+// distinct nonces keep the encryption randomness of jobs under one key apart
+constexpr int kNonceShift = 36;
+constexpr u32 kMaxNonce = (1u << 12) - 1;
+void job_set_nonce(Job* j, u32 nonce);
+// drop the kept batch outputs (after they were decrypted)
+void job_release_results(Job* j);
 // rotation steps whose keys the job needs
 std::vector<int> job_rotation_steps(const Job* j);
 void job_encrypt_inputs(Job* j, const double* X, const double* A, const double* y);

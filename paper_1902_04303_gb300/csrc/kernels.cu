@@ -2,6 +2,8 @@
 // product, fast base conversion (ModUp / ModDown), the key inner product,
 // rescale, Galois automorphisms, ChaCha20 sampling, and the FP64 encoding
 // procedure of the gwhe library.  See kernels.cuh for the interfaces.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace gwhe {
@@ -1265,12 +1267,13 @@ void encode_batch(Context* c, const double2* z, int count, double scale, i64* ou
   const int logM = c->logN - 1, M = 1 << logM;
   const int a = logM < 12 ? logM : 12;  // 4096-entry tiles: 64 KiB of shared memory
   const int T = 1 << a;
-  static bool smem_opt_in = false;
-  if (!smem_opt_in) {
+  // opt in to 64 KiB of dynamic shared memory once per process (idempotent,
+  // safe from several threads)
+  static std::once_flag smem_opt_in;
+  std::call_once(smem_opt_in, [] {
     GWHE_CUDA(cudaFuncSetAttribute(k_fx_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sizeof(longlong2) * 4096));
-    smem_opt_in = true;
-  }
+  });
   longlong2* G = (longlong2*)work;  // same size as count * M double2
   int* e = (int*)dalloc_bytes(c, (sizeof(int) + sizeof(unsigned long long)) * count + 8);
   unsigned long long* mx = (unsigned long long*)(e + count + (count & 1));

@@ -1,0 +1,317 @@
+// server.cu -- continuous batching of encrypted GWAS jobs on one GPU.
+//
+// A server owns W worker threads.  Each worker has its own CUDA stream and a
+// child context of the caller's context, so all workers share one set of
+// device-resident evaluation keys and tables while their kernels run on
+// separate streams and overlap on the device.  Requests (one GWAS job each:
+// n samples, d covariates, k SNPs, host inputs copied at submission) wait in
+// arrival order; a free worker admits the first waiting request whose
+// estimated device footprint fits in the HBM budget still unclaimed by the
+// running jobs, so small jobs flow past a large one that has to wait for
+// memory.  A job runs the covariate phase, then its SNP batches in chunks,
+// decrypting each chunk and dropping its ciphertexts before the next, which
+// bounds its footprint independently of k.  Results are kept until the caller
+// collects them.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+#include "capi_types.cuh"
+#include "gwas.cuh"
+
+using namespace gwhe;
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  long id = 0;
+  int n = 0, d = 0, layout = 0, kappa = 1;
+  long k = 0;
+  u32 nonce = 0;
+  std::vector<double> X, A, y, S;
+  size_t footprint = 0;
+  std::vector<double> num, den;
+  int status = GWHE_OK;
+  std::string error;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  bool done = false;
+};
+typedef std::shared_ptr<Request> ReqPtr;
+
+}  // namespace
+
+struct gwhe_server {
+  gwhe_ctx* owner = nullptr;
+  size_t budget = 0, in_use = 0, peak = 0;
+  int chunk = 64;
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ReqPtr> pending;
+  std::map<long, ReqPtr> reqs;
+  long next_id = 1, admitted = 0, running = 0;
+  bool stop = false;
+};
+
+namespace {
+
+// Estimated device bytes of one job beyond the shared keys: the device copy
+// of S, the encrypted inputs, the covariate phase's largest temporaries and
+// one chunk of SNP batches with its outputs.
+size_t footprint(const Context* c, int n, int d, long k, bool factored, int chunk) {
+  const Layout lay = make_layout(c->logN, n, d, k);
+  const double ct = 2.0 * c->N * 8.0;  // bytes per limb of a ciphertext
+  const int L = c->P.L;
+  const double inputs = (2.0 * d + 2 + (factored ? 0 : (double)d * lay.H)) * L * ct;
+  const double fit = ((double)d * d + 6.0 * d + 16) * L * ct * 2.0;
+  const long nb = std::min<long>(chunk, lay.batches);
+  const double batch = factored ? nb * ((4.0 * d + 8) * kFactLevel + 6.0) * ct * 2.0
+                                : ((double)n * kBatchLevel + nb * 16.0) * ct * 2.0 +
+                                      (double)n * kBatchLevel * ct;
+  const double state = factored ? 2.0 * d * kFactLevel * ct : (double)n * (kBatchLevel + 1) * ct;
+  return (size_t)((double)n * k * 8 + inputs + fit + batch + state);
+}
+
+void run_request(Context* c, Request& r, int chunk) {
+  std::unique_ptr<Job> j(job_create(c, r.n, r.d, r.k, r.layout));
+  job_set_nonce(j.get(), r.nonce);
+  job_encrypt_inputs(j.get(), r.X.data(), r.A.data(), r.y.data());
+  job_fit(j.get(), r.kappa);
+  r.num.assign(r.k, NAN);
+  r.den.assign(r.k, NAN);
+  Tmp S(c, sizeof(double) * r.S.size());
+  GWHE_CUDA(cudaMemcpyAsync(S.p, r.S.data(), sizeof(double) * r.S.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+  std::vector<double> num(r.k), den(r.k);
+  for (long b0 = 0; b0 < j->lay.batches; b0 += chunk) {
+    const long b1 = std::min<long>(j->lay.batches, b0 + chunk);
+    job_snp_stats(j.get(), S.as<double>(), b0, b1);
+    job_decrypt(j.get(), num.data(), den.data());
+    const long s0 = b0 * j->lay.tau, s1 = std::min<long>(r.k, b1 * j->lay.tau);
+    for (long s = s0; s < s1; ++s) {
+      r.num[s] = num[s];
+      r.den[s] = den[s];
+    }
+    job_release_results(j.get());
+  }
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void worker_main(gwhe_server* srv) {
+  cudaStream_t st = nullptr;
+  Context* c = nullptr;
+  try {
+    GWHE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    c = ctx_child(srv->owner->c, st);
+  } catch (...) {
+    // without a context this worker takes no work; the others carry on
+    if (st) cudaStreamDestroy(st);
+    return;
+  }
+  for (;;) {
+    ReqPtr r;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_work.wait(lk, [&] {
+        if (srv->stop) return true;
+        for (auto& p : srv->pending)
+          if (p->footprint <= srv->budget - srv->in_use) return true;
+        return false;
+      });
+      if (srv->stop) break;
+      for (auto it = srv->pending.begin(); it != srv->pending.end(); ++it)
+        if ((*it)->footprint <= srv->budget - srv->in_use) {
+          r = *it;
+          srv->pending.erase(it);
+          break;
+        }
+      srv->in_use += r->footprint;
+      srv->peak = std::max(srv->peak, srv->in_use);
+      ++srv->admitted;
+      ++srv->running;
+      r->t_start = now_ms();
+    }
+    try {
+      run_request(c, *r, srv->chunk);
+    } catch (const Error& e) {
+      r->status = e.code;
+      r->error = e.what();
+      cudaStreamSynchronize(st);
+    } catch (const std::exception& e) {
+      r->status = GWHE_EINVAL;
+      r->error = e.what();
+      cudaStreamSynchronize(st);
+    }
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->in_use -= r->footprint;
+      --srv->running;
+      r->t_done = now_ms();
+      r->done = true;
+      r->X.clear();
+      r->A.clear();
+      r->y.clear();
+      r->S.clear();
+      r->X.shrink_to_fit();
+      r->S.shrink_to_fit();
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+  }
+  ctx_destroy(c);
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
+                       gwhe_server** out) {
+  if (!ctx || !ctx->c || !out || workers < 1 || workers > 64 || chunk_batches < 1)
+    return GWHE_EINVAL;
+  *out = nullptr;
+  Context* c = ctx->c;
+  if (!c->have_keys) {
+    c->last_error = "server: generate the keys first";
+    return GWHE_ENOKEY;
+  }
+  std::unique_ptr<gwhe_server> s(new gwhe_server());
+  s->owner = ctx;
+  s->chunk = chunk_batches;
+  if (hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return GWHE_ECUDA;
+    hbm_budget = (uint64_t)(0.6 * (double)fr);
+  }
+  s->budget = hbm_budget;
+  for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s.get());
+  *out = s.release();
+  return GWHE_OK;
+}
+
+int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
+                       const double* X, const double* XtX_inv, const double* y, const double* S,
+                       long* id) {
+  if (!s || !X || !XtX_inv || !y || !S || !id || n < 1 || d < 1 || k < 1 || kappa < 1)
+    return GWHE_EINVAL;
+  Context* c = s->owner->c;
+  try {
+    const Layout lay = make_layout(c->logN, n, d, k);  // rejects shapes that do not fit
+    (void)lay;
+    if (nonce > kMaxNonce) throw Error(ST_EINVAL, "job nonce out of range");
+    if (layout != kLayoutAuto && layout != kLayoutMccp && layout != kLayoutFactored)
+      throw Error(ST_EINVAL, "bad layout mode");
+  } catch (const Error& e) {
+    c->last_error = e.what();
+    return e.code;
+  }
+  auto r = std::make_shared<Request>();
+  r->n = n;
+  r->d = d;
+  r->k = k;
+  r->layout = layout;
+  r->kappa = kappa;
+  r->nonce = nonce;
+  r->X.assign(X, X + (size_t)n * d);
+  r->A.assign(XtX_inv, XtX_inv + (size_t)d * d);
+  r->y.assign(y, y + n);
+  r->S.assign(S, S + (size_t)n * k);
+  const bool factored =
+      layout == kLayoutFactored || (layout == kLayoutAuto && c->P.L > kMLevel);
+  r->footprint = footprint(c, n, d, k, factored, s->chunk);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->footprint > s->budget) {
+      c->last_error = "server: the job's footprint exceeds the HBM budget";
+      return GWHE_ENOMEM;
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_ms();
+    s->reqs[r->id] = r;
+    s->pending.push_back(r);
+    *id = r->id;
+  }
+  s->cv_work.notify_all();
+  return GWHE_OK;
+}
+
+int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms) {
+  if (!s || !num || !den) return GWHE_EINVAL;
+  ReqPtr r;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return GWHE_EINVAL;
+    r = it->second;
+    s->cv_done.wait(lk, [&] { return r->done; });
+    s->reqs.erase(it);
+  }
+  if (times_ms) {
+    times_ms[0] = r->t_start - r->t_submit;  // waiting for admission
+    times_ms[1] = r->t_done - r->t_start;    // on a worker
+    times_ms[2] = r->t_done - r->t_submit;   // total latency
+  }
+  if (r->status != GWHE_OK) {
+    s->owner->c->last_error = "server job " + std::to_string(id) + ": " + r->error;
+    return r->status;
+  }
+  std::copy(r->num.begin(), r->num.end(), num);
+  std::copy(r->den.begin(), r->den.end(), den);
+  return GWHE_OK;
+}
+
+int gwhe_server_stats(gwhe_server* s, long out[6]) {
+  if (!s || !out) return GWHE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = s->admitted;
+  out[1] = s->running;
+  out[2] = (long)s->pending.size();
+  out[3] = (long)s->in_use;
+  out[4] = (long)s->peak;
+  out[5] = (long)s->budget;
+  return GWHE_OK;
+}
+
+int gwhe_server_destroy(gwhe_server* s) {
+  if (!s) return GWHE_EINVAL;
+  {
+    // running jobs finish; waiting ones end with an error
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    for (auto& r : s->pending) {
+      r->status = GWHE_EINVAL;
+      r->error = "server stopped before the job was admitted";
+      r->done = true;
+    }
+    s->pending.clear();
+  }
+  s->cv_work.notify_all();
+  s->cv_done.notify_all();
+  for (auto& t : s->workers) t.join();
+  delete s;
+  return GWHE_OK;
+}
+
+long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, int chunk_batches) {
+  if (!ctx || !ctx->c || n < 1 || d < 1 || k < 1 || chunk_batches < 1) return -1;
+  const Context* c = ctx->c;
+  try {
+    const bool factored =
+        layout == kLayoutFactored || (layout == kLayoutAuto && c->P.L > kMLevel);
+    return (long)footprint(c, n, d, k, factored, chunk_batches);
+  } catch (...) {
+    return -1;
+  }
+}
+
+}  // extern "C"

@@ -89,6 +89,15 @@ _SIGS = {
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
     "gwhe_job_create_ex": [_vp, _i, _i, _l, _i, ctypes.POINTER(_vp)],
     "gwhe_job_info": [_vp, ctypes.POINTER(_l)],
+    "gwhe_job_set_nonce": [_vp, _u32],
+    "gwhe_job_release_results": [_vp],
+    "gwhe_ctx_create_child": [_vp, _vp, ctypes.POINTER(_vp)],
+    "gwhe_server_create": [_vp, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)],
+    "gwhe_server_submit": [_vp, _i, _i, _l, _i, _i, _u32, _f64p, _f64p, _f64p, _f64p,
+                           ctypes.POINTER(_l)],
+    "gwhe_server_wait": [_vp, _l, _f64p, _f64p, _f64p],
+    "gwhe_server_stats": [_vp, ctypes.POINTER(_l)],
+    "gwhe_server_destroy": [_vp],
     "gwhe_rotate_sum": [_vp, _vp, ctypes.POINTER(ctypes.c_int32), _i, _vp],
     "gwhe_probe_butterflies": [_vp, _i, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)],
@@ -127,13 +136,16 @@ def lib():
         L.gwhe_job_keyswitches.restype = _l
         L.gwhe_launch_count.argtypes = [_vp]
         L.gwhe_launch_count.restype = _l
+        L.gwhe_job_footprint.argtypes = [_vp, _i, _i, _l, _i, _i]
+        L.gwhe_job_footprint.restype = _l
         _LIB = L
     return _LIB
 
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return sorted(list(_SIGS) + ["gwhe_last_error", "gwhe_job_keyswitches", "gwhe_launch_count"])
+    return sorted(list(_SIGS) + ["gwhe_last_error", "gwhe_job_keyswitches", "gwhe_launch_count",
+                                 "gwhe_job_footprint"])
 
 
 def _check(rc, ctx=None):
@@ -258,8 +270,10 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            # jobs first (they own ciphertexts), then ciphertext handles
-            kids = sorted(list(self._children), key=lambda x: 0 if isinstance(x, Job) else 1)
+            # servers first (their workers use the context), then jobs (they
+            # own ciphertexts), then ciphertext handles
+            kids = sorted(list(self._children),
+                          key=lambda x: 0 if isinstance(x, Server) else 1 if isinstance(x, Job) else 2)
             for kid in kids:
                 kid.close()
             lib().gwhe_ctx_destroy(self.h)
@@ -555,6 +569,13 @@ class Job:
         self.ctx._c(lib().gwhe_decrypt_results(self.h, num, den))
         return num, den
 
+    def set_nonce(self, nonce):
+        """offset of this job's encryption ids (distinct per live job under one key)."""
+        self.ctx._c(lib().gwhe_job_set_nonce(self.h, nonce))
+
+    def release_results(self):
+        self.ctx._c(lib().gwhe_job_release_results(self.h))
+
     def ct(self, which, index=0):
         """a view of a job ciphertext (valid while the job lives)."""
         h = _vp()
@@ -565,3 +586,65 @@ class Job:
 
     def keyswitches(self):
         return lib().gwhe_job_keyswitches(self.h)
+
+
+def job_footprint(ctx: Context, n, d, k, layout="auto", chunk_batches=64):
+    """estimated device bytes of one job beyond the shared keys."""
+    v = lib().gwhe_job_footprint(ctx.h, n, d, k, LAYOUTS[layout], chunk_batches)
+    if v < 0:
+        raise GwheError(-1, "bad job shape")
+    return v
+
+
+class Server:
+    """Continuous batching of GWAS jobs on the context's GPU: worker threads
+    with their own streams share the context's keys; jobs are admitted by
+    estimated HBM footprint as memory frees up and overlap on the device."""
+
+    def __init__(self, ctx: Context, workers=4, hbm_budget=0, chunk_batches=64):
+        self.ctx = ctx
+        h = _vp()
+        ctx._c(lib().gwhe_server_create(ctx.h, workers, hbm_budget, chunk_batches,
+                                        ctypes.byref(h)))
+        self.h = h
+        self._k = {}
+        ctx._children.add(self)
+
+    def submit(self, X, XtX_inv, y, S, kappa=1, layout="auto", nonce=0):
+        X = np.ascontiguousarray(X, np.float64)
+        A = np.ascontiguousarray(XtX_inv, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        S = np.ascontiguousarray(S, np.float64)
+        n, d = X.shape
+        k = S.shape[1]
+        rid = _l(0)
+        self.ctx._c(lib().gwhe_server_submit(self.h, n, d, k, LAYOUTS[layout], kappa, nonce,
+                                             X, A, y, S, ctypes.byref(rid)))
+        self._k[rid.value] = k
+        return rid.value
+
+    def wait(self, rid):
+        """(num[k], den[k], {"queue_ms", "run_ms", "latency_ms"})"""
+        k = self._k.pop(rid)
+        num = np.full(k, np.nan)
+        den = np.full(k, np.nan)
+        t = np.zeros(3)
+        self.ctx._c(lib().gwhe_server_wait(self.h, rid, num, den, t))
+        return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2]}
+
+    def stats(self):
+        out = (_l * 6)()
+        self.ctx._c(lib().gwhe_server_stats(self.h, out))
+        keys = ["admitted", "running", "waiting", "bytes_claimed", "peak_bytes_claimed", "budget"]
+        return {kk: int(v) for kk, v in zip(keys, out)}
+
+    def close(self):
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
+            lib().gwhe_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -158,6 +158,7 @@ def test_factored_layout_bit_exact(g):
     steps = rotation_steps(lay, factored=True)
     ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
     job = g.Job(ctx, n, d, k, layout="factored")
+    job.set_nonce(3)  # the encryption ids of a job with nonce 3, on both sides
     assert job.factored and sorted(job.rotation_steps()) == sorted(steps)
     assert job.layout["H"] == 0 and job.layout["batch_limbs"] == 6
     ctx.keygen(rot_steps=steps, conj=True)
@@ -171,7 +172,7 @@ def test_factored_layout_bit_exact(g):
     assert np.array_equal(ctx.ks_histogram() - ks0, want)
     o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
     o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
-    c = Circuit(o, lay, factored=True)
+    c = Circuit(o, lay, factored=True, nonce=3)
     c.encrypt_inputs(data.X, A, data.y)
     c.fit(kappa=1)
     for cc in range(d):
