@@ -94,19 +94,22 @@ class Layout:
             raise ValueError("a column of nb slots does not fit one ciphertext")
 
 
+LADDER_GROUP = 3  # ladder steps per hoisted key switch
+
+
 def ladder_groups(steps):
     """Hoisted evaluation of a doubling ladder v += Rotate(v, s) over steps:
-    consecutive steps r, 2r merge into one group {r, 2r, 3r} (the same sum of
-    rotations, v + Rot(v, r) + Rot(v, 2r) + Rot(v, 3r)); a step without a
-    partner stays alone."""
+    up to LADDER_GROUP consecutive steps r, 2r, 4r merge into one group over
+    the rotations r, 2r, ..., (2^m - 1) r (the same sum of rotations:
+    v + Rot(v, r) + ... + Rot(v, (2^m - 1) r)); a shorter run of m steps gives
+    2^m - 1 rotations."""
     out, i = [], 0
     while i < len(steps):
-        if i + 1 < len(steps) and steps[i + 1] == 2 * steps[i]:
-            out.append([steps[i], 2 * steps[i], 3 * steps[i]])
-            i += 2
-        else:
-            out.append([steps[i]])
-            i += 1
+        m = 1
+        while m < LADDER_GROUP and i + m < len(steps) and steps[i + m] == 2 * steps[i + m - 1]:
+            m += 1
+        out.append([t * steps[i] for t in range(1, 1 << m)])
+        i += m
     return out
 
 

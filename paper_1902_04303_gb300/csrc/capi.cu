@@ -354,7 +354,7 @@ int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int n
                     gwhe_ct* out) {
   return guard(C(ctx), [&] {
     Context* c = C(ctx);
-    need(a && out && steps && nsteps >= 1 && nsteps <= 3, "bad rotation sum");
+    need(a && out && steps && nsteps >= 1 && nsteps <= kMaxHoist, "bad rotation sum");
     const Ct& x = *a->ct;
     need(x.npoly == 2 && out->ct->npoly == 2 && out->ct->cap >= x.l, "bad ciphertexts");
     CtSetPtr s = set_new(c, 1, 2, x.l, x.l, x.scale);

@@ -832,17 +832,18 @@ void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs) {
 }
 
 std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps) {
-  // consecutive steps r, 2r of a doubling ladder merge into one hoisted step
-  // over the rotations r, 2r, 3r (the same sum of rotations)
+  // up to kLadderGroup consecutive doubling steps r, 2r, 4r, ... of a ladder
+  // merge into one hoisted step over the rotations r, 2r, ..., (2^m - 1) r
+  // (the same sum of rotations)
   std::vector<std::vector<int>> out;
   for (size_t i = 0; i < steps.size();) {
-    if (i + 1 < steps.size() && steps[i + 1] == 2 * steps[i]) {
-      out.push_back({steps[i], 2 * steps[i], 3 * steps[i]});
-      i += 2;
-    } else {
-      out.push_back({steps[i]});
-      i += 1;
-    }
+    size_t m = 1;
+    while (m < (size_t)kLadderGroup && i + m < steps.size() && steps[i + m] == 2 * steps[i + m - 1])
+      ++m;
+    std::vector<int> g;
+    for (int t = 1; t < (1 << m); ++t) g.push_back(t * steps[i]);
+    out.push_back(g);
+    i += m;
   }
   return out;
 }

@@ -109,9 +109,11 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
 // evaluated as hoisted sums over the groups of ladder_groups(steps)
 void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps);
 // s[i] += sum_{r in rs} Rotate(s[i], r) with the key switches hoisted (one
-// ModUp, one ModDown; at most three rotations)
+// ModUp, one ModDown; at most seven rotations)
 void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs);
-// consecutive doubling steps (r, 2r) -> one group {r, 2r, 3r}; others alone
+// up to kLadderGroup consecutive doubling steps (r, 2r, 4r) -> one group
+// {r, 2r, ..., 7r}; a shorter run -> {r, .., (2^m - 1) r}
+constexpr int kLadderGroup = 3;
 std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps);
 // out[i] = automorphism g of a[i] (rotation or conjugation)
 void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out);

@@ -218,9 +218,10 @@ __device__ __forceinline__ unsigned automorph_src(unsigned j, u64 g, int logN) {
 // Hoisted inner product for a sum of automorphisms: acc_p[u] = sum_g sum_j
 // sigma_g(x_j)[u] * key_g,j[p][u], x_j the ModUp digits of one c1 (the input
 // limb itself when u lies in digit j).  sigma_g is a permutation of NTT slots,
-// applied while reading; all G beta products are summed on 128 bits and
-// reduced once.  Each thread keeps its key words in registers for up to IB
-// items.
+// applied while reading; all G beta products of an item are summed on 128
+// bits (at most 28 terms below 2^120) and reduced once.  The loop runs over
+// the automorphisms outside: one key's words sit in registers while they are
+// applied to up to IB items, whose accumulators persist across g.
 template <int IB, int G>
 __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
                                  const u64* __restrict__ ext, HoistKeys hk,
@@ -235,40 +236,45 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
   const int mi = u < l ? u : L + (u - l);
   const int kr = u < l ? u : key_lmax + (u - l);
   const size_t KR = (size_t)(key_lmax + K);
-  u64 kb[G][kKsMaxBeta], ka[G][kKsMaxBeta];
-  unsigned src[G];
+  const int it0 = blockIdx.z * IB;
+  const int nit = min(IB, cnt - it0);
+  Acc128 s0[IB], s1[IB];
+#pragma unroll
+  for (int t = 0; t < IB; ++t) s0[t] = s1[t] = Acc128{0, 0};
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    src[g] = automorph_src((unsigned)k, hk.g[g], logN);
+    const unsigned src = automorph_src((unsigned)k, hk.g[g], logN);
+    u64 kb[kKsMaxBeta], ka[kKsMaxBeta];
 #pragma unroll
     for (int j = 0; j < kKsMaxBeta; ++j)
       if (j < beta) {
-        kb[g][j] = hk.key[g][(((size_t)j * 2 + 0) * KR + kr) * N + k];
-        ka[g][j] = hk.key[g][(((size_t)j * 2 + 1) * KR + kr) * N + k];
+        kb[j] = hk.key[g][(((size_t)j * 2 + 0) * KR + kr) * N + k];
+        ka[j] = hk.key[g][(((size_t)j * 2 + 1) * KR + kr) * N + k];
       }
-  }
-  const DevMod m = mod[mi];
-  const int it0 = blockIdx.z * IB;
-  const int it1 = min(it0 + IB, cnt);
-  for (int item = it0; item < it1; ++item) {
-    const u64* cx = c_ntt + (size_t)item * c_stride + (size_t)u * N;
-    const u64* ex = ext + (size_t)item * beta * ne * N;
-    Acc128 s0{0, 0}, s1{0, 0};
 #pragma unroll
-    for (int j = 0; j < kKsMaxBeta; ++j) {
-      if (j >= beta) break;
-      const int lo = j * alpha, hi = min(lo + alpha, l);
-      const u64* row = (u >= lo && u < hi) ? cx : ex + ((size_t)j * ne + u) * N;
+    for (int t = 0; t < IB; ++t) {
+      if (t >= nit) break;
+      const int item = it0 + t;
+      const u64* cx = c_ntt + (size_t)item * c_stride + (size_t)u * N;
+      const u64* ex = ext + (size_t)item * beta * ne * N;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const u64 x = row[src[g]];
-        mac128(s0, x, kb[g][j]);
-        mac128(s1, x, ka[g][j]);
+      for (int j = 0; j < kKsMaxBeta; ++j) {
+        if (j >= beta) break;
+        const int lo = j * alpha, hi = min(lo + alpha, l);
+        const u64* row = (u >= lo && u < hi) ? cx : ex + ((size_t)j * ne + u) * N;
+        const u64 x = row[src];
+        mac128(s0[t], x, kb[j]);
+        mac128(s1[t], x, ka[j]);
       }
     }
-    u64* ac = acc + (size_t)item * 2 * ne * N;
-    ac[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
-    ac[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+  }
+  const DevMod m = mod[mi];
+#pragma unroll
+  for (int t = 0; t < IB; ++t) {
+    if (t >= nit) break;
+    u64* ac = acc + (size_t)(it0 + t) * 2 * ne * N;
+    ac[(size_t)u * N + k] = reduce128(s0[t].lo, s0[t].hi, m);
+    ac[((size_t)ne + u) * N + k] = reduce128(s1[t].lo, s1[t].hi, m);
   }
 }
 
@@ -1067,6 +1073,16 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
   GWHE_LAUNCHED(c, 1);
 }
 
+template <int G>
+static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
+                         const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt, int beta) {
+  constexpr int IB = G <= 3 ? 8 : 4;
+  const dim3 grid(blocks_for(c->N), l + K, (cnt + IB - 1) / IB);
+  k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,
+                                                           c->P.L, key_lmax, c->alpha, beta,
+                                                           c->logN, cnt, c->d_mod);
+}
+
 void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
                         const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt) {
   const double ne_ = l + K, beta_ = (l + c->alpha - 1) / c->alpha;
@@ -1074,25 +1090,15 @@ void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, co
   const int beta = (l + c->alpha - 1) / c->alpha;
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
-  constexpr int IB = 8;
-  const dim3 grid(blocks_for(c->N), l + K, (cnt + IB - 1) / IB);
   switch (hk.G) {
-    case 1:
-      k_ks_inner_hoist<IB, 1><<<grid, kThreads, 0, c->stream>>>(
-          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
-          c->d_mod);
-      break;
-    case 2:
-      k_ks_inner_hoist<IB, 2><<<grid, kThreads, 0, c->stream>>>(
-          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
-          c->d_mod);
-      break;
-    case 3:
-      k_ks_inner_hoist<IB, 3><<<grid, kThreads, 0, c->stream>>>(
-          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
-          c->d_mod);
-      break;
-    default: throw Error(ST_EINVAL, "at most three hoisted automorphisms");
+    case 1: launch_hoist<1>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 2: launch_hoist<2>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 3: launch_hoist<3>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 4: launch_hoist<4>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 5: launch_hoist<5>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 6: launch_hoist<6>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    case 7: launch_hoist<7>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
+    default: throw Error(ST_EINVAL, "at most seven hoisted automorphisms");
   }
   GWHE_LAUNCHED(c, 1);
 }
@@ -1102,12 +1108,22 @@ void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, 
   ProfScope ps(c, PROF_ELEMWISE, (1.0 + hk.G) * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   const dim3 grid(blocks_for(c->N), l, cnt);
+#define GWHE_AUTOSUM(G)                                                                          \
+  case G:                                                                                        \
+    k_automorph_sum<G><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, \
+                                                         hk, c->d_mod);                          \
+    break;
   switch (hk.G) {
-    case 1: k_automorph_sum<1><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
-    case 2: k_automorph_sum<2><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
-    case 3: k_automorph_sum<3><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, hk, c->d_mod); break;
-    default: throw Error(ST_EINVAL, "at most three hoisted automorphisms");
+    GWHE_AUTOSUM(1)
+    GWHE_AUTOSUM(2)
+    GWHE_AUTOSUM(3)
+    GWHE_AUTOSUM(4)
+    GWHE_AUTOSUM(5)
+    GWHE_AUTOSUM(6)
+    GWHE_AUTOSUM(7)
+    default: throw Error(ST_EINVAL, "at most seven hoisted automorphisms");
   }
+#undef GWHE_AUTOSUM
   GWHE_LAUNCHED(c, 1);
 }
 

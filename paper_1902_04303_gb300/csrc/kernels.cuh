@@ -57,7 +57,7 @@ void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int
                          size_t a0_stride, size_t a1_stride);
 // Hoisted key switching of a sum of automorphisms (at most kMaxHoist): the
 // Galois elements and the key family each uses.
-constexpr int kMaxHoist = 3;
+constexpr int kMaxHoist = 7;
 struct HoistKeys {
   const u64* key[kMaxHoist];
   u64 g[kMaxHoist];

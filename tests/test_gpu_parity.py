@@ -24,7 +24,7 @@ def g():
     return gwhe
 
 
-def pair(g, logN, L, K, dnum, seed=3, rot=(1, -1, 2, 8, 3, 4, 6, -2, -3, 16, 24), conj=True,
+def pair(g, logN, L, K, dnum, seed=3, rot=(1, -1, 2, 8, 3, 4, 5, 6, 7, -2, -3, 16, 24), conj=True,
          keys=True):
     ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
     o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
@@ -224,7 +224,7 @@ def test_errors_are_status_codes(g, small):
         ctx.add(a, c)
     assert e.value.code == -4  # ESCALE
     with pytest.raises(g.GwheError) as e:
-        ctx.rotate(a, 5)  # no key for 5
+        ctx.rotate(a, 11)  # no key for 11
     assert e.value.code == -5  # ENOKEY
     one = ctx.import_ct(rand_ct(o, 1, 4).c, o.delta)
     with pytest.raises(g.GwheError) as e:
@@ -247,7 +247,8 @@ def test_full_size_keyswitch_and_rescale_bit_exact(g):
 
 
 @pytest.mark.parametrize("l,rs", [(6, [1, 2, 3]), (5, [8, 16, 24]), (3, [2, 4, 6]), (4, [-1, -2, -3]),
-                                  (2, [1]), (1, [2, 4, 6])])
+                                  (2, [1]), (1, [2, 4, 6]), (6, [1, 2, 3, 4, 5, 6, 7]),
+                                  (2, [1, 2, 3, 4, 5, 6, 7])])
 def test_hoisted_rotation_sum_bit_exact(g, small, l, rs):
     """a + sum_r Rotate(a, r) with one shared ModUp and ModDown, at levels
     with one and two key digits."""
@@ -263,3 +264,5 @@ def test_hoisted_rotation_sum_reduced_special_primes(g, wide, l):
     a = rand_ct(o, l, 230 + l)
     ga = ctx.import_ct(a.c, a.scale)
     assert np.array_equal(ctx.rotate_sum(ga, [1, 2, 3]).export(), o.rotate_sum(a, [1, 2, 3]).c)
+    rs = [1, 2, 3, 4, 5, 6, 7]
+    assert np.array_equal(ctx.rotate_sum(ga, rs).export(), o.rotate_sum(a, rs).c)

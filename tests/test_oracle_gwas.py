@@ -175,15 +175,15 @@ def test_encrypted_circuit_matches_o2():
 
 @pytest.mark.parametrize("n", [16, 64, 245])
 def test_batch_key_switch_count_closed_form(n):
-    """One SNP batch (Alg. 11 loop body) switches keys 6 + 3 ceil(log2(nb)/2)
+    """One SNP batch (Alg. 11 loop body) switches keys 6 + 3 ceil(log2(nb)/3)
     times: relinearisations of S', Dup(w z') S', Dup(w) S', WSS, WSC (5), the
     conjugation (1), and three column sums (Alg. 4) of log2(nb) rotation
-    steps, evaluated two steps per hoisted switch."""
+    steps, evaluated three steps per hoisted switch."""
     W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=5,
              k=10643)
     _, _, batch = job_ks_histogram(W, 1)
     nb = 1 << math.ceil(math.log2(n))
-    assert batch.sum() == 6 + 3 * math.ceil(math.log2(nb) / 2)
+    assert batch.sum() == 6 + 3 * math.ceil(math.log2(nb) / 3)
     # every batch switch happens at or below the batch entry level
     assert batch[5:].sum() == 0
 
@@ -191,15 +191,15 @@ def test_batch_key_switch_count_closed_form(n):
 @pytest.mark.parametrize("n,d", [(16, 3), (245, 5), (1000, 6)])
 def test_factored_batch_key_switch_count_closed_form(n, d):
     """The factored layout adds, per batch, d products, d column sums and d
-    in-block broadcasts of log2(nb) rotation steps each (two steps per hoisted
-    switch, h = ceil(log2(nb)/2) switches), and one relinearised tensor sum:
+    in-block broadcasts of log2(nb) rotation steps each (three steps per
+    hoisted switch, h = ceil(log2(nb)/3) switches), and one relinearised tensor sum:
     d + 2 d h + 1 switches, then the body shared with the M-CCP layout
     (5 + 3 h: four relinearisations, the conjugation, three column sums); per
     level d at 6 limbs, d h at 5, d h + 1 at 4."""
     W = dict(logN=16, L=24, q0_bits=60, scale_bits=45, K=8, sp_bits=60, dnum=3, n=n, d=d,
              k=50000)
     _, fit_f, batch_f = job_ks_histogram(W, 1, factored=True)
-    h = math.ceil(math.ceil(math.log2(n)) / 2)
+    h = math.ceil(math.ceil(math.log2(n)) / 3)
     assert batch_f.sum() == (d + 2 * d * h + 1) + (5 + 3 * h)
     assert batch_f[6] == d and batch_f[5] == d * h and batch_f[4] == d * h + 1
     assert batch_f[7:].sum() == 0  # the CCP batch enters at 6 limbs
