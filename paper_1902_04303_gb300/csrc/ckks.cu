@@ -114,7 +114,7 @@ static T* upload(Context* c, const std::vector<T>& v) {
 }
 
 Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
-  GWHE_REQUIRE(P.logN >= 4 && P.logN <= 16, ST_EINVAL, "logN must be in [4, 16]");
+  GWHE_REQUIRE(P.logN >= 4 && P.logN <= 17, ST_EINVAL, "logN must be in [4, 17]");
   GWHE_REQUIRE(P.L >= 1 && P.L <= kMaxRowLimbs && P.K >= 1 && P.K <= 16, ST_EINVAL,
                "need 1 <= L <= 64 and 1 <= K <= 16");
   GWHE_REQUIRE(P.dnum >= 1 && P.dnum <= P.L, ST_EINVAL, "need 1 <= dnum <= L");

@@ -1259,8 +1259,13 @@ void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m) {
 
 static void fft_stages(Context* c, double2* G, const double2* W, int count) {
   const int logM = c->logN - 1, M = 1 << logM;
-  const int a = logM < 11 ? logM : 11;
+  const int a = logM < 12 ? logM : 12;  // 4096-entry tiles: 64 KiB of shared memory
   const int T = 1 << a;
+  static std::once_flag smem_opt_in;
+  std::call_once(smem_opt_in, [] {
+    GWHE_CUDA(cudaFuncSetAttribute(k_fft_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(double2) * 4096));
+  });
   k_fft_tile<<<(unsigned)((size_t)count * (M / T)), 256, sizeof(double2) * T, c->stream>>>(G, W,
                                                                                           logM, a);
   GWHE_LAUNCHED(c, 1);

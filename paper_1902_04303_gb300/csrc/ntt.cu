@@ -8,14 +8,16 @@
 // between stages (and between the two passes) and return canonical residues
 // in [0, q).
 //
-// Layout for N = 2^12..2^16: the row is viewed as a 2^LA x 2^LB matrix
+// Layout for N = 2^12..2^17: the row is viewed as a 2^LA x 2^LB matrix
 // (element h * 2^LB + c).  Pass A runs the first LA stages as independent
 // 2^LA-point transforms down the columns, pass B the last LB stages along the
 // rows.  In each pass a 256-thread CTA owns 4096 residues: 16 per thread, the
 // first four local stages in registers in a strided layout (coalesced global
 // loads), a shared-memory transpose to a contiguous layout for the remaining
-// stages, and a transpose back for coalesced stores.  Each residue is read and
-// written once per pass.  Smaller rings use one CTA per row in shared memory.
+// stages, and a transpose back for coalesced stores; the 9-stage pass of
+// N = 2^17 uses 128-thread CTAs with 32 residues per thread (5 + 4 stages).
+// Each residue is read and written once per pass.  Smaller rings use one CTA
+// per row in shared memory.
 #include "core.cuh"
 
 namespace gwhe {
@@ -23,15 +25,23 @@ namespace gwhe {
 // One pass of the two-pass transform.  LS = log2 of this pass's sub-transform
 // size; the other dimension has 2^(LOGN-LS) entries.  PASSA: sub-transforms
 // are columns (stride 2^(LOGN-LS)), global stages 0..LS-1; otherwise rows
-// (contiguous), global stages LOGN-LS..LOGN-1.
-template <int LOGN, int LS, bool PASSA, bool FWD>
-__global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
-                                                  const NttTables tb, const int groups_per_row) {
+// (contiguous), global stages LOGN-LS..LOGN-1.  A CTA of NT threads holds E
+// residues per thread (LS <= 2 log2 E): log2 E stages in registers in a
+// strided layout, a shared-memory transpose to a contiguous layout for the
+// remaining stages, and a transpose back for coalesced stores.
+template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256>
+__global__ void __launch_bounds__(NT, 4) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
+                                                 const NttTables tb, const int groups_per_row) {
   constexpr int S = 1 << LS;
-  constexpr int TPS = S / 16;         // threads per sub-transform
-  constexpr int G = 256 / TPS;        // sub-transforms per CTA
+  constexpr int LE = E == 16 ? 4 : 5;  // log2 E
+  static_assert(E == 16 || E == 32, "16 or 32 residues per thread");
+  static_assert(LS <= 2 * LE && LS > LE, "sub-transform size out of range");
+  constexpr int TPS = S / E;          // threads per sub-transform
+  constexpr int G = NT / TPS;         // sub-transforms per CTA
   constexpr int LC = LOGN - LS;       // log2 of the other dimension
-  constexpr int PADS = PASSA ? (S + 1) : (S + S / 16);
+  // padding keeps the strided and contiguous accesses free of bank conflicts
+  constexpr bool PADE = !PASSA || E == 32;
+  constexpr int PADS = PADE ? (S + S / E + (E == 32 ? 1 : 0)) : (S + 1);
   constexpr int S0 = PASSA ? 0 : LC;  // global index of local stage 0
   __shared__ u64 sm[G * PADS];
 
@@ -52,22 +62,22 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
   auto gaddr = [&](int e) -> size_t {
     return PASSA ? (((size_t)e << LC) + g) : (((size_t)g << LS) + e);
   };
-  auto sidx = [&](int e) -> int { return PASSA ? (lg * PADS + e) : (lg * PADS + e + (e >> 4)); };
+  auto sidx = [&](int e) -> int { return PADE ? (lg * PADS + e + (e >> LE)) : (lg * PADS + e); };
   auto tw = [&](int s_local, int e) -> int {  // twiddle index for the pair led by e
     const int s = S0 + s_local;
     return (1 << s) + (PASSA ? 0 : (g << s_local)) + (e >> (LS - s_local));
   };
 
-  u64 x[16];
+  u64 x[E];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) x[m] = base[gaddr(r + TPS * m)];
+  for (int m = 0; m < E; ++m) x[m] = base[gaddr(r + TPS * m)];
 
   if (FWD) {
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp) {
-      const int st = 8 >> sp;
+    for (int sp = 0; sp < LE; ++sp) {
+      const int st = (E / 2) >> sp;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < E; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
         const ulonglong2 w = __ldg(W + idx);
@@ -75,59 +85,59 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
       }
     }
 #pragma unroll
-    for (int m = 0; m < 16; ++m) sm[sidx(r + TPS * m)] = x[m];
+    for (int m = 0; m < E; ++m) sm[sidx(r + TPS * m)] = x[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(16 * r + m)];
+    for (int m = 0; m < E; ++m) x[m] = sm[sidx(E * r + m)];
 #pragma unroll
-    for (int sp = 4; sp < LS; ++sp) {
+    for (int sp = LE; sp < LS; ++sp) {
       const int st = S >> (sp + 1);
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < E; ++m) {
         if (m & st) continue;
-        const int idx = tw(sp, 16 * r + m);
+        const int idx = tw(sp, E * r + m);
         const ulonglong2 w = __ldg(W + idx);
         ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) sm[sidx(16 * r + m)] = x[m];
+    for (int m = 0; m < E; ++m) sm[sidx(E * r + m)] = x[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(r + TPS * m)];
+    for (int m = 0; m < E; ++m) x[m] = sm[sidx(r + TPS * m)];
     if (!PASSA) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = reduce_8q(x[m], q);
+      for (int m = 0; m < E; ++m) x[m] = reduce_8q(x[m], q);
     }
   } else {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) sm[sidx(r + TPS * m)] = x[m];
+    for (int m = 0; m < E; ++m) sm[sidx(r + TPS * m)] = x[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(16 * r + m)];
+    for (int m = 0; m < E; ++m) x[m] = sm[sidx(E * r + m)];
 #pragma unroll
-    for (int sp = LS - 1; sp >= 4; --sp) {
+    for (int sp = LS - 1; sp >= LE; --sp) {
       const int st = S >> (sp + 1);
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < E; ++m) {
         if (m & st) continue;
-        const int idx = tw(sp, 16 * r + m);
+        const int idx = tw(sp, E * r + m);
         const ulonglong2 w = __ldg(W + idx);
         gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) sm[sidx(16 * r + m)] = x[m];
+    for (int m = 0; m < E; ++m) sm[sidx(E * r + m)] = x[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = sm[sidx(r + TPS * m)];
+    for (int m = 0; m < E; ++m) x[m] = sm[sidx(r + TPS * m)];
 #pragma unroll
-    for (int sp = 3; sp >= 0; --sp) {
-      const int st = 8 >> sp;
+    for (int sp = LE - 1; sp >= 0; --sp) {
+      const int st = (E / 2) >> sp;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < E; ++m) {
         if (m & st) continue;
         const int idx = tw(sp, TPS * m);
         const ulonglong2 w = __ldg(W + idx);
@@ -137,11 +147,11 @@ __global__ void __launch_bounds__(256, 4) k_ntt_pass(u64* __restrict__ data, con
     if (PASSA) {
       const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = shoup(x[m], ni, nish, q);
+      for (int m = 0; m < E; ++m) x[m] = shoup(x[m], ni, nish, q);
     }
   }
 #pragma unroll
-  for (int m = 0; m < 16; ++m) base[gaddr(r + TPS * m)] = x[m];
+  for (int m = 0; m < E; ++m) base[gaddr(r + TPS * m)] = x[m];
 }
 
 // Whole row in shared memory (N <= 2^11), one CTA per row.
@@ -190,18 +200,22 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
   }
 }
 
+// pass A: 2^LA-point columns, pass B: 2^LB-point rows; a pass of more than 8
+// stages holds 32 residues per thread in 128-thread CTAs
 template <int LOGN, int LA, int LB>
 static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
-  const int gA = (1 << (LOGN - LA)) / (256 / ((1 << LA) / 16));
-  const int gB = (1 << (LOGN - LB)) / (256 / ((1 << LB) / 16));
+  constexpr int EA = LA > 8 ? 32 : 16, NA = LA > 8 ? 128 : 256;
+  constexpr int EB = LB > 8 ? 32 : 16, NB = LB > 8 ? 128 : 256;
+  const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
+  const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
-    k_ntt_pass<LOGN, LA, true, true><<<rows * gA, 256, 0, c->stream>>>(data, rm, tb, gA);
-    k_ntt_pass<LOGN, LB, false, true><<<rows * gB, 256, 0, c->stream>>>(data, rm, tb, gB);
+    k_ntt_pass<LOGN, LA, true, true, EA, NA><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
+    k_ntt_pass<LOGN, LB, false, true, EB, NB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
   } else {
-    k_ntt_pass<LOGN, LB, false, false><<<rows * gB, 256, 0, c->stream>>>(data, rm, tb, gB);
-    k_ntt_pass<LOGN, LA, true, false><<<rows * gA, 256, 0, c->stream>>>(data, rm, tb, gA);
+    k_ntt_pass<LOGN, LB, false, false, EB, NB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
+    k_ntt_pass<LOGN, LA, true, false, EA, NA><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
   }
   GWHE_LAUNCHED(c, 2);
 }
@@ -213,6 +227,7 @@ static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
   ProfScope ps(c, PROF_NTT, 16.0 * rows * c->N);
   GWHE_REQUIRE(rm.nl <= kMaxRowLimbs, ST_EINVAL, "too many limbs in a row map");
   switch (c->logN) {
+    case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd); return;
     case 16: ntt_two_pass<16, 8, 8>(c, data, rm, fwd); return;
     case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd); return;
     case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd); return;

@@ -260,3 +260,52 @@ def test_sharded_batch_ranges_merge_into_one_job(g):
     num, den, complete = merge_shards(shards, k)
     assert complete
     assert np.array_equal(num, want_num) and np.array_equal(den, want_den)
+
+
+def test_kappa3_circuit_bit_exact(g):
+    """kappa = 3 Bohning iterations (Alg. 9) need about 40 limbs: the whole
+    factored circuit at N = 2^10 with 40 limbs and 12 special primes, against
+    the oracle bit for bit, and the FP64 reference with kappa = 3."""
+    logN, L, K, dnum, seed = 10, 40, 12, 3, 14
+    n, d, k = 16, 3, 64
+    data = make_gwas(n, d, k, seed=15)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(logN, n, d, k)
+    steps = rotation_steps(lay, factored=True)
+    ctx = g.Context(logN, L, q0_bits=60, scale_bits=45, K=K, dnum=dnum, seed=seed)
+    ctx.keygen(rot_steps=steps, conj=True)
+    job = g.Job(ctx, n, d, k, layout="factored")
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(3)
+    job.snp_stats(data.S)
+    o = OracleCKKS(logN=logN, L=L, q0_bits=60, scale_bits=45, K=K, dnum=dnum, seed=seed)
+    o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
+    c = Circuit(o, lay, factored=True)
+    c.encrypt_inputs(data.X, A, data.y)
+    c.fit(kappa=3)
+    assert np.array_equal(job.ct(7).export(), c.beta.c)
+    want = c.snp_batch_factored(c.encrypt_snp_batch_ccp(data.S, 0))
+    for which in range(3):
+        assert np.array_equal(job.ct(which, 0).export(), want[which].c), which
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=3, A=A)
+    check_accuracy(num, den, ref, k)
+
+
+def test_paper_ring_kappa3_accuracy(g):
+    """The paper's own geometry for its most accurate run: N = 2^17, kappa = 3
+    (tau = 512, 21 batches at n = 245), 40 limbs, against FP64 with kappa = 3."""
+    n, d, k = 245, 5, 10643
+    data = make_gwas(n, d, k, seed=1006)
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(17, 40, q0_bits=60, scale_bits=45, K=12, dnum=3, seed=1006)
+    job = g.Job(ctx, n, d, k)
+    assert job.factored and job.layout["tau"] == 512 and job.layout["batches"] == 21
+    ctx.keygen(rot_steps=job.rotation_steps(), conj=True)
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(3)
+    job.snp_stats(data.S)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=3, A=A)
+    db, dl = check_accuracy(num, den, ref, k)
+    print("N=2^17 kappa=3: max |d b'| = %.3g, max |d -log10 p| = %.3g" % (db, dl))

@@ -43,7 +43,7 @@ def rand_ct(o, l, seed, npoly=2):
 
 
 # ------------------------------------------------------------------ NTT
-@pytest.mark.parametrize("logN", [4, 7, 10, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("logN", [4, 7, 10, 12, 13, 14, 15, 16, 17])
 def test_ntt_roundtrip_and_negacyclic_product(g, logN):
     import torch
     L = 4  # one-limb digits with one 60-bit special prime
@@ -80,7 +80,7 @@ def test_keygen_bit_exact(g, logN, L, K, dnum):
             assert np.array_equal(got[k], want[k]), (kid, k)
 
 
-@pytest.mark.parametrize("logN", [5, 10, 13, 16])
+@pytest.mark.parametrize("logN", [5, 10, 13, 16, 17])
 def test_encode_bit_exact(g, logN):
     ctx = g.Context(logN, 2, K=1)
     o = OracleCKKS(logN=logN, L=2, K=1)
@@ -93,7 +93,7 @@ def test_encode_bit_exact(g, logN):
     assert np.array_equal(ctx.encode(z, 2.0 ** 40), o.encode_int(z, 2.0 ** 40))
 
 
-@pytest.mark.parametrize("logN,L,K,dnum", [(10, 6, 3, 3), (16, 5, 2, 3)])
+@pytest.mark.parametrize("logN,L,K,dnum", [(10, 6, 3, 3), (16, 5, 2, 3), (17, 4, 2, 2)])
 def test_encrypt_decrypt_bit_exact(g, logN, L, K, dnum):
     ctx, o = pair(g, logN, L, K, dnum, rot=(), conj=False)
     z = make_slots(ctx.M, 9)
@@ -266,3 +266,16 @@ def test_hoisted_rotation_sum_reduced_special_primes(g, wide, l):
     assert np.array_equal(ctx.rotate_sum(ga, [1, 2, 3]).export(), o.rotate_sum(a, [1, 2, 3]).c)
     rs = [1, 2, 3, 4, 5, 6, 7]
     assert np.array_equal(ctx.rotate_sum(ga, rs).export(), o.rotate_sum(a, rs).c)
+
+
+def test_ring_2_17_switches_and_rotations_bit_exact(g):
+    """N = 2^17 (the ring of the paper's own runs): relinearisation switch,
+    hoisted rotation sum, mult and rescale against the oracle."""
+    logN = 17
+    ctx, o = pair(g, logN, 5, 3, 2, seed=31, rot=(1, 2, 3), conj=False)
+    x = rand_ct(o, 5, 301, npoly=1).c[0]
+    assert np.array_equal(ctx.keyswitch(x, 0), o.keyswitch(x, 0))
+    a, b = rand_ct(o, 4, 302), rand_ct(o, 4, 303)
+    ga, gb = ctx.import_ct(a.c, a.scale), ctx.import_ct(b.c, b.scale)
+    assert np.array_equal(ctx.rotate_sum(ga, [1, 2, 3]).export(), o.rotate_sum(a, [1, 2, 3]).c)
+    assert np.array_equal(ctx.mult(ga, gb).export(), o.mult(a, b).c)
