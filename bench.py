@@ -338,7 +338,25 @@ def run_micro(ctx_stream, reps=3):
         ems.append(e0.elapsed_time(e1))
     t_enc = min(ems) / 1e3
     del zb, ob
-    ctx.keygen(rot_steps=steps, conj=False)
+    ctx.keygen(rot_steps=steps + [3, 5, 6, 7], conj=False)
+    # hoisted rotation sums (one ladder group of three doubling steps: rotations
+    # 1..7): 210 ciphertexts at 5 limbs (an SNP-batch chunk) and 5 at 20 limbs
+    # (a covariate-phase set)
+    hoist = {}
+    for cnt, lv in ((210, 5), (5, 20)):
+        src = [ctx.encrypt(make_slots(ctx.M, 900 + i), ctx.delta, lv, 0x900 + i) for i in range(cnt)]
+        outs = ctx.rotate_sum_batch(src, [1, 2, 3, 4, 5, 6, 7])
+        hm = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.rotate_sum_batch(src, [1, 2, 3, 4, 5, 6, 7], outs)
+            e1.record(stream)
+            e1.synchronize()
+            hm.append(e0.elapsed_time(e1))
+        hoist["hoisted7_ms_%dx%dlimbs" % (cnt, lv)] = round(min(hm), 3)
+        for c_ in src + outs:
+            c_.close()
     cts = [ctx.encrypt(make_slots(ctx.M, 7 + i), ctx.delta, L, 0x500 + i) for i in range(nct)]
     torch.cuda.synchronize()
     ks = []
@@ -362,7 +380,7 @@ def run_micro(ctx_stream, reps=3):
             "encode_ms_245": round(t_enc * 1e3, 3),
             "rotations": nct * len(steps),
             "keyswitch_per_s_level24": round(nct * len(steps) / t_ks, 1),
-            "rotate_rescale_ms_512": round(t_ks * 1e3, 2)}
+            "rotate_rescale_ms_512": round(t_ks * 1e3, 2), **hoist}
 
 
 def oracle_sample(W):

@@ -371,6 +371,37 @@ int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int n
   });
 }
 
+int gwhe_rotate_sum_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count,
+                          const int32_t* steps, int nsteps, gwhe_ct* const* out) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    need(a && out && steps && count >= 1 && nsteps >= 1 && nsteps <= kMaxHoist,
+         "bad rotation sum batch");
+    const Ct& x0 = *a[0]->ct;
+    for (int i = 0; i < count; ++i) {
+      const Ct& x = *a[i]->ct;
+      need(x.npoly == 2 && x.l == x0.l && x.scale == x0.scale, "inputs must share level and scale");
+      need(out[i]->ct->npoly == 2 && out[i]->ct->cap >= x.l, "output too small");
+    }
+    const size_t N = c->N;
+    const int l = x0.l;
+    CtSetPtr s = set_new(c, count, 2, l, l, x0.scale);
+    for (int i = 0; i < count; ++i)
+      for (int p = 0; p < 2; ++p)
+        GWHE_CUDA(cudaMemcpyAsync(s->item(i) + (size_t)p * l * N, a[i]->ct->poly(p),
+                                  sizeof(u64) * l * N, cudaMemcpyDeviceToDevice, c->stream));
+    set_rotate_sum(c, *s, std::vector<int>(steps, steps + nsteps));
+    for (int i = 0; i < count; ++i) {
+      Ct& o = *out[i]->ct;
+      for (int p = 0; p < 2; ++p)
+        GWHE_CUDA(cudaMemcpyAsync(o.poly(p), s->item(i) + (size_t)p * l * N, sizeof(u64) * l * N,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      o.l = l;
+      o.scale = x0.scale;
+    }
+  });
+}
+
 int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out) {
   return guard(C(ctx), [&] { op_conj(C(ctx), CT(a), CT(out)); });
 }

@@ -278,6 +278,52 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
   }
 }
 
+// The one-digit case (beta = 1: every switch at or below alpha limbs, i.e. the
+// SNP batches): all G keys' words of the thread's slot stay in registers and
+// the thread walks up to IB items, so each key is read once per IB items.
+template <int IB, int G>
+__global__ void k_ks_inner_hoist1(const u64* __restrict__ c_ntt, size_t c_stride,
+                                  const u64* __restrict__ ext, HoistKeys hk,
+                                  u64* __restrict__ acc, int l, int K, int L, int key_lmax,
+                                  int logN, int cnt, const DevMod* __restrict__ mod) {
+  const int u = blockIdx.y;
+  const int N = 1 << logN;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int ne = l + K;
+  const int mi = u < l ? u : L + (u - l);
+  const int kr = u < l ? u : key_lmax + (u - l);
+  const size_t KR = (size_t)(key_lmax + K);
+  unsigned src[G];
+  u64 kb[G], ka[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    src[g] = automorph_src((unsigned)k, hk.g[g], logN);
+    kb[g] = hk.key[g][((size_t)0 * KR + kr) * N + k];
+    ka[g] = hk.key[g][((size_t)1 * KR + kr) * N + k];
+  }
+  const DevMod m = mod[mi];
+  const int it0 = blockIdx.z * IB;
+  const int it1 = min(it0 + IB, cnt);
+  for (int item = it0; item < it1; ++item) {
+    // digit 0 holds every limb below l: those come from c1 itself
+    const u64* row = u < l ? c_ntt + (size_t)item * c_stride + (size_t)u * N
+                           : ext + ((size_t)item * ne + u) * N;
+    u64 x[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) x[g] = row[src[g]];
+    Acc128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      mac128(s0, x[g], kb[g]);
+      mac128(s1, x[g], ka[g]);
+    }
+    u64* ac = acc + (size_t)item * 2 * ne * N;
+    ac[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
+    ac[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
+  }
+}
+
 // out[item][i] = c0[item][i] + sum_g sigma_g(c0[item][i]) (NTT domain)
 template <int G>
 __global__ void k_automorph_sum(const u64* __restrict__ in, int in_cap, size_t in_stride,
@@ -1076,6 +1122,13 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
 template <int G>
 static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
                          const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt, int beta) {
+  if (beta == 1) {
+    constexpr int IB1 = 32;
+    const dim3 grid(blocks_for(c->N), l + K, (cnt + IB1 - 1) / IB1);
+    k_ks_inner_hoist1<IB1, G><<<grid, kThreads, 0, c->stream>>>(
+        c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
+    return;
+  }
   constexpr int IB = G <= 3 ? 8 : 4;
   const dim3 grid(blocks_for(c->N), l + K, (cnt + IB - 1) / IB);
   k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,

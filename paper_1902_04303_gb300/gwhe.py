@@ -99,6 +99,8 @@ _SIGS = {
     "gwhe_server_stats": [_vp, ctypes.POINTER(_l)],
     "gwhe_server_destroy": [_vp],
     "gwhe_rotate_sum": [_vp, _vp, ctypes.POINTER(ctypes.c_int32), _i, _vp],
+    "gwhe_rotate_sum_batch": [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(ctypes.c_int32), _i,
+                              ctypes.POINTER(_vp)],
     "gwhe_probe_butterflies": [_vp, _i, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)],
     "gwhe_job_rotation_steps": [_vp, ctypes.POINTER(ctypes.c_int32), _i, ctypes.POINTER(_i)],
@@ -440,6 +442,15 @@ class Context:
         o = self._out(a)
         self._c(lib().gwhe_conjugate(self.h, a.h, o.h))
         return o
+
+    def rotate_sum_batch(self, cts, steps, outs=None):
+        """[a + sum_r Rotate(a, r) for a in cts] as one set (shared level/scale)."""
+        outs = outs or [self._out(a) for a in cts]
+        arr = (ctypes.c_int32 * len(steps))(*steps)
+        ins = (_vp * len(cts))(*[a.h for a in cts])
+        ous = (_vp * len(outs))(*[o.h for o in outs])
+        self._c(lib().gwhe_rotate_sum_batch(self.h, ins, len(cts), arr, len(steps), ous))
+        return outs
 
     def rotate_sum(self, a, steps):
         """a + sum_r Rotate(a, r) over at most three steps, key switches hoisted."""

@@ -279,3 +279,14 @@ def test_ring_2_17_switches_and_rotations_bit_exact(g):
     ga, gb = ctx.import_ct(a.c, a.scale), ctx.import_ct(b.c, b.scale)
     assert np.array_equal(ctx.rotate_sum(ga, [1, 2, 3]).export(), o.rotate_sum(a, [1, 2, 3]).c)
     assert np.array_equal(ctx.mult(ga, gb).export(), o.mult(a, b).c)
+
+
+def test_hoisted_rotation_sum_batch_bit_exact(g, small):
+    """the batched entry point (one set of ciphertexts) equals the oracle's
+    hoisted sum of each ciphertext, seven rotations."""
+    ctx, o = small
+    rs = [1, 2, 3, 4, 5, 6, 7]
+    srcs = [rand_ct(o, 4, 400 + i) for i in range(11)]
+    outs = ctx.rotate_sum_batch([ctx.import_ct(a.c, a.scale) for a in srcs], rs)
+    for a, out in zip(srcs, outs):
+        assert np.array_equal(out.export(), o.rotate_sum(a, rs).c)
