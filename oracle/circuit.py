@@ -167,7 +167,7 @@ class Circuit:
         for a, b in pairs:
             t = ev.tensor(a, b)
             acc = t if acc is None else ev.add(acc, t)
-        return ev.rescale(ev.relin(acc))
+        return ev.relin_rescale(acc)
 
     def replicate(self, v: Ct, c: int) -> Ct:
         """Alg. 1 for entry c: mask slot c, then a log2(M) rotate-and-add ladder."""

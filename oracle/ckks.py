@@ -71,6 +71,7 @@ def lib():
         "or_rescale": (None, [vp, _u64p, i32, i32, _u64p]),
         "or_keyswitch": (None, [vp, _u64p, i32, _u64p, i32, _u64p]),
         "or_keyswitch_hoisted": (None, [vp, _u64p, i32, i32, _u64p, _u64p, i32, _u64p]),
+        "or_relin_rescale": (None, [vp, _u64p, i32, _u64p, i32, _u64p]),
         "or_fft_twiddles": (None, [i32, i32, _f64p, _f64p]),
         "or_encode": (None, [i32, _f64p, dbl, _i64p]),
         "or_to_rns": (None, [vp, _i64p, i32, _u64p]),
@@ -421,8 +422,22 @@ class OracleCKKS:
         lib().or_rescale(self._ctx, np.ascontiguousarray(a.c), npoly, l, out)
         return Ct(out, a.scale / float(self.q[l - 1]))
 
+    def relin_rescale(self, t: Ct) -> Ct:
+        """relinearisation fused with the rescale after it: y = keyproduct(d2)
+        + P (d0, d1) divided once by P q_{l-1}, rounding to nearest (one base
+        conversion from the special primes and q_{l-1})."""
+        assert t.c.shape[0] == 3
+        l = t.level
+        if l < 2:
+            raise ValueError("no level left to rescale")
+        k = self.ks_k[l]
+        out = np.zeros((2, l - 1, self.N), np.uint64)
+        lib().or_relin_rescale(self._ctx, np.ascontiguousarray(t.c), l,
+                               np.ascontiguousarray(self.keys[0][k]), self.key_lmax[k], out)
+        return Ct(out, t.scale / float(self.q[l - 1]))
+
     def mult(self, a: Ct, b: Ct) -> Ct:
-        return self.rescale(self.relin(self.tensor(a, b)))
+        return self.relin_rescale(self.tensor(a, b))
 
     def drop(self, a: Ct, level: int) -> Ct:
         if level > a.level:

@@ -611,14 +611,14 @@ void or_rescale(const void *ctx, const u64 *in, int npoly, int l, u64 *out)
     }
 }
 
-/* hybrid key switch of x (coefficient domain, [l][N] over q_0..q_{l-1}) with
- * switching key ksk ([dnum][2][L+K][N]).  out = (u0, u1), [2][l][N], with
- * u0 + u1 s ~ x * target.
+/* Hybrid key switching (in the form of the full-RNS CKKS literature; the paper
+ * only names the relinearisation and rotation keys):
  *   digits j: q-limbs [j alpha, min(j alpha + alpha, l))
  *   ModUp_j : y_i = [x_i (Q_j/q_i)^-1]_{q_i};  ext_t = sum_i y_i (Q_j/q_i) mod t
  *   inner   : acc_t = sum_j ext_{j,t} * ksk_j,t (negacyclic products)
  *   ModDown : z_k = [acc_{p_k} (P/p_k)^-1]_{p_k};  conv_i = sum_k z_k (P/p_k) mod q_i;
- *             out_i = (acc_i - conv_i) P^-1 mod q_i                                */
+ *             out_i = (acc_i - conv_i) P^-1 mod q_i
+ * with P the product of the K_l special primes of the level. */
 /* Hybrid key switch of x (coefficient domain, l limbs) with key families of
  * K_l = or_ks_special(l) special primes (built by or_keygen_ksk with that k
  * and key_lmax >= l): ModUp per digit, inner product, ModDown by P_{K_l}.
@@ -630,21 +630,36 @@ void or_rescale(const void *ctx, const u64 *in, int npoly, int l, u64 *out)
  * the extended basis, and one ModDown follows.  ngal = 0 is the plain switch
  * of x with the one key in ksk. */
 static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const u64 *gal,
-                          const u64 *ksk, int key_lmax, u64 *out);
+                          const u64 *ksk, int key_lmax, const u64 *fuse, u64 *out);
 
 void or_keyswitch(const void *ctx, const u64 *x, int l, const u64 *ksk, int key_lmax, u64 *out)
 {
-    keyswitch_sum((const or_ctx *)ctx, x, l, 0, NULL, ksk, key_lmax, out);
+    keyswitch_sum((const or_ctx *)ctx, x, l, 0, NULL, ksk, key_lmax, NULL, out);
 }
 
 void or_keyswitch_hoisted(const void *ctx, const u64 *x, int l, int ngal, const u64 *gal,
                           const u64 *ksk, int key_lmax, u64 *out)
 {
-    keyswitch_sum((const or_ctx *)ctx, x, l, ngal, gal, ksk, key_lmax, out);
+    keyswitch_sum((const or_ctx *)ctx, x, l, ngal, gal, ksk, key_lmax, NULL, out);
+}
+
+/* Relinearisation fused with the rescale that follows it (A tensor (d0, d1,
+ * d2) at level l, coefficient domain [3][l][N] -> [2][l-1][N]): the key
+ * product acc of d2 is not divided by P and then the sum by q_{l-1}; instead
+ * y = acc + P (d0, d1) is divided once by P' = P q_{l-1}, rounding to nearest:
+ *   B' = {p_0..p_{K-1}, q_{l-1}},  h = (P' - 1) / 2,
+ *   z_j   = [(y_j + h) (P'/m_j)^-1]_{m_j}           for m_j in B'
+ *   conv_i = sum_j z_j (P'/m_j) mod q_i             for i < l - 1
+ *   out_i = (y_i + h - conv_i) P'^-1 mod q_i. */
+void or_relin_rescale(const void *ctx, const u64 *t3, int l, const u64 *ksk, int key_lmax,
+                      u64 *out)
+{
+    keyswitch_sum((const or_ctx *)ctx, t3 + (size_t)2 * l * ((const or_ctx *)ctx)->N, l, 0,
+                  NULL, ksk, key_lmax, t3, out);
 }
 
 static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const u64 *gal,
-                          const u64 *ksk, int key_lmax, u64 *out)
+                          const u64 *ksk, int key_lmax, const u64 *fuse, u64 *out)
 {
     const int N = c->N, L = c->L, K = c->ks_k[l], nm = key_lmax + K, ne = l + K;
     const int beta = (l + c->alpha - 1) / c->alpha;
@@ -708,6 +723,61 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
             }
     }
     free(sg);
+    if (fuse) {
+        /* ModDown fused with the rescale: divide y = acc + P (d0, d1) by
+         * P' = P q_{l-1} through B' = {p_0..p_{K-1}, q_{l-1}} */
+        const int nb = K + 1, lo = l - 1;
+        u64 bm[OR_MAXMOD];
+        int brow[OR_MAXMOD];
+        for (int kk = 0; kk < K; kk++) { bm[kk] = c->mod[L + kk]; brow[kk] = l + kk; }
+        bm[K] = c->mod[l - 1];
+        brow[K] = l - 1;
+        u64 Pq[OR_MAXMOD];                /* P mod q_i, i < l         */
+        for (int i = 0; i < l; i++) {
+            Pq[i] = 1;
+            for (int kk = 0; kk < K; kk++) Pq[i] = mmul(Pq[i], c->mod[L + kk] % c->mod[i], c->mod[i]);
+        }
+        u64 bhinv[OR_MAXMOD], hb[OR_MAXMOD];  /* (P'/m_j)^-1 mod m_j, h mod m_j */
+        u64 bh[OR_MAXMOD][OR_MAXMOD];         /* (P'/m_j) mod q_i          */
+        for (int j = 0; j < nb; j++) {
+            u64 m = bm[j], r = 1;
+            for (int j2 = 0; j2 < nb; j2++) if (j2 != j) r = mmul(r, bm[j2] % m, m);
+            bhinv[j] = minv(r, m);
+            hb[j] = (m - 1) / 2;          /* P' = 0 mod m: h = -1/2 mod m */
+            for (int i = 0; i < lo; i++) {
+                u64 q = c->mod[i], v = 1;
+                for (int j2 = 0; j2 < nb; j2++) if (j2 != j) v = mmul(v, bm[j2] % q, q);
+                bh[j][i] = v;
+            }
+        }
+        u64 ppinv[OR_MAXMOD], hq[OR_MAXMOD];  /* P'^-1 mod q_i, h mod q_i */
+        for (int i = 0; i < lo; i++) {
+            u64 q = c->mod[i], Pp = 1;
+            for (int j = 0; j < nb; j++) Pp = mmul(Pp, bm[j] % q, q);
+            ppinv[i] = minv(Pp, q);
+            hq[i] = mmul(msub(Pp, 1, q), (q + 1) / 2, q);
+        }
+        for (int pz = 0; pz < 2; pz++) {
+            const u64 *a = acc + (size_t)pz * ne * N, *d = fuse + (size_t)pz * l * N;
+            for (int k = 0; k < N; k++) {
+                u64 z[OR_MAXMOD];
+                for (int j = 0; j < nb; j++) {
+                    u64 m = bm[j], y = a[(size_t)brow[j] * N + k];
+                    if (j == K) y = madd(y, mmul(Pq[l - 1], d[(size_t)(l - 1) * N + k], m), m);
+                    z[j] = mmul(madd(y, hb[j], m), bhinv[j], m);
+                }
+                for (int i = 0; i < lo; i++) {
+                    u64 q = c->mod[i], conv = 0;
+                    for (int j = 0; j < nb; j++) conv = madd(conv, mmul(z[j] % q, bh[j][i], q), q);
+                    u64 y = madd(a[(size_t)i * N + k], mmul(Pq[i], d[(size_t)i * N + k], q), q);
+                    out[((size_t)pz * lo + i) * N + k] =
+                        mmul(msub(madd(y, hq[i], q), conv, q), ppinv[i], q);
+                }
+            }
+        }
+        free(ext); free(acc); free(t);
+        return;
+    }
     /* ModDown */
     u64 phinv[OR_MAXMOD];           /* (P/p_k)^-1 mod p_k */
     u64 phmod[OR_MAXMOD][OR_MAXMOD]; /* (P/p_k) mod q_i    */

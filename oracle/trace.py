@@ -65,6 +65,13 @@ class LevelTrace(OracleCKKS):
     def automorphism(self, a: Ct, g: int) -> Ct:
         return Ct(np.zeros_like(a.c), a.scale)
 
+    def relin_rescale(self, t: Ct) -> Ct:
+        self.ks_hist[t.level] += 1
+        l = t.level
+        if l < 2:
+            raise ValueError("no level left to rescale")
+        return Ct(self._z(2, l - 1), t.scale / float(self.q[l - 1]))
+
     def rotate_sum(self, a: Ct, rs) -> Ct:
         self.ks_hist[a.level] += 1
         return Ct(np.zeros_like(a.c), a.scale)

@@ -275,8 +275,62 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       }
       add_table(t, in_mod, out_mod);
     }
+    // relinearisation fused with rescale at level l: B' = {p_0..p_{K_l-1},
+    // q_{l-1}} -> q_0..q_{l-2}
+    for (int l = 2; l <= L; ++l) {
+      ConvTable& t = c->fused[l];
+      t.in_lo = 0;
+      std::vector<int> in_mod, out_mod;
+      for (int kk = 0; kk < c->ks_k[l]; ++kk) in_mod.push_back(L + kk);
+      in_mod.push_back(l - 1);
+      for (int m : in_mod) t.in_pidx.push_back((uint8_t)m);
+      for (int i = 0; i < l - 1; ++i) {
+        out_mod.push_back(i);
+        t.out_limb.push_back((uint16_t)i);
+        t.out_pidx.push_back((uint8_t)i);
+      }
+      add_table(t, in_mod, out_mod);
+    }
     c->d_conv_store = upload(c.get(), store);
     for (auto& f : fix) f.first->dev = c->d_conv_store + f.second;
+    // constants of the fused division by P' = P q_{l-1}, per level:
+    // [P mod q_i, Shoup](i < l) [P'^-1 mod q_i, Shoup](i < l-1)
+    // [-h mod q_i](i < l-1) [h (P'/m_j)^-1 mod m_j](j <= K_l), h = (P' - 1)/2
+    // (the rounding offset, added to every coefficient inside the conversion)
+    for (int l = 2; l <= L; ++l) {
+      const int K_l = c->ks_k[l];
+      std::vector<u64> fz;
+      for (int i = 0; i < l; ++i) {
+        const u64 q = c->mod[i];
+        u64 Pm = 1;
+        for (int kk = 0; kk < K_l; ++kk) Pm = host_mulmod(Pm, c->mod[L + kk] % q, q);
+        fz.push_back(Pm);
+        fz.push_back(shoup_companion(Pm, q));
+      }
+      std::vector<u64> hq;
+      for (int i = 0; i < l - 1; ++i) {
+        const u64 q = c->mod[i];
+        u64 Pp = c->mod[l - 1] % q;
+        for (int kk = 0; kk < K_l; ++kk) Pp = host_mulmod(Pp, c->mod[L + kk] % q, q);
+        const u64 inv = host_inv(Pp, q);
+        fz.push_back(inv);
+        fz.push_back(shoup_companion(inv, q));
+        const u64 h = host_mulmod((Pp + q - 1) % q, (q + 1) / 2, q);  // (P' - 1) / 2 mod q
+        hq.push_back(h ? q - h : 0);
+      }
+      fz.insert(fz.end(), hq.begin(), hq.end());
+      std::vector<u64> bm;
+      for (int kk = 0; kk < K_l; ++kk) bm.push_back(c->mod[L + kk]);
+      bm.push_back(c->mod[l - 1]);
+      for (size_t jj = 0; jj < bm.size(); ++jj) {
+        const u64 m = bm[jj];
+        u64 r = 1;  // (P'/m_j) mod m_j
+        for (size_t j2 = 0; j2 < bm.size(); ++j2)
+          if (j2 != jj) r = host_mulmod(r, bm[j2] % m, m);
+        fz.push_back(host_mulmod((m - 1) / 2, host_inv(r, m), m));  // h = -1/2 mod m_j
+      }
+      c->d_fused[l] = upload(c.get(), fz);
+    }
     for (int k = 1; k <= K; ++k) {
       if (!c->key_lmax[k]) continue;
       std::vector<u64> pinv((size_t)L * 2);
@@ -366,6 +420,8 @@ void ctx_destroy(Context* c) {
     if (p) cudaFree(p);
   for (auto& kv : c->masks) cudaFree(kv.second);
   for (u64* p : c->d_pinv)
+    if (p) cudaFree(p);
+  for (u64* p : c->d_fused)
     if (p) cudaFree(p);
   for (auto& r : c->prof.recs) {
     cudaEventDestroy(r.a);
@@ -639,8 +695,7 @@ void op_mult(Context* c, const Ct& a, const Ct& b, Ct& out) {
   GWHE_REQUIRE(a.l == b.l, ST_ELEVEL, "operands at different levels");
   CtPtr t = ct_new(c, 3, a.l, a.l, 1.0);
   op_tensor_mac(c, {{&a, &b}}, *t);
-  op_relin(c, *t, out);
-  op_rescale(c, out);
+  op_relin_rescale(c, *t, out);
 }
 
 void op_galois(Context* c, const Ct& a, u32 g, Ct& out) {
@@ -917,12 +972,67 @@ void set_rescale(Context* c, CtSet& s) {
   s.scale = all.scale;
 }
 
+// Relinearisation fused with the rescale after it, for cnt tensors at level l
+// (item i at t3 + i t3_stride, cap t3_cap; NTT domain) into out (level
+// l - 1): ModUp of d2 and the key product acc as in a key switch, then
+// y = acc + P (d0, d1) divided once by P' = P q_{l-1}, rounding to nearest:
+// the B' = {p_0..p_{K-1}, q_{l-1}} rows of y + floor(P'/2) back to the
+// coefficient domain, their fast conversion to q_0..q_{l-2}, its NTT, and
+// (y + floor(P'/2) - conv) P'^-1.
+static void relin_rescale_items(Context* c, const u64* t3, size_t t3_stride, int t3_cap, int cnt,
+                                int l, u64* out, size_t o_stride, int o_cap) {
+  GWHE_REQUIRE(l >= 2, ST_ELEVEL, "no level left to rescale");
+  const size_t N = c->N;
+  const Ksk& fam = key_family(c, 0, l);
+  const int K = fam.k, L = c->P.L, ne = l + K;
+  const int beta = (l + c->alpha - 1) / c->alpha;
+  c->ks_count += cnt;
+  c->ks_by_level[l] += cnt;
+  const u64* d2 = t3 + (size_t)2 * t3_cap * N;
+  Tmp ext(c, sizeof(u64) * cnt * beta * ne * N);
+  modup_ext(c, d2, t3_stride, cnt, l, ext.u());
+  Tmp acc(c, sizeof(u64) * cnt * 2 * ne * N);
+  ks_inner_set(c, d2, t3_stride, l, ext.u(), fam, acc.u(), cnt);
+  Tmp bp(c, sizeof(u64) * cnt * 2 * (K + 1) * N);
+  fused_prep_set(c, acc.u(), t3, t3_stride, t3_cap, bp.u(), l, K, cnt);
+  RowMap rb;
+  rb.npoly = 2 * cnt;
+  rb.nl = K + 1;
+  rb.poly_stride = K + 1;
+  for (int j = 0; j <= K; ++j) {
+    rb.off[j] = (uint16_t)j;
+    rb.pidx[j] = (uint8_t)(j < K ? L + j : l - 1);
+  }
+  ntt_inverse(c, bp.u(), rb);
+  Tmp conv(c, sizeof(u64) * cnt * 2 * (l - 1) * N);
+  fused_convert_set(c, bp.u(), l, K, conv.u(), cnt);
+  ntt_forward(c, conv.u(), rows_q(2 * cnt, l - 1, l - 1));
+  fused_combine_set(c, acc.u(), t3, t3_stride, t3_cap, conv.u(), out, o_stride, o_cap, l, K, cnt);
+}
+
+void set_relin_rescale(Context* c, const CtSet& t3, CtSet& out) {
+  GWHE_REQUIRE(t3.npoly == 3 && out.npoly == 2 && out.cnt == t3.cnt && out.cap >= t3.l - 1,
+               ST_EINVAL, "relinearisation set shape");
+  GWHE_REQUIRE(out.d != t3.d, ST_EINVAL, "fused relinearisation output must not alias");
+  relin_rescale_items(c, t3.d, t3.stride(), t3.cap, t3.cnt, t3.l, out.d, out.stride(), out.cap);
+  out.l = t3.l - 1;
+  out.scale = t3.scale / (double)c->mod[t3.l - 1];
+}
+
+void op_relin_rescale(Context* c, const Ct& t3, Ct& out) {
+  GWHE_REQUIRE(t3.npoly == 3 && out.npoly == 2 && out.cap >= t3.l - 1, ST_EINVAL,
+               "relinearisation needs a tensor");
+  GWHE_REQUIRE(out.d != t3.d, ST_EINVAL, "fused relinearisation output must not alias");
+  relin_rescale_items(c, t3.d, 0, t3.cap, 1, t3.l, out.d, 0, out.cap);
+  out.l = t3.l - 1;
+  out.scale = t3.scale / (double)c->mod[t3.l - 1];
+}
+
 void set_mult(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs, CtSet& out) {
   const int l = pairs[0].first->l;
   CtSetPtr t3 = set_new(c, out.cnt, 3, l, l, 1.0);
   set_tensor_mac(c, pairs, 1, *t3);
-  set_relin(c, *t3, out);
-  set_rescale(c, out);
+  set_relin_rescale(c, *t3, out);
 }
 
 // ---------------------------------------------------------------- encoding

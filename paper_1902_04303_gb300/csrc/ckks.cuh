@@ -124,6 +124,10 @@ void set_mask(Context* c, const std::vector<MaskItem>& items, double src_scale, 
 void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs,
                     int npairs, CtSet& out3);
 void set_relin(Context* c, const CtSet& t3, CtSet& out);
+// relinearisation fused with the rescale that follows it: out = the tensor
+// divided once by P q_{l-1} (level l - 1, scale / q_{l-1})
+void set_relin_rescale(Context* c, const CtSet& t3, CtSet& out);
+void op_relin_rescale(Context* c, const Ct& t3, Ct& out);
 void set_rescale(Context* c, CtSet& s);
 // out[i] = a_i * b_i (tensor, relinearise, rescale)
 void set_mult(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs, CtSet& out);

@@ -257,6 +257,7 @@ struct ConvTable {  // fast base conversion constants, on the device
   const u64* dev;   // [n_in] hinv, [n_in] hinv_sh, [n_in][n_out] hmod
   int n_in, n_out;
   int in_lo;                          // first input q-limb (ModUp digits)
+  std::vector<uint8_t> in_pidx;       // modulus index of each input limb (empty: in_lo + i)
   std::vector<uint8_t> out_pidx;      // modulus index of each output limb
   std::vector<uint16_t> out_limb;     // position of each output limb in the extended basis
 };
@@ -307,6 +308,11 @@ struct Context {
   std::map<std::pair<int, int>, ConvTable> modup;
   ConvTable moddown[kMaxSpecial + 1];
   u64* d_pinv[kMaxSpecial + 1] = {};  // [L][2] P_k^-1 mod q_i (value, Shoup)
+  // relinearisation fused with rescale at level l: conversion from
+  // {p_0..p_{K_l-1}, q_{l-1}} to q_0..q_{l-2} and the constants of the
+  // division by P' = P q_{l-1} (see k_fused_prep / k_fused_combine)
+  ConvTable fused[kMaxRowLimbs + 1];
+  u64* d_fused[kMaxRowLimbs + 1] = {};
   u64* d_conv_store = nullptr; // backing store of all conversion tables
   // encoding procedure tables
   double2* d_fftW_dec = nullptr;

@@ -93,8 +93,7 @@ struct Eval {
     CtPtr t3 = ct_new(c, 3, l, l, 1.0);
     op_tensor_mac(c, pairs, *t3);
     CtPtr out = fresh(l);
-    op_relin(c, *t3, *out);
-    op_rescale(c, *out);
+    op_relin_rescale(c, *t3, *out);
     return out;
   }
   CtPtr mult(const Ct& a, const Ct& b) {
@@ -171,8 +170,7 @@ struct Eval {
     CtSetPtr t3 = set_new(c, d, 3, lv, lv, 1.0);
     set_tensor_mac(c, pairs, m, *t3);
     CtSetPtr out = set_new(c, d, 2, lv, lv, 1.0);
-    set_relin(c, *t3, *out);
-    set_rescale(c, *out);
+    set_relin_rescale(c, *t3, *out);
     return out;
   }
   // Alg. 6 with Alg. 5 inside: every DotProd(A(c), v) (product, log2(M) ladder)
@@ -549,8 +547,7 @@ void job_fit(Job* j, int kappa) {
   CtSetPtr t3 = set_new(c, lay.H, 3, l0, l0, 1.0);
   set_tensor_mac(c, pairs, d, *t3);
   CtSetPtr acc = set_new(c, lay.H, 2, l0, l0, 1.0);
-  set_relin(c, *t3, *acc);
-  set_rescale(c, *acc);
+  set_relin_rescale(c, *t3, *acc);
   j->Mct.clear();
   for (int h = 0; h < lay.H; ++h) {
     CtPtr ah = acc->view(h);
@@ -690,8 +687,7 @@ CtSetPtr sprime_mccp(Job* j, const double* Sd, long b0, long b1) {
     }
   }
   CtSetPtr Sp = set_new(c, nbt, 2, lb, lb, 1.0);
-  set_relin(c, *T3, *Sp);
-  set_rescale(c, *Sp);  // S' at lb - 1
+  set_relin_rescale(c, *T3, *Sp);  // S' at lb - 1
   return Sp;
 }
 
@@ -751,9 +747,8 @@ CtSetPtr sprime_factored(Job* j, Eval& ev, const double* Sd, long b0, long b1) {
   set_tensor_mac(c, pairs, d, *T3);
   R.reset();
   CtSetPtr P = set_new(c, nbt, 2, lr, lr, 1.0);
-  set_relin(c, *T3, *P);
+  set_relin_rescale(c, *T3, *P);
   T3.reset();
-  set_rescale(c, *P);
   GWHE_REQUIRE(P->l == lb - 1, ST_ELEVEL, "factored S' must leave at kBatchLevel - 1 limbs");
   CtSetPtr Sp = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
   Ct sa = Sset->slice(0, nbt, lb - 1).all(), pa = P->all(), oa = Sp->all();

@@ -111,13 +111,18 @@ __global__ void k_tensor_mac(PolyView out, const MacPair* __restrict__ pairs, in
 }
 
 // ------------------------------------------------------------- base conversion
+constexpr int kMaxConvIn = 16;
 struct ConvArgs {
   const u64* tab;  // [n_in] hinv, [n_in] hinv_sh, [n_in][n_out] hmod
   int n_in, n_out, hm_stride, in_mod0;
+  uint8_t in_pidx[kMaxConvIn];  // modulus of each input limb
+  // optional constants added to every coefficient: after the input's Shoup
+  // product (mod its modulus) and to each output (mod the output's modulus)
+  const u64* in_add = nullptr;
+  const u64* out_add = nullptr;
   uint8_t out_pidx[kMaxRowLimbs];
   uint16_t out_row[kMaxRowLimbs];
 };
-constexpr int kMaxConvIn = 16;
 
 // y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o.
 // Grid: x = coefficients, y = groups of kConvOG outputs, z = items (polynomials).
@@ -135,8 +140,9 @@ __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __r
 #pragma unroll
   for (int i = 0; i < kMaxConvIn; ++i) {
     if (i < a.n_in) {
-      const u64 q = mod[a.in_mod0 + i].q;
+      const u64 q = mod[a.in_pidx[i]].q;
       y[i] = shoup(xp[(size_t)i * N + k], a.tab[i], a.tab[a.n_in + i], q);
+      if (a.in_add) y[i] = addmod(y[i], a.in_add[i], q);
     }
   }
   const u64* hm = a.tab + 2 * a.n_in;
@@ -156,7 +162,12 @@ __global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __r
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (o + t < o1)
-        op[(size_t)a.out_row[o + t] * N + k] = reduce128(s[t].lo, s[t].hi, mod[a.out_pidx[o + t]]);
+      {
+        const DevMod& om = mod[a.out_pidx[o + t]];
+        u64 v = reduce128(s[t].lo, s[t].hi, om);
+        if (a.out_add) v = addmod(v, a.out_add[o + t], om.q);
+        op[(size_t)a.out_row[o + t] * N + k] = v;
+      }
   }
 }
 
@@ -366,6 +377,60 @@ __global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __rest
   const u64* add = p ? add1 : add0;
   if (add) v = addmod(v, add[(size_t)i * N + k], q);
   (p ? out1 : out0)[(size_t)i * N + k] = v;
+}
+
+// ------------------------------------------------------------- relin + rescale
+// Fused relinearisation and rescale at level l with K special primes: the key
+// product acc ([2][ne][N]) plus P (d0, d1) is divided by P' = P q_{l-1}
+// through B' = {p_0..p_{K-1}, q_{l-1}}.  fz = [Pq: 2l][ppinv: 2(l-1)]
+// [out_add: l-1][in_add: K+1]: P mod q_i and P'^-1 mod q_i with their Shoup
+// companions, and the conversion's constants for the rounding offset
+// h = floor(P'/2) added to every coefficient (in_add_j = h (P'/m_j)^-1 mod
+// m_j after the input product, out_add_i = -h mod q_i on the output, which
+// the combine's subtraction turns into +h).
+// prep: bp[item][p][j] = y_j (NTT domain) for the B' rows
+__global__ void k_fused_prep(const u64* __restrict__ acc, const u64* __restrict__ t3,
+                             size_t t3_stride, int t3_cap, u64* __restrict__ bp, int l, int K,
+                             int L, int N, const u64* __restrict__ fz,
+                             const DevMod* __restrict__ mod) {
+  const int row = blockIdx.y, nb = K + 1, p = row / nb, j = row - p * nb;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const size_t item = blockIdx.z;
+  const int ne = l + K;
+  const u64* a = acc + (item * 2 + p) * (size_t)ne * N;
+  u64 v;
+  if (j < K) {
+    v = a[(size_t)(l + j) * N + k];
+  } else {
+    const u64 q = mod[l - 1].q;
+    const u64 d = t3[item * t3_stride + ((size_t)p * t3_cap + (l - 1)) * N + k];
+    const u64 pd = shoup(d, fz[2 * (l - 1)], fz[2 * (l - 1) + 1], q);
+    v = addmod(a[(size_t)(l - 1) * N + k], pd, q);
+  }
+  bp[((item * 2 + p) * nb + j) * (size_t)N + k] = v;
+}
+
+// combine: out_i = (acc_i + P d_i - conv_i) P'^-1 mod q_i, i < l - 1 (conv
+// carries -h)
+__global__ void k_fused_combine(const u64* __restrict__ acc, const u64* __restrict__ t3,
+                                size_t t3_stride, int t3_cap, const u64* __restrict__ conv,
+                                u64* __restrict__ out, size_t o_stride, int o_cap, int l, int K,
+                                int N, const u64* __restrict__ fz,
+                                const DevMod* __restrict__ mod) {
+  const int lo = l - 1, row = blockIdx.y, p = row / lo, i = row - p * lo;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const size_t item = blockIdx.z;
+  const int ne = l + K;
+  const u64 q = mod[i].q;
+  const u64 a = acc[((item * 2 + p) * (size_t)ne + i) * N + k];
+  const u64 d = t3[item * t3_stride + ((size_t)p * t3_cap + i) * N + k];
+  const u64 cv = conv[((item * 2 + p) * (size_t)lo + i) * N + k];
+  const u64* ppinv = fz + 2 * l;
+  u64 y = addmod(a, shoup(d, fz[2 * i], fz[2 * i + 1], q), q);
+  y = submod(y, cv, q);
+  out[item * o_stride + ((size_t)p * o_cap + i) * N + k] = shoup(y, ppinv[2 * i], ppinv[2 * i + 1], q);
 }
 
 // ------------------------------------------------------------- rescale
@@ -1052,6 +1117,8 @@ static ConvArgs conv_args(const ConvTable& t, int in_mod0) {
   a.n_out = t.n_out;
   a.hm_stride = t.n_out;
   a.in_mod0 = in_mod0;
+  for (int i = 0; i < t.n_in; ++i)
+    a.in_pidx[i] = (uint8_t)(t.in_pidx.empty() ? in_mod0 + i : t.in_pidx[i]);
   for (int o = 0; o < t.n_out; ++o) {
     a.out_pidx[o] = t.out_pidx[o];
     a.out_row[o] = t.out_limb[o];
@@ -1177,6 +1244,35 @@ void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, 
     default: throw Error(ST_EINVAL, "at most seven hoisted automorphisms");
   }
 #undef GWHE_AUTOSUM
+  GWHE_LAUNCHED(c, 1);
+}
+
+void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
+                    u64* bp, int l, int K, int cnt) {
+  ProfScope ps(c, PROF_ELEMWISE, 3.0 * 2 * (K + 1) * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536 && l >= 2, ST_EINVAL, "bad fused batch");
+  k_fused_prep<<<dim3(blocks_for(c->N), 2 * (K + 1), cnt), kThreads, 0, c->stream>>>(
+      acc, t3, t3_stride, t3_cap, bp, l, K, c->P.L, c->N, c->d_fused[l], c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt) {
+  ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (K + l) * 8.0 * c->N);
+  const ConvTable& t = c->fused[l];
+  GWHE_REQUIRE(t.n_in == K + 1 && t.n_out == l - 1, ST_EINVAL, "fused conversion table");
+  ConvArgs a = conv_args(t, 0);
+  a.out_add = c->d_fused[l] + 2 * l + 2 * (l - 1);
+  a.in_add = a.out_add + (l - 1);
+  launch_baseconv(c, bp, (size_t)(K + 1) * c->N, conv, (size_t)(l - 1) * c->N, 2 * cnt, a);
+}
+
+void fused_combine_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
+                       const u64* conv, u64* out, size_t o_stride, int o_cap, int l, int K,
+                       int cnt) {
+  ProfScope ps(c, PROF_ELEMWISE, 4.0 * 2 * (l - 1) * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536 && l >= 2, ST_EINVAL, "bad fused batch");
+  k_fused_combine<<<dim3(blocks_for(c->N), 2 * (l - 1), cnt), kThreads, 0, c->stream>>>(
+      acc, t3, t3_stride, t3_cap, conv, out, o_stride, o_cap, l, K, c->N, c->d_fused[l], c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 

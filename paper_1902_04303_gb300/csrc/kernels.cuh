@@ -55,6 +55,16 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
 void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int K, int cnt,
                          u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                          size_t a0_stride, size_t a1_stride);
+// Relinearisation fused with rescale (level l, K = ks_k[l] special primes),
+// over cnt tensors (t3 items at t3 + i t3_stride, cap t3_cap): bp rows
+// [cnt][2][K+1][N] of y + floor(P'/2) over B' = {p_0..p_{K-1}, q_{l-1}},
+// their conversion to q_0..q_{l-2} ([cnt][2][l-1][N]), and the combine.
+void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
+                    u64* bp, int l, int K, int cnt);
+void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt);
+void fused_combine_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
+                       const u64* conv, u64* out, size_t o_stride, int o_cap, int l, int K,
+                       int cnt);
 // Hoisted key switching of a sum of automorphisms (at most kMaxHoist): the
 // Galois elements and the key family each uses.
 constexpr int kMaxHoist = 7;

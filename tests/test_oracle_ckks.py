@@ -367,6 +367,49 @@ def small_rot():
     return o
 
 
+def _centred_crt(o, res, l):
+    return np.array(o.crt_centered(res[:l]), dtype=object)
+
+
+@pytest.mark.parametrize("l", [5, 3, 2])
+def test_fused_relin_rescale_is_the_rounded_division(wide, l):
+    """Dec(relin_rescale(t)) = round(Dec3(t) / q_{l-1}) + e, |e| < 2^24, where
+    Dec3(t) = d0 + d1 s + d2 s^2 exactly (big-integer CRT): the one fused
+    division by P q_{l-1} must reproduce the exact rounded rescale of the
+    tensor's decryption up to switch noise; a wrong key breaks it."""
+    o = wide
+    rng = _rng(70 + l)
+    t = ckks.Ct(np.stack([np.stack([rng.integers(0, o.q[i], size=o.N, dtype=np.uint64)
+                                    for i in range(l)]) for _ in range(3)]), o.delta)
+    s1 = np.zeros((o.L + o.K, o.N), np.uint64)
+    s2 = np.zeros((o.L + o.K, o.N), np.uint64)
+    sk = o.secret_key()
+    L.or_to_rns(o._ctx, sk, o.L, s1[:o.L])
+    L.or_sk_square(o._ctx, s2)
+    dec3 = np.zeros((l, o.N), np.uint64)
+    for i in range(l):
+        q = o.q[i]
+        psi = L.or_primitive_root_2n(q, o.logN)
+        p1 = np.zeros(o.N, np.uint64)
+        p2 = np.zeros(o.N, np.uint64)
+        L.or_polymul(np.ascontiguousarray(t.c[1, i]), np.ascontiguousarray(s1[i]), p1, o.logN, q, psi)
+        L.or_polymul(np.ascontiguousarray(t.c[2, i]), np.ascontiguousarray(s2[i]), p2, o.logN, q, psi)
+        dec3[i] = ((t.c[0, i].astype(object) + p1.astype(object) + p2.astype(object)) % q).astype(np.uint64)
+    exact = _centred_crt(o, dec3, l)
+    ql = o.q[l - 1]
+    want = np.array([(int(v) + ql // 2) // ql if v >= 0 else -((-int(v) + ql // 2) // ql)
+                     for v in exact], dtype=object)
+    got = _centred_crt(o, o.decrypt(o.relin_rescale(t)), l - 1)
+    assert max(abs(int(a) - int(b)) for a, b in zip(got, want)) < 2 ** 24
+    saved = o.keys[0]
+    o.keys[0] = o.keys[galois_rot(9, 1)]
+    try:
+        bad = _centred_crt(o, o.decrypt(o.relin_rescale(t)), l - 1)
+    finally:
+        o.keys[0] = saved
+    assert max(abs(int(a) - int(b)) for a, b in zip(bad, want)) > math.prod(o.q[:l - 1]) // 2 ** 8
+
+
 def test_automorphism_rotates_slots():
     o = OracleCKKS(logN=8, L=2, K=1)
     rng = _rng(12)

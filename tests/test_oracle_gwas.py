@@ -15,10 +15,11 @@ from oracle.trace import job_ks_histogram
 from paper_1902_04303_gb300.datagen import make_gwas
 
 def _count_switches(o):
-    """per-level key switches of the oracle evaluator o: one per switch and
-    one per hoisted rotation group (shared ModUp and ModDown)"""
+    """per-level key switches of the oracle evaluator o: one per switch, one
+    per hoisted rotation group (shared ModUp and ModDown) and one per fused
+    relinearisation-rescale"""
     hist = np.zeros(65, np.int64)
-    real_ks, real_sum = o.keyswitch, o.rotate_sum
+    real_ks, real_sum, real_rr = o.keyswitch, o.rotate_sum, o.relin_rescale
 
     def counting_ks(x, key_id):
         hist[x.shape[0]] += 1
@@ -33,7 +34,11 @@ def _count_switches(o):
         finally:
             o.keyswitch = old
 
-    o.keyswitch, o.rotate_sum = counting_ks, counting_sum
+    def counting_rr(t):
+        hist[t.level] += 1
+        return real_rr(t)
+
+    o.keyswitch, o.rotate_sum, o.relin_rescale = counting_ks, counting_sum, counting_rr
     return hist
 
 
