@@ -149,6 +149,7 @@ def run_gpu(args):
     steps_rot, layout_used = probe.rotation_steps(), "factored" if probe.factored else "mccp"
     probe.close()
     ctx.keygen(rot_steps=steps_rot, conj=True)
+    tuned = ctx.autotune()  # the fastest compiled shape of the transform on this GPU
     data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"] + rank)
     A = client_preprocess(data.X)
     dev = {nm: torch.from_numpy(np.ascontiguousarray(v)).cuda()
@@ -269,6 +270,7 @@ def run_gpu(args):
         "e2e": {"value": round(snps / (e2e_ms / 1e3), 1), "unit": "SNPs/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "autotune": {"ntt_shape": tuned[0], "ms_per_shape": tuned[1]},
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -299,6 +301,7 @@ def run_micro(ctx_stream, reps=3):
     stream = ctx_stream
     ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
                        W["dnum"], seed=W["seed"], stream=stream.cuda_stream)
+    tuned = ctx.autotune()
     steps = [1 << i for i in range(8)]
     N, L, nct = ctx.N, W["L"], W["n_ct"]
     rows = nct * 2 * L
@@ -372,6 +375,7 @@ def run_micro(ctx_stream, reps=3):
         ks.append(e0.elapsed_time(e1))
     t_ks = min(ks) / 1e3
     return {"workload": W["name"], "ntt_roundtrip_exact": ok,
+            "ntt_shape": tuned[0], "ntt_ms_per_shape_512_rows": tuned[1],
             "ntt_limb_per_s": round(rows / t_ntt, 1),
             "ntt_gbs_algorithmic": round(rows * N * 16 / t_ntt / 1e9, 1),
             "ntt_ms_3072_limbs": round(t_ntt * 1e3, 3),
@@ -530,6 +534,7 @@ def _serving_ctx(gwhe, stream, shapes):
         steps += [r for r in job.rotation_steps() if r not in steps]
         job.close()
     ctx.keygen(rot_steps=steps, conj=True)
+    ctx.autotune()
     return ctx
 
 

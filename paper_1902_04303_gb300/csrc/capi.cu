@@ -588,6 +588,66 @@ int gwhe_ctx_create_child(gwhe_ctx* ctx, void* stream, gwhe_ctx** out) {
   });
 }
 
+int gwhe_set_ntt_variant(gwhe_ctx* ctx, int variant) {
+  return guard(C(ctx), [&] {
+    need(variant >= 0 && variant < kNttVariants, "no such transform shape");
+    C(ctx)->ntt_variant = variant;
+  });
+}
+
+int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    need(rows >= 1 && rows <= 4096, "rows must be in [1, 4096]");
+    for (int v = 0; v < kNttVariants; ++v)
+      if (ms) ms[v] = 0.0;
+    if (c->logN != 16) {  // one shape only
+      if (chosen) *chosen = c->ntt_variant;
+      return;
+    }
+    // zero residues are valid inputs; the transforms' cost does not depend on
+    // the values
+    Tmp buf(c, sizeof(u64) * (size_t)rows * c->N);
+    GWHE_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(u64) * (size_t)rows * c->N, c->stream));
+    RowMap rm;
+    rm.npoly = rows;
+    rm.nl = 1;
+    rm.poly_stride = 1;
+    rm.off[0] = 0;
+    rm.pidx[0] = 0;
+    cudaEvent_t e0, e1;
+    GWHE_CUDA(cudaEventCreate(&e0));
+    GWHE_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    double best_ms = 1e30;
+    for (int v = 0; v < kNttVariants; ++v) {
+      c->ntt_variant = v;
+      ntt_forward(c, buf.u(), rm);
+      ntt_inverse(c, buf.u(), rm);
+      float t = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        GWHE_CUDA(cudaEventRecord(e0, c->stream));
+        ntt_forward(c, buf.u(), rm);
+        ntt_inverse(c, buf.u(), rm);
+        GWHE_CUDA(cudaEventRecord(e1, c->stream));
+        GWHE_CUDA(cudaEventSynchronize(e1));
+        float x = 0.f;
+        GWHE_CUDA(cudaEventElapsedTime(&x, e0, e1));
+        t = std::min(t, x);
+      }
+      if (ms) ms[v] = t;
+      if (t < best_ms) {
+        best_ms = t;
+        best = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->ntt_variant = best;
+    if (chosen) *chosen = best;
+  });
+}
+
 int gwhe_ks_histogram(const gwhe_ctx* ctx, long* out, int n) {
   if (!ctx || !out || n < 1) return GWHE_EINVAL;
   for (int l = 0; l < n; ++l) out[l] = l <= kMaxRowLimbs ? ctx->c->ks_by_level[l] : 0;

@@ -200,14 +200,12 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
   }
 }
 
-// pass A: 2^LA-point columns, pass B: 2^LB-point rows; a pass of more than 8
-// stages holds 32 residues per thread in 128-thread CTAs
-template <int LOGN, int LA, int LB>
+// pass A: 2^LA-point columns, pass B: 2^LB-point rows, with EA / EB residues
+// per thread in NA / NB-thread CTAs
+template <int LOGN, int LA, int LB, int EA, int NA, int EB, int NB>
 static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
-  constexpr int EA = LA > 8 ? 32 : 16, NA = LA > 8 ? 128 : 256;
-  constexpr int EB = LB > 8 ? 32 : 16, NB = LB > 8 ? 128 : 256;
   const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
   const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
@@ -220,6 +218,25 @@ static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
   GWHE_LAUNCHED(c, 2);
 }
 
+// the default shape of a two-pass transform: a pass of more than 8 stages
+// holds 32 residues per thread in 128-thread CTAs
+template <int LOGN, int LA, int LB>
+static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
+  ntt_two_pass<LOGN, LA, LB, (LA > 8 ? 32 : 16), (LA > 8 ? 128 : 256), (LB > 8 ? 32 : 16),
+               (LB > 8 ? 128 : 256)>(c, data, rm, fwd);
+}
+
+// shapes of the N = 2^16 transform (identical results; the autotuner times
+// them on the device and keeps the fastest)
+static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd) {
+  switch (c->ntt_variant) {
+    case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd); return;
+    case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd); return;
+    case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd); return;
+    default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd); return;
+  }
+}
+
 static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
   const int rows = rm.npoly * rm.nl;
   if (rows <= 0) return;
@@ -228,7 +245,7 @@ static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
   GWHE_REQUIRE(rm.nl <= kMaxRowLimbs, ST_EINVAL, "too many limbs in a row map");
   switch (c->logN) {
     case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd); return;
-    case 16: ntt_two_pass<16, 8, 8>(c, data, rm, fwd); return;
+    case 16: ntt_2_16(c, data, rm, fwd); return;
     case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd); return;
     case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd); return;
     case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd); return;

@@ -89,6 +89,8 @@ _SIGS = {
     "gwhe_job_create": [_vp, _i, _i, _l, ctypes.POINTER(_vp)],
     "gwhe_job_create_ex": [_vp, _i, _i, _l, _i, ctypes.POINTER(_vp)],
     "gwhe_job_info": [_vp, ctypes.POINTER(_l)],
+    "gwhe_autotune": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)],
+    "gwhe_set_ntt_variant": [_vp, _i],
     "gwhe_job_set_nonce": [_vp, _u32],
     "gwhe_job_release_results": [_vp],
     "gwhe_ctx_create_child": [_vp, _vp, ctypes.POINTER(_vp)],
@@ -465,6 +467,17 @@ class Context:
         out = np.zeros((2, l, self.N), np.uint64)
         self._c(lib().gwhe_keyswitch(self.h, x, l, key_id, out))
         return out
+
+    def autotune(self, rows=512):
+        """time the compiled shapes of the N = 2^16 transform, keep the fastest;
+        returns (chosen shape, ms per shape)."""
+        ms = (ctypes.c_double * 4)()
+        ch = _i(0)
+        self._c(lib().gwhe_autotune(self.h, rows, ms, ctypes.byref(ch)))
+        return ch.value, [round(float(x), 4) for x in ms]
+
+    def set_ntt_variant(self, v):
+        self._c(lib().gwhe_set_ntt_variant(self.h, v))
 
     def probe_butterflies(self, rounds=2048):
         """butterflies/s of the NTT butterfly on register-resident data (the

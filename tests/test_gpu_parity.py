@@ -290,3 +290,29 @@ def test_hoisted_rotation_sum_batch_bit_exact(g, small):
     outs = ctx.rotate_sum_batch([ctx.import_ct(a.c, a.scale) for a in srcs], rs)
     for a, out in zip(srcs, outs):
         assert np.array_equal(out.export(), o.rotate_sum(a, rs).c)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_ntt_shape_is_bit_exact(g, variant):
+    """each compiled shape of the N = 2^16 transform gives the oracle's
+    residues (round trip, negacyclic product, one key switch)."""
+    import torch
+    ctx, o = pair(g, 16, 3, 2, 3, seed=41, rot=(1,), conj=False)
+    ctx.set_ntt_variant(variant)
+    x = rand_ct(o, 3, 500 + variant, npoly=1).c[0]
+    assert np.array_equal(ctx.keyswitch(x, 0), o.keyswitch(x, 0))
+    a, b = rand_ct(o, 3, 510), rand_ct(o, 3, 511)
+    ga, gb = ctx.import_ct(a.c, a.scale), ctx.import_ct(b.c, b.scale)
+    assert np.array_equal(ctx.mult(ga, gb).export(), o.mult(a, b).c)
+    t = torch.from_numpy(np.ascontiguousarray(a.c.astype(np.int64))).cuda()
+    ref = t.clone()
+    ctx.ntt_batch(t, 2, 3)
+    ctx.ntt_batch(t, 2, 3, inverse=True)
+    assert torch.equal(t, ref)
+
+
+def test_autotune_picks_a_shape(g):
+    ctx = g.Context(16, 2, K=1, dnum=2, seed=1)
+    v, ms = ctx.autotune(rows=64)
+    assert 0 <= v < 4 and len(ms) == 4 and all(x > 0 for x in ms)
+    assert ms[v] == min(ms)
