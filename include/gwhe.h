@@ -331,14 +331,16 @@ int gwhe_server_destroy(gwhe_server* s);
 int gwhe_ctx_create_child(gwhe_ctx* ctx, void* stream, gwhe_ctx** out);
 
 /* ------------------------------------------------------------ autotuning
- * The N = 2^16 transform is compiled in several shapes (two passes of 8 + 8,
- * 7 + 9 or 9 + 7 stages; 16 residues per thread in 256-thread CTAs or 32 in
- * 128-thread CTAs); every shape computes identical residues.
+ * The N = 2^16 transform is compiled in six shapes (two passes of 8 + 8,
+ * 7 + 9 or 9 + 7 stages; 16 residues per thread in 64-, 128- or 256-thread
+ * CTAs, or 32 in 128-thread CTAs); every shape computes identical residues.
  * gwhe_autotune times a forward and an inverse transform of `rows` rows in
  * each shape on the context's stream, keeps the fastest (for this context
- * and the child contexts made after it) and returns the times (ms[4], may be
+ * and the child contexts made after it) and returns the times (ms[6], may be
  * NULL) and the choice.  Other ring degrees have one shape (ms all 0).
- * gwhe_set_ntt_variant selects a shape directly (0..3, 0 = 8 + 8 x 16). */
+ * gwhe_set_ntt_variant selects a shape directly (0..5); a context starts
+ * with shape 4 (8 + 8 x 16 in 128-thread CTAs, the fastest measured on
+ * GB300). */
 int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen);
 int gwhe_set_ntt_variant(gwhe_ctx* ctx, int variant);
 

@@ -290,7 +290,8 @@ struct Context {
   const Context* parent = nullptr;
   Params P;
   int N = 0, logN = 0, alpha = 0, nmod = 0;
-  int ntt_variant = 0;         // shape of the N = 2^16 transform (kNttVariants)
+  int ntt_variant = 4;         // shape of the N = 2^16 transform (kNttVariants;
+                               // 4 = the fastest measured on GB300, see gwhe_autotune)
   u64 seed = 0;
   cudaStream_t stream = 0;
   std::vector<u64> mod;        // [L + K]: q_0..q_{L-1}, p_0..p_{K-1}
@@ -340,7 +341,7 @@ struct Context {
 };
 
 // shapes of the N = 2^16 transform compiled in (identical results)
-constexpr int kNttVariants = 4;
+constexpr int kNttVariants = 6;
 
 // the family of key id that a switch at level l uses (ST_ENOKEY if absent)
 const Ksk& key_family(const Context* c, u32 key_id, int l);

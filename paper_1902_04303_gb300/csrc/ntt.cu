@@ -29,9 +29,9 @@ namespace gwhe {
 // residues per thread (LS <= 2 log2 E): log2 E stages in registers in a
 // strided layout, a shared-memory transpose to a contiguous layout for the
 // remaining stages, and a transpose back for coalesced stores.
-template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256>
-__global__ void __launch_bounds__(NT, 4) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
-                                                 const NttTables tb, const int groups_per_row) {
+template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256, int MB = 4>
+__global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
+                                                  const NttTables tb, const int groups_per_row) {
   constexpr int S = 1 << LS;
   constexpr int LE = E == 16 ? 4 : 5;  // log2 E
   static_assert(E == 16 || E == 32, "16 or 32 residues per thread");
@@ -201,19 +201,19 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
 }
 
 // pass A: 2^LA-point columns, pass B: 2^LB-point rows, with EA / EB residues
-// per thread in NA / NB-thread CTAs
-template <int LOGN, int LA, int LB, int EA, int NA, int EB, int NB>
+// per thread in NA / NB-thread CTAs, at least MB CTAs per SM
+template <int LOGN, int LA, int LB, int EA, int NA, int EB, int NB, int MB = 4>
 static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
   const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
   const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
-    k_ntt_pass<LOGN, LA, true, true, EA, NA><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
-    k_ntt_pass<LOGN, LB, false, true, EB, NB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
+    k_ntt_pass<LOGN, LA, true, true, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
+    k_ntt_pass<LOGN, LB, false, true, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
   } else {
-    k_ntt_pass<LOGN, LB, false, false, EB, NB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
-    k_ntt_pass<LOGN, LA, true, false, EA, NA><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
+    k_ntt_pass<LOGN, LB, false, false, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
+    k_ntt_pass<LOGN, LA, true, false, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
   }
   GWHE_LAUNCHED(c, 2);
 }
@@ -233,6 +233,8 @@ static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd) {
     case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd); return;
     case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd); return;
     case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd); return;
+    case 4: ntt_two_pass<16, 8, 8, 16, 128, 16, 128, 8>(c, data, rm, fwd); return;
+    case 5: ntt_two_pass<16, 8, 8, 16, 64, 16, 64, 16>(c, data, rm, fwd); return;
     default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd); return;
   }
 }

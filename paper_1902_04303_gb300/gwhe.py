@@ -471,7 +471,7 @@ class Context:
     def autotune(self, rows=512):
         """time the compiled shapes of the N = 2^16 transform, keep the fastest;
         returns (chosen shape, ms per shape)."""
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 6)()
         ch = _i(0)
         self._c(lib().gwhe_autotune(self.h, rows, ms, ctypes.byref(ch)))
         return ch.value, [round(float(x), 4) for x in ms]
