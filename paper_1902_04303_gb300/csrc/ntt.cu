@@ -39,9 +39,12 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
   constexpr int TPS = S / E;          // threads per sub-transform
   constexpr int G = NT / TPS;         // sub-transforms per CTA
   constexpr int LC = LOGN - LS;       // log2 of the other dimension
-  // padding keeps the strided and contiguous accesses free of bank conflicts
-  constexpr bool PADE = !PASSA || E == 32;
-  constexpr int PADS = PADE ? (S + S / E + (E == 32 ? 1 : 0)) : (S + 1);
+  // padding keeps the strided and contiguous accesses free of bank conflicts:
+  // one word per E residues, and a row pitch that spreads the sub-transforms
+  // of a half-warp over distinct 64-bit banks (G < 16 column sub-transforms
+  // per CTA need a pitch of 2 mod 16, G = 16 one of 1 mod 16)
+  constexpr bool PADE = !PASSA || E == 32 || G < 16;
+  constexpr int PADS = PADE ? (S + S / E + (E == 32 ? 1 : (PASSA ? 2 : 0))) : (S + 1);
   constexpr int S0 = PASSA ? 0 : LC;  // global index of local stage 0
   __shared__ u64 sm[G * PADS];
 
