@@ -114,6 +114,8 @@ class Clocks:
 # the multiply-add pipe, not issue, bounds the transform.
 NUM_SMS = 152
 FMAHEAVY_CYCLES_PER_WARP_BFLY = 34.7
+# ncu, 3072 rows of 2^16: pass A 1.611 + 1.555 GB, pass B 1.846 + 1.561 GB
+NTT_DRAM_BYTES_PER_LIMB = round((1.611e9 + 1.555e9 + 1.846e9 + 1.561e9) / 3072)
 
 
 def alu_peak_gbfly(sm_mhz):
@@ -249,6 +251,12 @@ def run_gpu(args):
                                     "%.1f pipe cycles per warp-butterfly (ncu, probe)" %
                                     (NUM_SMS, clk_mhz, FMAHEAVY_CYCLES_PER_WARP_BFLY),
                      "probe_gbfly": round(probe / 1e9, 2),
+                     # DRAM bytes per limb transform (both passes) from the ncu capture
+                     # of the 3072-limb batch in profiles/ntt_pass_ntt-ks-micro.md,
+                     # against 2 MiB algorithmic for the two-pass layout
+                     "traffic": NTT_DRAM_BYTES_PER_LIMB,
+                     "traffic_unit": "bytes per limb transform (dram read + write, ncu)",
+                     "traffic_algorithmic": 2 * (1 << W["logN"]) * 8 * 2,
                      "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                                   "frac": round(achieved / hbm, 4)}})
     h2d = sum(host[nm].numel() * 8 for nm in host)
