@@ -254,7 +254,7 @@ def run_gpu(args):
                      # DRAM bytes per limb transform (both passes) from the ncu capture
                      # of the 3072-limb batch in profiles/ntt_pass_ntt-ks-micro.md,
                      # against 2 MiB algorithmic for the two-pass layout
-                     "traffic": NTT_DRAM_BYTES_PER_LIMB,
+                     "traffic": NTT_DRAM_BYTES_PER_LIMB if W["logN"] == 16 else None,
                      "traffic_unit": "bytes per limb transform (dram read + write, ncu)",
                      "traffic_algorithmic": 2 * (1 << W["logN"]) * 8 * 2,
                      "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
