@@ -803,30 +803,43 @@ void job_decrypt(Job* j, double* num, double* den) {
   GWHE_REQUIRE(!have.empty(), ST_EINVAL, "no batch results to decrypt");
   const int cnt = (int)have.size() * 3;
   Tmp m(c, sizeof(u64) * (size_t)cnt * N);
-  for (size_t h = 0; h < have.size(); ++h)
-    for (int o = 0; o < 3; ++o) {
-      Ct v = *j->out[have[h]][o];
-      v.owned = false;
-      v.l = 1;
-      decrypt_coeff(c, v, m.u() + (h * 3 + o) * (size_t)N);
-    }
+  {
+    // one decryption of every output's q0 limb, then one inverse transform
+    GWHE_REQUIRE(c->d_sk, ST_ENOKEY, "no secret key");
+    std::vector<const u64*> ptr(2 * (size_t)cnt);
+    for (size_t h = 0; h < have.size(); ++h)
+      for (int o = 0; o < 3; ++o) {
+        const Ct& v = *j->out[have[h]][o];
+        ptr[h * 3 + o] = v.poly(0);
+        ptr[cnt + h * 3 + o] = v.poly(1);
+      }
+    Tmp dp(c, sizeof(u64*) * ptr.size());
+    GWHE_CUDA(cudaMemcpyAsync(dp.p, ptr.data(), sizeof(u64*) * ptr.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    const u64* const* p0 = (const u64* const*)dp.p;
+    decrypt_q0_list(c, p0, p0 + cnt, cnt, m.u());
+    ntt_inverse(c, m.u(), rows_q(cnt, 1, 1));
+  }
   Tmp z(c, sizeof(double2) * (size_t)cnt * M);
   Tmp work(c, sizeof(double2) * (size_t)cnt * M);
   // scales differ per output: decode with scale 1 and divide on the host
   decode_batch(c, m.u(), cnt, 1.0, z.as<double2>(), work.as<double2>());
-  std::vector<double2> hz((size_t)cnt * M);
-  GWHE_CUDA(cudaMemcpyAsync(hz.data(), z.p, sizeof(double2) * hz.size(), cudaMemcpyDeviceToHost,
+  // only slot b * nb of each output holds a result: gather those B slots
+  const int B = lay.B;
+  gather_slots(c, z.as<double2>(), cnt, M, B, lay.nb, work.as<double2>());
+  std::vector<double2> hz((size_t)cnt * B);
+  GWHE_CUDA(cudaMemcpyAsync(hz.data(), work.p, sizeof(double2) * hz.size(), cudaMemcpyDeviceToHost,
                             c->stream));
   GWHE_CUDA(cudaStreamSynchronize(c->stream));
   for (size_t h = 0; h < have.size(); ++h) {
     const long bi = have[h];
     const double sn = j->out[bi][0]->scale, se = j->out[bi][1]->scale, so = j->out[bi][2]->scale;
-    const double2* zn = hz.data() + (h * 3 + 0) * M;
-    const double2* ze = hz.data() + (h * 3 + 1) * M;
-    const double2* zo = hz.data() + (h * 3 + 2) * M;
-    for (int b = 0; b < lay.B; ++b) {
+    const double2* zn = hz.data() + (h * 3 + 0) * B;
+    const double2* ze = hz.data() + (h * 3 + 1) * B;
+    const double2* zo = hz.data() + (h * 3 + 2) * B;
+    for (int b = 0; b < B; ++b) {
       const long s0 = bi * lay.tau + 2L * b;
-      const int slot = b * lay.nb;
+      const int slot = b;
       if (s0 < lay.k) {
         num[s0] = zn[slot].x / sn;
         den[s0] = ze[slot].x / se;

@@ -766,6 +766,26 @@ __global__ void k_decrypt(CPolyView ct, const u64* __restrict__ s, int l, u64* _
   m[(size_t)i * N + k] = addmod(c0, mulmod(c1, s[(size_t)i * N + k], md), md.q);
 }
 
+// m[i] = c0_i + c1_i s on the q0 limb (NTT domain) for a list of ciphertexts
+__global__ void k_decrypt_q0_list(const u64* const* __restrict__ c0s,
+                                  const u64* const* __restrict__ c1s,
+                                  const u64* __restrict__ s, u64* __restrict__ m, int N,
+                                  const DevMod* __restrict__ mod) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const size_t i = blockIdx.y;
+  const DevMod md = mod[0];
+  m[i * N + k] = addmod(c0s[i][k], mulmod(c1s[i][k], s[k], md), md.q);
+}
+
+__global__ void k_gather_slots(const double2* __restrict__ z, int cnt, int M, int B, int stride,
+                               double2* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)cnt * B) return;
+  const long i = t / B, b = t - i * B;
+  out[t] = z[i * M + b * stride];
+}
+
 // ------------------------------------------------------------- encoding FFT
 // Complex arithmetic as separately rounded IEEE operations (no FMA), in the
 // order of the encoding procedure.
@@ -1397,6 +1417,24 @@ void int_to_rns(Context* c, const i64* in, int count, int l, u64* out) {
   GWHE_REQUIRE((size_t)count * l < 65536, ST_EINVAL, "batch too large");
   k_int_to_rns<<<grid_rows(c->N, count * l), kThreads, 0, c->stream>>>(in, count, l, out, c->N,
                                                                        c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void decrypt_q0_list(Context* c, const u64* const* d_c0s, const u64* const* d_c1s, int cnt,
+                     u64* m) {
+  ProfScope ps(c, PROF_ELEMWISE, 4.0 * cnt * 8.0 * c->N);
+  GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "decryption batch too large");
+  k_decrypt_q0_list<<<dim3(blocks_for(c->N), cnt), kThreads, 0, c->stream>>>(d_c0s, d_c1s, c->d_sk, m,
+                                                                           c->N, c->d_mod);
+  GWHE_LAUNCHED(c, 1);
+}
+
+void gather_slots(Context* c, const double2* z, int cnt, int M, int B, int stride, double2* out) {
+  GWHE_REQUIRE(cnt >= 1 && B >= 1 && stride >= 1 && (long)(B - 1) * stride < M, ST_EINVAL,
+               "slot gather out of range");
+  const long n = (long)cnt * B;
+  k_gather_slots<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(z, cnt, M, B,
+                                                                                     stride, out);
   GWHE_LAUNCHED(c, 1);
 }
 

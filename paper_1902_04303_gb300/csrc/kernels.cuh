@@ -118,6 +118,13 @@ void decode_batch(Context* c, const u64* m_coeff_q0, int count, double scale, do
                   double2* work);
 
 // decryption inner product m = c0 + c1 s over l limbs (NTT domain)
+// m[i] = c0_i + c1_i s on limb 0 (NTT domain) for cnt ciphertexts given by
+// device arrays of their poly pointers
+void decrypt_q0_list(Context* c, const u64* const* d_c0s, const u64* const* d_c1s, int cnt,
+                     u64* m);
+// out[i * B + b] = z[i * M + b * stride] for i < cnt, b < B: the slots of a
+// batch of decoded vectors that hold results, gathered before the copy back
+void gather_slots(Context* c, const double2* z, int cnt, int M, int B, int stride, double2* out);
 void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m);
 
 // REP rows of a SNP batch as complex slots: rows j < n, slot b * nb + t =
