@@ -113,6 +113,17 @@ def ladder_groups(steps):
     return out
 
 
+def replicate_period(m: int, M: int) -> int:
+    """Period P of the shared replicate ladder for m entries: the smallest
+    power of 2^LADDER_GROUP that is >= m (at most M).  Its step lists
+    P, 2P, ..., M/2 and 1, 2, ..., P/2 split Alg. 1's ladder at a group
+    boundary, so they need no rotation keys beyond Alg. 1's own."""
+    P = 1 << LADDER_GROUP
+    while P < m:
+        P <<= LADDER_GROUP
+    return min(P, M)
+
+
 def circuit_ladders(layout: Layout, factored: bool = False):
     """The step lists of the circuit's ladders: Replicate/DotProd over all
     slots (Alg. 1, 5), colSum over nb (Alg. 4), Duplicate over the blocks
@@ -176,9 +187,30 @@ class Circuit:
         t = self.ladder(t, [1 << i for i in range(self.lay.logN - 1)])
         return t
 
+    def replicate_all(self, v: Ct, m: int):
+        """Alg. 1 for entries 0..m-1 of a vector that is zero beyond them,
+        with one shared ladder.  Alg. 1's ladder sums the rotations of the
+        masked slot by 0..M-1; here the steps P, 2P, ..., M/2 run first on v
+        itself (slot s then holds the sum of v over the slots = s mod P, which
+        is v_{s mod P}), the mask keeps the slots = c mod P, and the steps
+        1, 2, ..., P/2 fill the rest: the same sum, with the first part done
+        once for all m entries.  Same depth (one mask) and the same rotation
+        keys as Alg. 1."""
+        ev, M = self.ev, self.lay.M
+        P = replicate_period(m, M)
+        u = self.ladder(v, [P << i for i in range(int(math.log2(M // P)))])
+        reps = []
+        for c in range(m):
+            mask = np.zeros(M)
+            mask[c::P] = 1.0
+            t = ev.mul_mask(u, mask)
+            reps.append(self.ladder(t, [1 << i for i in range(int(math.log2(P)))]))
+        return reps
+
     def cp_matvec(self, cols, v: Ct, m: int) -> Ct:
-        """Alg. 2: sum_c A(c) * Replicate(v)(c)."""
-        reps = [self.replicate(v, c) for c in range(m)]
+        """Alg. 2: sum_c A(c) * Replicate(v)(c), the m replicates of v (zero
+        beyond its m entries in every use here) from one shared ladder."""
+        reps = self.replicate_all(v, m)
         lv = reps[0].level
         return self.mac_relin_rescale([(self.ev.drop(cols[c], lv), reps[c]) for c in range(m)])
 

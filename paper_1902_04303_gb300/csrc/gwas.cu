@@ -26,7 +26,9 @@ constexpr u64 kEncX = 0x100, kEncA = 0x200, kEncY = 0x300, kEncBeta0 = 0x301, kE
               kEncSccp = 0x100000000ull;
 
 // mask kinds for the plaintext cache
-enum MaskKind { kMaskSlot = 1, kMaskPrefix = 2, kMaskBlock = 3, kMaskEye = 4, kMaskHeads = 5 };
+enum MaskKind {
+  kMaskSlot = 1, kMaskPrefix = 2, kMaskBlock = 3, kMaskEye = 4, kMaskHeads = 5, kMaskResidue = 6
+};
 
 // batches of the factored layout processed together (bounds the temporaries:
 // d products per batch at kFactLevel limbs)
@@ -117,29 +119,49 @@ struct Eval {
     return out;
   }
 
-  // Alg. 1 for several (source, entry) pairs at once: mask the entry's slot
-  // (plaintext at scale q_last, rescale), then a log2(M) rotate-and-add ladder.
-  CtSetPtr replicate_set(const std::vector<std::pair<const Ct*, int>>& items) {
-    const Ct& v0 = *items[0].first;
+  // Period of the shared replicate ladder for m entries: the smallest power
+  // of 2^kLadderGroup >= m (at most M), so that its two step lists split
+  // Alg. 1's ladder at a hoisting-group boundary and use Alg. 1's keys.
+  int replicate_period(int m) const {
+    int P = 1 << kLadderGroup;
+    while (P < m) P <<= kLadderGroup;
+    return std::min(P, lay.M);
+  }
+  // Alg. 1 for entries 0..m-1 of every source, each source zero beyond its m
+  // entries: Alg. 1's ladder sums the rotations of the masked slot by
+  // 0..M-1; here the steps P, 2P, ..., M/2 run once per source on the source
+  // itself (slot s then holds v_{s mod P}), a mask keeps the slots = c mod P
+  // (plaintext at scale q_last, rescale), and the steps 1, ..., P/2 fill the
+  // rest.  Same sum, same depth, same keys; item r * m + c of the result is
+  // entry c of source r.
+  CtSetPtr replicate_all(const std::vector<const Ct*>& srcs, int m) {
+    const Ct& v0 = *srcs[0];
     const int l = v0.l;
-    const double ql = (double)c->mod[l - 1];
-    std::vector<MaskItem> mi;
-    for (auto& it : items) {
-      GWHE_REQUIRE(it.first->l == l && it.first->scale == v0.scale, ST_ELEVEL,
+    for (const Ct* v : srcs)
+      GWHE_REQUIRE(v->l == l && v->scale == v0.scale, ST_ELEVEL,
                    "replicated sources must share level and scale");
-      mi.push_back(MaskItem{it.first->d, it.first->cap,
-                            mask_pt(c, kMaskSlot, it.second, l, ql, e_slot(it.second))});
+    const int P = replicate_period(m);
+    CtSetPtr u = gather(srcs, l);
+    if (P < lay.M) set_ladder(c, *u, pow2_steps(ilog2(lay.M / P), P));
+    const double ql = (double)c->mod[l - 1];
+    std::vector<const u64*> pts;
+    for (int cidx = 0; cidx < m; ++cidx) {
+      auto z = slots_zero();
+      for (int s = cidx; s < lay.M; s += P) z[s] = make_double2(1, 0);
+      pts.push_back(mask_pt(c, kMaskResidue, ((long)P << 20) | cidx, l, ql, z));
     }
-    CtSetPtr set = set_new(c, (int)items.size(), 2, l, l, 1.0);
-    set_mask(c, mi, v0.scale, ql, *set, true);
-    set_ladder(c, *set, pow2_steps(lay.logN - 1));
+    std::vector<MaskItem> mi;
+    for (size_t r = 0; r < srcs.size(); ++r)
+      for (int cidx = 0; cidx < m; ++cidx) mi.push_back(MaskItem{u->item((int)r), u->cap, pts[cidx]});
+    CtSetPtr set = set_new(c, (int)mi.size(), 2, l, l, 1.0);
+    set_mask(c, mi, u->scale, ql, *set, true);
+    if (P > 1) set_ladder(c, *set, pow2_steps(ilog2(P)));
     return set;
   }
-  // Alg. 2: sum_c A(c) * Replicate(v)(c)
+  // Alg. 2: sum_c A(c) * Replicate(v)(c), v zero beyond its m entries (as
+  // every vector the circuit multiplies this way is)
   CtPtr cp_matvec(const std::vector<CtPtr>& cols, const Ct& v, int m) {
-    std::vector<std::pair<const Ct*, int>> items;
-    for (int cidx = 0; cidx < m; ++cidx) items.push_back({&v, cidx});
-    CtSetPtr reps = replicate_set(items);
+    CtSetPtr reps = replicate_all({&v}, m);
     const int lv = reps->l;
     std::vector<CtPtr> views, rv;
     std::vector<std::pair<const Ct*, const Ct*>> pairs;
@@ -154,10 +176,9 @@ struct Eval {
   // replicates and the d tensor sums run as sets.
   CtSetPtr cp_matmul(const std::vector<CtPtr>& X, const std::vector<CtPtr>& Acols, int m) {
     const int d = (int)Acols.size();
-    std::vector<std::pair<const Ct*, int>> items;
-    for (int r = 0; r < d; ++r)
-      for (int cidx = 0; cidx < m; ++cidx) items.push_back({Acols[r].get(), cidx});
-    CtSetPtr reps = replicate_set(items);
+    std::vector<const Ct*> srcs;
+    for (int r = 0; r < d; ++r) srcs.push_back(Acols[r].get());
+    CtSetPtr reps = replicate_all(srcs, m);
     const int lv = reps->l;
     std::vector<CtPtr> views, rv;
     for (int cidx = 0; cidx < m; ++cidx) views.push_back(view(*X[cidx], lv));

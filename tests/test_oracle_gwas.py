@@ -259,3 +259,43 @@ def test_encrypted_factored_circuit_matches_o2():
     dl = np.abs(gwas_fp64.neglog10p(b, 1 / den[ok]) - gwas_fp64.neglog10p(ref["b"][ok],
                                                                           ref["err"][ok]))
     assert np.max(dl) < 0.05
+
+
+@pytest.mark.parametrize("m", [1, 3, 5, 8, 9])
+def test_shared_replicate_equals_alg1(m):
+    """Replicate (Alg. 1) of entries 0..m-1 through one shared ladder: every
+    slot of result c decrypts to v_c (Alg. 1's definition), as Alg. 1's own
+    mask-then-ladder gives, at the same level, with fewer hoisted switches:
+    ceil(log2(M/P)/3) + m ceil(log2(P)/3) against m ceil(log2(M)/3).  A vector
+    that is not zero beyond its entries breaks it (the precondition)."""
+    from oracle.circuit import replicate_period
+    logN = 10
+    o = OracleCKKS(logN=logN, L=4, K=2, dnum=2, seed=21)
+    M = 1 << (logN - 1)
+    lay = Layout(logN, 16, m, 32)
+    o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay)])
+    c = Circuit(o, lay)
+    rng = np.random.default_rng(m)
+    v = rng.uniform(-1, 1, m)
+    ct = c.encrypt_vector(v, 0x77)
+    hist = _count_switches(o)
+    reps = c.replicate_all(ct, m)
+    shared = int(hist.sum())
+    P = replicate_period(m, M)
+    assert P >= m and P & (P - 1) == 0 and math.log2(P) % 3 == 0
+    assert shared == math.ceil(math.log2(M // P) / 3) + m * math.ceil(math.log2(P) / 3)
+    hist[:] = 0
+    alg1 = [c.replicate(ct, j) for j in range(m)]
+    assert int(hist.sum()) == m * math.ceil((logN - 1) / 3)
+    for j in range(m):
+        assert reps[j].level == alg1[j].level == ct.level - 1
+        got = o.decrypt_decode(reps[j])
+        ref = o.decrypt_decode(alg1[j])
+        assert np.max(np.abs(got - v[j])) < 1e-5
+        assert np.max(np.abs(got - ref)) < 1e-5
+    # planted violation: a nonzero slot beyond the entries lands in its class
+    bad = np.zeros(P + 1)
+    bad[:m] = v
+    bad[P] = 0.5
+    reps_bad = c.replicate_all(c.encrypt_vector(bad, 0x78), m)
+    assert np.max(np.abs(o.decrypt_decode(reps_bad[0]) - (v[0] + 0.5))) < 1e-5
