@@ -126,48 +126,65 @@ struct ConvArgs {
 
 // y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o.
 // Grid: x = coefficients, y = groups of kConvOG outputs, z = items (polynomials).
+// NI (the number of input limbs) is a template parameter, so the products and
+// their 128-bit sums unroll completely; the CTA's slice of the hmod table
+// (NI x kConvOG words, zero beyond the last output) is staged in shared
+// memory and read as warp-uniform broadcasts.
 constexpr int kConvOG = 8;
-__global__ void k_baseconv(const u64* __restrict__ x, size_t x_pstride, u64* __restrict__ out,
-                           size_t out_pstride, const ConvArgs a, int N,
-                           const DevMod* __restrict__ mod) {
+template <int NI, int T>
+__device__ __forceinline__ void conv_outputs(const u64 (&y)[NI], const u64* hs,
+                                             int o, const ConvArgs& a, int o0, u64* op,
+                                             int N, int k, const DevMod* __restrict__ mod) {
+  Acc128 s[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) s[t] = Acc128{0, 0};
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+#pragma unroll
+    for (int t = 0; t < T; ++t) mac128(s[t], y[i], hs[i * kConvOG + o + t]);
+  }
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int oo = o0 + o + t;
+    const DevMod& om = mod[a.out_pidx[oo]];
+    u64 v = reduce128(s[t].lo, s[t].hi, om);
+    if (a.out_add) v = addmod(v, a.out_add[oo], om.q);
+    op[(size_t)a.out_row[oo] * N + k] = v;
+  }
+}
+
+template <int NI>
+__global__ void __launch_bounds__(256) k_baseconv(const u64* __restrict__ x, size_t x_pstride,
+                                                  u64* __restrict__ out, size_t out_pstride,
+                                                  const ConvArgs a, int N,
+                                                  const DevMod* __restrict__ mod) {
+  __shared__ u64 hs[NI * kConvOG];
+  const int o0 = blockIdx.y * kConvOG;
+  const int no = min(kConvOG, a.n_out - o0);
+  for (int e = threadIdx.x; e < NI * kConvOG; e += blockDim.x) {
+    const int i = e / kConvOG, o = e - i * kConvOG;
+    hs[e] = o < no ? a.tab[2 * NI + i * a.hm_stride + o0 + o] : 0;
+  }
+  __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
-  const int o0 = blockIdx.y * kConvOG;
   const size_t p = blockIdx.z;
   const u64* xp = x + p * x_pstride;
   u64* op = out + p * out_pstride;
-  u64 y[kMaxConvIn];
+  u64 y[NI];
 #pragma unroll
-  for (int i = 0; i < kMaxConvIn; ++i) {
-    if (i < a.n_in) {
-      const u64 q = mod[a.in_pidx[i]].q;
-      y[i] = shoup(xp[(size_t)i * N + k], a.tab[i], a.tab[a.n_in + i], q);
-      if (a.in_add) y[i] = addmod(y[i], a.in_add[i], q);
-    }
+  for (int i = 0; i < NI; ++i) {
+    const u64 q = mod[a.in_pidx[i]].q;
+    y[i] = shoup(xp[(size_t)i * N + k], a.tab[i], a.tab[NI + i], q);
+    if (a.in_add) y[i] = addmod(y[i], a.in_add[i], q);
   }
-  const u64* hm = a.tab + 2 * a.n_in;
-  const int o1 = min(o0 + kConvOG, a.n_out);
-  // four outputs at a time: independent accumulation chains
-  for (int o = o0; o < o1; o += 4) {
-    Acc128 s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-#pragma unroll
-    for (int i = 0; i < kMaxConvIn; ++i) {
-      if (i < a.n_in) {
-        const u64* h = hm + i * a.hm_stride + o;
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (o + t < o1) mac128(s[t], y[i], __ldg(h + t));
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (o + t < o1)
-      {
-        const DevMod& om = mod[a.out_pidx[o + t]];
-        u64 v = reduce128(s[t].lo, s[t].hi, om);
-        if (a.out_add) v = addmod(v, a.out_add[o + t], om.q);
-        op[(size_t)a.out_row[o + t] * N + k] = v;
-      }
+  int o = 0;
+  for (; o + 4 <= no; o += 4) conv_outputs<NI, 4>(y, hs, o, a, o0, op, N, k, mod);
+  switch (no - o) {
+    case 3: conv_outputs<NI, 3>(y, hs, o, a, o0, op, N, k, mod); break;
+    case 2: conv_outputs<NI, 2>(y, hs, o, a, o0, op, N, k, mod); break;
+    case 1: conv_outputs<NI, 1>(y, hs, o, a, o0, op, N, k, mod); break;
+    default: break;
   }
 }
 
@@ -1150,7 +1167,18 @@ static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_
                             const ConvArgs& a) {
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "conversion batch too large");
   const dim3 grid(blocks_for(c->N), (a.n_out + kConvOG - 1) / kConvOG, cnt);
-  k_baseconv<<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, c->d_mod);
+#define GWHE_CONV_CASE(n)                                                                  \
+  case n:                                                                                  \
+    k_baseconv<n><<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, c->d_mod); \
+    break;
+  switch (a.n_in) {
+    GWHE_CONV_CASE(1) GWHE_CONV_CASE(2) GWHE_CONV_CASE(3) GWHE_CONV_CASE(4)
+    GWHE_CONV_CASE(5) GWHE_CONV_CASE(6) GWHE_CONV_CASE(7) GWHE_CONV_CASE(8)
+    GWHE_CONV_CASE(9) GWHE_CONV_CASE(10) GWHE_CONV_CASE(11) GWHE_CONV_CASE(12)
+    GWHE_CONV_CASE(13) GWHE_CONV_CASE(14) GWHE_CONV_CASE(15) GWHE_CONV_CASE(16)
+    default: GWHE_REQUIRE(false, ST_EINVAL, "conversion input count out of range");
+  }
+#undef GWHE_CONV_CASE
   GWHE_LAUNCHED(c, 1);
 }
 
