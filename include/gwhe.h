@@ -266,7 +266,13 @@ int gwhe_fit_covariates(gwhe_job* job, int kappa);
  * row-major), w and w*z' (n) in plaintext; they are duplicated and encrypted. */
 int gwhe_set_fit_state(gwhe_job* job, const double* M, const double* w, const double* wz);
 /* Alg. 11 loop for batches [b0, b1): S is n x k row-major genotypes (host or
- * device).  keep != 0 keeps each batch's output ciphertexts for export. */
+ * device; the caller keeps ownership).  Batches run in sets of 64.  A host S
+ * is never copied whole to the device (the host tier, the counterpart of the
+ * paper's cache module, section "Smart Cache Module"): each set's columns are
+ * gathered into one of two pinned staging buffers by the calling thread and
+ * copied on a second stream while the previous set computes; device memory
+ * used for S is 2 n min(k, 64 tau) doubles.  The results do not depend on
+ * where S lives.  keep != 0 keeps each batch's output ciphertexts for export. */
 int gwhe_snp_stats(gwhe_job* job, const double* S, long b0, long b1, int keep);
 /* Decrypt + decode the kept batch outputs: num[k], den[k] (host); b' = num/den,
  * err' = 1/den (eqs. estSNPeffect, estSNPerror). */
@@ -286,12 +292,23 @@ long gwhe_job_keyswitches(const gwhe_job* job);
  * gwhe_encrypt_inputs; jobs that may both be live under one key need
  * different nonces. */
 int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce);
+/* Host tier for the M-CCP layout's n Dup(M_j) ciphertexts (the matrix the
+ * paper's cache module keeps on disk, section "Smart Cache Module"): with
+ * chunk > 0 they are moved to pinned host memory once computed (call before
+ * gwhe_fit_covariates / gwhe_set_fit_state), and every set of 64 SNP batches
+ * prefetches them back chunk columns at a time into two device slots on a
+ * copy stream, each chunk serving all batches of the set.  Device memory for
+ * Dup(M_j) drops from n to 2 chunk ciphertexts; results are unchanged (the
+ * tensor sums are exact).  chunk = 0 keeps them on the device (default).
+ * GWHE_EINVAL for chunk < 0, or to turn the tier off once it holds them. */
+int gwhe_job_set_host_state(gwhe_job* job, int chunk);
 /* Drop the kept batch outputs (after gwhe_decrypt_results), so that a long
  * job can evaluate and decrypt its SNP batches chunk by chunk. */
 int gwhe_job_release_results(gwhe_job* job);
-/* Estimated device bytes of one job beyond the shared keys (device copy of S,
- * encrypted inputs, the covariate phase's temporaries, one chunk of
- * chunk_batches SNP batches and its outputs); -1 on bad arguments. */
+/* Estimated device bytes of one job beyond the shared keys (the two staging
+ * buffers of host genotypes, encrypted inputs, the covariate phase's
+ * temporaries, one chunk of chunk_batches SNP batches and its outputs); -1 on
+ * bad arguments. */
 long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, int chunk_batches);
 
 /* ------------------------------------------------------------ serving
@@ -306,13 +323,17 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
  * dropping each chunk.  Do not use ctx for other work while the server runs;
  * destroy the server before ctx.
  *   submit: copies the host inputs (X n x d row-major, (X^T X)^-1 d x d, y n,
- *           S n x k row-major); ENOMEM if the footprint exceeds the budget.
+ *           S n x k row-major; S stays in host memory and is staged per set
+ *           of batches, see gwhe_snp_stats).  An M-CCP job whose footprint
+ *           exceeds the budget with Dup(M_j) on the device runs with it in
+ *           the host tier (gwhe_job_set_host_state, min(32, n/4) columns per
+ *           chunk) if that fits; ENOMEM if neither fits.
  *   wait:   blocks until the job is done; num[k], den[k] as
  *           gwhe_decrypt_results; times_ms (optional) = {waiting for
  *           admission, running, total}; the job's status is returned and the
  *           job is forgotten.
  *   stats:  {admitted, running, waiting, bytes claimed, peak bytes claimed,
- *           budget}.
+ *           budget, jobs run with Dup(M_j) in the host tier}.
  *   destroy: running jobs finish, waiting ones end with GWHE_EINVAL. */
 typedef struct gwhe_server gwhe_server;
 int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
@@ -321,7 +342,7 @@ int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kap
                        const double* X, const double* XtX_inv, const double* y, const double* S,
                        long* id);
 int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms);
-int gwhe_server_stats(gwhe_server* s, long out[6]);
+int gwhe_server_stats(gwhe_server* s, long out[7]);
 int gwhe_server_destroy(gwhe_server* s);
 
 /* Child context on another stream (void* = cudaStream_t) that shares ctx's

@@ -573,6 +573,11 @@ int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce) {
   return guard(C(job->owner), [&] { job_set_nonce(job->job.get(), nonce); });
 }
 
+int gwhe_job_set_host_state(gwhe_job* job, int chunk) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] { job_set_host_state(job->job.get(), chunk); });
+}
+
 int gwhe_job_release_results(gwhe_job* job) {
   if (!job) return GWHE_EINVAL;
   return guard(C(job->owner), [&] { job_release_results(job->job.get()); });

@@ -932,7 +932,7 @@ void set_mask(Context* c, const std::vector<MaskItem>& items, double src_scale, 
 }
 
 void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs,
-                    int npairs, CtSet& out3) {
+                    int npairs, CtSet& out3, bool accumulate) {
   GWHE_REQUIRE(out3.npoly == 3 && (int)pairs.size() == npairs * out3.cnt, ST_EINVAL,
                "tensor set shape");
   const int l = pairs[0].first->l;
@@ -945,9 +945,13 @@ void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*
     hp.push_back(MacPair{pr.first->d, pr.second->d, pr.first->cap, pr.second->cap});
   }
   GWHE_REQUIRE(out3.cap >= l, ST_EINVAL, "tensor output too small");
+  if (accumulate) {
+    GWHE_REQUIRE(out3.l == l, ST_ELEVEL, "accumulated tensor at another level");
+    check_scales(out3.scale, sc);
+  }
   Tmp d(c, sizeof(MacPair) * hp.size());
   tensor_mac_set(c, PolyView{out3.d, out3.cap}, out3.stride(), upload_async(c, d, hp), npairs,
-                 out3.cnt, l);
+                 out3.cnt, l, accumulate);
   out3.l = l;
   out3.scale = sc;
 }
@@ -1101,7 +1105,7 @@ void ct_export(Context* c, const Ct& ct, u64* host_coeff) {
   Tmp t(c, sizeof(u64) * ct.npoly * ct.l * N);
   for (int p = 0; p < ct.npoly; ++p)
     GWHE_CUDA(cudaMemcpyAsync(t.u() + (size_t)p * ct.l * N, ct.poly(p), sizeof(u64) * ct.l * N,
-                              cudaMemcpyDeviceToDevice, c->stream));
+                              cudaMemcpyDefault, c->stream));  // device or host tier
   ntt_inverse(c, t.u(), rows_q(ct.npoly, ct.l, ct.l));
   GWHE_CUDA(cudaMemcpyAsync(host_coeff, t.p, sizeof(u64) * ct.npoly * ct.l * N,
                             cudaMemcpyDeviceToHost, c->stream));

@@ -120,9 +120,10 @@ void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out);
 // out[i] = items[i].src * items[i].pt, scale = src scale * pt_scale (then rescale)
 void set_mask(Context* c, const std::vector<MaskItem>& items, double src_scale, double pt_scale,
               CtSet& out, bool rescale);
-// out3[i] = sum_j tensor(pairs[i npairs + j]) (out3 has npoly = 3)
+// out3[i] = sum_j tensor(pairs[i npairs + j]) (out3 has npoly = 3); with
+// accumulate, out3[i] += that sum (out3 already at the pairs' level and scale)
 void set_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>>& pairs,
-                    int npairs, CtSet& out3);
+                    int npairs, CtSet& out3, bool accumulate = false);
 void set_relin(Context* c, const CtSet& t3, CtSet& out);
 // relinearisation fused with the rescale that follows it: out = the tensor
 // divided once by P q_{l-1} (level l - 1, scale / q_{l-1})

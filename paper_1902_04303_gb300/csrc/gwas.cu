@@ -14,6 +14,8 @@
 // rounds).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <memory>
 
 #include "gwas.cuh"
 
@@ -32,7 +34,8 @@ enum MaskKind {
 
 // batches of the factored layout processed together (bounds the temporaries:
 // d products per batch at kFactLevel limbs)
-constexpr int kFactChunk = 64;
+// SNP batches evaluated as one set (and, for host genotypes, staged at once)
+constexpr long kSnpChunk = 64;
 
 // eq. sigma7 coefficients of x^1, x^3, x^5, x^7 (the printed c_k / 8^k)
 const double kSig[4] = {-1.73496 / 8.0, 4.19407 / 512.0, -5.43402 / 32768.0,
@@ -318,7 +321,57 @@ Layout make_layout(int logN, int n, int d, long k) {
 }
 
 Job::~Job() {
-  if (DupM_store && c) dfree(c, DupM_store);
+  DupM.clear();
+  if (DupM_host && c) {
+    // kernels of this job may still read it
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(DupM_host);
+  }
+}
+
+// Move Dup(M_j) to one pinned host block (the host tier) and point the job's
+// Dup(M_j) handles at it; the device copies are dropped by the caller.
+static void spill_dupm(Job* j) {
+  Context* c = j->c;
+  const int n = (int)j->DupM.size();
+  const int l = j->DupM[0]->l;
+  const size_t per = (size_t)2 * l * c->N;
+  GWHE_CUDA(cudaHostAlloc((void**)&j->DupM_host, sizeof(u64) * per * n, cudaHostAllocDefault));
+  for (int jj = 0; jj < n; ++jj) {
+    const Ct& src = *j->DupM[jj];
+    GWHE_REQUIRE(src.l == l, ST_ELEVEL, "Dup(M_j) at different levels");
+    for (int p = 0; p < 2; ++p)
+      GWHE_CUDA(cudaMemcpyAsync(j->DupM_host + jj * per + (size_t)p * l * c->N, src.poly(p),
+                                sizeof(u64) * l * c->N, cudaMemcpyDeviceToHost, c->stream));
+  }
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<CtPtr> hv;
+  for (int jj = 0; jj < n; ++jj) {
+    CtPtr v(new Ct());
+    v->ctx = c;
+    v->d = j->DupM_host + jj * per;
+    v->cap = v->l = l;
+    v->scale = j->DupM[jj]->scale;
+    v->owned = false;
+    hv.push_back(std::move(v));
+  }
+  j->DupM = std::move(hv);
+}
+
+// forget Dup(M_j), wherever it lives
+static void drop_dupm(Job* j) {
+  j->DupM.clear();
+  if (j->DupM_host) {
+    GWHE_CUDA(cudaStreamSynchronize(j->c->stream));
+    cudaFreeHost(j->DupM_host);
+    j->DupM_host = nullptr;
+  }
+}
+
+void job_set_host_state(Job* j, int chunk) {
+  GWHE_REQUIRE(chunk >= 0, ST_EINVAL, "negative chunk");
+  GWHE_REQUIRE(!j->DupM_host || chunk > 0, ST_EINVAL, "Dup(M_j) already in host memory");
+  j->dupm_chunk = chunk;
 }
 
 Job* job_create(Context* c, int n, int d, long k, int mode) {
@@ -437,7 +490,7 @@ static void make_dup_state(Job* j, Eval& ev) {
   const Layout& lay = j->lay;
   const int lb = kBatchLevel;
   GWHE_REQUIRE(j->wzp->l >= lb - 1, ST_ELEVEL, "depth exhausted before the SNP batches");
-  j->DupM.clear();
+  drop_dupm(j);
   if (!j->factored) {
   // Dup(M_j) for every column j: mask block (j mod B) of ciphertext j / B at
   // lb + 1 limbs (plaintext at scale q_last, rescale), then Alg. 7's ladder
@@ -456,7 +509,10 @@ static void make_dup_state(Job* j, Eval& ev) {
   set_mask(c, mi, src[0]->scale, ql, *dm, true);
   set_ladder(c, *dm, ev.dup_steps());
   for (int jj = 0; jj < lay.n; ++jj) j->DupM.push_back(dm->view(jj));
-  j->sets.push_back(std::move(dm));
+  if (j->dupm_chunk > 0)
+    spill_dupm(j);  // dm (the device copy) is freed at scope exit
+  else
+    j->sets.push_back(std::move(dm));
   }
   CtSetPtr dw = ev.single(*j->w_m, lb - 1);
   set_ladder(c, *dw, ev.dup_steps());
@@ -602,9 +658,10 @@ void job_set_fit_state(Job* j, const double* Mp, const double* wp, const double*
       for (int t = 0; t < n; ++t) z[b * lay.nb + t] = make_double2(v[(size_t)t * stride + off], 0);
     return z;
   };
-  j->DupM.clear();
+  drop_dupm(j);
   for (int jj = 0; jj < n; ++jj)
     j->DupM.push_back(ev.encrypt_vec(dup(M, n, jj), j->enc_base + kEncDupM + jj, lb, delta));
+  if (j->dupm_chunk > 0) spill_dupm(j);
   j->DupW = ev.encrypt_vec(dup(w, 1, 0), j->enc_base + kEncDupW, lb - 1, delta);
   j->DupWZ = ev.encrypt_vec(dup(wz, 1, 0), j->enc_base + kEncDupWZ, lb - 1, delta);
 }
@@ -675,37 +732,166 @@ void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
   j->sets.push_back(std::move(D));
 }
 
+// Host-to-device copies into two device slots on a copy stream, for
+// prefetching the next chunk while the compute stream works on the current
+// one.  copy(s, ...) queues the copy once the compute stream has released
+// slot s (release(s) after the work that reads it) and makes the compute
+// stream wait for the copy; wait_copied(s) blocks the host until the slot's
+// last copy has left its source.  Waits are on CUDA events, which complete or
+// fail.
+struct TwoSlotCopy {
+  Context* c;
+  size_t cap;
+  std::unique_ptr<Tmp> dev[2];
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  TwoSlotCopy(Context* c_, size_t cap_bytes) : c(c_), cap(cap_bytes) {
+    try {
+      GWHE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      for (int s = 0; s < 2; ++s) {
+        dev[s].reset(new Tmp(c, cap));
+        GWHE_CUDA(cudaEventCreateWithFlags(&copied[s], cudaEventDisableTiming));
+        GWHE_CUDA(cudaEventCreateWithFlags(&freed[s], cudaEventDisableTiming));
+      }
+      // the slots come from the compute stream's pool
+      GWHE_CUDA(cudaEventRecord(freed[0], c->stream));
+      GWHE_CUDA(cudaStreamWaitEvent(cs, freed[0], 0));
+    } catch (...) {
+      destroy();
+      throw;
+    }
+  }
+  void wait_copied(int s) {
+    if (used[s]) GWHE_CUDA(cudaEventSynchronize(copied[s]));
+  }
+  void* copy(int s, const void* src, size_t bytes) {
+    GWHE_REQUIRE(bytes >= 1 && bytes <= cap, ST_EINVAL, "staged chunk too large");
+    if (used[s]) GWHE_CUDA(cudaStreamWaitEvent(cs, freed[s], 0));
+    GWHE_CUDA(cudaMemcpyAsync(dev[s]->p, src, bytes, cudaMemcpyHostToDevice, cs));
+    GWHE_CUDA(cudaEventRecord(copied[s], cs));
+    GWHE_CUDA(cudaStreamWaitEvent(c->stream, copied[s], 0));
+    used[s] = true;
+    return dev[s]->p;
+  }
+  void release(int s) { GWHE_CUDA(cudaEventRecord(freed[s], c->stream)); }
+  void destroy() {
+    if (cs) cudaStreamSynchronize(cs);
+    for (int s = 0; s < 2; ++s) {
+      if (copied[s]) cudaEventDestroy(copied[s]);
+      if (freed[s]) cudaEventDestroy(freed[s]);
+      copied[s] = freed[s] = nullptr;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+  }
+  ~TwoSlotCopy() {
+    // the slots go back to the compute stream's pool after everything queued
+    cudaStreamSynchronize(c->stream);
+    destroy();
+  }
+};
+
+// Genotype column ranges from host memory: stage() gathers the n row
+// segments [col0, col0 + w) into the slot's pinned buffer (after the slot's
+// previous copy has left it) and copies them to the device.
+struct HostStager {
+  int n;
+  long wmax;
+  double* pin[2] = {nullptr, nullptr};
+  TwoSlotCopy cp;
+  HostStager(Context* c, int n_, long wmax_)
+      : n(n_), wmax(wmax_), cp(c, sizeof(double) * (size_t)n_ * wmax_) {
+    for (int s = 0; s < 2; ++s)
+      if (cudaHostAlloc((void**)&pin[s], sizeof(double) * (size_t)n * wmax, cudaHostAllocDefault) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        free_pinned();
+        throw Error(ST_ENOMEM, "pinned staging allocation failed");
+      }
+  }
+  const double* stage(int s, const double* S, long k, long col0, long w) {
+    GWHE_REQUIRE(w >= 1 && w <= wmax, ST_EINVAL, "staged column range too wide");
+    cp.wait_copied(s);
+    for (int t = 0; t < n; ++t)
+      std::memcpy(pin[s] + (size_t)t * w, S + (size_t)t * k + col0, sizeof(double) * w);
+    return (const double*)cp.copy(s, pin[s], sizeof(double) * (size_t)n * w);
+  }
+  void release(int s) { cp.release(s); }
+  void free_pinned() {
+    for (int s = 0; s < 2; ++s)
+      if (pin[s]) cudaFreeHost(pin[s]);
+    pin[0] = pin[1] = nullptr;
+  }
+  ~HostStager() {
+    cp.wait_copied(0);
+    cp.wait_copied(1);
+    free_pinned();
+  }
+};
+
+// genotype columns col0.. of every sample on the device, row pitch ld
+struct SnpSrc {
+  const double* S;
+  long ld, col0;
+};
+
 // M-CCP layout: per batch encode + encrypt the n REP rows, then the tensor
 // sum of Alg. 8 (S' = sum_j Dup(M_j) S_ij), relinearise and rescale
-CtSetPtr sprime_mccp(Job* j, const double* Sd, long b0, long b1) {
+CtSetPtr sprime_mccp(Job* j, const SnpSrc& src, long b0, long b1) {
   Context* c = j->c;
   const Layout& lay = j->lay;
   const int n = lay.n, lb = kBatchLevel, N = c->N;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const int nbt = (int)(b1 - b0);
   CtSetPtr T3 = set_new(c, nbt, 3, lb, lb, 1.0);
-  {
-    Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
-    Tmp sct(c, sizeof(u64) * (size_t)n * 2 * lb * N);
-    std::vector<Ct> srow(n);
-    for (int jj = 0; jj < n; ++jj) {
-      srow[jj].ctx = c;
-      srow[jj].d = sct.u() + (size_t)jj * 2 * lb * N;
-      srow[jj].cap = lb;
-      srow[jj].l = lb;
-      srow[jj].scale = delta;
-      srow[jj].owned = false;
-    }
+  // Dup(M_j) for columns [j0, j0 + J) at a time: on the device, one chunk of
+  // all n; in the host tier, chunks prefetched into two device slots, each
+  // used by every batch of the set (the partial tensor sums accumulate)
+  const bool host = j->DupM_host != nullptr;
+  const int J = host ? std::min(n, j->dupm_chunk) : n;
+  const size_t per = (size_t)2 * lb * N;
+  std::unique_ptr<TwoSlotCopy> cp;
+  if (host) {
+    GWHE_REQUIRE(j->DupM[0]->l == lb, ST_ELEVEL, "Dup(M_j) not at the batch level");
+    cp.reset(new TwoSlotCopy(c, sizeof(u64) * per * J));
+  }
+  Tmp z(c, sizeof(double2) * (size_t)J * lay.M);
+  Tmp sct(c, sizeof(u64) * (size_t)J * per);
+  std::vector<Ct> srow(J), dm(J);
+  for (int jj = 0; jj < J; ++jj) {
+    srow[jj].ctx = dm[jj].ctx = c;
+    srow[jj].d = sct.u() + (size_t)jj * per;
+    srow[jj].cap = srow[jj].l = dm[jj].cap = dm[jj].l = lb;
+    srow[jj].scale = delta;
+    srow[jj].owned = dm[jj].owned = false;
+  }
+  for (int j0 = 0, ci = 0; j0 < n; j0 += J, ++ci) {
+    const int jn = std::min(J, n - j0);
     std::vector<std::pair<const Ct*, const Ct*>> pairs;
-    for (int jj = 0; jj < n; ++jj) pairs.push_back({j->DupM[jj].get(), &srow[jj]});
+    if (host) {
+      const u64* dd = (const u64*)cp->copy(ci & 1, j->DupM_host + (size_t)j0 * per,
+                                           sizeof(u64) * per * jn);
+      for (int jj = 0; jj < jn; ++jj) {
+        dm[jj].d = (u64*)dd + (size_t)jj * per;
+        dm[jj].scale = j->DupM[j0 + jj]->scale;
+        pairs.push_back({&dm[jj], &srow[jj]});
+      }
+    } else {
+      for (int jj = 0; jj < jn; ++jj) pairs.push_back({j->DupM[j0 + jj].get(), &srow[jj]});
+    }
     for (long bi = b0; bi < b1; ++bi) {
-      build_snp_rep(c, Sd, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
-      encrypt_slots(c, z.as<double2>(), n, delta, lb, j->enc_base + kEncS + (u64)bi * n, sct.u(),
-                    lb);
+      // REP rows j0 .. j0 + jn of batch bi (encryption ids per sample row)
+      build_snp_rep(c, src.S + (size_t)j0 * src.ld, src.ld, src.col0, jn, lay.k, bi * lay.tau,
+                    lay.nb, lay.B, lay.M, z.as<double2>());
+      encrypt_slots(c, z.as<double2>(), jn, delta, lb,
+                    j->enc_base + kEncS + (u64)bi * n + (u64)j0, sct.u(), lb);
       CtSet t = T3->slice((int)(bi - b0), 1, lb);
-      set_tensor_mac(c, pairs, n, t);
+      if (j0 > 0) t.scale = T3->scale;
+      set_tensor_mac(c, pairs, jn, t, j0 > 0);
       T3->scale = t.scale;
     }
+    if (host) cp->release(ci & 1);
   }
   CtSetPtr Sp = set_new(c, nbt, 2, lb, lb, 1.0);
   set_relin_rescale(c, *T3, *Sp);  // S' at lb - 1
@@ -717,7 +903,7 @@ CtSetPtr sprime_mccp(Job* j, const double* Sd, long b0, long b1) {
 //   U_ic = Dup(X_c) S_i; colSum (Alg. 5) puts (X^T S_i)[c, .] at the block heads
 //   R_ic = U_ic masked to the heads, broadcast down the block (right ladder)
 //   S'_i = S_i - sum_c Dup((XA)_c) R_ic   (tensor sum, relinearise, rescale)
-CtSetPtr sprime_factored(Job* j, Eval& ev, const double* Sd, long b0, long b1) {
+CtSetPtr sprime_factored(Job* j, Eval& ev, const SnpSrc& src, long b0, long b1) {
   Context* c = j->c;
   const Layout& lay = j->lay;
   const int d = lay.d, lf = kFactLevel, lb = kBatchLevel;
@@ -726,8 +912,8 @@ CtSetPtr sprime_factored(Job* j, Eval& ev, const double* Sd, long b0, long b1) {
   CtSetPtr Sset = set_new(c, nbt, 2, lf, lf, delta);
   {
     Tmp z(c, sizeof(double2) * (size_t)nbt * lay.M);
-    build_snp_ccp(c, Sd, lay.n, lay.k, b0 * lay.tau, nbt, lay.tau, lay.nb, lay.B, lay.M,
-                  z.as<double2>());
+    build_snp_ccp(c, src.S, src.ld, src.col0, lay.n, lay.k, b0 * lay.tau, nbt, lay.tau, lay.nb,
+                  lay.B, lay.M, z.as<double2>());
     encrypt_slots(c, z.as<double2>(), nbt, delta, lf, j->enc_base + kEncSccp + (u64)b0, Sset->d,
                   lf);
   }
@@ -794,23 +980,30 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
                  "covariate phase not done (fit or set the fit state first)");
   GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
   if (b0 == b1) return;
-  const bool dev = is_device_ptr(S);
-  const double* Sd = S;
-  std::unique_ptr<Tmp> Sbuf;
-  if (!dev) {
-    Sbuf.reset(new Tmp(c, sizeof(double) * (size_t)n * lay.k));
-    GWHE_CUDA(cudaMemcpyAsync(Sbuf->p, S, sizeof(double) * (size_t)n * lay.k,
-                              cudaMemcpyHostToDevice, c->stream));
-    Sd = Sbuf->as<double>();
-  }
   if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
-  if (!j->factored) {
-    batch_body(j, ev, sprime_mccp(j, Sd, b0, b1), b0);
+  auto run_chunk = [&](const SnpSrc& src, long c0, long c1) {
+    if (j->factored)
+      batch_body(j, ev, sprime_factored(j, ev, src, c0, c1), c0);
+    else
+      batch_body(j, ev, sprime_mccp(j, src, c0, c1), c0);
+  };
+  if (is_device_ptr(S)) {
+    for (long c0 = b0; c0 < b1; c0 += kSnpChunk)
+      run_chunk(SnpSrc{S, lay.k, 0}, c0, std::min(b1, c0 + kSnpChunk));
     return;
   }
-  for (long c0 = b0; c0 < b1; c0 += kFactChunk) {
-    const long c1 = std::min(b1, c0 + kFactChunk);
-    batch_body(j, ev, sprime_factored(j, ev, Sd, c0, c1), c0);
+  // Genotypes in host memory (the host tier): never copied whole.  Each chunk
+  // of batches takes its columns through one of two pinned staging buffers
+  // (filled by this thread while the device works on the previous chunk) and
+  // one of two device buffers (filled by a copy stream that overlaps the
+  // compute stream).
+  HostStager st(c, n, std::min<long>(lay.k, (long)kSnpChunk * lay.tau));
+  for (long c0 = b0, i = 0; c0 < b1; c0 += kSnpChunk, ++i) {
+    const long c1 = std::min(b1, c0 + kSnpChunk);
+    const long col0 = c0 * lay.tau, w = std::min(lay.k, c1 * lay.tau) - col0;
+    const double* dev = st.stage((int)(i & 1), S, lay.k, col0, w);
+    run_chunk(SnpSrc{dev, w, col0}, c0, c1);
+    st.release((int)(i & 1));
   }
 }
 

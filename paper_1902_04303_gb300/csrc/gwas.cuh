@@ -49,7 +49,10 @@ struct Job {
   u64 enc_base = 0;  // job nonce << 36, added to every encryption id
   std::vector<std::array<CtPtr, 3>> out;  // per batch: num, denEven, denOdd (views)
   std::vector<CtSetPtr> sets;             // storage behind the views above
-  u64* DupM_store = nullptr;              // unused (kept zero)
+  // host tier: Dup(M_j) held in pinned host memory (columns per prefetched
+  // chunk when dupm_chunk > 0; 0 keeps it on the device)
+  int dupm_chunk = 0;
+  u64* DupM_host = nullptr;
   ~Job();
 };
 
@@ -65,7 +68,10 @@ std::vector<int> job_rotation_steps(const Job* j);
 void job_encrypt_inputs(Job* j, const double* X, const double* A, const double* y);
 void job_fit(Job* j, int kappa);
 void job_set_fit_state(Job* j, const double* M, const double* w, const double* wz);
-void job_snp_stats(Job* j, const double* S_dev, long b0, long b1);
+void job_snp_stats(Job* j, const double* S, long b0, long b1);
+// keep Dup(M_j) (M-CCP layout) in pinned host memory, streamed back to the
+// device in chunks of `chunk` columns per set of SNP batches; 0 = device
+void job_set_host_state(Job* j, int chunk);
 void job_decrypt(Job* j, double* num, double* den);
 
 }  // namespace gwhe

@@ -530,8 +530,10 @@ __global__ void k_mask_set(const MaskItem* __restrict__ items, u64* __restrict__
 }
 
 // out[item] = sum over the item's npairs pairs of the tensor products
+// (accumulate: out[item] += that sum)
 __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair* __restrict__ pairs,
-                                 int npairs, int l, int N, const DevMod* __restrict__ mod) {
+                                 int npairs, int l, int N, int accumulate,
+                                 const DevMod* __restrict__ mod) {
   const int i = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -539,8 +541,14 @@ __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair*
   const size_t item = blockIdx.z;
   pairs += item * npairs;
   Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
-  u64 r0 = 0, r1 = 0, r2 = 0;
   const size_t off = (size_t)i * N + k;
+  u64* o = out.d + item * out_stride;
+  u64 r0 = 0, r1 = 0, r2 = 0;
+  if (accumulate) {
+    r0 = o[off];
+    r1 = o[(size_t)out.cap * N + off];
+    r2 = o[(size_t)2 * out.cap * N + off];
+  }
   for (int j = 0; j < npairs; ++j) {
     const MacPair P = pairs[j];
     const u64 a0 = P.a[off], a1 = P.a[(size_t)P.capa * N + off];
@@ -561,7 +569,6 @@ __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair*
   r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
   r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
   r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
-  u64* o = out.d + item * out_stride;
   o[off] = r0;
   o[(size_t)out.cap * N + off] = r1;
   o[(size_t)2 * out.cap * N + off] = r2;
@@ -1043,8 +1050,9 @@ __global__ void k_decode_gather(const double2* __restrict__ G, const int* __rest
   z[gid] = make_double2(g.x / scale, g.y / scale);
 }
 
-__global__ void k_build_snp_rep(const double* __restrict__ S, int n, long k, long k0, int nb,
-                                int B, int M, double2* __restrict__ z) {
+// S holds the genotype columns [col0, col0 + width) of every sample, row pitch ld
+__global__ void k_build_snp_rep(const double* __restrict__ S, long ld, long col0, int n, long k,
+                                long k0, int nb, int B, int M, double2* __restrict__ z) {
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (size_t)n * M) return;
   const size_t j = gid / M;
@@ -1053,15 +1061,16 @@ __global__ void k_build_snp_rep(const double* __restrict__ S, int n, long k, lon
   const long col = k0 + 2L * b;
   double re = 0.0, im = 0.0;
   if (b < B) {
-    if (col < k) re = S[j * (size_t)k + col];
-    if (col + 1 < k) im = S[j * (size_t)k + col + 1];
+    if (col < k) re = S[j * (size_t)ld + (col - col0)];
+    if (col + 1 < k) im = S[j * (size_t)ld + (col + 1 - col0)];
   }
   z[gid] = make_double2(re, im);
 }
 
 // CCP SNP batches (factored layout): batch i of count, slot b*nb + t =
 // S[t, c] + i S[t, c + 1] with c = k0 + i*tau + 2b, zero for t >= n or c >= k
-__global__ void k_build_snp_ccp(const double* __restrict__ S, int n, long k, long k0, int count,
+__global__ void k_build_snp_ccp(const double* __restrict__ S, long ld, long col0, int n, long k,
+                                long k0, int count,
                                 int tau, int nb, int B, int M, double2* __restrict__ z) {
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (size_t)count * M) return;
@@ -1071,8 +1080,8 @@ __global__ void k_build_snp_ccp(const double* __restrict__ S, int n, long k, lon
   const long col = k0 + (long)i * tau + 2L * b;
   double re = 0.0, im = 0.0;
   if (b < B && t < n) {
-    if (col < k) re = S[(size_t)t * k + col];
-    if (col + 1 < k) im = S[(size_t)t * k + col + 1];
+    if (col < k) re = S[(size_t)t * ld + (col - col0)];
+    if (col + 1 < k) im = S[(size_t)t * ld + (col + 1 - col0)];
   }
   z[gid] = make_double2(re, im);
 }
@@ -1343,11 +1352,11 @@ void mask_set(Context* c, const MaskItem* d_items, int cnt, u64* out, int out_ca
 }
 
 void tensor_mac_set(Context* c, PolyView out3, size_t out_stride, const MacPair* d_pairs,
-                    int npairs, int cnt, int l) {
+                    int npairs, int cnt, int l, bool accumulate) {
   ProfScope ps(c, PROF_TENSOR_MAC, (4.0 * npairs + 3.0) * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   k_tensor_mac_set<<<dim3(blocks_for(c->N), l, cnt), kThreads, 0, c->stream>>>(
-      out3, out_stride, d_pairs, npairs, l, c->N, c->d_mod);
+      out3, out_stride, d_pairs, npairs, l, c->N, accumulate ? 1 : 0, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1547,19 +1556,22 @@ void decode_batch(Context* c, const u64* m_coeff_q0, int count, double scale, do
   GWHE_LAUNCHED(c, 1);
 }
 
-void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, int B, int M,
-                   double2* z) {
+void build_snp_rep(Context* c, const double* S, long ld, long col0, int n, long k, long k0, int nb,
+                   int B, int M, double2* z) {
   ProfScope ps(c, PROF_ELEMWISE, 16.0 * n * M);
-  k_build_snp_rep<<<blocks_for((size_t)n * M), kThreads, 0, c->stream>>>(S, n, k, k0, nb, B, M, z);
+  GWHE_REQUIRE(k0 >= col0 && ld >= 1, ST_EINVAL, "genotype columns not held");
+  k_build_snp_rep<<<blocks_for((size_t)n * M), kThreads, 0, c->stream>>>(S, ld, col0, n, k, k0, nb,
+                                                                          B, M, z);
   GWHE_LAUNCHED(c, 1);
 }
 
-void build_snp_ccp(Context* c, const double* S, int n, long k, long k0, int count, int tau, int nb,
-                   int B, int M, double2* z) {
+void build_snp_ccp(Context* c, const double* S, long ld, long col0, int n, long k, long k0,
+                   int count, int tau, int nb, int B, int M, double2* z) {
   ProfScope ps(c, PROF_ELEMWISE, 16.0 * (double)count * M);
   if (count == 0) return;
-  k_build_snp_ccp<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(S, n, k, k0, count,
-                                                                             tau, nb, B, M, z);
+  GWHE_REQUIRE(k0 >= col0 && ld >= 1, ST_EINVAL, "genotype columns not held");
+  k_build_snp_ccp<<<blocks_for((size_t)count * M), kThreads, 0, c->stream>>>(
+      S, ld, col0, n, k, k0, count, tau, nb, B, M, z);
   GWHE_LAUNCHED(c, 1);
 }
 

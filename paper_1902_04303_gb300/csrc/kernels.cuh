@@ -85,7 +85,7 @@ void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_strid
 void mask_set(Context* c, const MaskItem* d_items, int cnt, u64* out, int out_cap,
               size_t out_stride, int l);
 void tensor_mac_set(Context* c, PolyView out3, size_t out_stride, const MacPair* d_pairs,
-                    int npairs, int cnt, int l);
+                    int npairs, int cnt, int l, bool accumulate = false);
 void sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, int cnt, u64* out,
              int out_cap, int l);
 
@@ -127,13 +127,16 @@ void decrypt_q0_list(Context* c, const u64* const* d_c0s, const u64* const* d_c1
 void gather_slots(Context* c, const double2* z, int cnt, int M, int B, int stride, double2* out);
 void decrypt_ntt(Context* c, CPolyView ct, int l, u64* m);
 
+// The genotype source of both builders is a device array holding the columns
+// col0.. of every sample's row, row pitch ld: genotype S[j, col] is at
+// S[j * ld + col - col0] (the whole n x k matrix: ld = k, col0 = 0).
 // REP rows of a SNP batch as complex slots: rows j < n, slot b * nb + t =
 // S[j, k0 + 2b] + i S[j, k0 + 2b + 1] (zero beyond k)
-void build_snp_rep(Context* c, const double* S, int n, long k, long k0, int nb, int B, int M,
-                   double2* z);
+void build_snp_rep(Context* c, const double* S, long ld, long col0, int n, long k, long k0, int nb,
+                   int B, int M, double2* z);
 // count CCP SNP batches from k0 (tau SNPs each): slot b*nb + t of batch i =
 // S[t, k0 + i tau + 2b] + i S[t, k0 + i tau + 2b + 1]
-void build_snp_ccp(Context* c, const double* S, int n, long k, long k0, int count, int tau, int nb,
-                   int B, int M, double2* z);
+void build_snp_ccp(Context* c, const double* S, long ld, long col0, int n, long k, long k0,
+                   int count, int tau, int nb, int B, int M, double2* z);
 
 }  // namespace gwhe

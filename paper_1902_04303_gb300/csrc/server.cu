@@ -39,6 +39,7 @@ struct Request {
   u32 nonce = 0;
   std::vector<double> X, A, y, S;
   size_t footprint = 0;
+  int dupm_chunk = 0;  // > 0: Dup(M_j) in the host tier
   std::vector<double> num, den;
   int status = GWHE_OK;
   std::string error;
@@ -58,16 +59,23 @@ struct gwhe_server {
   std::condition_variable cv_work, cv_done;
   std::deque<ReqPtr> pending;
   std::map<long, ReqPtr> reqs;
-  long next_id = 1, admitted = 0, running = 0;
+  long next_id = 1, admitted = 0, running = 0, host_tier = 0;
   bool stop = false;
 };
 
 namespace {
 
-// Estimated device bytes of one job beyond the shared keys: the device copy
-// of S, the encrypted inputs, the covariate phase's largest temporaries and
-// one chunk of SNP batches with its outputs.
-size_t footprint(const Context* c, int n, int d, long k, bool factored, int chunk) {
+// Estimated device bytes of one job beyond the shared keys: the two device
+// staging buffers of the genotype columns (S itself stays in host memory),
+// the encrypted inputs, the covariate phase's largest temporaries and one
+// chunk of SNP batches with its outputs.
+// (dupm_chunk > 0: the M-CCP layout's Dup(M_j) lives in the host tier and
+// only two prefetch slots of dupm_chunk ciphertexts are on the device.)
+// columns per prefetched chunk of Dup(M_j) when the server spills it: a
+// quarter of the columns, at most 32 (two slots stay well below n columns)
+int serve_dupm_chunk(int n) { return std::max(1, std::min(32, n / 4)); }
+size_t footprint(const Context* c, int n, int d, long k, bool factored, int chunk,
+                 int dupm_chunk = 0) {
   const Layout lay = make_layout(c->logN, n, d, k);
   const double ct = 2.0 * c->N * 8.0;  // bytes per limb of a ciphertext
   const int L = c->P.L;
@@ -77,24 +85,27 @@ size_t footprint(const Context* c, int n, int d, long k, bool factored, int chun
   const double batch = factored ? nb * ((4.0 * d + 8) * kFactLevel + 6.0) * ct * 2.0
                                 : ((double)n * kBatchLevel + nb * 16.0) * ct * 2.0 +
                                       (double)n * kBatchLevel * ct;
-  const double state = factored ? 2.0 * d * kFactLevel * ct : (double)n * (kBatchLevel + 1) * ct;
-  return (size_t)((double)n * k * 8 + inputs + fit + batch + state);
+  const double dupm = dupm_chunk > 0 ? 2.0 * std::min(n, dupm_chunk) * kBatchLevel * ct
+                                     : (double)n * (kBatchLevel + 1) * ct;
+  const double state = factored ? 2.0 * d * kFactLevel * ct : dupm;
+  const long cols = std::min<long>(k, (long)std::min(chunk, 64) * lay.tau);
+  const double staging = 2.0 * n * (double)cols * 8;
+  return (size_t)(staging + inputs + fit + batch + state);
 }
 
 void run_request(Context* c, Request& r, int chunk) {
   std::unique_ptr<Job> j(job_create(c, r.n, r.d, r.k, r.layout));
   job_set_nonce(j.get(), r.nonce);
+  job_set_host_state(j.get(), r.dupm_chunk);
   job_encrypt_inputs(j.get(), r.X.data(), r.A.data(), r.y.data());
   job_fit(j.get(), r.kappa);
   r.num.assign(r.k, NAN);
   r.den.assign(r.k, NAN);
-  Tmp S(c, sizeof(double) * r.S.size());
-  GWHE_CUDA(cudaMemcpyAsync(S.p, r.S.data(), sizeof(double) * r.S.size(), cudaMemcpyHostToDevice,
-                            c->stream));
+  // the genotypes stay in host memory; each chunk's columns are staged
   std::vector<double> num(r.k), den(r.k);
   for (long b0 = 0; b0 < j->lay.batches; b0 += chunk) {
     const long b1 = std::min<long>(j->lay.batches, b0 + chunk);
-    job_snp_stats(j.get(), S.as<double>(), b0, b1);
+    job_snp_stats(j.get(), r.S.data(), b0, b1);
     job_decrypt(j.get(), num.data(), den.data());
     const long s0 = b0 * j->lay.tau, s1 = std::min<long>(r.k, b1 * j->lay.tau);
     for (long s = s0; s < s1; ++s) {
@@ -138,6 +149,7 @@ void worker_main(gwhe_server* srv) {
       srv->peak = std::max(srv->peak, srv->in_use);
       ++srv->admitted;
       ++srv->running;
+      if (r->dupm_chunk > 0) ++srv->host_tier;
       r->t_start = now_ms();
     }
     try {
@@ -229,6 +241,14 @@ int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kap
   const bool factored =
       layout == kLayoutFactored || (layout == kLayoutAuto && c->P.L > kMLevel);
   r->footprint = footprint(c, n, d, k, factored, s->chunk);
+  if (r->footprint > s->budget && !factored) {
+    // over the budget with Dup(M_j) on the device: try the host tier
+    const size_t fh = footprint(c, n, d, k, false, s->chunk, serve_dupm_chunk(n));
+    if (fh <= s->budget) {
+      r->footprint = fh;
+      r->dupm_chunk = serve_dupm_chunk(n);
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (r->footprint > s->budget) {
@@ -270,7 +290,7 @@ int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* 
   return GWHE_OK;
 }
 
-int gwhe_server_stats(gwhe_server* s, long out[6]) {
+int gwhe_server_stats(gwhe_server* s, long out[7]) {
   if (!s || !out) return GWHE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   out[0] = s->admitted;
@@ -279,6 +299,7 @@ int gwhe_server_stats(gwhe_server* s, long out[6]) {
   out[3] = (long)s->in_use;
   out[4] = (long)s->peak;
   out[5] = (long)s->budget;
+  out[6] = s->host_tier;
   return GWHE_OK;
 }
 

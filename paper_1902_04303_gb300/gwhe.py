@@ -92,6 +92,7 @@ _SIGS = {
     "gwhe_autotune": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)],
     "gwhe_set_ntt_variant": [_vp, _i],
     "gwhe_job_set_nonce": [_vp, _u32],
+    "gwhe_job_set_host_state": [_vp, _i],
     "gwhe_job_release_results": [_vp],
     "gwhe_ctx_create_child": [_vp, _vp, ctypes.POINTER(_vp)],
     "gwhe_server_create": [_vp, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)],
@@ -597,6 +598,11 @@ class Job:
         """offset of this job's encryption ids (distinct per live job under one key)."""
         self.ctx._c(lib().gwhe_job_set_nonce(self.h, nonce))
 
+    def set_host_state(self, chunk=32):
+        """keep Dup(M_j) (M-CCP layout) in pinned host memory, prefetched back
+        `chunk` columns at a time per set of SNP batches (0: on the device)."""
+        self.ctx._c(lib().gwhe_job_set_host_state(self.h, chunk))
+
     def release_results(self):
         self.ctx._c(lib().gwhe_job_release_results(self.h))
 
@@ -657,9 +663,10 @@ class Server:
         return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2]}
 
     def stats(self):
-        out = (_l * 6)()
+        out = (_l * 7)()
         self.ctx._c(lib().gwhe_server_stats(self.h, out))
-        keys = ["admitted", "running", "waiting", "bytes_claimed", "peak_bytes_claimed", "budget"]
+        keys = ["admitted", "running", "waiting", "bytes_claimed", "peak_bytes_claimed", "budget",
+                "host_tier_jobs"]
         return {kk: int(v) for kk, v in zip(keys, out)}
 
     def close(self):

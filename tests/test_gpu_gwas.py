@@ -309,3 +309,92 @@ def test_paper_ring_kappa3_accuracy(g):
     ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=3, A=A)
     db, dl = check_accuracy(num, den, ref, k)
     print("N=2^17 kappa=3: max |d b'| = %.3g, max |d -log10 p| = %.3g" % (db, dl))
+
+
+@pytest.mark.parametrize("layout", ["factored", "mccp"])
+def test_host_genotypes_stream_in_chunks(g, layout):
+    """Genotypes in host memory stay there: each chunk of 64 batches takes its
+    columns through one of two pinned staging slots.  Over three chunks with a
+    ragged tail (130 batches of 64 SNPs, the last short) every output
+    ciphertext equals that of the same job with S on the device, and a batch
+    of the last chunk equals the oracle's."""
+    import torch
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 12
+    n, d = 16, 3
+    k = 130 * 64 - 21
+    data = make_gwas(n, d, k, seed=8)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(logN, n, d, k)
+    assert lay.batches == 130 and lay.tau == 64
+    fact = layout == "factored"
+    steps = rotation_steps(lay, factored=fact)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    ctx.keygen(rot_steps=steps, conj=True)
+    outs, res = [], []
+    for S in (data.S, torch.from_numpy(data.S).cuda()):
+        job = g.Job(ctx, n, d, k, layout=layout)
+        job.encrypt_inputs(data.X, A, data.y)
+        job.fit(1)
+        job.snp_stats(S)
+        outs.append([[job.ct(w, bi).export() for w in range(3)] for bi in range(lay.batches)])
+        res.append(job.decrypt_results())
+        job.close()
+    for bi in range(lay.batches):
+        for w in range(3):
+            assert np.array_equal(outs[0][bi][w], outs[1][bi][w]), (bi, w)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(res[0][0], res[0][1], ref, k)
+    if fact:
+        o = OracleCKKS(logN=logN, L=L, K=K, dnum=dnum, seed=seed)
+        o.keygen(galois=[galois_rot(logN, r) for r in steps] + [galois_conj(logN)])
+        c = Circuit(o, lay, factored=True)
+        c.encrypt_inputs(data.X, A, data.y)
+        c.fit(kappa=1)
+        want = c.snp_batch_factored(c.encrypt_snp_batch_ccp(data.S, 129))
+        for w in range(3):
+            assert np.array_equal(outs[0][129][w], want[w].c), w
+
+
+@pytest.mark.parametrize("chunk", [5, 16])
+def test_mccp_host_tier_state(g, chunk):
+    """Dup(M_j) in the host tier (pinned host memory, prefetched chunk columns
+    at a time per set of 64 batches, partial tensor sums accumulated): every
+    Dup(M_j) and every batch output equals the device-resident job's, over
+    three sets of batches and ragged column chunks; split mode as well."""
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 11
+    n, d = 16, 3
+    k = 130 * 64 - 21
+    data = make_gwas(n, d, k, seed=9)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(logN, n, d, k)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    ctx.keygen(rot_steps=rotation_steps(lay), conj=True)
+    outs = []
+    for host in (0, chunk):
+        job = g.Job(ctx, n, d, k, layout="mccp")
+        job.set_host_state(host)
+        job.encrypt_inputs(data.X, A, data.y)
+        job.fit(1)
+        job.snp_stats(data.S)
+        outs.append(([job.ct(3, jj).export() for jj in range(n)],
+                     [[job.ct(w, bi).export() for w in range(3)] for bi in range(lay.batches)]))
+        job.close()
+    for jj in range(n):
+        assert np.array_equal(outs[0][0][jj], outs[1][0][jj]), jj
+    for bi in range(lay.batches):
+        for w in range(3):
+            assert np.array_equal(outs[0][1][bi][w], outs[1][1][bi][w]), (bi, w)
+    # split mode: the client's Dup(M_j) encryptions go to the host tier too
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    res = []
+    for host in (0, chunk):
+        job = g.Job(ctx, n, d, k, layout="mccp")
+        job.set_host_state(host)
+        job.set_fit_state(ref["M"], ref["w"], ref["w"] * ref["zp"])
+        job.snp_stats(data.S, 0, 3)
+        res.append([[job.ct(w, bi).export() for w in range(3)] for bi in range(3)])
+        job.close()
+    assert all(np.array_equal(a, b) for ra, rb in zip(*res) for a, b in zip(ra, rb))
+    with pytest.raises(g.GwheError):
+        g.Job(ctx, n, d, k, layout="mccp").set_host_state(-1)

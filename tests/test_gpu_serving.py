@@ -91,3 +91,28 @@ def test_oversized_request_is_refused(g, setup):
         srv.submit(data.X, A, data.y, data.S, nonce=nonce)
     assert e.value.code == -2  # ENOMEM
     srv.close()
+
+
+def test_mccp_job_over_budget_runs_in_host_tier(g, setup):
+    """An M-CCP job whose footprint with Dup(M_j) on the device exceeds the
+    budget is admitted with Dup(M_j) in the host tier; its results equal the
+    same job run alone on the device, bit for bit."""
+    ctx, reqs, _ = setup
+    data, A, nonce = reqs[0]
+    n, d = data.X.shape
+    k = data.S.shape[1]
+    job = g.Job(ctx, n, d, k, layout="mccp")
+    job.set_nonce(nonce)
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    num0, den0 = job.decrypt_results()
+    job.close()
+    fp = g.job_footprint(ctx, n, d, k, layout="mccp", chunk_batches=2)
+    srv = g.Server(ctx, workers=2, hbm_budget=fp - 1, chunk_batches=2)
+    rid = srv.submit(data.X, A, data.y, data.S, layout="mccp", nonce=nonce)
+    num, den, _ = srv.wait(rid)
+    assert np.array_equal(num, num0) and np.array_equal(den, den0)
+    st = srv.stats()
+    assert st["host_tier_jobs"] == 1 and st["peak_bytes_claimed"] < fp
+    srv.close()
