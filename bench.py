@@ -162,6 +162,8 @@ def run_gpu(args):
 
     def step(src):
         job = gwhe.Job(ctx, W["n"], W["d"], W["k"], layout=args.layout)
+        if args.host_state:
+            job.set_host_state(args.host_state)  # Dup(M_j) in pinned host memory
         job.encrypt_inputs(src["X"], src["A"], src["y"])
         job.fit(W["kappa"])
         job.snp_stats(src["S"])
@@ -272,7 +274,8 @@ def run_gpu(args):
                    "special_primes": W["K"], "dnum": W["dnum"], "n": W["n"], "d": W["d"],
                    "k": W["k"], "kappa": W["kappa"], "layout": layout_used,
                    "parallelism": "independent jobs per GPU",
-                   "l2": "flushed between steps (256 MiB write)"},
+                   "l2": "flushed between steps (256 MiB write)",
+                   "dupm_host_tier_chunk": args.host_state},
         "keyswitch_per_s": round(ks_per_job * world / (step_ms / 1e3), 1),
         "keyswitches_per_job": ks_per_job,
         "e2e": {"value": round(snps / (e2e_ms / 1e3), 1), "unit": "SNPs/s",
@@ -702,6 +705,9 @@ def main():
     ap.add_argument("--layout", default="auto", choices=["auto", "mccp", "factored"],
                     help="SNP-phase layout: S' = M S with M as a CCP matrix, or the "
                          "factored S' = S - XA(X^T S) with S in CCP")
+    ap.add_argument("--host-state", type=int, default=0,
+                    help="M-CCP layout: keep Dup(M_j) in pinned host memory, prefetched this "
+                         "many columns at a time (0: on the device)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--micro-only", action="store_true",
