@@ -827,6 +827,9 @@ static void moddown_out(Context* c, u64* acc, int cnt, int l, int K, u64* out0, 
   ntt_inverse(c, acc, rk);
   Tmp conv(c, sizeof(u64) * cnt * 2 * l * N);
   moddown_convert_set(c, acc, l, K, conv.u(), cnt);
+  // the transform's row pass ends with (acc - NTT(conv)) P^-1 + add
+  const MdEpi epi{acc, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv[K]};
+  if (ntt_forward_moddown(c, conv.u(), cnt, epi)) return;
   ntt_forward(c, conv.u(), rows_q(2 * cnt, l, l));
   moddown_combine_set(c, acc, conv.u(), l, K, cnt, out0, out1, o_stride, add0, add1, a0_stride,
                       a1_stride);

@@ -377,6 +377,23 @@ void* dalloc_bytes(Context* c, size_t bytes);
 
 // ntt.cu
 void ntt_forward(Context* c, u64* data, const RowMap& rm);
+// ModDown's last step fused into a forward transform: data holds the
+// converted limbs conv [cnt][2][l][N] (coefficient domain); instead of
+// writing NTT(conv) back, the row pass writes
+//   out_p[item][i] = (acc[item][p][i] - NTT(conv)[item][p][i]) P^-1 (+ add_p[item][i])
+// with acc [cnt][2][l + K][N] (extended basis, NTT domain), pinv = the
+// (P^-1 mod q_i, Shoup companion) pairs, add0/add1 optional.  data is left
+// partly transformed.  Rings below 2^12 return false (not fused).
+struct MdEpi {
+  const u64* acc;
+  int l, K;
+  u64 *out0, *out1;
+  size_t o_stride;
+  const u64 *add0, *add1;
+  size_t a0_stride, a1_stride;
+  const u64* pinv;
+};
+bool ntt_forward_moddown(Context* c, u64* data, int cnt, const MdEpi& epi);
 void ntt_inverse(Context* c, u64* data, const RowMap& rm);
 RowMap rows_q(int npoly, int l, int poly_stride);  // limbs 0..l-1 of q-primes
 

@@ -29,9 +29,13 @@ namespace gwhe {
 // residues per thread (LS <= 2 log2 E): log2 E stages in registers in a
 // strided layout, a shared-memory transpose to a contiguous layout for the
 // remaining stages, and a transpose back for coalesced stores.
-template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256, int MB = 4>
+// MD (forward row pass only): ModDown epilogue, see ntt_forward_moddown.
+template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256, int MB = 4,
+          bool MD = false>
 __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
-                                                  const NttTables tb, const int groups_per_row) {
+                                                  const NttTables tb, const int groups_per_row,
+                                                  const MdEpi epi = MdEpi{}) {
+  static_assert(!MD || (FWD && !PASSA), "the ModDown epilogue ends a forward transform");
   constexpr int S = 1 << LS;
   constexpr int LE = E == 16 ? 4 : 5;  // log2 E
   static_assert(E == 16 || E == 32, "16 or 32 residues per thread");
@@ -112,6 +116,25 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
     if (!PASSA) {
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = reduce_8q(x[m], q);
+    }
+    if (MD) {
+      // row = (item, poly p, limb) of conv [cnt][2][l][N]
+      const size_t N = (size_t)1 << LOGN;
+      const int item = poly >> 1, p = poly & 1;
+      const u64* a = epi.acc + ((size_t)item * 2 * (epi.l + epi.K) + (size_t)p * (epi.l + epi.K) +
+                                limb) * N;
+      u64* o = (p ? epi.out1 : epi.out0) + item * epi.o_stride + (size_t)limb * N;
+      const u64* ad = p ? epi.add1 : epi.add0;
+      if (ad) ad += item * (p ? epi.a1_stride : epi.a0_stride) + (size_t)limb * N;
+      const u64 pi = epi.pinv[2 * limb], pish = epi.pinv[2 * limb + 1];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const size_t k = gaddr(r + TPS * m);
+        u64 v = shoup(submod(a[k], x[m], q), pi, pish, q);
+        if (ad) v = addmod(v, ad[k], q);
+        o[k] = v;
+      }
+      return;
     }
   } else {
 #pragma unroll
@@ -205,15 +228,21 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
 
 // pass A: 2^LA-point columns, pass B: 2^LB-point rows, with EA / EB residues
 // per thread in NA / NB-thread CTAs, at least MB CTAs per SM
+// (epi: forward only, the row pass ends with the ModDown epilogue)
 template <int LOGN, int LA, int LB, int EA, int NA, int EB, int NB, int MB = 4>
-static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
+static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
+                         const MdEpi* epi = nullptr) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
   const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
   const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
     k_ntt_pass<LOGN, LA, true, true, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
-    k_ntt_pass<LOGN, LB, false, true, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
+    if (epi)
+      k_ntt_pass<LOGN, LB, false, true, EB, NB, MB, true>
+          <<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB, *epi);
+    else
+      k_ntt_pass<LOGN, LB, false, true, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
   } else {
     k_ntt_pass<LOGN, LB, false, false, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
     k_ntt_pass<LOGN, LA, true, false, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
@@ -224,39 +253,43 @@ static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
 // the default shape of a two-pass transform: a pass of more than 8 stages
 // holds 32 residues per thread in 128-thread CTAs
 template <int LOGN, int LA, int LB>
-static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd) {
+static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
+                         const MdEpi* epi = nullptr) {
   ntt_two_pass<LOGN, LA, LB, (LA > 8 ? 32 : 16), (LA > 8 ? 128 : 256), (LB > 8 ? 32 : 16),
-               (LB > 8 ? 128 : 256)>(c, data, rm, fwd);
+               (LB > 8 ? 128 : 256)>(c, data, rm, fwd, epi);
 }
 
 // shapes of the N = 2^16 transform (identical results; the autotuner times
 // them on the device and keeps the fastest)
-static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd) {
+static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi) {
   switch (c->ntt_variant) {
-    case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd); return;
-    case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd); return;
-    case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd); return;
-    case 4: ntt_two_pass<16, 8, 8, 16, 128, 16, 128, 8>(c, data, rm, fwd); return;
-    case 5: ntt_two_pass<16, 8, 8, 16, 64, 16, 64, 16>(c, data, rm, fwd); return;
-    default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd); return;
+    case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd, epi); return;
+    case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd, epi); return;
+    case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd, epi); return;
+    case 4: ntt_two_pass<16, 8, 8, 16, 128, 16, 128, 8>(c, data, rm, fwd, epi); return;
+    case 5: ntt_two_pass<16, 8, 8, 16, 64, 16, 64, 16>(c, data, rm, fwd, epi); return;
+    default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd, epi); return;
   }
 }
 
-static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
+// true if the ring has a two-pass transform (and epi, if given, was applied)
+static bool ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd,
+                         const MdEpi* epi = nullptr) {
   const int rows = rm.npoly * rm.nl;
-  if (rows <= 0) return;
+  if (rows <= 0) return true;
   // algorithmic traffic: every residue read once and written once
   ProfScope ps(c, PROF_NTT, 16.0 * rows * c->N);
   GWHE_REQUIRE(rm.nl <= kMaxRowLimbs, ST_EINVAL, "too many limbs in a row map");
   switch (c->logN) {
-    case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd); return;
-    case 16: ntt_2_16(c, data, rm, fwd); return;
-    case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd); return;
-    case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd); return;
-    case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd); return;
-    case 12: ntt_two_pass<12, 6, 6>(c, data, rm, fwd); return;
+    case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd, epi); return true;
+    case 16: ntt_2_16(c, data, rm, fwd, epi); return true;
+    case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd, epi); return true;
+    case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd, epi); return true;
+    case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd, epi); return true;
+    case 12: ntt_two_pass<12, 6, 6>(c, data, rm, fwd, epi); return true;
     default: break;
   }
+  if (epi) return false;
   GWHE_REQUIRE(c->logN >= 2 && c->logN <= 11, ST_EINVAL, "unsupported ring degree");
   const NttTables tb = c->tables();
   const size_t shm = sizeof(u64) << c->logN;
@@ -265,9 +298,16 @@ static void ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd) {
   else
     k_ntt_small<false><<<rows, 256, shm, c->stream>>>(data, rm, tb, c->logN);
   GWHE_LAUNCHED(c, 1);
+  return true;
 }
 
 void ntt_forward(Context* c, u64* data, const RowMap& rm) { ntt_dispatch(c, data, rm, true); }
+bool ntt_forward_moddown(Context* c, u64* data, int cnt, const MdEpi& epi) {
+  GWHE_REQUIRE(cnt >= 1 && epi.l >= 1 && epi.acc && epi.out0 && epi.out1 && epi.pinv, ST_EINVAL,
+               "bad ModDown epilogue");
+  if (c->logN < 12) return false;
+  return ntt_dispatch(c, data, rows_q(2 * cnt, epi.l, epi.l), true, &epi);
+}
 void ntt_inverse(Context* c, u64* data, const RowMap& rm) { ntt_dispatch(c, data, rm, false); }
 
 RowMap rows_q(int npoly, int l, int poly_stride) {
