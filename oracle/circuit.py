@@ -232,6 +232,18 @@ class Circuit:
             acc = t if acc is None else ev.add(acc, t)
         return ev.rescale(acc)
 
+    def cp_rp_matvec(self, acols, rows, v: Ct, m: int) -> Ct:
+        """A (R v): Alg. 2 over the DotProds of Alg. 6.  DotProd(R(c), v)
+        (Alg. 5) ends with (R v)_c in every slot, which is what Replicate
+        (Alg. 1) makes of entry c, so Alg. 6's masks e_c and Alg. 2's
+        replicates cancel.  v is dropped two levels first: the result leaves at
+        the level Alg. 6 then Alg. 2 would give."""
+        ev = self.ev
+        vv = ev.drop(v, v.level - 2)
+        dps = [self.dotprod(ev.drop(rows[c], vv.level), vv) for c in range(m)]
+        lv = dps[0].level
+        return self.mac_relin_rescale([(ev.drop(acols[c], lv), dps[c]) for c in range(m)])
+
     def colsum(self, v: Ct) -> Ct:
         """Alg. 4: log2(nb) rotate-and-add steps; sums land at slots c*nb."""
         v = self.ladder(v, [1 << i for i in range(int(math.log2(self.lay.nb)))])
@@ -355,8 +367,7 @@ class Circuit:
             xb = self.cp_matvec(self.X, beta, d)
             p = self.sigma7(xb)
             ymp = ev.sub(ev.drop(self.y, p.level), p)
-            g = self.rp_matvec(self.X, ymp, d)
-            ag = self.cp_matvec(self.A, g, d)
+            ag = self.cp_rp_matvec(self.A, self.X, ymp, d)  # A g, g = X^T (y - p)
             ag4 = ev.mul_int(ag, 4)
             beta = ev.sub(ev.drop(beta, ag4.level), ag4)
         self.beta = beta
@@ -381,8 +392,7 @@ class Circuit:
         lv = min(xb.level, r.level)
         z = ev.add(ev.drop(xb, lv), ev.drop(r, lv))
         # eq. zprime, second form: z' = z - X (A (X^T z))
-        xtz = self.rp_matvec(self.X, z, d)
-        axtz = self.cp_matvec(self.A, xtz, d)
+        axtz = self.cp_rp_matvec(self.A, self.X, z, d)
         xaxtz = self.cp_matvec(self.X, axtz, d)
         zp = ev.sub(ev.drop(z, xaxtz.level), xaxtz)
         wzp = ev.mult(ev.drop(w_m, zp.level), zp)

@@ -81,11 +81,6 @@ struct Eval {
     op_rescale(c, *out);
     return out;
   }
-  std::vector<double2> e_slot(int s) {
-    auto z = slots_zero();
-    z[s] = make_double2(1, 0);
-    return z;
-  }
 
   std::vector<int> pow2_steps(int count, int base = 1) {
     std::vector<int> s;
@@ -197,32 +192,33 @@ struct Eval {
     set_relin_rescale(c, *t3, *out);
     return out;
   }
-  // Alg. 6 with Alg. 5 inside: every DotProd(A(c), v) (product, log2(M) ladder)
-  // as one set, then the masks e_c summed before one rescale.
-  CtPtr rp_matvec(const std::vector<CtPtr>& rows, const Ct& v, int m) {
+  // A (R v): Alg. 2 over the DotProds of Alg. 6.  DotProd(R(c), v) (Alg. 5)
+  // ends with (R v)_c in every slot, which is Replicate (Alg. 1) of entry c,
+  // so Alg. 6's masks and Alg. 2's replicates cancel; v is taken two levels
+  // lower, where the result of Alg. 6 then Alg. 2 would leave.
+  CtPtr cp_rp_matvec(const std::vector<CtPtr>& acols, const std::vector<CtPtr>& rows, const Ct& v,
+                     int m) {
+    const int l = v.l - 2;
+    GWHE_REQUIRE(l >= 2, ST_ELEVEL, "depth exhausted");
+    CtPtr vv = view(v, l);
     std::vector<CtPtr> views;
     std::vector<std::pair<const Ct*, const Ct*>> pairs;
     for (int cidx = 0; cidx < m; ++cidx) {
-      views.push_back(view(*rows[cidx], v.l));
-      pairs.push_back({views.back().get(), &v});
+      views.push_back(view(*rows[cidx], l));
+      pairs.push_back({views.back().get(), vv.get()});
     }
-    CtSetPtr dp = set_new(c, m, 2, v.l, v.l, 1.0);
+    CtSetPtr dp = set_new(c, m, 2, l, l, 1.0);
     set_mult(c, pairs, *dp);
     set_ladder(c, *dp, pow2_steps(lay.logN - 1));
-    const int l = dp->l;
-    const double ql = (double)c->mod[l - 1];
-    std::vector<MaskItem> mi;
-    for (int cidx = 0; cidx < m; ++cidx)
-      mi.push_back(MaskItem{dp->item(cidx), dp->cap,
-                            mask_pt(c, kMaskSlot, cidx, l, ql, e_slot(cidx))});
-    CtSetPtr masked = set_new(c, m, 2, l, l, 1.0);
-    set_mask(c, mi, dp->scale, ql, *masked, false);
-    CtPtr acc = fresh(l);
-    sum_set(c, masked->d, masked->cap, masked->stride(), m, acc->d, acc->cap, l);
-    acc->l = l;
-    acc->scale = masked->scale;
-    op_rescale(c, *acc);
-    return acc;
+    const int lv = dp->l;
+    std::vector<CtPtr> av, dv;
+    std::vector<std::pair<const Ct*, const Ct*>> mac;
+    for (int cidx = 0; cidx < m; ++cidx) {
+      av.push_back(view(*acols[cidx], lv));
+      dv.push_back(dp->view(cidx));
+      mac.push_back({av.back().get(), dv.back().get()});
+    }
+    return mac_relin_rescale(mac);
   }
   // Alg. 4: log2(nb) rotate-and-add steps; block sums land at slots c*nb
   std::vector<int> colsum_steps() { return pow2_steps(ilog2(lay.nb)); }
@@ -539,8 +535,7 @@ void job_fit(Job* j, int kappa) {
     p = ev.sigma7(*xb);
     CtPtr yv = ev.view(*j->y, p->l);
     ymp = ev.sub(*yv, *p);
-    CtPtr g = ev.rp_matvec(j->X, *ymp, d);
-    CtPtr ag = ev.cp_matvec(j->A, *g, d);
+    CtPtr ag = ev.cp_rp_matvec(j->A, j->X, *ymp, d);  // A g, g = X^T (y - p)
     op_mul_int(c, *ag, 4);
     CtPtr bv = ev.view(*beta, ag->l);
     beta = ev.sub(*bv, *ag);
@@ -582,8 +577,7 @@ void job_fit(Job* j, int kappa) {
   CtPtr xbv = ev.view(*xb, lv), rv = ev.view(*r, lv);
   j->z = ev.add(*xbv, *rv);
   // eq. zprime, second form: z' = z - X (A (X^T z))
-  CtPtr xtz = ev.rp_matvec(j->X, *j->z, d);
-  CtPtr axtz = ev.cp_matvec(j->A, *xtz, d);
+  CtPtr axtz = ev.cp_rp_matvec(j->A, j->X, *j->z, d);
   CtPtr xaxtz = ev.cp_matvec(j->X, *axtz, d);
   CtPtr zv = ev.view(*j->z, xaxtz->l);
   j->zp = ev.sub(*zv, *xaxtz);

@@ -299,3 +299,41 @@ def test_shared_replicate_equals_alg1(m):
     bad[P] = 0.5
     reps_bad = c.replicate_all(c.encrypt_vector(bad, 0x78), m)
     assert np.max(np.abs(o.decrypt_decode(reps_bad[0]) - (v[0] + 0.5))) < 1e-5
+
+
+def test_composed_rp_cp_matvec_equals_alg6_then_alg2():
+    """A (X^T v) through Alg. 2 over Alg. 6's DotProds (the masks e_c and the
+    replicates cancel) decrypts to the plaintext product and to Alg. 6 then
+    Alg. 2, at the same level, without the replicate ladders: m (1 + h) + 1
+    key switches (h = ceil(log2(M)/3) hoisted groups per DotProd ladder)
+    against m (1 + h) + (ceil(log2(M/8)/3) + m) + 1."""
+    logN, n, d = 10, 16, 3
+    dat = make_gwas(n, d, 32, seed=31)
+    A = gwas_fp64.xtx_inv(dat.X)
+    o = OracleCKKS(logN=logN, L=8, K=3, dnum=2, seed=33)
+    lay = Layout(logN, n, d, 32)
+    o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay)])
+    c = Circuit(o, lay)
+    c.encrypt_inputs(dat.X, A, dat.y)
+    rng = np.random.default_rng(5)
+    v = rng.uniform(-1, 1, n)
+    vct = c.encrypt_vector(v, 0x99)
+    want = A @ (dat.X.T @ v)
+    hist = _count_switches(o)
+    fused = c.cp_rp_matvec(c.A, c.X, vct, d)
+    n_fused = int(hist.sum())
+    hist[:] = 0
+    two = c.cp_matvec(c.A, c.rp_matvec(c.X, vct, d), d)
+    n_two = int(hist.sum())
+    assert fused.level == two.level == vct.level - 4
+    got_f = o.decrypt_decode(fused).real[:d]
+    got_t = o.decrypt_decode(two).real[:d]
+    assert np.max(np.abs(got_f - want)) < 1e-4 and np.max(np.abs(got_t - want)) < 1e-4
+    assert np.max(np.abs(got_f - got_t)) < 1e-4
+    M = 1 << (logN - 1)
+    per_ladder = math.ceil((logN - 1) / 3)
+    assert n_fused == d * (1 + per_ladder) + 1
+    assert n_two == d * (1 + per_ladder) + (math.ceil(math.log2(M // 8) / 3) + d) + 1
+    # a planted error: a wrong column of A shows up in the result
+    bad = c.cp_rp_matvec(c.A[::-1], c.X, vct, d)
+    assert np.max(np.abs(o.decrypt_decode(bad).real[:d] - want)) > 1e-2
