@@ -392,6 +392,8 @@ Context* ctx_child(const Context* base, cudaStream_t stream) {
   c->parent = base;
   c->stream = stream;
   c->masks.clear();
+  c->pin_stage[0] = c->pin_stage[1] = nullptr;  // staging buffers are per context
+  c->pin_stage_bytes = 0;
   c->ks_count = 0;
   c->launches = 0;
   for (long& v : c->ks_by_level) v = 0;
@@ -403,6 +405,8 @@ Context* ctx_child(const Context* base, cudaStream_t stream) {
 void ctx_destroy(Context* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (void* p : c->pin_stage)
+    if (p) cudaFreeHost(p);
   if (c->parent) {  // only the child's own state
     for (auto& kv : c->masks) cudaFree(kv.second);
     for (auto& r : c->prof.recs) {

@@ -288,6 +288,10 @@ struct Context {
   // a child context (ctx_child) shares its parent's tables and keys
   // read-only and owns only its stream, caches and counters
   const Context* parent = nullptr;
+  // pinned host staging buffers of the genotype columns (grow-only, kept
+  // across calls: pinned allocation and release are slow and synchronising)
+  void* pin_stage[2] = {nullptr, nullptr};
+  size_t pin_stage_bytes = 0;
   Params P;
   int N = 0, logN = 0, alpha = 0, nmod = 0;
   int ntt_variant = 4;         // shape of the N = 2^16 transform (kNttVariants;

@@ -788,7 +788,8 @@ struct TwoSlotCopy {
 
 // Genotype column ranges from host memory: stage() gathers the n row
 // segments [col0, col0 + w) into the slot's pinned buffer (after the slot's
-// previous copy has left it) and copies them to the device.
+// previous copy has left it) and copies them to the device.  The pinned
+// buffers belong to the context and are reused by later calls.
 struct HostStager {
   int n;
   long wmax;
@@ -796,13 +797,22 @@ struct HostStager {
   TwoSlotCopy cp;
   HostStager(Context* c, int n_, long wmax_)
       : n(n_), wmax(wmax_), cp(c, sizeof(double) * (size_t)n_ * wmax_) {
-    for (int s = 0; s < 2; ++s)
-      if (cudaHostAlloc((void**)&pin[s], sizeof(double) * (size_t)n * wmax, cudaHostAllocDefault) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        free_pinned();
-        throw Error(ST_ENOMEM, "pinned staging allocation failed");
+    const size_t need = sizeof(double) * (size_t)n * wmax;
+    if (c->pin_stage_bytes < need) {
+      for (void*& p : c->pin_stage) {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
       }
+      c->pin_stage_bytes = 0;
+      for (void*& p : c->pin_stage)
+        if (cudaHostAlloc(&p, need, cudaHostAllocDefault) != cudaSuccess) {
+          cudaGetLastError();
+          p = nullptr;
+          throw Error(ST_ENOMEM, "pinned staging allocation failed");
+        }
+      c->pin_stage_bytes = need;
+    }
+    for (int s = 0; s < 2; ++s) pin[s] = (double*)c->pin_stage[s];
   }
   const double* stage(int s, const double* S, long k, long col0, long w) {
     GWHE_REQUIRE(w >= 1 && w <= wmax, ST_EINVAL, "staged column range too wide");
@@ -812,15 +822,10 @@ struct HostStager {
     return (const double*)cp.copy(s, pin[s], sizeof(double) * (size_t)n * w);
   }
   void release(int s) { cp.release(s); }
-  void free_pinned() {
-    for (int s = 0; s < 2; ++s)
-      if (pin[s]) cudaFreeHost(pin[s]);
-    pin[0] = pin[1] = nullptr;
-  }
   ~HostStager() {
+    // the context's buffers must be free for the next call
     cp.wait_copied(0);
     cp.wait_copied(1);
-    free_pinned();
   }
 };
 
