@@ -176,6 +176,28 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
     }
     c->d_psi = upload(c.get(), psi);
     c->d_ipsi = upload(c.get(), ipsi);
+    if (P.logN == 16) {
+      // the row pass's last four stages in the transposed order of NttTables
+      std::vector<ulonglong2> pb((size_t)nm * kTwBPerMod), ipb((size_t)nm * kTwBPerMod);
+      for (int u = 0; u < nm; ++u) {
+        size_t off = (size_t)u * kTwBPerMod;
+        for (int sp = 4; sp < 8; ++sp) {
+          const int nj = 1 << (sp - 4);
+          for (int g = 0; g < 256; ++g)
+            for (int j = 0; j < nj; ++j)
+              for (int r = 0; r < 16; ++r) {
+                const size_t src = (size_t)u * N + (1u << (8 + sp)) + ((size_t)g << sp) +
+                                   (size_t)r * nj + j;
+                const size_t dst = off + ((size_t)g << sp) + 16 * j + r;
+                pb[dst] = psi[src];
+                ipb[dst] = ipsi[src];
+              }
+          off += (size_t)256 << sp;
+        }
+      }
+      c->d_psiB = upload(c.get(), pb);
+      c->d_ipsiB = upload(c.get(), ipb);
+    }
     c->d_ninv = upload(c.get(), ninv);
     c->d_ninv_sh = upload(c.get(), ninv_sh);
   }
@@ -417,6 +439,7 @@ void ctx_destroy(Context* c) {
     delete c;
     return;
   }
+  for (void* p : {(void*)c->d_psiB, (void*)c->d_ipsiB}) if (p) cudaFree(p);
   for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
                   (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
                   (void*)c->d_fftWq, (void*)c->d_fftTq,

@@ -208,9 +208,17 @@ struct RowMap {
 // Tables of the negacyclic NTT for one modulus index u, each of length N:
 // psi[i] = (psi^brv(i), Shoup companion), ipsi[i] = (psi^-brv(i), companion),
 // interleaved so that one 16-byte load fetches a twiddle and its companion.
+// psiB / ipsiB (N = 2^16 only): the twiddles of the row pass's stages 12-15
+// (local stages 4-7 of the 8 + 8 split with 16 residues per thread),
+// transposed so that a warp's loads are contiguous: for local stage sp,
+// row g, the thread r of the row and its j-th distinct twiddle j < 2^(sp-4),
+// entry kTwB[sp] + g 2^sp + 16 j + r = psi[2^(8+sp) + g 2^sp + r 2^(sp-4) + j].
+constexpr int kTwBPerMod = 256 * (16 + 32 + 64 + 128);
 struct NttTables {
   const ulonglong2* psi;
   const ulonglong2* ipsi;
+  const ulonglong2* psiB;   // [nmod][kTwBPerMod] or null
+  const ulonglong2* ipsiB;
   const u64* ninv;     // [nmod] N^-1 mod q_u
   const u64* ninv_sh;  // [nmod]
   const DevMod* mod;   // [nmod]
@@ -302,6 +310,7 @@ struct Context {
   std::vector<DevMod> hmod;
   DevMod* d_mod = nullptr;
   ulonglong2 *d_psi = nullptr, *d_ipsi = nullptr;
+  ulonglong2 *d_psiB = nullptr, *d_ipsiB = nullptr;  // row-pass twiddles, N = 2^16
   u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l - 1 (value, Shoup)
   u64* d_rescale = nullptr;    // [L][L][2]
@@ -340,7 +349,7 @@ struct Context {
   Prof prof;
   std::string last_error;
   NttTables tables() const {
-    return NttTables{d_psi, d_ipsi, d_ninv, d_ninv_sh, d_mod};
+    return NttTables{d_psi, d_ipsi, d_psiB, d_ipsiB, d_ninv, d_ninv_sh, d_mod};
   }
 };
 

@@ -74,6 +74,14 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
     const int s = S0 + s_local;
     return (1 << s) + (PASSA ? 0 : (g << s_local)) + (e >> (LS - s_local));
   };
+  // the row pass of the 8 + 8 split at 16 residues per thread reads its
+  // contiguous-layout stages from the transposed table (coalesced per warp)
+  constexpr bool TWB = !PASSA && LOGN == 16 && LS == 8 && E == 16;
+  const ulonglong2* WB = TWB ? (FWD ? tb.psiB : tb.ipsiB) + (size_t)u * kTwBPerMod : nullptr;
+  auto twb = [&](int sp, int m) -> ulonglong2 {  // stage sp >= 4, pair led by E r + m
+    const int off = 256 * ((1 << sp) - 16);     // sum over the earlier stages 4..sp-1
+    return __ldg(WB + off + (g << sp) + ((m >> (8 - sp)) << 4) + r);
+  };
 
   u64 x[E];
 #pragma unroll
@@ -102,8 +110,7 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         if (m & st) continue;
-        const int idx = tw(sp, E * r + m);
-        const ulonglong2 w = __ldg(W + idx);
+        const ulonglong2 w = TWB ? twb(sp, m) : __ldg(W + tw(sp, E * r + m));
         ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
@@ -148,8 +155,7 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         if (m & st) continue;
-        const int idx = tw(sp, E * r + m);
-        const ulonglong2 w = __ldg(W + idx);
+        const ulonglong2 w = TWB ? twb(sp, m) : __ldg(W + tw(sp, E * r + m));
         gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
