@@ -114,8 +114,9 @@ class Clocks:
 # the multiply-add pipe, not issue, bounds the transform.
 NUM_SMS = 152
 FMAHEAVY_CYCLES_PER_WARP_BFLY = 34.7
-# ncu, 3072 rows of 2^16: pass A 1.611 + 1.555 GB, pass B 1.846 + 1.561 GB
-NTT_DRAM_BYTES_PER_LIMB = round((1.611e9 + 1.555e9 + 1.846e9 + 1.561e9) / 3072)
+# ncu, 3072 rows of 2^16 (the row pass reading its last stages' twiddles from
+# the transposed table): pass A 1.611 + 1.555 GB, pass B 1.849 + 1.557 GB
+NTT_DRAM_BYTES_PER_LIMB = round((1.611e9 + 1.555e9 + 1.849e9 + 1.557e9) / 3072)
 
 
 def alu_peak_gbfly(sm_mhz):
