@@ -423,3 +423,60 @@ def test_automorphism_rotates_slots():
     ct = ckks.Ct(np.stack([res, np.zeros_like(res)]), o.delta)
     cj = o.automorphism(ct, galois_conj(8))
     assert np.max(np.abs(o.decode(cj.c[0], o.delta) - np.conj(z))) < 1e-7
+
+
+# ------------------------------------------------- evaluation at a 2N-th root
+def _root_2n(q, N, seed):
+    """an element of multiplicative order 2N mod the prime q (2N | q - 1),
+    found from random bases: h = b^((q-1)/2N) has order 2N iff h^N = -1"""
+    import random
+    rng = random.Random(seed)
+    while True:
+        h = pow(rng.randrange(2, q - 1), (q - 1) // (2 * N), q)
+        if pow(h, N, q) == q - 1:
+            return h
+
+
+def _eval(poly, x, q):
+    """poly(x) mod q by Horner's rule on Python integers"""
+    acc = 0
+    for c in reversed([int(v) for v in poly]):
+        acc = (acc * x + c) % q
+    return acc
+
+
+def test_ring_maps_by_evaluation_at_a_root(small):
+    """Evaluation at x with x^N = -1 mod q is a ring map Z_q[X]/(X^N + 1) -> Z_q.
+    Through it: the plaintext product decrypts to Dec(ct)(x) pt(x) exactly (no
+    noise term: Dec(c0 p, c1 p) = (c0 + c1 s) p), the Galois image of the secret
+    key evaluates to s(x^g) and its square to s(x)^2 on every q- and special
+    prime, and the RNS conversion of signed integers is the least residue."""
+    o = small
+    N = o.N
+    rng = _rng(77)
+    s = o.secret_key()
+    l = 3
+    ct = o.encrypt(o.encode(rng.uniform(-1, 1, o.M), o.delta, l), 0x5151, o.delta)
+    coeffs = rng.integers(-1000, 1000, N)
+    pt = o.to_rns(coeffs, l)
+    for i in range(l):
+        assert all(int(pt[i][j]) == int(coeffs[j]) % o.q[i] for j in range(N))
+    m, mp = o.decrypt(ct), o.decrypt(o.mul_plain(ct, pt, 1.0))
+    for i in range(l):
+        q = o.q[i]
+        x = _root_2n(q, N, i)
+        assert _eval(mp[i], x, q) == _eval(m[i], x, q) * _eval(pt[i], x, q) % q
+    mods = o.q + o.p
+    s2 = np.zeros((len(mods), N), np.uint64)
+    L.or_sk_square(o._ctx, s2)
+    for g in (galois_rot(o.logN, 1), galois_rot(o.logN, 5), galois_conj(o.logN)):
+        t = np.zeros((len(mods), N), np.uint64)
+        L.or_sk_galois(o._ctx, g, t)
+        for i, q in enumerate(mods):
+            x = _root_2n(q, N, 100 + i)
+            sq = [int(v) % q for v in s]
+            assert _eval(t[i], x, q) == _eval(sq, pow(x, g, q), q), (g, i)
+            # a planted wrong exponent does not match
+            assert _eval(t[i], x, q) != _eval(sq, pow(x, g + 2, q), q), (g, i)
+            if g == galois_conj(o.logN):
+                assert _eval(s2[i], x, q) == _eval(sq, x, q) ** 2 % q, i
