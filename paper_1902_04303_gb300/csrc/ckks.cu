@@ -416,6 +416,9 @@ Context* ctx_child(const Context* base, cudaStream_t stream) {
   c->masks.clear();
   c->pin_stage[0] = c->pin_stage[1] = nullptr;  // staging buffers are per context
   c->pin_stage_bytes = 0;
+  c->pin_state = nullptr;
+  c->pin_state_bytes = 0;
+  c->pin_state_lent = false;
   c->ks_count = 0;
   c->launches = 0;
   for (long& v : c->ks_by_level) v = 0;
@@ -429,6 +432,7 @@ void ctx_destroy(Context* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->pin_stage)
     if (p) cudaFreeHost(p);
+  if (c->pin_state) cudaFreeHost(c->pin_state);
   if (c->parent) {  // only the child's own state
     for (auto& kv : c->masks) cudaFree(kv.second);
     for (auto& r : c->prof.recs) {

@@ -300,6 +300,11 @@ struct Context {
   // across calls: pinned allocation and release are slow and synchronising)
   void* pin_stage[2] = {nullptr, nullptr};
   size_t pin_stage_bytes = 0;
+  // pinned block for one job's Dup(M_j) in the host tier (grow-only; lent
+  // to one job at a time, others allocate their own)
+  void* pin_state = nullptr;
+  size_t pin_state_bytes = 0;
+  bool pin_state_lent = false;
   Params P;
   int N = 0, logN = 0, alpha = 0, nmod = 0;
   int ntt_variant = 4;         // shape of the N = 2^16 transform (kNttVariants;

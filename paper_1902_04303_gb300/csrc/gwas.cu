@@ -316,13 +316,22 @@ Layout make_layout(int logN, int n, int d, long k) {
   return L;
 }
 
+// Give back (or free) the pinned block holding Dup(M_j), once the job's
+// kernels are done with it.
+static void release_dupm_host(Job* j) {
+  if (!j->DupM_host || !j->c) return;
+  cudaStreamSynchronize(j->c->stream);
+  if (j->DupM_host_lent)
+    j->c->pin_state_lent = false;
+  else
+    cudaFreeHost(j->DupM_host);
+  j->DupM_host = nullptr;
+  j->DupM_host_lent = false;
+}
+
 Job::~Job() {
   DupM.clear();
-  if (DupM_host && c) {
-    // kernels of this job may still read it
-    cudaStreamSynchronize(c->stream);
-    cudaFreeHost(DupM_host);
-  }
+  release_dupm_host(this);
 }
 
 // Move Dup(M_j) to one pinned host block (the host tier) and point the job's
@@ -332,7 +341,23 @@ static void spill_dupm(Job* j) {
   const int n = (int)j->DupM.size();
   const int l = j->DupM[0]->l;
   const size_t per = (size_t)2 * l * c->N;
-  GWHE_CUDA(cudaHostAlloc((void**)&j->DupM_host, sizeof(u64) * per * n, cudaHostAllocDefault));
+  const size_t need = sizeof(u64) * per * n;
+  if (!c->pin_state_lent) {
+    // the context's block (grown if needed): pinned allocation and release
+    // are slow and synchronise the device, so jobs reuse it
+    if (c->pin_state_bytes < need) {
+      if (c->pin_state) cudaFreeHost(c->pin_state);
+      c->pin_state = nullptr;
+      c->pin_state_bytes = 0;
+      GWHE_CUDA(cudaHostAlloc(&c->pin_state, need, cudaHostAllocDefault));
+      c->pin_state_bytes = need;
+    }
+    j->DupM_host = (u64*)c->pin_state;
+    j->DupM_host_lent = true;
+    c->pin_state_lent = true;
+  } else {
+    GWHE_CUDA(cudaHostAlloc((void**)&j->DupM_host, need, cudaHostAllocDefault));
+  }
   for (int jj = 0; jj < n; ++jj) {
     const Ct& src = *j->DupM[jj];
     GWHE_REQUIRE(src.l == l, ST_ELEVEL, "Dup(M_j) at different levels");
@@ -357,11 +382,7 @@ static void spill_dupm(Job* j) {
 // forget Dup(M_j), wherever it lives
 static void drop_dupm(Job* j) {
   j->DupM.clear();
-  if (j->DupM_host) {
-    GWHE_CUDA(cudaStreamSynchronize(j->c->stream));
-    cudaFreeHost(j->DupM_host);
-    j->DupM_host = nullptr;
-  }
+  release_dupm_host(j);
 }
 
 void job_set_host_state(Job* j, int chunk) {

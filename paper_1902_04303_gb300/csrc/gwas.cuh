@@ -53,6 +53,7 @@ struct Job {
   // chunk when dupm_chunk > 0; 0 keeps it on the device)
   int dupm_chunk = 0;
   u64* DupM_host = nullptr;
+  bool DupM_host_lent = false;  // DupM_host is the context's pinned block
   ~Job();
 };
 
