@@ -337,3 +337,35 @@ def test_composed_rp_cp_matvec_equals_alg6_then_alg2():
     # a planted error: a wrong column of A shows up in the result
     bad = c.cp_rp_matvec(c.A[::-1], c.X, vct, d)
     assert np.max(np.abs(o.decrypt_decode(bad).real[:d] - want)) > 1e-2
+
+
+def test_encrypted_circuit_kappa3_matches_o2():
+    """kappa = 3 Bohning iterations (Alg. 9; the paper's HEAAN setting) over
+    O1 with 40 limbs (factored layout, N = 2^10): the decrypted beta equals the
+    FP64 circuit's beta, and b' and -log10 p stay within the acceptance
+    tolerances, with the key switches the level trace predicts."""
+    logN, L, K, dnum = 10, 40, 12, 3
+    n, d, k = 16, 3, 64
+    dat = make_gwas(n, d, k, seed=15)
+    A = gwas_fp64.xtx_inv(dat.X)
+    lay = Layout(logN, n, d, k)
+    o = OracleCKKS(logN=logN, L=L, q0_bits=60, scale_bits=45, K=K, dnum=dnum, seed=14)
+    o.keygen(galois=[galois_rot(logN, r) for r in rotation_steps(lay, factored=True)]
+             + [galois_conj(logN)])
+    hist = _count_switches(o)
+    c = Circuit(o, lay, factored=True)
+    c.encrypt_inputs(dat.X, A, dat.y)
+    c.fit(kappa=3)
+    num, de, do = c.snp_batch_factored(c.encrypt_snp_batch_ccp(dat.S, 0))
+    W = dict(logN=logN, L=L, q0_bits=60, scale_bits=45, K=K, sp_bits=60, dnum=dnum, n=n, d=d, k=k)
+    want, _, _ = job_ks_histogram(W, 3, factored=True)
+    assert np.array_equal(hist, want)
+    ref = gwas_fp64.semi_parallel_fp64(dat.X, dat.y, dat.S, kappa=3, A=A)
+    beta = o.decrypt_decode(c.beta).real[:d]
+    assert np.max(np.abs(beta - ref["beta"])) < 1e-3
+    a, b = c.extract(num, de, do, 0)
+    ok = np.abs(ref["den"]) > 1e-6
+    assert np.max(np.abs(a[ok] / b[ok] - ref["b"][ok])) < 5e-3
+    dl = np.abs(gwas_fp64.neglog10p(a[ok] / b[ok], 1 / b[ok])
+                - gwas_fp64.neglog10p(ref["b"][ok], ref["err"][ok]))
+    assert np.max(dl) < 0.05
