@@ -98,10 +98,23 @@ int gwhe_layout(int logN, int n, long k, long out[5]);
 
 /* ------------------------------------------------------------ context */
 /* Creates a context: primes, NTT / base-conversion / encoding tables on the
- * current CUDA device.  seed keys all randomness.  stream = cudaStream_t or
- * NULL.  On failure *out is NULL and the status says why. */
+ * current CUDA device, which becomes the context's device.  seed keys all
+ * randomness.  stream = cudaStream_t (of that device) or NULL.  Every later
+ * call on the context (and on its ciphertexts, jobs and child contexts) must
+ * be made with that device current, else it returns GWHE_EINVAL and does
+ * nothing; gwhe_ctx_destroy switches to it by itself.  On failure *out is
+ * NULL and the status says why. */
 int gwhe_ctx_create(const gwhe_params* prm, uint64_t seed, void* stream, gwhe_ctx** out);
 int gwhe_ctx_destroy(gwhe_ctx* ctx);
+/* the context's CUDA device */
+int gwhe_ctx_device(const gwhe_ctx* ctx, int* device);
+/* The device rule above as a host-only check: GWHE_OK when current_device
+ * equals context_device (>= 0), else GWHE_EINVAL.  Needs no GPU. */
+int gwhe_device_ok(int context_device, int current_device);
+/* Device memory as the library sees it: out = {bytes in use from the
+ * device's stream-ordered pool, bytes the pool has reserved, free bytes of
+ * the device, total bytes of the device}.  Synchronises nothing. */
+int gwhe_mem_info(gwhe_ctx* ctx, uint64_t out[4]);
 const char* gwhe_last_error(const gwhe_ctx* ctx);
 /* moduli q_0..q_{L-1}, p_0..p_{K-1} (L + K values) */
 int gwhe_ctx_moduli(const gwhe_ctx* ctx, uint64_t* out);
@@ -210,13 +223,14 @@ int gwhe_ntt_batch(gwhe_ctx* ctx, uint64_t* dev, int npoly, int nlimbs, int inve
  * device array (2^22 words) that every GPU loading the library holds until
  * exit; a switch at level l needs (3 l + (ceil(l/alpha) + 2)(l + K)) N words,
  * larger requests return GWHE_EINVAL with the sizes in gwhe_last_error.  The
- * first call on a device looks up the array's address with that device
- * current: make that first call before any stream capture.  Every call
- * shares the one array, so calls that overlap on the GPU (other streams,
- * other contexts on the same device) race and must be serialised by the
- * caller.  The array keeps the previous call's contents; nothing in it needs
- * to start at zero.  Allocates nothing while the kernel timers
- * (gwhe_prof_enable) are off. */
+ * array's address on a device is looked up, its module loaded and its memory
+ * committed by gwhe_ctx_create on that device, so the calls themselves
+ * reserve nothing; a call with another device current than the context's
+ * returns GWHE_EINVAL.  Every call shares the one array, so calls that
+ * overlap on the GPU (other streams, other contexts on the same device) race
+ * and must be serialised by the caller.  The array keeps the previous call's
+ * contents; nothing in it needs to start at zero.  Allocates nothing while
+ * the kernel timers (gwhe_prof_enable) are off. */
 int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int l, uint32_t key_id,
                            uint64_t* out_ntt);
 
@@ -333,8 +347,12 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
  *           admission, running, total}; the job's status is returned and the
  *           job is forgotten.
  *   stats:  {admitted, running, waiting, bytes claimed, peak bytes claimed,
- *           budget, jobs run with Dup(M_j) in the host tier}.
- *   destroy: running jobs finish, waiting ones end with GWHE_EINVAL. */
+ *           budget, jobs run with Dup(M_j) in the host tier, most jobs
+ *           running at once, workers alive}.
+ *   destroy: running jobs finish, waiting ones end with GWHE_EINVAL.
+ * Creation waits until every worker has set up its stream and child context
+ * (on ctx's device); if none could, it returns GWHE_ECUDA with the reason in
+ * gwhe_last_error(ctx) rather than a server that would never run a job. */
 typedef struct gwhe_server gwhe_server;
 int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
                        gwhe_server** out);
@@ -342,7 +360,7 @@ int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kap
                        const double* X, const double* XtX_inv, const double* y, const double* S,
                        long* id);
 int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms);
-int gwhe_server_stats(gwhe_server* s, long out[7]);
+int gwhe_server_stats(gwhe_server* s, long out[9]);
 int gwhe_server_destroy(gwhe_server* s);
 
 /* Child context on another stream (void* = cudaStream_t) that shares ctx's

@@ -9,9 +9,13 @@ using namespace gwhe;
 
 namespace {
 
+// Runs f with exceptions turned into status codes.  A call on a context is
+// refused (GWHE_EINVAL) unless the context's device is current: its tables,
+// keys and pool live there.
 template <class F>
 int guard(Context* c, F&& f) {
   try {
+    if (c) require_device(c);
     f();
     return GWHE_OK;
   } catch (const Error& e) {
@@ -675,6 +679,33 @@ int gwhe_prof_read(gwhe_ctx* ctx, double* ms, double* bytes, long* count) {
   return guard(C(ctx), [&] {
     need(ms && bytes && count, "null output");
     prof_read(C(ctx), ms, bytes, count);
+  });
+}
+
+int gwhe_device_ok(int context_device, int current_device) {
+  return device_check(context_device, current_device);
+}
+
+int gwhe_ctx_device(const gwhe_ctx* ctx, int* device) {
+  if (!ctx || !ctx->c || !device) return GWHE_EINVAL;
+  *device = ctx->c->device;
+  return GWHE_OK;
+}
+
+int gwhe_mem_info(gwhe_ctx* ctx, uint64_t out[4]) {
+  return guard(C(ctx), [&] {
+    need(out != nullptr, "null output");
+    cudaMemPool_t pool;
+    GWHE_CUDA(cudaDeviceGetDefaultMemPool(&pool, C(ctx)->device));
+    uint64_t used = 0, reserved = 0;
+    GWHE_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    GWHE_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    size_t fr = 0, tot = 0;
+    GWHE_CUDA(cudaMemGetInfo(&fr, &tot));
+    out[0] = used;
+    out[1] = reserved;
+    out[2] = fr;
+    out[3] = tot;
   });
 }
 

@@ -137,6 +137,11 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   c->nmod = P.L + P.K;
   c->seed = seed;
   c->stream = stream;
+  GWHE_CUDA(cudaGetDevice(&c->device));
+  // the allocation-free key switch's scratch array: its module is loaded and
+  // its memory committed here, on this device, so that the entry point's
+  // calls themselves reserve nothing
+  c->noalloc_scratch = noalloc_scratch_lookup();
   const int N = c->N, L = P.L, K = P.K, nm = c->nmod;
   c->mod.resize(nm);
   if (gen_primes(P.logN, L, P.q0_bits, P.scale_bits, K, P.sp_bits, c->mod.data(),
@@ -147,9 +152,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
 
   // stream-ordered pool: keep freed blocks for reuse
   cudaMemPool_t pool;
-  int dev = 0;
-  GWHE_CUDA(cudaGetDevice(&dev));
-  GWHE_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  GWHE_CUDA(cudaDeviceGetDefaultMemPool(&pool, c->device));
   uint64_t thr = UINT64_MAX;
   GWHE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
 
@@ -410,6 +413,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
 Context* ctx_child(const Context* base, cudaStream_t stream) {
   GWHE_REQUIRE(base && !base->parent, ST_EINVAL, "a child needs a root context");
   GWHE_REQUIRE(base->have_keys, ST_ENOKEY, "generate the keys before making child contexts");
+  require_device(base);
   std::unique_ptr<Context> c(new Context(*base));
   c->parent = base;
   c->stream = stream;
@@ -427,8 +431,30 @@ Context* ctx_child(const Context* base, cudaStream_t stream) {
   return c.release();
 }
 
+int device_check(int context_device, int current_device) {
+  return (context_device >= 0 && current_device == context_device) ? ST_OK : ST_EINVAL;
+}
+
+void require_device(const Context* c) {
+  int cur = -1;
+  GWHE_CUDA(cudaGetDevice(&cur));
+  if (device_check(c->device, cur) != ST_OK)
+    throw Error(ST_EINVAL, "the current CUDA device (" + std::to_string(cur) +
+                               ") is not the context's device (" + std::to_string(c->device) + ")");
+}
+
+// releases the context's memory on its own device and restores the caller's
+static void ctx_destroy_on_device(Context* c);
 void ctx_destroy(Context* c) {
   if (!c) return;
+  int cur = -1;
+  const bool have = cudaGetDevice(&cur) == cudaSuccess;
+  if (have && cur != c->device) cudaSetDevice(c->device);
+  ctx_destroy_on_device(c);
+  if (have && cur != c->device) cudaSetDevice(cur);
+}
+
+static void ctx_destroy_on_device(Context* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->pin_stage)
     if (p) cudaFreeHost(p);

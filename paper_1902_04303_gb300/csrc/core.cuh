@@ -306,6 +306,12 @@ struct Context {
   size_t pin_state_bytes = 0;
   bool pin_state_lent = false;
   Params P;
+  // the CUDA device the context's tables, keys and pool live on (current at
+  // creation); every call must be made with this device current
+  int device = 0;
+  // device address of the allocation-free key switch's static scratch array
+  // on that device (resolved at creation, see noalloc.cu)
+  u64* noalloc_scratch = nullptr;
   int N = 0, logN = 0, alpha = 0, nmod = 0;
   int ntt_variant = 4;         // shape of the N = 2^16 transform (kNttVariants;
                                // 4 = the fastest measured on GB300, see gwhe_autotune)
@@ -387,6 +393,15 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_read(Context* c, double* ms, double* bytes, long* count);
+
+// noalloc.cu: the static scratch array's address on the current device
+// (loads the array's module and commits its memory there)
+u64* noalloc_scratch_lookup();
+
+// ST_OK when current_device is the context's device, else ST_EINVAL
+int device_check(int context_device, int current_device);
+// the context's device must be current (ST_EINVAL otherwise)
+void require_device(const Context* c);
 
 // device memory helpers (stream-ordered pool)
 u64* dalloc_u64(Context* c, size_t words);

@@ -11,11 +11,10 @@
 //
 // The array is a module-level __device__ object: every GPU that loads the
 // library holds it until the process exits.  Host code cannot use its name as
-// a device address; its address is looked up once per device with
-// cudaGetSymbolAddress, on that device, by the first call made there.
-#include <mutex>
-#include <vector>
-
+// a device address; its address on a device is looked up with
+// cudaGetSymbolAddress, with that device current, when a context is created
+// there (ctx_create), which also loads this file's module and commits the
+// array's memory, so the entry point's own calls reserve nothing.
 #include "capi_types.cuh"
 
 using namespace gwhe;
@@ -28,25 +27,19 @@ namespace {
 constexpr size_t kScratchWords = (size_t)1 << 22;
 static __device__ __align__(256) u64 g_ks_scratch[kScratchWords];
 
-// device address of g_ks_scratch on the current device (looked up once)
-u64* scratch_on_current_device() {
-  static std::mutex mu;
-  static std::vector<u64*> addr;
-  int dev = 0;
-  GWHE_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lock(mu);
-  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_ks_scratch);
-    if (e != cudaSuccess)
-      throw Error(ST_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    addr[dev] = (u64*)p;
-  }
-  return addr[dev];
+}  // namespace
+
+namespace gwhe {
+
+u64* noalloc_scratch_lookup() {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_ks_scratch);
+  if (e != cudaSuccess)
+    throw Error(ST_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+  return (u64*)p;
 }
 
-}  // namespace
+}  // namespace gwhe
 
 extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int l,
                                       uint32_t key_id, uint64_t* out_ntt) {
@@ -64,7 +57,10 @@ extern "C" int gwhe_keyswitch_noalloc(gwhe_ctx* ctx, const uint64_t* x_ntt, int 
       throw Error(ST_EINVAL, "keyswitch_noalloc: level " + std::to_string(l) + " needs " +
                                  std::to_string(need) + " scratch words, the static array holds " +
                                  std::to_string(kScratchWords));
-    u64* base = scratch_on_current_device();
+    // the array of the context's device (its keys and tables live there too)
+    require_device(c);
+    u64* base = c->noalloc_scratch;
+    if (!base) throw Error(ST_ECUDA, "keyswitch_noalloc: scratch array not resolved");
     // carve the scratch: nothing in it needs to start at zero (every region
     // is fully written before it is read)
     u64* xc = base;                          // [l][N]  input, coefficient domain

@@ -59,7 +59,11 @@ struct gwhe_server {
   std::condition_variable cv_work, cv_done;
   std::deque<ReqPtr> pending;
   std::map<long, ReqPtr> reqs;
-  long next_id = 1, admitted = 0, running = 0, host_tier = 0;
+  long next_id = 1, admitted = 0, running = 0, host_tier = 0, max_running = 0;
+  // workers that set up their stream and child context / that failed to
+  int live = 0, failed = 0;
+  std::string setup_error;
+  std::condition_variable cv_setup;
   bool stop = false;
 };
 
@@ -121,13 +125,27 @@ void worker_main(gwhe_server* srv) {
   cudaStream_t st = nullptr;
   Context* c = nullptr;
   try {
+    // a new thread starts on device 0: the stream and the child context
+    // belong on the owner's device, with its keys and tables
+    GWHE_CUDA(cudaSetDevice(srv->owner->c->device));
     GWHE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     c = ctx_child(srv->owner->c, st);
-  } catch (...) {
+  } catch (const std::exception& e) {
     // without a context this worker takes no work; the others carry on
     if (st) cudaStreamDestroy(st);
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      ++srv->failed;
+      srv->setup_error = e.what();
+    }
+    srv->cv_setup.notify_all();
     return;
   }
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    ++srv->live;
+  }
+  srv->cv_setup.notify_all();
   for (;;) {
     ReqPtr r;
     {
@@ -149,6 +167,7 @@ void worker_main(gwhe_server* srv) {
       srv->peak = std::max(srv->peak, srv->in_use);
       ++srv->admitted;
       ++srv->running;
+      srv->max_running = std::max(srv->max_running, srv->running);
       if (r->dupm_chunk > 0) ++srv->host_tier;
       r->t_start = now_ms();
     }
@@ -193,6 +212,13 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
     return GWHE_EINVAL;
   *out = nullptr;
   Context* c = ctx->c;
+  if (device_check(c->device, [] {
+        int d = -1;
+        return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+      }()) != ST_OK) {
+    c->last_error = "server: the current CUDA device is not the context's device";
+    return GWHE_EINVAL;
+  }
   if (!c->have_keys) {
     c->last_error = "server: generate the keys first";
     return GWHE_ENOKEY;
@@ -207,6 +233,19 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
   }
   s->budget = hbm_budget;
   for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s.get());
+  {
+    // every worker has set up or failed; with none alive, no job could ever
+    // run (a submitted job would wait forever), so creation fails
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_setup.wait(lk, [&] { return s->live + s->failed == workers; });
+    if (s->live == 0) {
+      c->last_error = "server: no worker could set up its stream and context: " + s->setup_error;
+      s->stop = true;
+      lk.unlock();
+      for (auto& t : s->workers) t.join();
+      return GWHE_ECUDA;
+    }
+  }
   *out = s.release();
   return GWHE_OK;
 }
@@ -290,9 +329,11 @@ int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* 
   return GWHE_OK;
 }
 
-int gwhe_server_stats(gwhe_server* s, long out[7]) {
+int gwhe_server_stats(gwhe_server* s, long out[9]) {
   if (!s || !out) return GWHE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
+  out[7] = s->max_running;
+  out[8] = s->live;
   out[0] = s->admitted;
   out[1] = s->running;
   out[2] = (long)s->pending.size();

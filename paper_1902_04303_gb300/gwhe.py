@@ -117,6 +117,9 @@ _SIGS = {
     "gwhe_prof_enable": [_vp, _i],
     "gwhe_ks_histogram": [_vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS"), _i],
     "gwhe_prof_read": [_vp, _f64p, _f64p, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")],
+    "gwhe_ctx_device": [_vp, ctypes.POINTER(_i)],
+    "gwhe_device_ok": [_i, _i],
+    "gwhe_mem_info": [_vp, np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")],
 }
 
 PROF_CLASSES = ("ntt", "ks_inner", "tensor_mac", "baseconv", "elementwise", "encode", "sample")
@@ -506,6 +509,17 @@ class Context:
         self._c(lib().gwhe_prof_read(self.h, ms, by, n))
         return {k: (float(ms[i]), float(by[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}
 
+    def device(self):
+        d = _i(0)
+        self._c(lib().gwhe_ctx_device(self.h, ctypes.byref(d)))
+        return d.value
+
+    def mem_info(self):
+        """{pool_used, pool_reserved, free, total} bytes of the context's device"""
+        out = np.zeros(4, np.uint64)
+        self._c(lib().gwhe_mem_info(self.h, out))
+        return dict(zip(("pool_used", "pool_reserved", "free", "total"), (int(v) for v in out)))
+
     def keyswitch_noalloc(self, x_dev, l, key_id, out_dev):
         """Key switch of device rows x_dev[l][N] (NTT domain) into out_dev
         [2][l][N] using the library's static scratch (no device allocation)."""
@@ -663,10 +677,10 @@ class Server:
         return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2]}
 
     def stats(self):
-        out = (_l * 7)()
+        out = (_l * 9)()
         self.ctx._c(lib().gwhe_server_stats(self.h, out))
         keys = ["admitted", "running", "waiting", "bytes_claimed", "peak_bytes_claimed", "budget",
-                "host_tier_jobs"]
+                "host_tier_jobs", "max_running", "live_workers"]
         return {kk: int(v) for kk, v in zip(keys, out)}
 
     def close(self):

@@ -73,3 +73,14 @@ def test_layout_matches_paper_and_oracle(g):
 def test_bad_parameters_are_rejected_without_gpu(g):
     with pytest.raises(g.GwheError):
         g.gen_primes(g.params(16, 24, K=200))
+
+
+def test_device_rule_without_gpu(g):
+    """A call on a context is refused unless the context's device is current:
+    the host-side check behind every entry point (no GPU is touched)."""
+    lib = g.lib()
+    assert lib.gwhe_device_ok(0, 0) == 0
+    assert lib.gwhe_device_ok(3, 3) == 0
+    assert lib.gwhe_device_ok(1, 0) == -1  # worker thread left on device 0
+    assert lib.gwhe_device_ok(0, 1) == -1
+    assert lib.gwhe_device_ok(-1, -1) == -1  # no device recorded
