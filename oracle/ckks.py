@@ -76,6 +76,8 @@ def lib():
         "or_encode": (None, [i32, _f64p, dbl, _i64p]),
         "or_to_rns": (None, [vp, _i64p, i32, _u64p]),
         "or_to_rns_mods": (None, [i32, _i64p, _u64p, i32, _u64p]),
+        "or_set_threads": (None, [i32]),
+        "or_get_threads": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -40,6 +40,37 @@ typedef unsigned __int128 u128;
 
 #define OR_MAXMOD 128
 
+/* Independent limbs, polynomials and coefficients may be computed by several
+ * host threads (OpenMP when the compiler has it).  Every output is computed by
+ * one thread in the same order as the serial loop, so results do not depend
+ * on the thread count. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#define OR_PARALLEL_FOR_COLLAPSE2 _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define OR_PARALLEL_FOR
+#define OR_PARALLEL_FOR_COLLAPSE2
+#endif
+
+/* number of host threads the loops above use (1 without OpenMP) */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* scalar modular arithmetic                                            */
 /* ------------------------------------------------------------------ */
@@ -410,18 +441,20 @@ void or_keygen_pk(const void *ctx, u64 *b, u64 *a)
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N;
     i64 *s = (i64 *)malloc(sizeof(i64) * N), *e = (i64 *)malloc(sizeof(i64) * N);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
     or_sample_cbd(c->seed, OBJ_PK_E, c->logN, e);
+    OR_PARALLEL_FOR
     for (int i = 0; i < c->L; i++) {
         u64 q = c->mod[i];
+        u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
         u64 *ai = a + (size_t)i * N, *bi = b + (size_t)i * N;
         or_sample_uniform(c->seed, OBJ_PK_A, (u32)i, q, c->logN, ai);
         for (int k = 0; k < N; k++) sr[k] = mred_i64(s[k], q);
         or_polymul(ai, sr, t, c->logN, q, c->psi[i]);
         for (int k = 0; k < N; k++) bi[k] = madd(msub(0, t[k], q), mred_i64(e[k], q), q);
+        free(sr); free(t);
     }
-    free(s); free(e); free(sr); free(t);
+    free(s); free(e);
 }
 
 /* Switching key from target t (residues over all L+K moduli, [L+K][N]) to s,
@@ -436,12 +469,13 @@ void or_keygen_ksk(const void *ctx, u32 key_id, int k, int lmax, const u64 *targ
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N, nm = lmax + k, dk = (lmax + c->alpha - 1) / c->alpha;
     i64 *s = (i64 *)malloc(sizeof(i64) * N), *e = (i64 *)malloc(sizeof(i64) * N);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
     for (int j = 0; j < dk; j++) {
         or_sample_cbd(c->seed, OBJ_KSK_E(key_id, k, j), c->logN, e);
         int lo = j * c->alpha, hi = lo + c->alpha < lmax ? lo + c->alpha : lmax;
+        OR_PARALLEL_FOR
         for (int u = 0; u < nm; u++) {
+            u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
             int gm = u < lmax ? u : c->L + (u - lmax); /* index into mod[] */
             u64 m = c->mod[gm];
             u64 *bj = out + (((size_t)j * 2 + 0) * nm + u) * N;
@@ -457,9 +491,10 @@ void or_keygen_ksk(const void *ctx, u32 key_id, int k, int lmax, const u64 *targ
                 if (in_digit) v = madd(v, mmul(Pm, target[(size_t)gm * N + kk], m), m);
                 bj[kk] = v;
             }
+            free(sr); free(t);
         }
     }
-    free(s); free(e); free(sr); free(t);
+    free(s); free(e);
 }
 
 /* residues of s^2 and of s(X^g) over all L+K moduli ([L+K][N]) */
@@ -468,13 +503,15 @@ void or_sk_square(const void *ctx, u64 *out)
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N, nm = c->L + c->K;
     i64 *s = (i64 *)malloc(sizeof(i64) * N);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
+    OR_PARALLEL_FOR
     for (int u = 0; u < nm; u++) {
+        u64 *sr = (u64 *)malloc(sizeof(u64) * N);
         for (int k = 0; k < N; k++) sr[k] = mred_i64(s[k], c->mod[u]);
         or_polymul(sr, sr, out + (size_t)u * N, c->logN, c->mod[u], c->psi[u]);
+        free(sr);
     }
-    free(s); free(sr);
+    free(s);
 }
 
 /* automorphism X -> X^g on one residue polynomial: coefficient i moves to
@@ -494,13 +531,15 @@ void or_sk_galois(const void *ctx, u64 g, u64 *out)
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N, nm = c->L + c->K;
     i64 *s = (i64 *)malloc(sizeof(i64) * N);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
+    OR_PARALLEL_FOR
     for (int u = 0; u < nm; u++) {
+        u64 *sr = (u64 *)malloc(sizeof(u64) * N);
         for (int k = 0; k < N; k++) sr[k] = mred_i64(s[k], c->mod[u]);
         or_automorphism(sr, out + (size_t)u * N, c->logN, g, c->mod[u]);
+        free(sr);
     }
-    free(s); free(sr);
+    free(s);
 }
 
 /* ------------------------------------------------------------------ */
@@ -515,12 +554,13 @@ void or_encrypt(const void *ctx, const u64 *m, int l, u64 enc_id, const u64 *pk_
     const int N = c->N;
     i64 *v = (i64 *)malloc(sizeof(i64) * N), *e0 = (i64 *)malloc(sizeof(i64) * N),
         *e1 = (i64 *)malloc(sizeof(i64) * N);
-    u64 *vr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
     or_sample_ternary(c->seed, OBJ_ENC_V(enc_id), c->logN, v);
     or_sample_cbd(c->seed, OBJ_ENC_E0(enc_id), c->logN, e0);
     or_sample_cbd(c->seed, OBJ_ENC_E1(enc_id), c->logN, e1);
+    OR_PARALLEL_FOR
     for (int i = 0; i < l; i++) {
         u64 q = c->mod[i];
+        u64 *vr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
         for (int k = 0; k < N; k++) vr[k] = mred_i64(v[k], q);
         u64 *c0 = ct + (size_t)i * N, *c1 = ct + ((size_t)l + i) * N;
         or_polymul(vr, pk_b + (size_t)i * N, t, c->logN, q, c->psi[i]);
@@ -528,8 +568,9 @@ void or_encrypt(const void *ctx, const u64 *m, int l, u64 enc_id, const u64 *pk_
             c0[k] = madd(madd(t[k], m[(size_t)i * N + k], q), mred_i64(e0[k], q), q);
         or_polymul(vr, pk_a + (size_t)i * N, t, c->logN, q, c->psi[i]);
         for (int k = 0; k < N; k++) c1[k] = madd(t[k], mred_i64(e1[k], q), q);
+        free(vr); free(t);
     }
-    free(v); free(e0); free(e1); free(vr); free(t);
+    free(v); free(e0); free(e1);
 }
 
 /* m = c0 + c1 s mod q_i; ct is [2][l][N], m is [l][N] */
@@ -538,15 +579,17 @@ void or_decrypt(const void *ctx, const u64 *ct, int l, u64 *m)
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N;
     i64 *s = (i64 *)malloc(sizeof(i64) * N);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
     or_keygen_sk(ctx, s);
+    OR_PARALLEL_FOR
     for (int i = 0; i < l; i++) {
         u64 q = c->mod[i];
+        u64 *sr = (u64 *)malloc(sizeof(u64) * N), *t = (u64 *)malloc(sizeof(u64) * N);
         for (int k = 0; k < N; k++) sr[k] = mred_i64(s[k], q);
         or_polymul(ct + ((size_t)l + i) * N, sr, t, c->logN, q, c->psi[i]);
         for (int k = 0; k < N; k++) m[(size_t)i * N + k] = madd(ct[(size_t)i * N + k], t[k], q);
+        free(sr); free(t);
     }
-    free(s); free(sr); free(t);
+    free(s);
 }
 
 /* ------------------------------------------------------------------ */
@@ -558,6 +601,7 @@ void or_mul_plain(const void *ctx, const u64 *a, int npoly, const u64 *b, int l,
 {
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N;
+    OR_PARALLEL_FOR_COLLAPSE2
     for (int p = 0; p < npoly; p++)
         for (int i = 0; i < l; i++)
             or_polymul(a + ((size_t)p * l + i) * N, b + (size_t)i * N,
@@ -569,9 +613,10 @@ void or_tensor(const void *ctx, const u64 *a, const u64 *b, int l, u64 *out)
 {
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N;
-    u64 *t = (u64 *)malloc(sizeof(u64) * N);
+    OR_PARALLEL_FOR
     for (int i = 0; i < l; i++) {
         u64 q = c->mod[i];
+        u64 *t = (u64 *)malloc(sizeof(u64) * N);
         const u64 *a0 = a + (size_t)i * N, *a1 = a + ((size_t)l + i) * N;
         const u64 *b0 = b + (size_t)i * N, *b1 = b + ((size_t)l + i) * N;
         u64 *d0 = out + (size_t)i * N, *d1 = out + ((size_t)l + i) * N,
@@ -581,8 +626,8 @@ void or_tensor(const void *ctx, const u64 *a, const u64 *b, int l, u64 *out)
         or_polymul(a0, b1, d1, c->logN, q, c->psi[i]);
         or_polymul(a1, b0, t, c->logN, q, c->psi[i]);
         for (int k = 0; k < N; k++) d1[k] = madd(d1[k], t[k], q);
+        free(t);
     }
-    free(t);
 }
 
 /* rescale (paper: Rescale) in RNS form: drops q_{l-1}.  For the CRT integer
@@ -594,9 +639,10 @@ void or_rescale(const void *ctx, const u64 *in, int npoly, int l, u64 *out)
     const or_ctx *c = (const or_ctx *)ctx;
     const int N = c->N;
     const u64 ql = c->mod[l - 1], h = ql / 2;
+    OR_PARALLEL_FOR_COLLAPSE2
     for (int p = 0; p < npoly; p++) {
-        const u64 *last = in + ((size_t)p * l + (l - 1)) * N;
         for (int i = 0; i < l - 1; i++) {
+            const u64 *last = in + ((size_t)p * l + (l - 1)) * N;
             u64 q = c->mod[i];
             u64 qlinv = minv(ql % q, q);
             const u64 *ci = in + ((size_t)p * l + i) * N;
@@ -671,7 +717,6 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
     }
     u64 *ext = (u64 *)malloc(sizeof(u64) * (size_t)beta * ne * N);
     u64 *acc = (u64 *)calloc((size_t)2 * ne * N, sizeof(u64));
-    u64 *t = (u64 *)malloc(sizeof(u64) * N);
     /* ModUp, digit by digit */
     for (int j = 0; j < beta; j++) {
         int lo = j * c->alpha, hi = lo + c->alpha < l ? lo + c->alpha : l;
@@ -688,6 +733,7 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
                 hmod[i - lo][u] = h;
             }
         }
+        OR_PARALLEL_FOR
         for (int k = 0; k < N; k++) {
             u64 y[OR_MAXMOD];
             for (int i = lo; i < hi; i++) y[i - lo] = mmul(x[(size_t)i * N + k], hinv[i - lo], c->mod[i]);
@@ -702,11 +748,12 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
     /* inner product with the key (or the sum over the automorphisms' keys) */
     const int dk = (key_lmax + c->alpha - 1) / c->alpha;
     const size_t fam_words = (size_t)dk * 2 * nm * N;
-    u64 *sg = (u64 *)malloc(sizeof(u64) * N);
     for (int gi = 0; gi < (ngal > 0 ? ngal : 1); gi++) {
         const u64 *key = ksk + (size_t)gi * fam_words;
+        OR_PARALLEL_FOR_COLLAPSE2
         for (int pz = 0; pz < 2; pz++)
             for (int u = 0; u < ne; u++) {
+                u64 *t = (u64 *)malloc(sizeof(u64) * N), *sg = (u64 *)malloc(sizeof(u64) * N);
                 u64 m = emod[u];
                 u64 psi = u < l ? c->psi[u] : c->psi[L + (u - l)];
                 u64 *a = acc + ((size_t)pz * ne + u) * N;
@@ -720,9 +767,9 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
                     or_polymul(ej, kj, t, c->logN, m, psi);
                     for (int k = 0; k < N; k++) a[k] = madd(a[k], t[k], m);
                 }
+                free(t); free(sg);
             }
     }
-    free(sg);
     if (fuse) {
         /* ModDown fused with the rescale: divide y = acc + P (d0, d1) by
          * P' = P q_{l-1} through B' = {p_0..p_{K-1}, q_{l-1}} */
@@ -759,6 +806,7 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
         }
         for (int pz = 0; pz < 2; pz++) {
             const u64 *a = acc + (size_t)pz * ne * N, *d = fuse + (size_t)pz * l * N;
+            OR_PARALLEL_FOR
             for (int k = 0; k < N; k++) {
                 u64 z[OR_MAXMOD];
                 for (int j = 0; j < nb; j++) {
@@ -775,7 +823,7 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
                 }
             }
         }
-        free(ext); free(acc); free(t);
+        free(ext); free(acc);
         return;
     }
     /* ModDown */
@@ -799,6 +847,7 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
     }
     for (int pz = 0; pz < 2; pz++) {
         const u64 *a = acc + (size_t)pz * ne * N;
+        OR_PARALLEL_FOR
         for (int k = 0; k < N; k++) {
             u64 z[OR_MAXMOD];
             for (int kk = 0; kk < K; kk++)
@@ -810,7 +859,7 @@ static void keyswitch_sum(const or_ctx *c, const u64 *x, int l, int ngal, const 
             }
         }
     }
-    free(ext); free(acc); free(t);
+    free(ext); free(acc);
 }
 
 /* ------------------------------------------------------------------ */

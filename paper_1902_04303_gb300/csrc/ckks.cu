@@ -705,7 +705,7 @@ void op_tensor_mac(Context* c, const std::vector<std::pair<const Ct*, const Ct*>
   GWHE_CUDA(cudaMemcpyAsync(dp.p, hp.data(), sizeof(MacPair) * hp.size(), cudaMemcpyHostToDevice,
                             c->stream));
   GWHE_REQUIRE(out3.npoly == 3 && out3.cap >= l, ST_EINVAL, "tensor output too small");
-  tensor_mac(c, pv(out3), dp.as<MacPair>(), (int)hp.size(), l);
+  tensor_mac_set(c, pv(out3), 0, dp.as<MacPair>(), (int)hp.size(), 1, l);
   out3.l = l;
   out3.scale = terms[0].first->scale * terms[0].second->scale;
 }

@@ -74,42 +74,6 @@ __global__ void k_add_plain0(PolyView ct, const u64* __restrict__ pt, int N,
   *p = addmod(*p, pt[(size_t)i * N + k], mod[i].q);
 }
 
-// Sum over pairs of (a0 b0, a0 b1 + a1 b0, a1 b1), 128-bit accumulation with a
-// reduction every 32 pairs (at most 64 products of < 2^120 per accumulator).
-__global__ void k_tensor_mac(PolyView out, const MacPair* __restrict__ pairs, int npairs, int l,
-                             int N, const DevMod* __restrict__ mod) {
-  const int i = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  const DevMod m = mod[i];
-  Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
-  u64 r0 = 0, r1 = 0, r2 = 0;
-  const size_t off = (size_t)i * N + k;
-  for (int j = 0; j < npairs; ++j) {
-    const MacPair P = pairs[j];
-    const u64 a0 = P.a[off], a1 = P.a[(size_t)P.capa * N + off];
-    const u64 b0 = P.b[off], b1 = P.b[(size_t)P.capb * N + off];
-    mac128(s0, a0, b0);
-    mac128(s1, a0, b1);
-    mac128(s1, a1, b0);
-    mac128(s2, a1, b1);
-    if ((j & 31) == 31) {
-      r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
-      r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
-      r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
-      s0 = Acc128{0, 0};
-      s1 = Acc128{0, 0};
-      s2 = Acc128{0, 0};
-    }
-  }
-  r0 = addmod(r0, reduce128(s0.lo, s0.hi, m), m.q);
-  r1 = addmod(r1, reduce128(s1.lo, s1.hi, m), m.q);
-  r2 = addmod(r2, reduce128(s2.lo, s2.hi, m), m.q);
-  out.d[off] = r0;
-  out.d[(size_t)out.cap * N + off] = r1;
-  out.d[(size_t)2 * out.cap * N + off] = r2;
-}
-
 // ------------------------------------------------------------- base conversion
 constexpr int kMaxConvIn = 16;
 struct ConvArgs {
@@ -530,7 +494,9 @@ __global__ void k_mask_set(const MaskItem* __restrict__ items, u64* __restrict__
 }
 
 // out[item] = sum over the item's npairs pairs of the tensor products
-// (accumulate: out[item] += that sum)
+// (a0 b0, a0 b1 + a1 b0, a1 b1), on 128 bits with a reduction every 32 pairs
+// (at most 64 products below 2^120 per accumulator); accumulate: out[item] +=
+// that sum.  One item is the single tensor sum of the CP-REP inner loop.
 __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair* __restrict__ pairs,
                                  int npairs, int l, int N, int accumulate,
                                  const DevMod* __restrict__ mod) {
@@ -1144,14 +1110,6 @@ void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt) {
   ProfScope ps(c, PROF_ELEMWISE, 3.0 * l * 8.0 * c->N);
   if (l == 0) return;
   k_add_plain0<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, pt, c->N, c->d_mod);
-  GWHE_LAUNCHED(c, 1);
-}
-
-void tensor_mac(Context* c, PolyView out3, const MacPair* d_pairs, int npairs, int l) {
-  ProfScope ps(c, PROF_TENSOR_MAC, (4.0 * npairs + 3.0) * l * 8.0 * c->N);
-  if (l == 0) return;
-  k_tensor_mac<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(out3, d_pairs, npairs, l, c->N,
-                                                               c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 

@@ -42,8 +42,6 @@ void ew_add_scalar_poly0(Context* c, PolyView ct, int l, const u64* v);
 void ew_mul_plain(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* pt);
 // c0 += pt
 void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt);
-// out (3 polys) = sum over pairs of the tensor (a0 b0, a0 b1 + a1 b0, a1 b1)
-void tensor_mac(Context* c, PolyView out3, const MacPair* d_pairs, int npairs, int l);
 
 // key switching pieces, over cnt items (strides in words).  A switch at level
 // l uses K = ks_k[l] special primes; ext rows: for each digit j, ne = l + K

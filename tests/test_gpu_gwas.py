@@ -398,3 +398,92 @@ def test_mccp_host_tier_state(g, chunk):
     assert all(np.array_equal(a, b) for ra, rb in zip(*res) for a, b in zip(ra, rb))
     with pytest.raises(g.GwheError):
         g.Job(ctx, n, d, k, layout="mccp").set_host_state(-1)
+
+
+def _oracle_job(W, lay, steps, data, A, factored, nonce=0):
+    o = OracleCKKS(logN=W["logN"], L=W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
+    o.keygen(galois=[galois_rot(W["logN"], r) for r in steps] + [galois_conj(W["logN"])])
+    c = Circuit(o, lay, factored=factored, nonce=nonce)
+    c.encrypt_inputs(data.X, A, data.y)
+    c.fit(kappa=1)
+    return c
+
+
+def test_factored_job_bit_exact_on_two_pass_transforms_and_full_groups(g):
+    """The factored job at N = 2^12, the smallest ring on the two-pass
+    transform (with its ModDown epilogue) that the paper-shaped job runs on:
+    12 batches in one set (the last ragged, 100 SNPs), so the colSum ladder's
+    one-digit hoisted inner product walks 36 items (a full group of 32 and a
+    ragged one).  The covariate state (beta, z, z', masked w, Dup(X_c),
+    Dup((XA)_c), Dup(w), Dup(w z')) and the outputs of the first and the
+    ragged last batch equal the oracle's circuit, which computes its own
+    state batch by batch."""
+    W = dict(logN=12, L=21, q0_bits=60, scale_bits=40, K=7, sp_bits=60, dnum=3, seed=14,
+             n=16, d=3, k=11 * 256 + 100)
+    data = make_gwas(W["n"], W["d"], W["k"], seed=8)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(W["logN"], W["n"], W["d"], W["k"])
+    assert lay.tau == 256 and lay.batches == 12
+    steps = rotation_steps(lay, factored=True)
+    ctx = g.Context(W["logN"], W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
+    ctx.keygen(rot_steps=steps, conj=True)
+    job = g.Job(ctx, W["n"], W["d"], W["k"], layout="factored")
+    job.set_nonce(5)
+    ks0 = ctx.ks_histogram().copy()
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    want_h, _, _ = job_ks_histogram(W, 1, factored=True)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want_h)
+    c = _oracle_job(W, lay, steps, data, A, factored=True, nonce=5)
+    for which, ref in ((7, c.beta), (9, c.z), (6, c.zp), (10, c.w_m), (4, c.DupW),
+                       (5, c.DupWZ)):
+        assert np.array_equal(job.ct(which).export(), ref.c), which
+    for cc in range(W["d"]):
+        assert np.array_equal(job.ct(11, cc).export(), c.DupX[cc].c), cc
+        assert np.array_equal(job.ct(12, cc).export(), c.DupB[cc].c), cc
+    for bi in (0, lay.batches - 1):
+        want = c.snp_batch_factored(c.encrypt_snp_batch_ccp(data.S, bi))
+        for which in range(3):
+            assert np.array_equal(job.ct(which, bi).export(), want[which].c), (bi, which)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, W["k"])
+
+
+def test_mccp_job_bit_exact_with_64_pair_tensor_sums(g):
+    """The paper's own M-CCP layout at N = 2^12 with 64 samples: each batch's
+    S' is a tensor sum of 64 pairs (two 32-pair partial reductions) over all
+    four batches of one set, the last ragged (8 SNPs); Dup(M_j) spans both
+    CCP ciphertexts of M.  M, Dup(M_j), beta, z' and the first and last
+    batch outputs equal the oracle's circuit."""
+    W = dict(logN=12, L=21, q0_bits=60, scale_bits=40, K=7, sp_bits=60, dnum=3, seed=13,
+             n=64, d=3, k=200)
+    data = make_gwas(W["n"], W["d"], W["k"], seed=7)
+    A = gwas_fp64.xtx_inv(data.X)
+    lay = Layout(W["logN"], W["n"], W["d"], W["k"])
+    assert lay.nb == 64 and lay.B == 32 and lay.H == 2 and lay.batches == 4
+    steps = rotation_steps(lay)
+    ctx = g.Context(W["logN"], W["L"], K=W["K"], dnum=W["dnum"], seed=W["seed"])
+    ctx.keygen(rot_steps=steps, conj=True)
+    job = g.Job(ctx, W["n"], W["d"], W["k"], layout="mccp")
+    ks0 = ctx.ks_histogram().copy()
+    job.encrypt_inputs(data.X, A, data.y)
+    job.fit(1)
+    job.snp_stats(data.S)
+    want_h, _, _ = job_ks_histogram(W, 1)
+    assert np.array_equal(ctx.ks_histogram() - ks0, want_h)
+    c = _oracle_job(W, lay, steps, data, A, factored=False)
+    assert np.array_equal(job.ct(7).export(), c.beta.c)
+    assert np.array_equal(job.ct(6).export(), c.zp.c)
+    for h in range(lay.H):
+        assert np.array_equal(job.ct(8, h).export(), c.Mct[h].c), h
+    for jj in (0, 31, 32, 63):
+        assert np.array_equal(job.ct(3, jj).export(), c.DupM[jj].c), jj
+    for bi in (0, lay.batches - 1):
+        want = c.snp_batch(c.encrypt_snp_batch(data.S, bi))
+        for which in range(3):
+            assert np.array_equal(job.ct(which, bi).export(), want[which].c), (bi, which)
+    num, den = job.decrypt_results()
+    ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
+    check_accuracy(num, den, ref, W["k"])

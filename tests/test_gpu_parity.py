@@ -316,3 +316,51 @@ def test_autotune_picks_a_shape(g):
     v, ms = ctx.autotune(rows=64)
     assert 0 <= v < 6 and len(ms) == 6 and all(x > 0 for x in ms)
     assert ms[v] == min(ms)
+
+
+# ------------------------------------------------------------------ the job's basis, set widths
+@pytest.fixture(scope="module")
+def paper_basis(g):
+    """The paper-shaped job's ring and basis: N = 2^16, 24 q-limbs (60 + 23 x
+    45 bits), 8 special primes of 60 bits, dnum = 3, with the keys of one
+    hoisted ladder group (rotations 1..7), on both sides."""
+    logN, L, K, dnum, seed = 16, 24, 8, 3, 29
+    rot = (1, 2, 3, 4, 5, 6, 7)
+    ctx = g.Context(logN, L, q0_bits=60, scale_bits=45, K=K, sp_bits=60, dnum=dnum, seed=seed)
+    ctx.keygen(rot_steps=rot, conj=False)
+    o = OracleCKKS(logN=logN, L=L, q0_bits=60, scale_bits=45, K=K, sp_bits=60, dnum=dnum,
+                   seed=seed)
+    o.keygen(galois=[galois_rot(logN, r) for r in rot])
+    return ctx, o
+
+
+def test_job_width_hoisted_sum_batch_at_paper_basis(g, paper_basis):
+    """66 ciphertexts at 5 limbs (one key digit): the one-digit hoisted inner
+    product walks the set in groups of 32 items (two full groups and a ragged
+    one of 2), as the SNP batches' colSum and broadcast ladders do.  Items
+    from every group equal the oracle's hoisted sum of seven rotations."""
+    ctx, o = paper_basis
+    rs = [1, 2, 3, 4, 5, 6, 7]
+    cnt, l = 66, 5
+    srcs = [rand_ct(o, l, 4000 + i) for i in range(cnt)]
+    outs = ctx.rotate_sum_batch([ctx.import_ct(a.c, a.scale) for a in srcs], rs)
+    for i in (0, 1, 31, 32, 33, 63, 64, 65):
+        assert np.array_equal(outs[i].export(), o.rotate_sum(srcs[i], rs).c), i
+
+
+def test_job_width_tensor_sum_at_paper_basis(g, paper_basis):
+    """A tensor sum of 70 pairs at 4 limbs (the CP-REP inner loop's width:
+    two 32-pair partial reductions and a ragged tail) equals the sum of the
+    oracle's exact negacyclic tensors."""
+    ctx, o = paper_basis
+    npairs, l = 70, 4
+    a = [rand_ct(o, l, 5000 + i) for i in range(npairs)]
+    b = [rand_ct(o, l, 6000 + i) for i in range(npairs)]
+    got = ctx.tensor_sum([(ctx.import_ct(x.c, x.scale), ctx.import_ct(y.c, y.scale))
+                          for x, y in zip(a, b)]).export()
+    q = np.array(o.q[:l], dtype=np.uint64).reshape(1, l, 1)
+    want = np.zeros((3, l, o.N), dtype=np.uint64)
+    for x, y in zip(a, b):
+        want = want + o.tensor(x, y).c  # both below q < 2^60: no wrap
+        want = np.where(want >= q, want - q, want)
+    assert np.array_equal(got, want)
