@@ -119,6 +119,13 @@ const char* gwhe_last_error(const gwhe_ctx* ctx);
 /* moduli q_0..q_{L-1}, p_0..p_{K-1} (L + K values) */
 int gwhe_ctx_moduli(const gwhe_ctx* ctx, uint64_t* out);
 int gwhe_sync(gwhe_ctx* ctx);
+/* Later calls on ctx (and its jobs and ciphertexts) run on `stream`
+ * (cudaStream_t of the context's device, NULL = the legacy default stream).
+ * Work already queued on the previous stream stays ordered before them: the
+ * new stream waits for it.  Memory the library frees later may have come
+ * from the previous stream's pool order; that order is kept by the same
+ * wait. */
+int gwhe_ctx_set_stream(gwhe_ctx* ctx, void* stream);
 
 /* KeyGen (section "Homomorphic Encryption"): secret, public key, the
  * relinearisation key and one switching key per rotation step in rot_steps
@@ -205,6 +212,11 @@ int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int n
  * nsteps <= 7; out[i] != a[j]. */
 int gwhe_rotate_sum_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count,
                           const int32_t* steps, int nsteps, gwhe_ct* const* out);
+/* out[i] = Rotate(a[i], step) for count ciphertexts of one level and scale,
+ * as one set (every launch covers all of them), then with rescale != 0 the
+ * rescale of each; out[i] != a[j]. */
+int gwhe_rotate_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count, int32_t step,
+                      int rescale, gwhe_ct* const* out);
 int gwhe_drop(gwhe_ct* ct, int l);                                          /* keep l limbs */
 /* Hybrid key switch of one coefficient-domain polynomial x (uint64[l][N],
  * host) with key key_id: out = uint64[2][l][N] coefficient domain (host). */
@@ -273,6 +285,23 @@ int gwhe_job_rotation_steps(const gwhe_job* job, int32_t* steps, int cap, int* c
  * pre-processing, section "Hessian Matrix Approximation") as CP, X^T as REP,
  * y (n) and beta0 = Enc(0), all at the top level (Alg. 9 / Alg. 11 inputs). */
 int gwhe_encrypt_inputs(gwhe_job* job, const double* X, const double* XtX_inv, const double* y);
+/* The same ciphertexts as gwhe_encrypt_inputs (same encryption ids, bit for
+ * bit) in the two calls of the paper's problem statement (section
+ * "Semi-Parallel GWAS with Homomorphic Encryption", the server's inputs):
+ * the covariates X (CP), (X^T X)^-1 (CP) and X^T (REP, M-CCP layout only),
+ * then the phenotype y with beta0 = Enc(0).  gwhe_encrypt_inputs does both
+ * in one batched encoding and encryption. */
+int gwhe_encrypt_covariates(gwhe_job* job, const double* X, const double* XtX_inv);
+int gwhe_encrypt_phenotype(gwhe_job* job, const double* y);
+/* Encrypt SNP batches [b0, b1) of S (n x k row-major genotypes, host or
+ * device; streamable: call it for consecutive ranges) ahead of the Alg. 11
+ * loop: factored layout one CCP ciphertext per batch at 6 limbs, M-CCP the n
+ * REP rows of each batch at 4 limbs, with the encryption ids the fused loop
+ * uses, so gwhe_snp_stats(job, NULL, ...) then gives the same ciphertexts bit
+ * for bit.  They stay on the device until the loop consumes them: 96 N bytes
+ * per batch (factored) or 64 n N bytes per batch (M-CCP).  The fused route (gwhe_snp_stats with S) encrypts each set of 64
+ * batches right before its tensor sums and never holds more than one set. */
+int gwhe_encrypt_snps(gwhe_job* job, const double* S, long b0, long b1);
 /* Alg. 9 (kappa iterations), Alg. 10, eqs. z / M / zprime, then Dup(M_j),
  * Dup(w), Dup(w z') for the batches (Alg. 7, Alg. 8). */
 int gwhe_fit_covariates(gwhe_job* job, int kappa);
@@ -280,7 +309,9 @@ int gwhe_fit_covariates(gwhe_job* job, int kappa);
  * row-major), w and w*z' (n) in plaintext; they are duplicated and encrypted. */
 int gwhe_set_fit_state(gwhe_job* job, const double* M, const double* w, const double* wz);
 /* Alg. 11 loop for batches [b0, b1): S is n x k row-major genotypes (host or
- * device; the caller keeps ownership).  Batches run in sets of 64.  A host S
+ * device; the caller keeps ownership), or NULL to take the batches encrypted
+ * by gwhe_encrypt_snps (GWHE_EINVAL if one of them was not; each is freed once
+ * used).  Batches run in sets of 64.  A host S
  * is never copied whole to the device (the host tier, the counterpart of the
  * paper's cache module, section "Smart Cache Module"): each set's columns are
  * gathered into one of two pinned staging buffers by the calling thread and

@@ -98,6 +98,22 @@ int gwhe_ctx_moduli(const gwhe_ctx* ctx, uint64_t* out) {
   return GWHE_OK;
 }
 
+int gwhe_ctx_set_stream(gwhe_ctx* ctx, void* stream) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    const cudaStream_t ns = (cudaStream_t)stream;
+    if (ns == c->stream) return;
+    // work queued so far on the old stream comes first on the new one
+    cudaEvent_t e;
+    GWHE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, c->stream);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(ns, e, 0);
+    cudaEventDestroy(e);
+    GWHE_CUDA(r);
+    c->stream = ns;
+  });
+}
+
 int gwhe_sync(gwhe_ctx* ctx) {
   return guard(C(ctx), [&] { sync(C(ctx)); });
 }
@@ -406,6 +422,39 @@ int gwhe_rotate_sum_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count,
   });
 }
 
+int gwhe_rotate_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count, int32_t step,
+                      int rescale, gwhe_ct* const* out) {
+  return guard(C(ctx), [&] {
+    Context* c = C(ctx);
+    need(a && out && count >= 1, "bad rotation batch");
+    const Ct& x0 = *a[0]->ct;
+    const int l = x0.l;
+    need(!rescale || l >= 2, "no level left to rescale");
+    for (int i = 0; i < count; ++i) {
+      const Ct& x = *a[i]->ct;
+      need(x.npoly == 2 && x.l == l && x.scale == x0.scale, "inputs must share level and scale");
+      need(out[i]->ct->npoly == 2 && out[i]->ct->cap >= l, "output too small");
+    }
+    const size_t N = c->N;
+    CtSetPtr s = set_new(c, count, 2, l, l, x0.scale);
+    for (int i = 0; i < count; ++i)
+      for (int p = 0; p < 2; ++p)
+        GWHE_CUDA(cudaMemcpyAsync(s->item(i) + (size_t)p * l * N, a[i]->ct->poly(p),
+                                  sizeof(u64) * l * N, cudaMemcpyDeviceToDevice, c->stream));
+    CtSetPtr r = set_new(c, count, 2, l, l, x0.scale);
+    set_galois(c, *s, galois_for_rotation(c, step), *r);
+    if (rescale) set_rescale(c, *r);
+    for (int i = 0; i < count; ++i) {
+      Ct& o = *out[i]->ct;
+      for (int p = 0; p < 2; ++p)
+        GWHE_CUDA(cudaMemcpyAsync(o.poly(p), r->item(i) + (size_t)p * r->cap * N,
+                                  sizeof(u64) * r->l * N, cudaMemcpyDeviceToDevice, c->stream));
+      o.l = r->l;
+      o.scale = r->scale;
+    }
+  });
+}
+
 int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out) {
   return guard(C(ctx), [&] { op_conj(C(ctx), CT(a), CT(out)); });
 }
@@ -498,6 +547,30 @@ int gwhe_encrypt_inputs(gwhe_job* job, const double* X, const double* XtX_inv, c
   });
 }
 
+int gwhe_encrypt_covariates(gwhe_job* job, const double* X, const double* XtX_inv) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] {
+    need(X && XtX_inv, "null input");
+    job_encrypt_covariates(job->job.get(), X, XtX_inv);
+  });
+}
+
+int gwhe_encrypt_phenotype(gwhe_job* job, const double* y) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] {
+    need(y != nullptr, "null input");
+    job_encrypt_phenotype(job->job.get(), y);
+  });
+}
+
+int gwhe_encrypt_snps(gwhe_job* job, const double* S, long b0, long b1) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] {
+    need(S != nullptr, "null input");
+    job_encrypt_snps(job->job.get(), S, b0, b1);
+  });
+}
+
 int gwhe_fit_covariates(gwhe_job* job, int kappa) {
   if (!job) return GWHE_EINVAL;
   return guard(C(job->owner), [&] { job_fit(job->job.get(), kappa); });
@@ -514,10 +587,7 @@ int gwhe_set_fit_state(gwhe_job* job, const double* M, const double* w, const do
 int gwhe_snp_stats(gwhe_job* job, const double* S, long b0, long b1, int keep) {
   (void)keep;
   if (!job) return GWHE_EINVAL;
-  return guard(C(job->owner), [&] {
-    need(S, "null input");
-    job_snp_stats(job->job.get(), S, b0, b1);
-  });
+  return guard(C(job->owner), [&] { job_snp_stats(job->job.get(), S, b0, b1); });
 }
 
 int gwhe_decrypt_results(gwhe_job* job, double* num, double* den) {

@@ -407,7 +407,7 @@ Job* job_create(Context* c, int n, int d, long k, int mode) {
 
 void job_set_nonce(Job* j, u32 nonce) {
   GWHE_REQUIRE(nonce <= kMaxNonce, ST_EINVAL, "job nonce out of range");
-  GWHE_REQUIRE(j->X.empty(), ST_EINVAL, "set the nonce before encrypting the inputs");
+  GWHE_REQUIRE(j->X.empty() && !j->y, ST_EINVAL, "set the nonce before encrypting the inputs");
   j->enc_base = (u64)nonce << kNonceShift;
 }
 
@@ -442,43 +442,57 @@ std::vector<int> job_rotation_steps(const Job* j) {
   return s;
 }
 
-void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double* yp) {
+// The Alg. 9 / Alg. 11 inputs at the top level, encryption ids as in the
+// spec: with kInCov X (CP), (X^T X)^-1 (CP) and, in the M-CCP layout, X^T as
+// REP; with kInPheno y and beta0 = Enc(0).  All requested ciphertexts are
+// encoded and encrypted as one batch.
+enum { kInCov = 1, kInPheno = 2 };
+static void encrypt_input_parts(Job* j, const double* Xp, const double* Ap, const double* yp,
+                                int parts) {
   Context* c = j->c;
   const Layout& lay = j->lay;
   const int n = lay.n, d = lay.d, L = c->P.L, M = lay.M;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
-  const std::vector<double> X = to_host(c, Xp, (size_t)n * d), A = to_host(c, Ap, (size_t)d * d),
-                            y = to_host(c, yp, n);
-  // all inputs (X as CP, (X^T X)^-1 as CP, y, beta0 = 0, X^T as REP) in one
-  // batched encryption at the top level; encryption ids as in the spec.  The
-  // factored layout has no CCP matrix M and needs no X^T.
+  const bool cov = parts & kInCov, pheno = parts & kInPheno;
+  std::vector<double> X, A, y;
+  if (cov) {
+    X = to_host(c, Xp, (size_t)n * d);
+    A = to_host(c, Ap, (size_t)d * d);
+  }
+  if (pheno) y = to_host(c, yp, n);
+  // the factored layout has no CCP matrix M and needs no X^T
   const int H = j->factored ? 0 : lay.H;
-  const int cnt = 2 * d + 2 + d * H;
+  const int cnt = (cov ? 2 * d + d * H : 0) + (pheno ? 2 : 0);
   std::vector<double2> z((size_t)cnt * M, make_double2(0, 0));
   std::vector<u64> ids(cnt);
   int it = 0;
-  for (int col = 0; col < d; ++col, ++it) {
-    ids[it] = j->enc_base + kEncX + col;
-    for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(X[(size_t)t * d + col], 0);
-  }
-  for (int col = 0; col < d; ++col, ++it) {
-    ids[it] = j->enc_base + kEncA + col;
-    for (int r = 0; r < d; ++r) z[(size_t)it * M + r] = make_double2(A[(size_t)r * d + col], 0);
-  }
-  ids[it] = j->enc_base + kEncY;
-  for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(y[t], 0);
-  ++it;
-  ids[it++] = j->enc_base + kEncBeta0;
-  for (int col = 0; col < d; ++col)
-    for (int h = 0; h < H; ++h, ++it) {
-      ids[it] = j->enc_base + kEncXtRep + (u64)col * 4096 + h;
-      for (int b = 0; b < lay.B; ++b) {
-        const int s = h * lay.B + b;
-        if (s >= n) continue;
-        for (int t = 0; t < lay.nb; ++t)
-          z[(size_t)it * M + b * lay.nb + t] = make_double2(X[(size_t)s * d + col], 0);
-      }
+  if (cov) {
+    for (int col = 0; col < d; ++col, ++it) {
+      ids[it] = j->enc_base + kEncX + col;
+      for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(X[(size_t)t * d + col], 0);
     }
+    for (int col = 0; col < d; ++col, ++it) {
+      ids[it] = j->enc_base + kEncA + col;
+      for (int r = 0; r < d; ++r) z[(size_t)it * M + r] = make_double2(A[(size_t)r * d + col], 0);
+    }
+  }
+  if (pheno) {
+    ids[it] = j->enc_base + kEncY;
+    for (int t = 0; t < n; ++t) z[(size_t)it * M + t] = make_double2(y[t], 0);
+    ++it;
+    ids[it++] = j->enc_base + kEncBeta0;
+  }
+  if (cov)
+    for (int col = 0; col < d; ++col)
+      for (int h = 0; h < H; ++h, ++it) {
+        ids[it] = j->enc_base + kEncXtRep + (u64)col * 4096 + h;
+        for (int b = 0; b < lay.B; ++b) {
+          const int s = h * lay.B + b;
+          if (s >= n) continue;
+          for (int t = 0; t < lay.nb; ++t)
+            z[(size_t)it * M + b * lay.nb + t] = make_double2(X[(size_t)s * d + col], 0);
+        }
+      }
   CtSetPtr in = set_new(c, cnt, 2, L, L, delta);
   {
     Tmp dz(c, sizeof(double2) * z.size()), did(c, sizeof(u64) * cnt);
@@ -488,18 +502,33 @@ void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double
                               c->stream));
     encrypt_slots(c, dz.as<double2>(), cnt, delta, L, 0, in->d, L, did.u());
   }
-  j->X.clear();
-  j->A.clear();
-  j->XtREP.clear();
-  j->XtREP.resize(d);
   it = 0;
-  for (int col = 0; col < d; ++col) j->X.push_back(in->view(it++));
-  for (int col = 0; col < d; ++col) j->A.push_back(in->view(it++));
-  j->y = in->view(it++);
-  j->beta0 = in->view(it++);
-  for (int col = 0; col < d; ++col)
-    for (int h = 0; h < H; ++h) j->XtREP[col].push_back(in->view(it++));
+  if (cov) {
+    j->X.clear();
+    j->A.clear();
+    j->XtREP.clear();
+    j->XtREP.resize(d);
+    for (int col = 0; col < d; ++col) j->X.push_back(in->view(it++));
+    for (int col = 0; col < d; ++col) j->A.push_back(in->view(it++));
+  }
+  if (pheno) {
+    j->y = in->view(it++);
+    j->beta0 = in->view(it++);
+  }
+  if (cov)
+    for (int col = 0; col < d; ++col)
+      for (int h = 0; h < H; ++h) j->XtREP[col].push_back(in->view(it++));
   j->sets.push_back(std::move(in));
+}
+
+void job_encrypt_inputs(Job* j, const double* Xp, const double* Ap, const double* yp) {
+  encrypt_input_parts(j, Xp, Ap, yp, kInCov | kInPheno);
+}
+void job_encrypt_covariates(Job* j, const double* Xp, const double* Ap) {
+  encrypt_input_parts(j, Xp, Ap, nullptr, kInCov);
+}
+void job_encrypt_phenotype(Job* j, const double* yp) {
+  encrypt_input_parts(j, nullptr, nullptr, yp, kInPheno);
 }
 
 static void make_dup_state(Job* j, Eval& ev) {
@@ -543,7 +572,8 @@ static void make_dup_state(Job* j, Eval& ev) {
 
 void job_fit(Job* j, int kappa) {
   GWHE_REQUIRE(kappa >= 1, ST_EINVAL, "kappa >= 1");
-  GWHE_REQUIRE(!j->X.empty(), ST_EINVAL, "inputs not encrypted");
+  GWHE_REQUIRE(!j->X.empty() && j->y && j->beta0, ST_EINVAL,
+               "inputs not encrypted (covariates and phenotype)");
   Context* c = j->c;
   const Layout& lay = j->lay;
   Eval ev{c, lay};
@@ -858,7 +888,7 @@ struct SnpSrc {
 
 // M-CCP layout: per batch encode + encrypt the n REP rows, then the tensor
 // sum of Alg. 8 (S' = sum_j Dup(M_j) S_ij), relinearise and rescale
-CtSetPtr sprime_mccp(Job* j, const SnpSrc& src, long b0, long b1) {
+CtSetPtr sprime_mccp(Job* j, const SnpSrc* src, long b0, long b1) {
   Context* c = j->c;
   const Layout& lay = j->lay;
   const int n = lay.n, lb = kBatchLevel, N = c->N;
@@ -876,8 +906,10 @@ CtSetPtr sprime_mccp(Job* j, const SnpSrc& src, long b0, long b1) {
     GWHE_REQUIRE(j->DupM[0]->l == lb, ST_ELEVEL, "Dup(M_j) not at the batch level");
     cp.reset(new TwoSlotCopy(c, sizeof(u64) * per * J));
   }
-  Tmp z(c, sizeof(double2) * (size_t)J * lay.M);
-  Tmp sct(c, sizeof(u64) * (size_t)J * per);
+  // the rows are encrypted here from the genotypes (src) or were encrypted
+  // ahead of the loop (job_encrypt_snps)
+  Tmp z(c, src ? sizeof(double2) * (size_t)J * lay.M : 8);
+  Tmp sct(c, src ? sizeof(u64) * (size_t)J * per : 8);
   std::vector<Ct> srow(J), dm(J);
   for (int jj = 0; jj < J; ++jj) {
     srow[jj].ctx = dm[jj].ctx = c;
@@ -901,11 +933,20 @@ CtSetPtr sprime_mccp(Job* j, const SnpSrc& src, long b0, long b1) {
       for (int jj = 0; jj < jn; ++jj) pairs.push_back({j->DupM[j0 + jj].get(), &srow[jj]});
     }
     for (long bi = b0; bi < b1; ++bi) {
-      // REP rows j0 .. j0 + jn of batch bi (encryption ids per sample row)
-      build_snp_rep(c, src.S + (size_t)j0 * src.ld, src.ld, src.col0, jn, lay.k, bi * lay.tau,
-                    lay.nb, lay.B, lay.M, z.as<double2>());
-      encrypt_slots(c, z.as<double2>(), jn, delta, lb,
-                    j->enc_base + kEncS + (u64)bi * n + (u64)j0, sct.u(), lb);
+      std::vector<CtPtr> rows;
+      if (src) {
+        // REP rows j0 .. j0 + jn of batch bi (encryption ids per sample row)
+        build_snp_rep(c, src->S + (size_t)j0 * src->ld, src->ld, src->col0, jn, lay.k,
+                      bi * lay.tau, lay.nb, lay.B, lay.M, z.as<double2>());
+        encrypt_slots(c, z.as<double2>(), jn, delta, lb,
+                      j->enc_base + kEncS + (u64)bi * n + (u64)j0, sct.u(), lb);
+      } else {
+        const Job::EncBatch& e = j->enc_snps.at(bi);
+        for (int jj = 0; jj < jn; ++jj) {
+          rows.push_back(e.set->view(e.first + j0 + jj));
+          pairs[jj].second = rows.back().get();
+        }
+      }
       CtSet t = T3->slice((int)(bi - b0), 1, lb);
       if (j0 > 0) t.scale = T3->scale;
       set_tensor_mac(c, pairs, jn, t, j0 > 0);
@@ -923,19 +964,35 @@ CtSetPtr sprime_mccp(Job* j, const SnpSrc& src, long b0, long b1) {
 //   U_ic = Dup(X_c) S_i; colSum (Alg. 5) puts (X^T S_i)[c, .] at the block heads
 //   R_ic = U_ic masked to the heads, broadcast down the block (right ladder)
 //   S'_i = S_i - sum_c Dup((XA)_c) R_ic   (tensor sum, relinearise, rescale)
-CtSetPtr sprime_factored(Job* j, Eval& ev, const SnpSrc& src, long b0, long b1) {
+// count CCP SNP batches from b0 into out ([count][2][lf][N]), encryption id
+// of batch b = kEncSccp + b
+void encrypt_ccp_batches(Job* j, const SnpSrc& src, long b0, int count, u64* out) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  Tmp z(c, sizeof(double2) * (size_t)count * lay.M);
+  build_snp_ccp(c, src.S, src.ld, src.col0, lay.n, lay.k, b0 * lay.tau, count, lay.tau, lay.nb,
+                lay.B, lay.M, z.as<double2>());
+  encrypt_slots(c, z.as<double2>(), count, delta, kFactLevel, j->enc_base + kEncSccp + (u64)b0,
+                out, kFactLevel);
+}
+
+CtSetPtr sprime_factored(Job* j, Eval& ev, const SnpSrc* src, long b0, long b1) {
   Context* c = j->c;
   const Layout& lay = j->lay;
   const int d = lay.d, lf = kFactLevel, lb = kBatchLevel;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const int nbt = (int)(b1 - b0);
   CtSetPtr Sset = set_new(c, nbt, 2, lf, lf, delta);
-  {
-    Tmp z(c, sizeof(double2) * (size_t)nbt * lay.M);
-    build_snp_ccp(c, src.S, src.ld, src.col0, lay.n, lay.k, b0 * lay.tau, nbt, lay.tau, lay.nb,
-                  lay.B, lay.M, z.as<double2>());
-    encrypt_slots(c, z.as<double2>(), nbt, delta, lf, j->enc_base + kEncSccp + (u64)b0, Sset->d,
-                  lf);
+  if (src) {
+    encrypt_ccp_batches(j, *src, b0, nbt, Sset->d);
+  } else {
+    // the batches encrypted ahead of the loop, gathered into one set
+    for (int i = 0; i < nbt; ++i) {
+      const Job::EncBatch& e = j->enc_snps.at(b0 + i);
+      GWHE_CUDA(cudaMemcpyAsync(Sset->item(i), e.set->item(e.first), sizeof(u64) * Sset->stride(),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    }
   }
   std::vector<CtPtr> sv;
   for (int i = 0; i < nbt; ++i) sv.push_back(Sset->view(i));
@@ -984,7 +1041,60 @@ CtSetPtr sprime_factored(Job* j, Eval& ev, const SnpSrc& src, long b0, long b1) 
   return Sp;
 }
 
+// Runs fn(src, c0, c1) over [b0, b1) in chunks of kSnpChunk batches with the
+// chunk's genotype columns on the device.  Genotypes in host memory (the host
+// tier) are never copied whole: each chunk's columns go through one of two
+// pinned staging buffers (filled by this thread while the device works on the
+// previous chunk) and one of two device buffers (filled by a copy stream that
+// overlaps the compute stream).
+template <class F>
+void for_each_snp_chunk(Job* j, const double* S, long b0, long b1, F&& fn) {
+  const Layout& lay = j->lay;
+  if (is_device_ptr(S)) {
+    for (long c0 = b0; c0 < b1; c0 += kSnpChunk)
+      fn(SnpSrc{S, lay.k, 0}, c0, std::min(b1, c0 + kSnpChunk));
+    return;
+  }
+  HostStager st(j->c, lay.n, std::min<long>(lay.k, (long)kSnpChunk * lay.tau));
+  for (long c0 = b0, i = 0; c0 < b1; c0 += kSnpChunk, ++i) {
+    const long c1 = std::min(b1, c0 + kSnpChunk);
+    const long col0 = c0 * lay.tau, w = std::min(lay.k, c1 * lay.tau) - col0;
+    const double* dev = st.stage((int)(i & 1), S, lay.k, col0, w);
+    fn(SnpSrc{dev, w, col0}, c0, c1);
+    st.release((int)(i & 1));
+  }
+}
+
 }  // namespace
+
+void job_encrypt_snps(Job* j, const double* S, long b0, long b1) {
+  Context* c = j->c;
+  const Layout& lay = j->lay;
+  const int n = lay.n, lb = kBatchLevel, lf = kFactLevel;
+  const double delta = std::ldexp(1.0, c->P.scale_bits);
+  GWHE_REQUIRE(S, ST_EINVAL, "null genotypes");
+  GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
+  for_each_snp_chunk(j, S, b0, b1, [&](const SnpSrc& src, long c0, long c1) {
+    const int nbt = (int)(c1 - c0);
+    if (j->factored) {
+      std::shared_ptr<CtSet> set(set_new(c, nbt, 2, lf, lf, delta).release());
+      encrypt_ccp_batches(j, src, c0, nbt, set->d);
+      for (int i = 0; i < nbt; ++i) j->enc_snps[c0 + i] = Job::EncBatch{set, i};
+      return;
+    }
+    // M-CCP: the n REP rows of every batch (encryption id kEncS + b n + row)
+    std::shared_ptr<CtSet> set(set_new(c, nbt * n, 2, lb, lb, delta).release());
+    Tmp z(c, sizeof(double2) * (size_t)n * lay.M);
+    for (long bi = c0; bi < c1; ++bi) {
+      const int first = (int)(bi - c0) * n;
+      build_snp_rep(c, src.S, src.ld, src.col0, n, lay.k, bi * lay.tau, lay.nb, lay.B, lay.M,
+                    z.as<double2>());
+      encrypt_slots(c, z.as<double2>(), n, delta, lb, j->enc_base + kEncS + (u64)bi * n,
+                    set->item(first), lb);
+      j->enc_snps[bi] = Job::EncBatch{set, first};
+    }
+  });
+}
 
 void job_snp_stats(Job* j, const double* S, long b0, long b1) {
   Context* c = j->c;
@@ -1001,30 +1111,26 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
   GWHE_REQUIRE(0 <= b0 && b0 <= b1 && b1 <= lay.batches, ST_EINVAL, "bad batch range");
   if (b0 == b1) return;
   if ((long)j->out.size() < lay.batches) j->out.resize(lay.batches);
-  auto run_chunk = [&](const SnpSrc& src, long c0, long c1) {
+  auto run_chunk = [&](const SnpSrc* src, long c0, long c1) {
     if (j->factored)
       batch_body(j, ev, sprime_factored(j, ev, src, c0, c1), c0);
     else
       batch_body(j, ev, sprime_mccp(j, src, c0, c1), c0);
   };
-  if (is_device_ptr(S)) {
-    for (long c0 = b0; c0 < b1; c0 += kSnpChunk)
-      run_chunk(SnpSrc{S, lay.k, 0}, c0, std::min(b1, c0 + kSnpChunk));
+  if (!S) {
+    // the batches' ciphertexts from job_encrypt_snps, freed once consumed
+    for (long bi = b0; bi < b1; ++bi)
+      GWHE_REQUIRE(j->enc_snps.count(bi), ST_EINVAL,
+                   "batch " + std::to_string(bi) + " was not encrypted (gwhe_encrypt_snps)");
+    for (long c0 = b0; c0 < b1; c0 += kSnpChunk) {
+      const long c1 = std::min(b1, c0 + kSnpChunk);
+      run_chunk(nullptr, c0, c1);
+      for (long bi = c0; bi < c1; ++bi) j->enc_snps.erase(bi);
+    }
     return;
   }
-  // Genotypes in host memory (the host tier): never copied whole.  Each chunk
-  // of batches takes its columns through one of two pinned staging buffers
-  // (filled by this thread while the device works on the previous chunk) and
-  // one of two device buffers (filled by a copy stream that overlaps the
-  // compute stream).
-  HostStager st(c, n, std::min<long>(lay.k, (long)kSnpChunk * lay.tau));
-  for (long c0 = b0, i = 0; c0 < b1; c0 += kSnpChunk, ++i) {
-    const long c1 = std::min(b1, c0 + kSnpChunk);
-    const long col0 = c0 * lay.tau, w = std::min(lay.k, c1 * lay.tau) - col0;
-    const double* dev = st.stage((int)(i & 1), S, lay.k, col0, w);
-    run_chunk(SnpSrc{dev, w, col0}, c0, c1);
-    st.release((int)(i & 1));
-  }
+  for_each_snp_chunk(j, S, b0, b1,
+                     [&](const SnpSrc& src, long c0, long c1) { run_chunk(&src, c0, c1); });
 }
 
 void job_decrypt(Job* j, double* num, double* den) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <array>
+#include <map>
 
 #include "ckks.cuh"
 
@@ -54,6 +55,15 @@ struct Job {
   int dupm_chunk = 0;
   u64* DupM_host = nullptr;
   bool DupM_host_lent = false;  // DupM_host is the context's pinned block
+  // SNP batches encrypted ahead of the loop (job_encrypt_snps): batch b ->
+  // items [first, first + per batch) of a shared set (factored: one CCP
+  // ciphertext at kFactLevel; M-CCP: the n REP rows at kBatchLevel); a set
+  // is freed once the loop has consumed all of its batches
+  struct EncBatch {
+    std::shared_ptr<CtSet> set;
+    int first = 0;
+  };
+  std::map<long, EncBatch> enc_snps;
   ~Job();
 };
 
@@ -67,8 +77,16 @@ void job_release_results(Job* j);
 // rotation steps whose keys the job needs
 std::vector<int> job_rotation_steps(const Job* j);
 void job_encrypt_inputs(Job* j, const double* X, const double* A, const double* y);
+// the same ciphertexts in two calls: X as CP, (X^T X)^-1 as CP, X^T as REP;
+// then y and beta0 = Enc(0)
+void job_encrypt_covariates(Job* j, const double* X, const double* A);
+void job_encrypt_phenotype(Job* j, const double* y);
+// encrypt SNP batches [b0, b1) of S (host or device, n x k row-major) ahead
+// of the loop, with the encryption ids the fused loop uses
+void job_encrypt_snps(Job* j, const double* S, long b0, long b1);
 void job_fit(Job* j, int kappa);
 void job_set_fit_state(Job* j, const double* M, const double* w, const double* wz);
+// S == nullptr: the batches' ciphertexts from job_encrypt_snps
 void job_snp_stats(Job* j, const double* S, long b0, long b1);
 // keep Dup(M_j) (M-CCP layout) in pinned host memory, streamed back to the
 // device in chunks of `chunk` columns per set of SNP batches; 0 = device

@@ -118,6 +118,11 @@ _SIGS = {
     "gwhe_ks_histogram": [_vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS"), _i],
     "gwhe_prof_read": [_vp, _f64p, _f64p, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")],
     "gwhe_ctx_device": [_vp, ctypes.POINTER(_i)],
+    "gwhe_ctx_set_stream": [_vp, _vp],
+    "gwhe_rotate_batch": [_vp, ctypes.POINTER(_vp), _i, ctypes.c_int32, _i, ctypes.POINTER(_vp)],
+    "gwhe_encrypt_covariates": [_vp, _vp, _vp],
+    "gwhe_encrypt_phenotype": [_vp, _vp],
+    "gwhe_encrypt_snps": [_vp, _vp, _l, _l],
     "gwhe_device_ok": [_i, _i],
     "gwhe_mem_info": [_vp, np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")],
 }
@@ -458,6 +463,15 @@ class Context:
         self._c(lib().gwhe_rotate_sum_batch(self.h, ins, len(cts), arr, len(steps), ous))
         return outs
 
+    def rotate_batch(self, cts, step, rescale=False, outs=None):
+        """[Rotate(a, step) for a in cts] as one set (shared level/scale),
+        each then rescaled if asked."""
+        outs = outs or [self._out(a) for a in cts]
+        ins = (_vp * len(cts))(*[a.h for a in cts])
+        ous = (_vp * len(outs))(*[o.h for o in outs])
+        self._c(lib().gwhe_rotate_batch(self.h, ins, len(cts), step, 1 if rescale else 0, ous))
+        return outs
+
     def rotate_sum(self, a, steps):
         """a + sum_r Rotate(a, r) over at most three steps, key switches hoisted."""
         o = self._out(a)
@@ -508,6 +522,12 @@ class Context:
         n = np.zeros(len(PROF_CLASSES), np.int64)
         self._c(lib().gwhe_prof_read(self.h, ms, by, n))
         return {k: (float(ms[i]), float(by[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def set_stream(self, stream):
+        """later calls run on `stream` (torch stream, raw handle or None),
+        ordered after the work already queued on the current one"""
+        h = getattr(stream, "cuda_stream", stream)
+        self._c(lib().gwhe_ctx_set_stream(self.h, _ptr(h)))
 
     def device(self):
         d = _i(0)
@@ -588,6 +608,21 @@ class Job:
         y, py = self._arr(y)
         self.ctx._c(lib().gwhe_encrypt_inputs(self.h, px, pa, py))
 
+    def encrypt_covariates(self, X, XtX_inv):
+        X, px = self._arr(X)
+        A, pa = self._arr(XtX_inv)
+        self.ctx._c(lib().gwhe_encrypt_covariates(self.h, px, pa))
+
+    def encrypt_phenotype(self, y):
+        y, py = self._arr(y)
+        self.ctx._c(lib().gwhe_encrypt_phenotype(self.h, py))
+
+    def encrypt_snps(self, S, b0=0, b1=None):
+        """encrypt SNP batches [b0, b1) ahead of snp_stats(None, ...)"""
+        S, ps = self._arr(S)
+        b1 = self.layout["batches"] if b1 is None else b1
+        self.ctx._c(lib().gwhe_encrypt_snps(self.h, ps, b0, b1))
+
     def fit(self, kappa):
         self.ctx._c(lib().gwhe_fit_covariates(self.h, kappa))
 
@@ -598,7 +633,9 @@ class Job:
         self.ctx._c(lib().gwhe_set_fit_state(self.h, pm, pw, pz))
 
     def snp_stats(self, S, b0=0, b1=None):
-        S, ps = self._arr(S)
+        """Alg. 11 loop over batches [b0, b1); S = None takes the batches
+        encrypted by encrypt_snps"""
+        S, ps = (None, None) if S is None else self._arr(S)
         b1 = self.layout["batches"] if b1 is None else b1
         self.ctx._c(lib().gwhe_snp_stats(self.h, ps, b0, b1, 1))
 

@@ -487,3 +487,45 @@ def test_mccp_job_bit_exact_with_64_pair_tensor_sums(g):
     num, den = job.decrypt_results()
     ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
     check_accuracy(num, den, ref, W["k"])
+
+
+@pytest.mark.parametrize("layout", ["factored", "mccp"])
+def test_split_encryption_phase_equals_fused_path(g, layout):
+    """The encryption phase as its own calls (covariates, phenotype, SNP
+    batches in two streamed ranges) and the loop over the pre-encrypted
+    batches give the fused path's ciphertexts bit for bit; the second job
+    also moves to another CUDA stream midway (gwhe_ctx_set_stream)."""
+    import torch
+    logN, L, K, dnum, seed = 10, 21, 7, 3, 15
+    n, d, k = 16, 3, 100  # two batches of 64 SNPs, the second ragged
+    data = make_gwas(n, d, k, seed=9)
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(logN, L, K=K, dnum=dnum, seed=seed)
+    fused = g.Job(ctx, n, d, k, layout=layout)
+    ctx.keygen(rot_steps=fused.rotation_steps(), conj=True)
+    fused.encrypt_inputs(data.X, A, data.y)
+    fused.fit(1)
+    fused.snp_stats(data.S)
+    split = g.Job(ctx, n, d, k, layout=layout)
+    split.encrypt_covariates(data.X, A)
+    split.encrypt_phenotype(data.y)
+    with pytest.raises(g.GwheError) as e:
+        split.snp_stats(None)  # no covariate phase, no encrypted batches
+    assert e.value.code == -1
+    split.fit(1)
+    split.encrypt_snps(data.S, 0, 1)
+    side = torch.cuda.Stream()
+    ctx.set_stream(side)
+    split.encrypt_snps(data.S, 1, 2)
+    split.snp_stats(None)
+    ctx.set_stream(None)
+    with pytest.raises(g.GwheError):
+        split.snp_stats(None)  # consumed: freed after the loop used them
+    for which in (7, 6, 4, 5):
+        assert np.array_equal(split.ct(which).export(), fused.ct(which).export()), which
+    for bi in range(2):
+        for which in range(3):
+            assert np.array_equal(split.ct(which, bi).export(), fused.ct(which, bi).export()), \
+                (bi, which)
+    a, b = fused.decrypt_results(), split.decrypt_results()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
