@@ -187,7 +187,10 @@ def run_gpu(args):
     ctx.keygen(rot_steps=steps_rot, conj=True)
     torch.cuda.synchronize()
     t_ctxgen = time.perf_counter() - t0
-    tuned = ctx.autotune()  # the fastest compiled shape of the transform on this GPU
+    # the fastest compiled shapes of the transform on this GPU, for large
+    # launches and for those of a few waves or less
+    tuned = ctx.autotune()
+    tuned_small = ctx.autotune(rows=32)
     data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"] + rank)
     A = client_preprocess(data.X)
     dev = {nm: torch.from_numpy(np.ascontiguousarray(v)).cuda()
@@ -359,7 +362,8 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "phases_ms": phases,
-        "autotune": {"ntt_shape": tuned[0], "ms_per_shape": tuned[1]},
+        "autotune": {"ntt_shape": tuned[0], "ms_per_shape": tuned[1],
+                     "ntt_shape_small": tuned_small[0], "ms_per_shape_small": tuned_small[1]},
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -765,6 +769,7 @@ def _serving_ctx(gwhe, stream, shapes):
         job.close()
     ctx.keygen(rot_steps=steps, conj=True)
     ctx.autotune()
+    ctx.autotune(rows=32)
     return ctx
 
 

@@ -347,6 +347,22 @@ int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce);
  * tensor sums are exact).  chunk = 0 keeps them on the device (default).
  * GWHE_EINVAL for chunk < 0, or to turn the tier off once it holds them. */
 int gwhe_job_set_host_state(gwhe_job* job, int chunk);
+/* The SNP loop's batch-invariant state, computed by the covariate phase
+ * (factored layout: Dup(X_c) and Dup((X (X^T X)^-1)_c) for c < d; M-CCP:
+ * Dup(M_j) for j < n; both: Dup(w), Dup(w z'), the inputs of the Alg. 11 loop),
+ * as one flat buffer of *words uint64 (host or device memory, caller-owned):
+ * a 7-word header (magic, version, N, layout, n, d, count), each
+ * ciphertext's level and scale, then its NTT-domain residues [2][l][N].
+ * A process holding the same context (parameters, seed, keys) imports it
+ * into a job of the same shape and layout and runs SNP batches with no fit
+ * of its own: the batches' ciphertexts are bit for bit those of the
+ * exporting job.  This is the one broadcast that shards a job's batches over
+ * GPUs (section "Batching SNPs": the batches are independent once the state
+ * exists).  export: GWHE_EINVAL before the fit or into too small a buffer;
+ * import: GWHE_EINVAL if the header does not match the job. */
+int gwhe_job_state_size(const gwhe_job* job, size_t* words);
+int gwhe_job_export_state(const gwhe_job* job, uint64_t* buf, size_t words);
+int gwhe_job_import_state(gwhe_job* job, const uint64_t* buf, size_t words);
 /* Drop the kept batch outputs (after gwhe_decrypt_results), so that a long
  * job can evaluate and decrypt its SNP batches chunk by chunk. */
 int gwhe_job_release_results(gwhe_job* job);
@@ -358,9 +374,12 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
 
 /* ------------------------------------------------------------ serving
  * Continuous batching of GWAS jobs on one GPU (no counterpart in the paper,
- * which runs one job).  `workers` threads each own a CUDA stream and a child
- * context sharing ctx's tables and device-resident keys (generated first,
- * with every rotation the jobs need), so jobs overlap on the device.  A free
+ * which runs one job).  `workers` threads each own two CUDA streams (the
+ * device's highest and lowest priority) and a child context sharing ctx's
+ * tables and device-resident keys (generated first, with every rotation the
+ * jobs need), so jobs overlap on the device.  One running job at a time holds
+ * the high-priority stream: its kernels are scheduled first and the other
+ * running jobs' kernels fill the SMs it leaves idle.  A free
  * worker admits the first waiting job whose estimated footprint
  * (gwhe_job_footprint) fits in hbm_budget bytes minus the running jobs'
  * (hbm_budget 0 = 60% of the free device memory); a job runs the covariate
@@ -374,9 +393,11 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
  *           the host tier (gwhe_job_set_host_state, min(32, n/4) columns per
  *           chunk) if that fits; ENOMEM if neither fits.
  *   wait:   blocks until the job is done; num[k], den[k] as
- *           gwhe_decrypt_results; times_ms (optional) = {waiting for
- *           admission, running, total}; the job's status is returned and the
- *           job is forgotten.
+ *           gwhe_decrypt_results; times_ms (optional, 6 entries) =
+ *           {waiting for admission, running, total (host clock, ms), start
+ *           and end of the job's work on the device (ms after the server's
+ *           creation, device clock), 1 if it ran on the high-priority
+ *           stream}; the job's status is returned and the job is forgotten.
  *   stats:  {admitted, running, waiting, bytes claimed, peak bytes claimed,
  *           budget, jobs run with Dup(M_j) in the host tier, most jobs
  *           running at once, workers alive}.
@@ -401,16 +422,22 @@ int gwhe_server_destroy(gwhe_server* s);
 int gwhe_ctx_create_child(gwhe_ctx* ctx, void* stream, gwhe_ctx** out);
 
 /* ------------------------------------------------------------ autotuning
- * The N = 2^16 transform is compiled in six shapes (two passes of 8 + 8,
- * 7 + 9 or 9 + 7 stages; 16 residues per thread in 64-, 128- or 256-thread
- * CTAs, or 32 in 128-thread CTAs); every shape computes identical residues.
- * gwhe_autotune times a forward and an inverse transform of `rows` rows in
- * each shape on the context's stream, keeps the fastest (for this context
- * and the child contexts made after it) and returns the times (ms[6], may be
- * NULL) and the choice.  Other ring degrees have one shape (ms all 0).
- * gwhe_set_ntt_variant selects a shape directly (0..5); a context starts
- * with shape 4 (8 + 8 x 16 in 128-thread CTAs, the fastest measured on
- * GB300). */
+ * The N = 2^16 transform is compiled in seven shapes: 0-5 in two launches
+ * (passes of 8 + 8, 7 + 9 or 9 + 7 stages; 16 residues per thread in 64-,
+ * 128- or 256-thread CTAs, or 32 in 128-thread CTAs), 6 in one launch on a
+ * cluster of eight 512-thread CTAs whose distributed shared memory carries
+ * the residues between the column and the row stages (each limb read from and
+ * written to HBM once); every shape computes identical residues.
+ * Launches of fewer than 128 rows (a few waves of CTAs or less, as in the
+ * covariate phase's single-ciphertext operations) and larger launches each
+ * have their own shape.  gwhe_autotune times a forward and an inverse
+ * transform of `rows` rows in each shape on the context's stream, keeps the
+ * fastest for launches of that size class (rows < 128 or >= 128; for this
+ * context and the child contexts made after it) and returns the times (ms[7],
+ * may be NULL) and the choice.  Other ring degrees have one shape (ms all 0).
+ * gwhe_set_ntt_variant selects a shape directly (0..6) for both classes; a
+ * context starts with shape 4 (8 + 8 x 16 in 128-thread CTAs, the fastest
+ * measured on GB300). */
 int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen);
 int gwhe_set_ntt_variant(gwhe_ctx* ctx, int variant);
 

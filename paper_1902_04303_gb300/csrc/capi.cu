@@ -642,6 +642,27 @@ int gwhe_job_ct(gwhe_job* job, int which, long index, gwhe_ct** view) {
   });
 }
 
+int gwhe_job_state_size(const gwhe_job* job, size_t* words) {
+  if (!job || !words) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] { *words = job_state_words(job->job.get()); });
+}
+
+int gwhe_job_export_state(const gwhe_job* job, uint64_t* buf, size_t words) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] {
+    need(buf != nullptr, "null buffer");
+    job_export_state(job->job.get(), buf, words);
+  });
+}
+
+int gwhe_job_import_state(gwhe_job* job, const uint64_t* buf, size_t words) {
+  if (!job) return GWHE_EINVAL;
+  return guard(C(job->owner), [&] {
+    need(buf != nullptr, "null buffer");
+    job_import_state(job->job.get(), buf, words);
+  });
+}
+
 int gwhe_job_set_nonce(gwhe_job* job, uint32_t nonce) {
   if (!job) return GWHE_EINVAL;
   return guard(C(job->owner), [&] { job_set_nonce(job->job.get(), nonce); });
@@ -671,6 +692,7 @@ int gwhe_set_ntt_variant(gwhe_ctx* ctx, int variant) {
   return guard(C(ctx), [&] {
     need(variant >= 0 && variant < kNttVariants, "no such transform shape");
     C(ctx)->ntt_variant = variant;
+    C(ctx)->ntt_variant_small = variant;
   });
 }
 
@@ -681,7 +703,7 @@ int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen) {
     for (int v = 0; v < kNttVariants; ++v)
       if (ms) ms[v] = 0.0;
     if (c->logN != 16) {  // one shape only
-      if (chosen) *chosen = c->ntt_variant;
+      if (chosen) *chosen = rows >= kNttSmallRows ? c->ntt_variant : c->ntt_variant_small;
       return;
     }
     // zero residues are valid inputs; the transforms' cost does not depend on
@@ -699,12 +721,15 @@ int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen) {
     GWHE_CUDA(cudaEventCreate(&e1));
     int best = 0;
     double best_ms = 1e30;
+    // the size class being tuned: launches of at least kNttSmallRows rows,
+    // or the smaller ones
+    int& slot = rows >= kNttSmallRows ? c->ntt_variant : c->ntt_variant_small;
     for (int v = 0; v < kNttVariants; ++v) {
-      c->ntt_variant = v;
+      slot = v;
       ntt_forward(c, buf.u(), rm);
       ntt_inverse(c, buf.u(), rm);
       float t = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < (rows < kNttSmallRows ? 10 : 3); ++rep) {
         GWHE_CUDA(cudaEventRecord(e0, c->stream));
         ntt_forward(c, buf.u(), rm);
         ntt_inverse(c, buf.u(), rm);
@@ -722,7 +747,7 @@ int gwhe_autotune(gwhe_ctx* ctx, int rows, double* ms, int* chosen) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->ntt_variant = best;
+    slot = best;
     if (chosen) *chosen = best;
   });
 }

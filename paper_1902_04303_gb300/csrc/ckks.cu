@@ -852,18 +852,20 @@ static void modup_ext(Context* c, const u64* x, size_t x_stride, int cnt, int l,
                               cnt, cudaMemcpyDeviceToDevice, c->stream));
   ntt_inverse(c, xc.u(), rows_q(cnt, l, l));
   modup_convert_set(c, xc.u(), l, ext, cnt);
+  // the new limbs of every digit in one transform launch
+  RowMap rm;
+  rm.npoly = cnt;
+  rm.nl = 0;
+  rm.poly_stride = beta * ne;
   for (int j = 0; j < beta; ++j) {
     const ConvTable& t = c->modup.at({l, j});
-    RowMap rm;
-    rm.npoly = cnt;
-    rm.nl = t.n_out;
-    rm.poly_stride = beta * ne;
-    for (int o = 0; o < t.n_out; ++o) {
-      rm.off[o] = (uint16_t)(j * ne + t.out_limb[o]);
-      rm.pidx[o] = t.out_pidx[o];
+    GWHE_REQUIRE(rm.nl + t.n_out <= kMaxRowMap, ST_EINVAL, "ModUp rows exceed a row map");
+    for (int o = 0; o < t.n_out; ++o, ++rm.nl) {
+      rm.off[rm.nl] = (uint16_t)(j * ne + t.out_limb[o]);
+      rm.pidx[rm.nl] = t.out_pidx[o];
     }
-    ntt_forward(c, ext, rm);
   }
+  ntt_forward(c, ext, rm);
 }
 
 // ModDown of cnt key products acc ([cnt][2][ne][N], NTT domain) by P_K into

@@ -26,6 +26,8 @@ typedef unsigned __int128 u128;
 
 constexpr int kMaxMod = 96;     // q-limbs + special primes
 constexpr int kMaxRowLimbs = 64;
+// rows per item of one batched transform (a ModUp's new limbs of every digit)
+constexpr int kMaxRowMap = 192;
 
 // Status codes of the C ABI.
 enum Status {
@@ -201,8 +203,8 @@ struct RowMap {
   int npoly;
   int nl;
   int poly_stride;
-  uint16_t off[kMaxRowLimbs];
-  uint8_t pidx[kMaxRowLimbs];
+  uint16_t off[kMaxRowMap];
+  uint8_t pidx[kMaxRowMap];
 };
 
 // Tables of the negacyclic NTT for one modulus index u, each of length N:
@@ -315,6 +317,7 @@ struct Context {
   int N = 0, logN = 0, alpha = 0, nmod = 0;
   int ntt_variant = 4;         // shape of the N = 2^16 transform (kNttVariants;
                                // 4 = the fastest measured on GB300, see gwhe_autotune)
+  int ntt_variant_small = 4;   // the shape for launches below kNttSmallRows rows
   u64 seed = 0;
   cudaStream_t stream = 0;
   std::vector<u64> mod;        // [L + K]: q_0..q_{L-1}, p_0..p_{K-1}
@@ -365,7 +368,9 @@ struct Context {
 };
 
 // shapes of the N = 2^16 transform compiled in (identical results)
-constexpr int kNttVariants = 6;
+constexpr int kNttVariants = 7;
+// launches with fewer rows (a few waves of CTAs or less) use their own shape
+constexpr int kNttSmallRows = 128;
 
 // the family of key id that a switch at level l uses (ST_ENOKEY if absent)
 const Ksk& key_family(const Context* c, u32 key_id, int l);

@@ -224,8 +224,6 @@ struct Eval {
   std::vector<int> colsum_steps() { return pow2_steps(ilog2(lay.nb)); }
   // Alg. 7: doubling ladder v += Rotate(v, nb 2^i) over the M/nb blocks
   std::vector<int> dup_steps() { return pow2_steps(ilog2(lay.B), lay.nb); }
-  // a one-ciphertext set holding a copy of a at level l (for the ladders)
-  CtSetPtr single(const Ct& a, int l) { return gather({&a}, l); }
   // a set holding copies of the given ciphertexts (same scale) at level l
   CtSetPtr gather(const std::vector<const Ct*>& src, int l) {
     CtSetPtr s = set_new(c, (int)src.size(), 2, l, l, src[0]->scale);
@@ -383,6 +381,128 @@ static void spill_dupm(Job* j) {
 static void drop_dupm(Job* j) {
   j->DupM.clear();
   release_dupm_host(j);
+}
+
+// ------------------------------------------------------------- state transfer
+// The batch-invariant state of the SNP loop in one flat buffer (words):
+//   header [kStateHeader]: magic, version, N, layout, n, d, cts
+//   per ciphertext: level l, scale (IEEE bits)
+//   then each ciphertext's residues, uint64[2][l][N], NTT domain
+// Order: factored Dup(X_c) c < d, Dup((XA)_c) c < d; M-CCP Dup(M_j) j < n;
+// then Dup(w), Dup(w z').
+constexpr u64 kStateMagic = 0x6777686573746174ull;  // "gwhestat"
+constexpr int kStateHeader = 7;
+
+static std::vector<const Ct*> state_cts(const Job* j) {
+  std::vector<const Ct*> v;
+  if (j->factored) {
+    for (auto& x : j->DupX) v.push_back(x.get());
+    for (auto& x : j->DupB) v.push_back(x.get());
+  } else {
+    for (auto& x : j->DupM) v.push_back(x.get());
+  }
+  v.push_back(j->DupW.get());
+  v.push_back(j->DupWZ.get());
+  return v;
+}
+
+static size_t state_words_of(const Job* j, const std::vector<int>& levels) {
+  size_t w = kStateHeader + 2 * levels.size();
+  for (int l : levels) w += (size_t)2 * l * j->c->N;
+  return w;
+}
+
+size_t job_state_words(const Job* j) {
+  const auto v = state_cts(j);
+  GWHE_REQUIRE(v.size() >= 2 && v.back() && v[v.size() - 2], ST_EINVAL,
+               "covariate phase not done (fit first)");
+  std::vector<int> lv;
+  for (const Ct* c : v) {
+    GWHE_REQUIRE(c != nullptr, ST_EINVAL, "covariate phase not done (fit first)");
+    lv.push_back(c->l);
+  }
+  return state_words_of(j, lv);
+}
+
+void job_export_state(const Job* j, u64* buf, size_t words) {
+  Context* c = j->c;
+  const auto v = state_cts(j);
+  GWHE_REQUIRE(words >= job_state_words(j), ST_EINVAL, "state buffer too small");
+  std::vector<u64> head(kStateHeader + 2 * v.size());
+  head[0] = kStateMagic;
+  head[1] = 1;
+  head[2] = (u64)c->N;
+  head[3] = j->factored ? kLayoutFactored : kLayoutMccp;
+  head[4] = (u64)j->lay.n;
+  head[5] = (u64)j->lay.d;
+  head[6] = (u64)v.size();
+  for (size_t i = 0; i < v.size(); ++i) {
+    head[kStateHeader + 2 * i] = (u64)v[i]->l;
+    std::memcpy(&head[kStateHeader + 2 * i + 1], &v[i]->scale, sizeof(double));
+  }
+  GWHE_CUDA(cudaMemcpyAsync(buf, head.data(), sizeof(u64) * head.size(), cudaMemcpyDefault,
+                            c->stream));
+  size_t off = head.size();
+  for (const Ct* ct : v)
+    for (int p = 0; p < 2; ++p) {
+      // Dup(M_j) may live in the pinned host tier
+      GWHE_CUDA(cudaMemcpyAsync(buf + off, ct->poly(p), sizeof(u64) * ct->l * c->N,
+                                cudaMemcpyDefault, c->stream));
+      off += (size_t)ct->l * c->N;
+    }
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void job_import_state(Job* j, const u64* buf, size_t words) {
+  Context* c = j->c;
+  GWHE_REQUIRE(words >= (size_t)kStateHeader, ST_EINVAL, "state buffer too small");
+  std::vector<u64> head(kStateHeader);
+  GWHE_CUDA(cudaMemcpyAsync(head.data(), buf, sizeof(u64) * kStateHeader, cudaMemcpyDefault,
+                            c->stream));
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  const size_t cnt = head[6];
+  const size_t want_cnt = j->factored ? 2 * (size_t)j->lay.d + 2 : (size_t)j->lay.n + 2;
+  GWHE_REQUIRE(head[0] == kStateMagic && head[1] == 1 && head[2] == (u64)c->N &&
+                   head[3] == (u64)(j->factored ? kLayoutFactored : kLayoutMccp) &&
+                   head[4] == (u64)j->lay.n && head[5] == (u64)j->lay.d && cnt == want_cnt,
+               ST_EINVAL, "the state buffer was made for another job shape or ring");
+  std::vector<u64> meta(2 * cnt);
+  GWHE_CUDA(cudaMemcpyAsync(meta.data(), buf + kStateHeader, sizeof(u64) * meta.size(),
+                            cudaMemcpyDefault, c->stream));
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<int> lv(cnt);
+  for (size_t i = 0; i < cnt; ++i) {
+    lv[i] = (int)meta[2 * i];
+    GWHE_REQUIRE(lv[i] >= 1 && lv[i] <= c->P.L, ST_EINVAL, "bad level in the state buffer");
+  }
+  GWHE_REQUIRE(words >= state_words_of(j, lv), ST_EINVAL, "state buffer too small");
+  std::vector<CtPtr> cts;
+  size_t off = kStateHeader + 2 * cnt;
+  for (size_t i = 0; i < cnt; ++i) {
+    double sc;
+    std::memcpy(&sc, &meta[2 * i + 1], sizeof(double));
+    CtPtr ct = ct_new(c, 2, lv[i], lv[i], sc);
+    for (int p = 0; p < 2; ++p) {
+      GWHE_CUDA(cudaMemcpyAsync(ct->poly(p), buf + off, sizeof(u64) * lv[i] * c->N,
+                                cudaMemcpyDefault, c->stream));
+      off += (size_t)lv[i] * c->N;
+    }
+    cts.push_back(std::move(ct));
+  }
+  GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  drop_dupm(j);
+  j->DupX.clear();
+  j->DupB.clear();
+  size_t it = 0;
+  if (j->factored) {
+    for (int cc = 0; cc < j->lay.d; ++cc) j->DupX.push_back(std::move(cts[it++]));
+    for (int cc = 0; cc < j->lay.d; ++cc) j->DupB.push_back(std::move(cts[it++]));
+  } else {
+    for (int jj = 0; jj < j->lay.n; ++jj) j->DupM.push_back(std::move(cts[it++]));
+    if (j->dupm_chunk > 0) spill_dupm(j);
+  }
+  j->DupW = std::move(cts[it++]);
+  j->DupWZ = std::move(cts[it++]);
 }
 
 void job_set_host_state(Job* j, int chunk) {
@@ -560,14 +680,23 @@ static void make_dup_state(Job* j, Eval& ev) {
   else
     j->sets.push_back(std::move(dm));
   }
-  CtSetPtr dw = ev.single(*j->w_m, lb - 1);
-  set_ladder(c, *dw, ev.dup_steps());
-  j->DupW = dw->view(0);
-  j->sets.push_back(std::move(dw));
-  CtSetPtr dwz = ev.single(*j->wzp, lb - 1);
-  set_ladder(c, *dwz, ev.dup_steps());
-  j->DupWZ = dwz->view(0);
-  j->sets.push_back(std::move(dwz));
+  // Dup(w) and Dup(w z') (Alg. 7) share one ladder set: the ladder's key
+  // switches and sums do not read the scales, so each view keeps its source's
+  CtSetPtr dd = set_new(c, 2, 2, lb - 1, lb - 1, 1.0);
+  const Ct* dsrc[2] = {j->w_m.get(), j->wzp.get()};
+  for (int i = 0; i < 2; ++i) {
+    GWHE_REQUIRE(dsrc[i]->l >= lb - 1, ST_ELEVEL, "depth exhausted before the SNP batches");
+    for (int p = 0; p < 2; ++p)
+      GWHE_CUDA(cudaMemcpyAsync(dd->item(i) + (size_t)p * (lb - 1) * c->N, dsrc[i]->poly(p),
+                                sizeof(u64) * (lb - 1) * c->N, cudaMemcpyDeviceToDevice,
+                                c->stream));
+  }
+  set_ladder(c, *dd, ev.dup_steps());
+  j->DupW = dd->view(0);
+  j->DupW->scale = j->w_m->scale;
+  j->DupWZ = dd->view(1);
+  j->DupWZ->scale = j->wzp->scale;
+  j->sets.push_back(std::move(dd));
 }
 
 void job_fit(Job* j, int kappa) {

@@ -91,6 +91,12 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1);
 // keep Dup(M_j) (M-CCP layout) in pinned host memory, streamed back to the
 // device in chunks of `chunk` columns per set of SNP batches; 0 = device
 void job_set_host_state(Job* j, int chunk);
+// the SNP loop's batch-invariant state (factored: Dup(X_c), Dup((XA)_c);
+// M-CCP: Dup(M_j); both: Dup(w), Dup(w z')) as one flat buffer, host or
+// device, so that other processes can run batches without the fit
+size_t job_state_words(const Job* j);
+void job_export_state(const Job* j, u64* buf, size_t words);
+void job_import_state(Job* j, const u64* buf, size_t words);
 void job_decrypt(Job* j, double* num, double* den);
 
 }  // namespace gwhe

@@ -2,6 +2,7 @@
 // product, fast base conversion (ModUp / ModDown), the key inner product,
 // rescale, Galois automorphisms, ChaCha20 sampling, and the FP64 encoding
 // procedure of the gwhe library.  See kernels.cuh for the interfaces.
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -96,7 +97,7 @@ struct ConvArgs {
 // memory and read as warp-uniform broadcasts.
 constexpr int kConvOG = 8;
 template <int NI, int T>
-__device__ __forceinline__ void conv_outputs(const u64 (&y)[NI], const u64* hs,
+__device__ __forceinline__ void conv_outputs(const u64 (&y)[NI], const u64* hs, int og,
                                              int o, const ConvArgs& a, int o0, u64* op,
                                              int N, int k, const DevMod* __restrict__ mod) {
   Acc128 s[T];
@@ -105,7 +106,7 @@ __device__ __forceinline__ void conv_outputs(const u64 (&y)[NI], const u64* hs,
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
 #pragma unroll
-    for (int t = 0; t < T; ++t) mac128(s[t], y[i], hs[i * kConvOG + o + t]);
+    for (int t = 0; t < T; ++t) mac128(s[t], y[i], hs[i * og + o + t]);
   }
 #pragma unroll
   for (int t = 0; t < T; ++t) {
@@ -117,16 +118,20 @@ __device__ __forceinline__ void conv_outputs(const u64 (&y)[NI], const u64* hs,
   }
 }
 
+// Each CTA converts one block of coefficients of one polynomial to the og
+// outputs [blockIdx.y og, +og): with og = n_out (the large batches) every
+// input's Shoup product is formed once per coefficient; a small batch splits
+// the outputs over kConvOG-wide CTAs to fill the GPU.
 template <int NI>
 __global__ void __launch_bounds__(256) k_baseconv(const u64* __restrict__ x, size_t x_pstride,
                                                   u64* __restrict__ out, size_t out_pstride,
-                                                  const ConvArgs a, int N,
+                                                  const ConvArgs a, int N, int og,
                                                   const DevMod* __restrict__ mod) {
-  __shared__ u64 hs[NI * kConvOG];
-  const int o0 = blockIdx.y * kConvOG;
-  const int no = min(kConvOG, a.n_out - o0);
-  for (int e = threadIdx.x; e < NI * kConvOG; e += blockDim.x) {
-    const int i = e / kConvOG, o = e - i * kConvOG;
+  __shared__ u64 hs[NI * kMaxRowLimbs];
+  const int o0 = blockIdx.y * og;
+  const int no = min(og, a.n_out - o0);
+  for (int e = threadIdx.x; e < NI * og; e += blockDim.x) {
+    const int i = e / og, o = e - i * og;
     hs[e] = o < no ? a.tab[2 * NI + i * a.hm_stride + o0 + o] : 0;
   }
   __syncthreads();
@@ -143,15 +148,20 @@ __global__ void __launch_bounds__(256) k_baseconv(const u64* __restrict__ x, siz
     if (a.in_add) y[i] = addmod(y[i], a.in_add[i], q);
   }
   int o = 0;
-  for (; o + 4 <= no; o += 4) conv_outputs<NI, 4>(y, hs, o, a, o0, op, N, k, mod);
+  for (; o + 4 <= no; o += 4) conv_outputs<NI, 4>(y, hs, og, o, a, o0, op, N, k, mod);
   switch (no - o) {
-    case 3: conv_outputs<NI, 3>(y, hs, o, a, o0, op, N, k, mod); break;
-    case 2: conv_outputs<NI, 2>(y, hs, o, a, o0, op, N, k, mod); break;
-    case 1: conv_outputs<NI, 1>(y, hs, o, a, o0, op, N, k, mod); break;
+    case 3: conv_outputs<NI, 3>(y, hs, og, o, a, o0, op, N, k, mod); break;
+    case 2: conv_outputs<NI, 2>(y, hs, og, o, a, o0, op, N, k, mod); break;
+    case 1: conv_outputs<NI, 1>(y, hs, og, o, a, o0, op, N, k, mod); break;
     default: break;
   }
 }
 
+// Grid of the three inner-product kernels: x = groups of items, y = blocks of
+// coefficients, z = extended limb u.  The groups of one (limb, coefficient
+// block) are adjacent in launch order, so the key words they share are read
+// from DRAM once and from L2 by the other groups.
+//
 // acc_p[u] = sum_j x_j[u] * key_j[p][u] over digits, for the l + K extended limbs;
 // x_j[u] is the input limb itself when u lies in digit j, else the converted limb.
 // Each thread keeps its key words in registers and applies them to up to IB
@@ -163,8 +173,8 @@ __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
                            const u64* __restrict__ ext, const u64* __restrict__ key,
                            u64* __restrict__ acc, int l, int K, int L, int key_lmax, int alpha,
                            int beta, int N, int cnt, const DevMod* __restrict__ mod) {
-  const int u = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = blockIdx.z;
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
   const int mi = u < l ? u : L + (u - l);        // modulus of extended limb u
@@ -178,7 +188,7 @@ __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
       ka[j] = key[(((size_t)j * 2 + 1) * KR + kr) * N + k];
     }
   const DevMod m = mod[mi];
-  const int it0 = blockIdx.z * IB;
+  const int it0 = blockIdx.x * IB;
   const int it1 = min(it0 + IB, cnt);
   for (int item = it0; item < it1; ++item) {
     const u64* cx = c_ntt + (size_t)item * c_stride;
@@ -220,15 +230,15 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
                                  u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                  int alpha, int beta, int logN, int cnt,
                                  const DevMod* __restrict__ mod) {
-  const int u = blockIdx.y;
+  const int u = blockIdx.z;
   const int N = 1 << logN;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
   const int mi = u < l ? u : L + (u - l);
   const int kr = u < l ? u : key_lmax + (u - l);
   const size_t KR = (size_t)(key_lmax + K);
-  const int it0 = blockIdx.z * IB;
+  const int it0 = blockIdx.x * IB;
   const int nit = min(IB, cnt - it0);
   Acc128 s0[IB], s1[IB];
 #pragma unroll
@@ -278,9 +288,9 @@ __global__ void k_ks_inner_hoist1(const u64* __restrict__ c_ntt, size_t c_stride
                                   const u64* __restrict__ ext, HoistKeys hk,
                                   u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                   int logN, int cnt, const DevMod* __restrict__ mod) {
-  const int u = blockIdx.y;
+  const int u = blockIdx.z;
   const int N = 1 << logN;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int ne = l + K;
   const int mi = u < l ? u : L + (u - l);
@@ -295,7 +305,7 @@ __global__ void k_ks_inner_hoist1(const u64* __restrict__ c_ntt, size_t c_stride
     ka[g] = hk.key[g][((size_t)1 * KR + kr) * N + k];
   }
   const DevMod m = mod[mi];
-  const int it0 = blockIdx.z * IB;
+  const int it0 = blockIdx.x * IB;
   const int it1 = min(it0 + IB, cnt);
   for (int item = it0; item < it1; ++item) {
     // digit 0 holds every limb below l: those come from c1 itself
@@ -1133,10 +1143,15 @@ static ConvArgs conv_args(const ConvTable& t, int in_mod0) {
 static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_t os, int cnt,
                             const ConvArgs& a) {
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "conversion batch too large");
-  const dim3 grid(blocks_for(c->N), (a.n_out + kConvOG - 1) / kConvOG, cnt);
-#define GWHE_CONV_CASE(n)                                                                  \
-  case n:                                                                                  \
-    k_baseconv<n><<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, c->d_mod); \
+  GWHE_REQUIRE(a.n_out >= 1 && a.n_out <= kMaxRowLimbs, ST_EINVAL, "conversion outputs");
+  // all outputs per CTA once the launch has at least two waves of CTAs
+  // (152 SMs x 8 CTAs of 256 threads), else kConvOG outputs per CTA
+  const long ctas = (long)blocks_for(c->N) * cnt;
+  const int og = ctas >= 2L * 152 * 8 ? a.n_out : std::min(a.n_out, kConvOG);
+  const dim3 grid(blocks_for(c->N), (a.n_out + og - 1) / og, cnt);
+#define GWHE_CONV_CASE(n)                                                                      \
+  case n:                                                                                      \
+    k_baseconv<n><<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, og, c->d_mod); \
     break;
   switch (a.n_in) {
     GWHE_CONV_CASE(1) GWHE_CONV_CASE(2) GWHE_CONV_CASE(3) GWHE_CONV_CASE(4)
@@ -1195,7 +1210,7 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
   GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
   GWHE_REQUIRE(key.d && key.lmax >= l && beta <= key.dk, ST_ENOKEY, "key family does not reach the level");
   constexpr int IB = 8;
-  k_ks_inner<IB><<<dim3(blocks_for(c->N), l + K, (cnt + IB - 1) / IB), kThreads, 0,
+  k_ks_inner<IB><<<dim3((cnt + IB - 1) / IB, blocks_for(c->N), l + K), kThreads, 0,
                    c->stream>>>(c_ntt, c_stride, ext, key.d, acc, l, K, c->P.L, key.lmax,
                                 c->alpha, beta, c->N, cnt, c->d_mod);
   GWHE_LAUNCHED(c, 1);
@@ -1206,13 +1221,13 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
                          const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt, int beta) {
   if (beta == 1) {
     constexpr int IB1 = 32;
-    const dim3 grid(blocks_for(c->N), l + K, (cnt + IB1 - 1) / IB1);
+    const dim3 grid((cnt + IB1 - 1) / IB1, blocks_for(c->N), l + K);
     k_ks_inner_hoist1<IB1, G><<<grid, kThreads, 0, c->stream>>>(
         c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
     return;
   }
   constexpr int IB = G <= 3 ? 8 : 4;
-  const dim3 grid(blocks_for(c->N), l + K, (cnt + IB - 1) / IB);
+  const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
   k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,
                                                            c->P.L, key_lmax, c->alpha, beta,
                                                            c->logN, cnt, c->d_mod);

@@ -18,6 +18,10 @@
 // N = 2^17 uses 128-thread CTAs with 32 residues per thread (5 + 4 stages).
 // Each residue is read and written once per pass.  Smaller rings use one CTA
 // per row in shared memory.
+#include <cooperative_groups.h>
+
+#include <mutex>
+
 #include "core.cuh"
 
 namespace gwhe {
@@ -232,6 +236,230 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
   }
 }
 
+// One-launch N = 2^16 transform on a cluster of kClusterCtas CTAs.  The row
+// is the same 256 x 256 matrix as in the two-pass kernel (element h 256 + c):
+// CTA q of the cluster owns columns [32 q, 32 q + 32) in the column pass and
+// rows [32 q, 32 q + 32) in the row pass.  Between the passes each thread
+// writes its 16 residues straight into the distributed shared memory of the
+// CTA that owns them next (a column pass's residues of row h go to CTA
+// h / 32), so a limb is read from and written to HBM once.  Two cluster
+// barriers frame the exchange: every CTA has finished reading its own
+// buffer before any is overwritten, and every write has landed before the
+// second pass reads.  The butterflies, the twiddle indexing, the lazy
+// ranges, the thread layouts and the ModDown epilogue are those of
+// k_ntt_pass<16, 8, ..., 16, *>, so the residues are identical.
+constexpr int kClusterCtas = 8;
+constexpr int kMaxDevices = 64;
+constexpr int kClusterThreads = 512;
+constexpr int kClusterPitchA = 256 + 1;          // column pass: [32][257]
+constexpr int kClusterPitchB = 256 + 256 / 16;   // row pass: [32][272], + e / 16
+constexpr size_t kClusterSmem = sizeof(u64) * 32 * kClusterPitchB;
+
+template <bool FWD, bool MD>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 2)
+    k_ntt_cluster(u64* __restrict__ data, const RowMap rm, const NttTables tb,
+                  const MdEpi epi = MdEpi{}) {
+  static_assert(!MD || FWD, "the ModDown epilogue ends a forward transform");
+  constexpr int LOGN = 16, LS = 8, E = 16, TPS = 16, G = 32;
+  extern __shared__ u64 sm[];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int grp = (int)cluster.block_rank();  // 0..7: columns / rows 32 grp ..
+  const int row = blockIdx.x / kClusterCtas;
+  const int poly = row / rm.nl;
+  const int limb = row - poly * rm.nl;
+  const int u = rm.pidx[limb];
+  u64* base = data + ((size_t)poly * rm.poly_stride + rm.off[limb]) * ((size_t)1 << LOGN);
+  const u64 q = tb.mod[u].q, q4 = 4 * q, nq = 0 - q;
+  const ulonglong2* W = (FWD ? tb.psi : tb.ipsi) + ((size_t)u << LOGN);
+  const ulonglong2* WB = (FWD ? tb.psiB : tb.ipsiB) + (size_t)u * kTwBPerMod;
+  const int t = threadIdx.x;
+  // column pass: sub-transform lgA = column, thread rA of it; row pass: lgB = row
+  const int lgA = t % G, rA = t / G, gA = grp * G + lgA;
+  const int lgB = t / TPS, rB = t % TPS, gB = grp * G + lgB;
+  auto sA = [&](int lg, int e) -> int { return lg * kClusterPitchA + e; };
+  auto sB = [&](int lg, int e) -> int { return lg * kClusterPitchB + e + (e >> 4); };
+  // twiddle index of the pair led by local element e at local stage sl
+  auto twA = [&](int sl, int e) -> int { return (1 << sl) + (e >> (LS - sl)); };
+  auto twB = [&](int sl, int e) -> int { return (1 << (8 + sl)) + (gB << sl) + (e >> (LS - sl)); };
+  auto twb = [&](int sp, int m) -> ulonglong2 {  // row-pass stage sp >= 4, pair led by E rB + m
+    const int off = 256 * ((1 << sp) - 16);
+    return __ldg(WB + off + (gB << sp) + ((m >> (8 - sp)) << 4) + rB);
+  };
+  u64 x[E];
+  if (FWD) {
+    // ---- column pass (global stages 0-7), residues from HBM
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = base[((size_t)(rA + TPS * m) << 8) + gA];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int st = (E / 2) >> sp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twA(sp, TPS * m));
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sA(lgA, rA + TPS * m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sA(lgA, E * rA + m)];
+#pragma unroll
+    for (int sp = 4; sp < LS; ++sp) {
+      const int st = 256 >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twA(sp, E * rA + m));
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    // ---- exchange: residue h = E rA + m of column gA goes to row h's CTA
+    cluster.sync();
+    {
+      u64* dst = cluster.map_shared_rank(sm, (unsigned)(rA >> 1));
+      const int lr0 = (rA & 1) * E;
+#pragma unroll
+      for (int m = 0; m < E; ++m) dst[sB(lr0 + m, gA)] = x[m];
+    }
+    cluster.sync();
+    // ---- row pass (global stages 8-15) from this CTA's buffer
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sB(lgB, rB + TPS * m)];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int st = (E / 2) >> sp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twB(sp, TPS * m));
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sB(lgB, rB + TPS * m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sB(lgB, E * rB + m)];
+#pragma unroll
+    for (int sp = 4; sp < LS; ++sp) {
+      const int st = 256 >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = twb(sp, m);
+        ct_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sB(lgB, E * rB + m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = reduce_8q(sm[sB(lgB, rB + TPS * m)], q);
+    if (MD) {
+      // row = (item, poly p, limb) of conv [cnt][2][l][N]
+      const size_t N = (size_t)1 << LOGN;
+      const int item = poly >> 1, p = poly & 1;
+      const u64* a = epi.acc + ((size_t)item * 2 * (epi.l + epi.K) + (size_t)p * (epi.l + epi.K) +
+                                limb) * N;
+      u64* o = (p ? epi.out1 : epi.out0) + item * epi.o_stride + (size_t)limb * N;
+      const u64* ad = p ? epi.add1 : epi.add0;
+      if (ad) ad += item * (p ? epi.a1_stride : epi.a0_stride) + (size_t)limb * N;
+      const u64 pi = epi.pinv[2 * limb], pish = epi.pinv[2 * limb + 1];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const size_t k = ((size_t)gB << 8) + rB + TPS * m;
+        u64 v = shoup(submod(a[k], x[m], q), pi, pish, q);
+        if (ad) v = addmod(v, ad[k], q);
+        o[k] = v;
+      }
+      return;
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) base[((size_t)gB << 8) + rB + TPS * m] = x[m];
+  } else {
+    // ---- row pass (global stages 15-8), residues from HBM
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = base[((size_t)gB << 8) + rB + TPS * m];
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sB(lgB, rB + TPS * m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sB(lgB, E * rB + m)];
+#pragma unroll
+    for (int sp = LS - 1; sp >= 4; --sp) {
+      const int st = 256 >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = twb(sp, m);
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sB(lgB, E * rB + m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sB(lgB, rB + TPS * m)];
+#pragma unroll
+    for (int sp = 3; sp >= 0; --sp) {
+      const int st = (E / 2) >> sp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twB(sp, TPS * m));
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    // ---- exchange: residue c = rB + TPS m of row gB goes to column c's CTA
+    cluster.sync();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      u64* dst = cluster.map_shared_rank(sm, (unsigned)(m >> 1));
+      dst[sA(rB + TPS * (m & 1), gB)] = x[m];
+    }
+    cluster.sync();
+    // ---- column pass (global stages 7-0) from this CTA's buffer, read
+    // directly in the contiguous layout of its last stages
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sA(lgA, E * rA + m)];
+#pragma unroll
+    for (int sp = LS - 1; sp >= 4; --sp) {
+      const int st = 256 >> (sp + 1);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twA(sp, E * rA + m));
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) sm[sA(lgA, E * rA + m)] = x[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = sm[sA(lgA, rA + TPS * m)];
+#pragma unroll
+    for (int sp = 3; sp >= 0; --sp) {
+      const int st = (E / 2) >> sp;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        if (m & st) continue;
+        const ulonglong2 w = __ldg(W + twA(sp, TPS * m));
+        gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
+      }
+    }
+    const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+#pragma unroll
+    for (int m = 0; m < E; ++m) base[((size_t)(rA + TPS * m) << 8) + gA] = shoup(x[m], ni, nish, q);
+  }
+}
+
 // pass A: 2^LA-point columns, pass B: 2^LB-point rows, with EA / EB residues
 // per thread in NA / NB-thread CTAs, at least MB CTAs per SM
 // (epi: forward only, the row pass ends with the ModDown epilogue)
@@ -265,10 +493,44 @@ static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
                (LB > 8 ? 128 : 256)>(c, data, rm, fwd, epi);
 }
 
+// the one-launch cluster transform of N = 2^16 (k_ntt_cluster)
+static void ntt_cluster_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi) {
+  const NttTables tb = c->tables();
+  const int rows = rm.npoly * rm.nl;
+  GWHE_REQUIRE(tb.psiB && tb.ipsiB, ST_EINVAL, "row-pass twiddle table missing");
+  // the kernels' dynamic shared memory above 48 KB, allowed once per device
+  static std::mutex mu;
+  static bool attr_set[kMaxDevices] = {};
+  GWHE_REQUIRE(c->device >= 0 && c->device < kMaxDevices, ST_EINVAL, "device index out of range");
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr_set[c->device]) {
+      GWHE_CUDA(cudaFuncSetAttribute(k_ntt_cluster<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem));
+      GWHE_CUDA(cudaFuncSetAttribute(k_ntt_cluster<true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem));
+      GWHE_CUDA(cudaFuncSetAttribute(k_ntt_cluster<false, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem));
+      attr_set[c->device] = true;
+    }
+  }
+  const dim3 grid((unsigned)rows * kClusterCtas);
+  if (!fwd)
+    k_ntt_cluster<false, false><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb);
+  else if (epi)
+    k_ntt_cluster<true, true><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb,
+                                                                                  *epi);
+  else
+    k_ntt_cluster<true, false><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb);
+  GWHE_LAUNCHED(c, 1);
+}
+
 // shapes of the N = 2^16 transform (identical results; the autotuner times
 // them on the device and keeps the fastest)
 static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi) {
-  switch (c->ntt_variant) {
+  const int rows = rm.npoly * rm.nl;
+  switch (rows < kNttSmallRows ? c->ntt_variant_small : c->ntt_variant) {
+    case 6: ntt_cluster_16(c, data, rm, fwd, epi); return;
     case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd, epi); return;
     case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd, epi); return;
     case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd, epi); return;
@@ -285,7 +547,7 @@ static bool ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd,
   if (rows <= 0) return true;
   // algorithmic traffic: every residue read once and written once
   ProfScope ps(c, PROF_NTT, 16.0 * rows * c->N);
-  GWHE_REQUIRE(rm.nl <= kMaxRowLimbs, ST_EINVAL, "too many limbs in a row map");
+  GWHE_REQUIRE(rm.nl <= kMaxRowMap, ST_EINVAL, "too many limbs in a row map");
   switch (c->logN) {
     case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd, epi); return true;
     case 16: ntt_2_16(c, data, rm, fwd, epi); return true;

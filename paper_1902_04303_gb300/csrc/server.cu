@@ -44,6 +44,9 @@ struct Request {
   int status = GWHE_OK;
   std::string error;
   double t_submit = 0, t_start = 0, t_done = 0;
+  // device timeline of the job (ms after the server's reference event)
+  double dev_start = 0, dev_end = 0;
+  bool hi = false;  // ran on its worker's high-priority stream
   bool done = false;
 };
 typedef std::shared_ptr<Request> ReqPtr;
@@ -64,6 +67,11 @@ struct gwhe_server {
   int live = 0, failed = 0;
   std::string setup_error;
   std::condition_variable cv_setup;
+  // one running job at a time holds the high-priority token: its kernels
+  // are scheduled first, the others' fill the SMs it leaves idle
+  bool hi_taken = false;
+  // reference point of the jobs' device timelines (recorded at creation)
+  cudaEvent_t t0 = nullptr;
   bool stop = false;
 };
 
@@ -122,17 +130,26 @@ void run_request(Context* c, Request& r, int chunk) {
 }
 
 void worker_main(gwhe_server* srv) {
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr, st_lo = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   Context* c = nullptr;
   try {
-    // a new thread starts on device 0: the stream and the child context
+    // a new thread starts on device 0: the streams and the child context
     // belong on the owner's device, with its keys and tables
     GWHE_CUDA(cudaSetDevice(srv->owner->c->device));
-    GWHE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    GWHE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GWHE_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest));
+    GWHE_CUDA(cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, least));
+    GWHE_CUDA(cudaEventCreate(&e0));
+    GWHE_CUDA(cudaEventCreate(&e1));
     c = ctx_child(srv->owner->c, st);
   } catch (const std::exception& e) {
     // without a context this worker takes no work; the others carry on
     if (st) cudaStreamDestroy(st);
+    if (st_lo) cudaStreamDestroy(st_lo);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       ++srv->failed;
@@ -169,21 +186,35 @@ void worker_main(gwhe_server* srv) {
       ++srv->running;
       srv->max_running = std::max(srv->max_running, srv->running);
       if (r->dupm_chunk > 0) ++srv->host_tier;
+      r->hi = !srv->hi_taken;
+      if (r->hi) srv->hi_taken = true;
       r->t_start = now_ms();
     }
+    // the previous job on this worker has finished on both streams (its
+    // run ended with a synchronisation), so switching needs no ordering
+    c->stream = r->hi ? st : st_lo;
     try {
+      GWHE_CUDA(cudaEventRecord(e0, c->stream));
       run_request(c, *r, srv->chunk);
+      GWHE_CUDA(cudaEventRecord(e1, c->stream));
+      GWHE_CUDA(cudaEventSynchronize(e1));
+      float a = 0.f, b = 0.f;
+      GWHE_CUDA(cudaEventElapsedTime(&a, srv->t0, e0));
+      GWHE_CUDA(cudaEventElapsedTime(&b, srv->t0, e1));
+      r->dev_start = a;
+      r->dev_end = b;
     } catch (const Error& e) {
       r->status = e.code;
       r->error = e.what();
-      cudaStreamSynchronize(st);
+      cudaStreamSynchronize(c->stream);
     } catch (const std::exception& e) {
       r->status = GWHE_EINVAL;
       r->error = e.what();
-      cudaStreamSynchronize(st);
+      cudaStreamSynchronize(c->stream);
     }
     {
       std::lock_guard<std::mutex> lk(srv->mu);
+      if (r->hi) srv->hi_taken = false;
       srv->in_use -= r->footprint;
       --srv->running;
       r->t_done = now_ms();
@@ -198,8 +229,12 @@ void worker_main(gwhe_server* srv) {
     srv->cv_done.notify_all();
     srv->cv_work.notify_all();
   }
+  c->stream = st;
   ctx_destroy(c);
   cudaStreamDestroy(st);
+  cudaStreamDestroy(st_lo);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 }  // namespace
@@ -232,6 +267,12 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
     hbm_budget = (uint64_t)(0.6 * (double)fr);
   }
   s->budget = hbm_budget;
+  if (cudaEventCreate(&s->t0) != cudaSuccess || cudaEventRecord(s->t0, c->stream) != cudaSuccess ||
+      cudaEventSynchronize(s->t0) != cudaSuccess) {
+    if (s->t0) cudaEventDestroy(s->t0);
+    c->last_error = "server: reference event failed";
+    return GWHE_ECUDA;
+  }
   for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s.get());
   {
     // every worker has set up or failed; with none alive, no job could ever
@@ -243,6 +284,7 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
       s->stop = true;
       lk.unlock();
       for (auto& t : s->workers) t.join();
+      cudaEventDestroy(s->t0);
       return GWHE_ECUDA;
     }
   }
@@ -319,6 +361,9 @@ int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* 
     times_ms[0] = r->t_start - r->t_submit;  // waiting for admission
     times_ms[1] = r->t_done - r->t_start;    // on a worker
     times_ms[2] = r->t_done - r->t_submit;   // total latency
+    times_ms[3] = r->dev_start;              // device timeline
+    times_ms[4] = r->dev_end;
+    times_ms[5] = r->hi ? 1.0 : 0.0;
   }
   if (r->status != GWHE_OK) {
     s->owner->c->last_error = "server job " + std::to_string(id) + ": " + r->error;
@@ -360,6 +405,7 @@ int gwhe_server_destroy(gwhe_server* s) {
   s->cv_work.notify_all();
   s->cv_done.notify_all();
   for (auto& t : s->workers) t.join();
+  if (s->t0) cudaEventDestroy(s->t0);
   delete s;
   return GWHE_OK;
 }

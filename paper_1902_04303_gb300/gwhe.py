@@ -120,6 +120,9 @@ _SIGS = {
     "gwhe_ctx_device": [_vp, ctypes.POINTER(_i)],
     "gwhe_ctx_set_stream": [_vp, _vp],
     "gwhe_rotate_batch": [_vp, ctypes.POINTER(_vp), _i, ctypes.c_int32, _i, ctypes.POINTER(_vp)],
+    "gwhe_job_state_size": [_vp, ctypes.POINTER(_sz)],
+    "gwhe_job_export_state": [_vp, _vp, _sz],
+    "gwhe_job_import_state": [_vp, _vp, _sz],
     "gwhe_encrypt_covariates": [_vp, _vp, _vp],
     "gwhe_encrypt_phenotype": [_vp, _vp],
     "gwhe_encrypt_snps": [_vp, _vp, _l, _l],
@@ -489,7 +492,7 @@ class Context:
     def autotune(self, rows=512):
         """time the compiled shapes of the N = 2^16 transform, keep the fastest;
         returns (chosen shape, ms per shape)."""
-        ms = (ctypes.c_double * 6)()
+        ms = (ctypes.c_double * NTT_SHAPES)()
         ch = _i(0)
         self._c(lib().gwhe_autotune(self.h, rows, ms, ctypes.byref(ch)))
         return ch.value, [round(float(x), 4) for x in ms]
@@ -551,6 +554,7 @@ class Context:
 
 
 LAYOUTS = {"auto": 0, "mccp": 1, "factored": 2}
+NTT_SHAPES = 7  # compiled shapes of the N = 2^16 transform (gwhe_autotune)
 
 
 class Job:
@@ -645,6 +649,27 @@ class Job:
         self.ctx._c(lib().gwhe_decrypt_results(self.h, num, den))
         return num, den
 
+    def state_words(self):
+        """size (uint64 words) of the batch-invariant state after the fit"""
+        w = _sz(0)
+        self.ctx._c(lib().gwhe_job_state_size(self.h, ctypes.byref(w)))
+        return w.value
+
+    def export_state(self, out=None):
+        """the covariate phase's batch-invariant state as a flat uint64 buffer
+        (numpy array, or into `out`: a torch tensor of int64 on host or device)"""
+        words = self.state_words()
+        if out is None:
+            out = np.zeros(words, np.uint64)
+        self.ctx._c(lib().gwhe_job_export_state(self.h, _ptr(out), words))
+        return out
+
+    def import_state(self, buf):
+        """take the state exported by a job of the same shape under the same
+        keys (numpy uint64 array or torch int64 tensor, host or device)"""
+        n = buf.numel() if hasattr(buf, "numel") else buf.size
+        self.ctx._c(lib().gwhe_job_import_state(self.h, _ptr(buf), n))
+
     def set_nonce(self, nonce):
         """offset of this job's encryption ids (distinct per live job under one key)."""
         self.ctx._c(lib().gwhe_job_set_nonce(self.h, nonce))
@@ -705,13 +730,16 @@ class Server:
         return rid.value
 
     def wait(self, rid):
-        """(num[k], den[k], {"queue_ms", "run_ms", "latency_ms"})"""
+        """(num[k], den[k], {"queue_ms", "run_ms", "latency_ms", "device_start_ms",
+        "device_end_ms", "high_priority"})"""
         k = self._k.pop(rid)
         num = np.full(k, np.nan)
         den = np.full(k, np.nan)
-        t = np.zeros(3)
+        t = np.zeros(6)
         self.ctx._c(lib().gwhe_server_wait(self.h, rid, num, den, t))
-        return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2]}
+        return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2],
+                          "device_start_ms": t[3], "device_end_ms": t[4],
+                          "high_priority": bool(t[5])}
 
     def stats(self):
         out = (_l * 9)()

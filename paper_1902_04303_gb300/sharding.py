@@ -3,12 +3,15 @@
 After the covariate phase (Alg. 9, the preamble of Alg. 11) the SNP batches
 of the loop in Alg. 11 are independent: each needs only the batch-invariant
 state (Dup(w), Dup(w z'), and Dup(M_j) or Dup(X_c)/Dup((XA)_c)) and its own
-tau SNP columns.  A job therefore shards by batch ranges: every rank runs the
-covariate phase on the same encrypted inputs (it is deterministic, so all
-ranks hold identical state without moving gigabytes of ciphertexts), then
-evaluates its own contiguous range of batches; the decrypted per-SNP
-numerators and denominators are gathered once at the end (8 bytes x 2 per
-SNP).  There is no collective on the data path.
+tau SNP columns.  A job therefore shards by batch ranges.  Rank 0 encrypts
+the inputs and runs the covariate phase; its batch-invariant state (about 66
+MB at the paper's shape in the factored layout) is broadcast once to the
+other ranks, which import it into their own job handle (same context seed,
+hence the same keys); every rank then evaluates its own contiguous range of
+batches, and the decrypted per-SNP numerators and denominators are gathered
+once at the end (8 bytes x 2 per SNP).  Without the broadcast every rank
+would repeat the deterministic fit.  The batches' data path has no
+collective.
 
 Independent jobs (several cohorts, or one job per GPU in the benchmark) need
 no coordination at all beyond the timing barrier.
@@ -94,14 +97,42 @@ def max_over_ranks(value: float, group=None, device=None) -> float:
     return float(t.item())
 
 
+def broadcast_state(job, rank: int, src: int = 0, group=None, device=None):
+    """One broadcast of the batch-invariant state: rank src exports its job's
+    state (after its fit), every other rank imports it into its own job.
+    job needs state_words(), export_state(buf) and import_state(buf); the
+    buffer is an int64 tensor on `device` (cpu for gloo, cuda for nccl).
+    Returns the number of 8-byte words moved."""
+    import torch
+    import torch.distributed as dist
+
+    dev = device if device is not None else "cpu"
+    n = torch.tensor([job.state_words() if rank == src else 0], dtype=torch.int64, device=dev)
+    dist.broadcast(n, src, group=group)
+    buf = torch.empty(int(n.item()), dtype=torch.int64, device=dev)
+    if rank == src:
+        job.export_state(buf)
+    dist.broadcast(buf, src, group=group)
+    if rank != src:
+        job.import_state(buf)
+    return int(n.item())
+
+
 def run_sharded_job(ctx, job, X, A, y, S, kappa: int, rank: int, world: int, group=None,
-                    device=None):
-    """One encrypted GWAS job over ranks: every rank encrypts the inputs and
-    runs the covariate phase (identical, deterministic state), evaluates its
-    own batch range, decrypts it, and the results are gathered on all ranks.
+                    device=None, share_state: bool = True):
+    """One encrypted GWAS job over ranks: rank 0 encrypts the inputs and runs
+    the covariate phase and its state is broadcast (share_state; otherwise
+    every rank repeats the deterministic fit), every rank evaluates its own
+    batch range and decrypts it, and the results are gathered on all ranks.
     Returns (num[k], den[k], (b0, b1))."""
-    job.encrypt_inputs(X, A, y)
-    job.fit(kappa)
+    if share_state and world > 1:
+        if rank == 0:
+            job.encrypt_inputs(X, A, y)
+            job.fit(kappa)
+        broadcast_state(job, rank, 0, group, device)
+    else:
+        job.encrypt_inputs(X, A, y)
+        job.fit(kappa)
     b0, b1 = shard_batches(job.layout["batches"], world, rank)
     if b1 > b0:
         job.snp_stats(S, b0, b1)

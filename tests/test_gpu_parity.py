@@ -292,7 +292,7 @@ def test_hoisted_rotation_sum_batch_bit_exact(g, small):
         assert np.array_equal(out.export(), o.rotate_sum(a, rs).c)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_every_ntt_shape_is_bit_exact(g, variant):
     """each compiled shape of the N = 2^16 transform gives the oracle's
     residues (round trip, negacyclic product, one key switch)."""
@@ -313,9 +313,10 @@ def test_every_ntt_shape_is_bit_exact(g, variant):
 
 def test_autotune_picks_a_shape(g):
     ctx = g.Context(16, 2, K=1, dnum=2, seed=1)
-    v, ms = ctx.autotune(rows=64)
-    assert 0 <= v < 6 and len(ms) == 6 and all(x > 0 for x in ms)
-    assert ms[v] == min(ms)
+    for rows in (64, 512):  # the small- and the large-launch class
+        v, ms = ctx.autotune(rows=rows)
+        assert 0 <= v < g.NTT_SHAPES and len(ms) == g.NTT_SHAPES and all(x > 0 for x in ms)
+        assert ms[v] == min(ms)
 
 
 # ------------------------------------------------------------------ the job's basis, set widths

@@ -54,16 +54,31 @@ def test_results_are_the_same_alone_and_in_the_mix(g, setup):
     ctx, reqs, alone = setup
     srv = g.Server(ctx, workers=3, chunk_batches=2)
     ids = [srv.submit(data.X, A, data.y, data.S, nonce=nonce) for data, A, nonce in reqs]
+    spans = []
     for rid, (data, A, nonce), (num0, den0) in zip(ids, reqs, alone):
         num, den, t = srv.wait(rid)
         assert np.array_equal(num, num0) and np.array_equal(den, den0), nonce
         assert t["latency_ms"] >= t["run_ms"] > 0
+        assert t["device_end_ms"] > t["device_start_ms"] >= 0
+        spans.append((t["device_start_ms"], t["device_end_ms"], t["high_priority"]))
         ref = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1, A=A)
         ok = np.abs(ref["den"]) > 1e-6
         assert np.max(np.abs(num[ok] / den[ok] - ref["b"][ok])) <= 5e-3
     st = srv.stats()
     assert st["admitted"] == len(reqs) and st["running"] == 0 and st["waiting"] == 0
     assert st["peak_bytes_claimed"] <= st["budget"]
+    assert st["live_workers"] == 3
+    # the jobs were resident at once and their work overlapped on the device:
+    # at some device time at least two jobs' spans are open, and at most one
+    # of the jobs running together holds the high-priority stream
+    fps = [g.job_footprint(ctx, *data.X.shape, data.S.shape[1], chunk_batches=2)
+           for data, _, _ in reqs]
+    assert st["max_running"] >= 2 and st["peak_bytes_claimed"] > max(fps)
+    overlap = max(sum(1 for a, b, _ in spans if a <= s0 < b) for s0, _, _ in spans)
+    assert overlap >= 2, spans
+    for s0, _, hi in spans:
+        if hi:
+            assert sum(1 for a, b, h in spans if h and a <= s0 < b) == 1
     srv.close()
 
 

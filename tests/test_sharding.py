@@ -122,6 +122,28 @@ class _PlainJob:
         self.calls.append(("batches", b0, b1))
         self.kept.append((b0, b1, S))
 
+    # the batch-invariant state: here the plaintext inputs the fit used,
+    # as float64 words carried in an int64 buffer
+    def _state(self):
+        return np.concatenate([self.X.ravel(), self.A.ravel(), self.y.ravel(), [self.kappa]])
+
+    def state_words(self):
+        return self._state().size
+
+    def export_state(self, buf):
+        import torch
+        self.calls.append("export")
+        buf.copy_(torch.from_numpy(self._state().view(np.int64)))
+
+    def import_state(self, buf):
+        self.calls.append("import")
+        v = buf.numpy().view(np.float64)
+        n, d = self.n, self.d
+        self.X = v[:n * d].reshape(n, d)
+        self.A = v[n * d:n * d + d * d].reshape(d, d)
+        self.y = v[n * d + d * d:n * d + d * d + n]
+        self.kappa = int(v[-1])
+
     def decrypt_results(self):
         num = np.full(self.k, np.nan)
         den = np.full(self.k, np.nan)
@@ -133,7 +155,7 @@ class _PlainJob:
         return num, den
 
 
-def _job_main(rank, world, port, out_dir):
+def _job_main(rank, world, port, out_dir, share_state=True):
     import torch.distributed as dist
 
     from paper_1902_04303_gb300.sharding import run_sharded_job
@@ -146,19 +168,22 @@ def _job_main(rank, world, port, out_dir):
         data = make_gwas(n, d, k, seed=9)
         job = _PlainJob(n, d, k, tau)
         num, den, rng = run_sharded_job(None, job, data.X, gwas_fp64.xtx_inv(data.X), data.y,
-                                        data.S, 1, rank, world)
+                                        data.S, 1, rank, world, share_state=share_state)
         np.savez(os.path.join(out_dir, "job%d.npz" % rank), num=num, den=den, rng=np.array(rng),
                  calls=np.array([str(c) for c in job.calls]))
     finally:
         dist.destroy_process_group()
 
 
-def test_run_sharded_job_on_gloo_ranks(tmp_path):
-    """every rank fits, evaluates only its own batch range, and ends with the
-    complete results (4 batches over 2 ranks)."""
+@pytest.mark.parametrize("share_state", [True, False])
+def test_run_sharded_job_on_gloo_ranks(tmp_path, share_state):
+    """With share_state rank 0 alone fits and broadcasts the batch-invariant
+    state, which rank 1 imports; without it every rank fits.  Each rank
+    evaluates only its own batch range and ends with the complete results
+    (4 batches over 2 ranks)."""
     import torch.multiprocessing as mp
 
-    mp.start_processes(_job_main, args=(2, _free_port(), str(tmp_path)), nprocs=2,
+    mp.start_processes(_job_main, args=(2, _free_port(), str(tmp_path), share_state), nprocs=2,
                        start_method="spawn", join=True)
     data = make_gwas(32, 3, 200, seed=9)
     full = gwas_fp64.semi_parallel_fp64(data.X, data.y, data.S, kappa=1,
@@ -167,6 +192,13 @@ def test_run_sharded_job_on_gloo_ranks(tmp_path):
     for r in range(2):
         got = np.load(tmp_path / ("job%d.npz" % r))
         assert tuple(got["rng"]) == want_ranges[r]
-        assert list(got["calls"]) == ["encrypt", "fit", str(("batches",) + want_ranges[r])]
+        batches = str(("batches",) + want_ranges[r])
+        if not share_state:
+            want_calls = ["encrypt", "fit", batches]
+        elif r == 0:
+            want_calls = ["encrypt", "fit", "export", batches]
+        else:
+            want_calls = ["import", batches]
+        assert list(got["calls"]) == want_calls
         assert np.allclose(got["num"], full["num"], rtol=1e-12, atol=1e-12)
         assert np.allclose(got["den"], full["den"], rtol=1e-12, atol=1e-12)
