@@ -191,6 +191,12 @@ def run_gpu(args):
     # launches and for those of a few waves or less
     tuned = ctx.autotune()
     tuned_small = ctx.autotune(rows=32)
+    if args.ntt_shape >= 0:
+        # a fixed shape (profiler captures, whose serialised launches would
+        # mislead the autotuner)
+        ctx.set_ntt_variant(args.ntt_shape)
+        tuned = (args.ntt_shape, tuned[1])
+        tuned_small = (args.ntt_shape, tuned_small[1])
     data = make_gwas(W["n"], W["d"], W["k"], seed=W["seed"] + rank)
     A = client_preprocess(data.X)
     dev = {nm: torch.from_numpy(np.ascontiguousarray(v)).cuda()
@@ -818,7 +824,7 @@ def run_cohorts(args):
     t_seq = time.perf_counter() - t0
     srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64)
     t0 = time.perf_counter()
-    ids = [srv.submit(data.X, A, data.y, data.S, kappa=W["kappa"], nonce=i + 1)
+    ids = [srv.submit(data.X, A, data.y, data.S, kappa=W["kappa"], nonce=i + 1, borrow=True)
            for i, (data, A) in enumerate(inputs)]
     res = [srv.wait(rid) for rid in ids]
     t_srv = time.perf_counter() - t0
@@ -885,7 +891,7 @@ def run_serving(args):
         if dt > 0:
             time.sleep(dt)
         data, A = inputs[i]
-        rid = srv.submit(data.X, A, data.y, data.S, nonce=i + 1)
+        rid = srv.submit(data.X, A, data.y, data.S, nonce=i + 1, borrow=True)
         th = threading.Thread(target=waiter, args=(i, rid))
         th.start()
         threads.append(th)
@@ -935,6 +941,9 @@ def main():
                          "N=2^17 with kappa=3; cohorts16: 16 uneven cohorts one at a time and "
                          "batched; serving: Poisson request stream")
     ap.add_argument("--workers", type=int, default=4, help="serving-engine workers")
+    ap.add_argument("--ntt-shape", type=int, default=-1,
+                    help="use this compiled shape of the N=2^16 transform for every launch "
+                         "instead of the autotuned ones (for profiler captures)")
     ap.add_argument("--requests", type=int, default=SERVING["requests"])
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals/s (0: ~80%% busy)")
     args = ap.parse_args()

@@ -411,6 +411,13 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
 int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
                        const double* X, const double* XtX_inv, const double* y, const double* S,
                        long* id);
+/* As gwhe_server_submit, but S (host memory) is not copied: the caller keeps
+ * it alive and unchanged until gwhe_server_wait has returned for this job
+ * (the genotype matrix of a large job is gigabytes; its copy would run on
+ * the submitting thread). */
+int gwhe_server_submit_borrowed(gwhe_server* s, int n, int d, long k, int layout, int kappa,
+                                uint32_t nonce, const double* X, const double* XtX_inv,
+                                const double* y, const double* S, long* id);
 int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms);
 int gwhe_server_stats(gwhe_server* s, long out[9]);
 int gwhe_server_destroy(gwhe_server* s);

@@ -460,7 +460,7 @@ static void ctx_destroy_on_device(Context* c) {
     if (p) cudaFreeHost(p);
   if (c->pin_state) cudaFreeHost(c->pin_state);
   if (c->parent) {  // only the child's own state
-    for (auto& kv : c->masks) cudaFree(kv.second);
+    for (auto& kv : c->masks) cudaFreeAsync(kv.second, c->stream);
     for (auto& r : c->prof.recs) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -475,7 +475,7 @@ static void ctx_destroy_on_device(Context* c) {
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
                   (void*)c->d_slot_u, (void*)c->d_slot_inv})
     if (p) cudaFree(p);
-  for (auto& kv : c->masks) cudaFree(kv.second);
+  for (auto& kv : c->masks) cudaFreeAsync(kv.second, c->stream);
   for (u64* p : c->d_pinv)
     if (p) cudaFree(p);
   for (u64* p : c->d_fused)
@@ -1121,10 +1121,10 @@ const u64* mask_pt(Context* c, int kind, long index, int l, double scale,
   Tmp z(c, sizeof(double2) * M);
   GWHE_CUDA(cudaMemcpyAsync(z.p, slots.data(), sizeof(double2) * M, cudaMemcpyHostToDevice,
                             c->stream));
-  u64* pt = nullptr;
-  GWHE_CUDA(cudaMalloc(&pt, sizeof(u64) * l * c->N));
+  // from the stream-ordered pool and without a host wait: the mask is used
+  // only by this context's later launches on the same stream
+  u64* pt = dalloc_u64(c, (size_t)l * c->N);
   encode_to_ntt(c, z.as<double2>(), 1, scale, l, pt);
-  GWHE_CUDA(cudaStreamSynchronize(c->stream));
   c->masks[key] = pt;
   return pt;
 }

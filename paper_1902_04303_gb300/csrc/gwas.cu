@@ -960,8 +960,9 @@ struct TwoSlotCopy {
     cs = nullptr;
   }
   ~TwoSlotCopy() {
-    // the slots go back to the compute stream's pool after everything queued
-    cudaStreamSynchronize(c->stream);
+    // the copy stream is drained; the slots then go back to the compute
+    // stream's pool in stream order, after the work queued there that reads
+    // them (the compute stream waited for every copy), with no host wait
     destroy();
   }
 };
@@ -977,7 +978,11 @@ struct HostStager {
   TwoSlotCopy cp;
   HostStager(Context* c, int n_, long wmax_)
       : n(n_), wmax(wmax_), cp(c, sizeof(double) * (size_t)n_ * wmax_) {
-    const size_t need = sizeof(double) * (size_t)n * wmax;
+    // any job's set of 64 batches fits n x 64 tau <= 64 N doubles (n <= nb,
+    // tau = N / nb): the buffers are allocated at that size once per context,
+    // since pinned allocation and release synchronise the whole device
+    const size_t need = std::max(sizeof(double) * (size_t)n * wmax,
+                                 sizeof(double) * (size_t)kSnpChunk * c->N);
     if (c->pin_stage_bytes < need) {
       for (void*& p : c->pin_stage) {
         if (p) cudaFreeHost(p);

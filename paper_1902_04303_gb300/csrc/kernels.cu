@@ -1226,6 +1226,9 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
         c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
     return;
   }
+  // items per thread (each key word is read once per IB items); eight with
+  // more than three automorphisms would cost occupancy: measured slower even
+  // for sets of five to eight, where it saves the second read of the keys
   constexpr int IB = G <= 3 ? 8 : 4;
   const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
   k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,

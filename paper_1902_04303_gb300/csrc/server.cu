@@ -38,6 +38,7 @@ struct Request {
   long k = 0;
   u32 nonce = 0;
   std::vector<double> X, A, y, S;
+  const double* S_borrowed = nullptr;  // the caller's genotypes (not copied)
   size_t footprint = 0;
   int dupm_chunk = 0;  // > 0: Dup(M_j) in the host tier
   std::vector<double> num, den;
@@ -117,7 +118,7 @@ void run_request(Context* c, Request& r, int chunk) {
   std::vector<double> num(r.k), den(r.k);
   for (long b0 = 0; b0 < j->lay.batches; b0 += chunk) {
     const long b1 = std::min<long>(j->lay.batches, b0 + chunk);
-    job_snp_stats(j.get(), r.S.data(), b0, b1);
+    job_snp_stats(j.get(), r.S_borrowed ? r.S_borrowed : r.S.data(), b0, b1);
     job_decrypt(j.get(), num.data(), den.data());
     const long s0 = b0 * j->lay.tau, s1 = std::min<long>(r.k, b1 * j->lay.tau);
     for (long s = s0; s < s1; ++s) {
@@ -292,9 +293,9 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
   return GWHE_OK;
 }
 
-int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
-                       const double* X, const double* XtX_inv, const double* y, const double* S,
-                       long* id) {
+static int server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa,
+                         uint32_t nonce, const double* X, const double* XtX_inv, const double* y,
+                         const double* S, bool borrow, long* id) {
   if (!s || !X || !XtX_inv || !y || !S || !id || n < 1 || d < 1 || k < 1 || kappa < 1)
     return GWHE_EINVAL;
   Context* c = s->owner->c;
@@ -318,7 +319,10 @@ int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kap
   r->X.assign(X, X + (size_t)n * d);
   r->A.assign(XtX_inv, XtX_inv + (size_t)d * d);
   r->y.assign(y, y + n);
-  r->S.assign(S, S + (size_t)n * k);
+  if (borrow)
+    r->S_borrowed = S;
+  else
+    r->S.assign(S, S + (size_t)n * k);
   const bool factored =
       layout == kLayoutFactored || (layout == kLayoutAuto && c->P.L > kMLevel);
   r->footprint = footprint(c, n, d, k, factored, s->chunk);
@@ -344,6 +348,18 @@ int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kap
   }
   s->cv_work.notify_all();
   return GWHE_OK;
+}
+
+int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
+                       const double* X, const double* XtX_inv, const double* y, const double* S,
+                       long* id) {
+  return server_submit(s, n, d, k, layout, kappa, nonce, X, XtX_inv, y, S, false, id);
+}
+
+int gwhe_server_submit_borrowed(gwhe_server* s, int n, int d, long k, int layout, int kappa,
+                                uint32_t nonce, const double* X, const double* XtX_inv,
+                                const double* y, const double* S, long* id) {
+  return server_submit(s, n, d, k, layout, kappa, nonce, X, XtX_inv, y, S, true, id);
 }
 
 int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* times_ms) {

@@ -99,6 +99,8 @@ _SIGS = {
     "gwhe_server_submit": [_vp, _i, _i, _l, _i, _i, _u32, _f64p, _f64p, _f64p, _f64p,
                            ctypes.POINTER(_l)],
     "gwhe_server_wait": [_vp, _l, _f64p, _f64p, _f64p],
+    "gwhe_server_submit_borrowed": [_vp, _i, _i, _l, _i, _i, _u32, _f64p, _f64p, _f64p, _f64p,
+                                    ctypes.POINTER(_l)],
     "gwhe_server_stats": [_vp, ctypes.POINTER(_l)],
     "gwhe_server_destroy": [_vp],
     "gwhe_rotate_sum": [_vp, _vp, ctypes.POINTER(ctypes.c_int32), _i, _vp],
@@ -716,7 +718,9 @@ class Server:
         self._k = {}
         ctx._children.add(self)
 
-    def submit(self, X, XtX_inv, y, S, kappa=1, layout="auto", nonce=0):
+    def submit(self, X, XtX_inv, y, S, kappa=1, layout="auto", nonce=0, borrow=False):
+        """queue one job; borrow=True leaves S in place (kept referenced here
+        until wait) instead of copying it"""
         X = np.ascontiguousarray(X, np.float64)
         A = np.ascontiguousarray(XtX_inv, np.float64)
         y = np.ascontiguousarray(y, np.float64)
@@ -724,15 +728,16 @@ class Server:
         n, d = X.shape
         k = S.shape[1]
         rid = _l(0)
-        self.ctx._c(lib().gwhe_server_submit(self.h, n, d, k, LAYOUTS[layout], kappa, nonce,
-                                             X, A, y, S, ctypes.byref(rid)))
-        self._k[rid.value] = k
+        f = lib().gwhe_server_submit_borrowed if borrow else lib().gwhe_server_submit
+        self.ctx._c(f(self.h, n, d, k, LAYOUTS[layout], kappa, nonce, X, A, y, S,
+                      ctypes.byref(rid)))
+        self._k[rid.value] = (k, S if borrow else None)
         return rid.value
 
     def wait(self, rid):
         """(num[k], den[k], {"queue_ms", "run_ms", "latency_ms", "device_start_ms",
         "device_end_ms", "high_priority"})"""
-        k = self._k.pop(rid)
+        k, _held = self._k.pop(rid)  # a borrowed S stays referenced until here
         num = np.full(k, np.nan)
         den = np.full(k, np.nan)
         t = np.zeros(6)

@@ -89,7 +89,9 @@ def test_budget_admits_one_job_at_a_time(g, setup):
            for data, _, _ in reqs]
     budget = max(fps) + min(fps) - 1
     srv = g.Server(ctx, workers=3, hbm_budget=budget, chunk_batches=2)
-    ids = [srv.submit(data.X, A, data.y, data.S, nonce=nonce) for data, A, nonce in reqs]
+    # the genotypes borrowed, not copied, at submission
+    ids = [srv.submit(data.X, A, data.y, data.S, nonce=nonce, borrow=True)
+           for data, A, nonce in reqs]
     for rid, (num0, den0) in zip(ids, alone):
         num, den, _ = srv.wait(rid)
         assert np.array_equal(num, num0) and np.array_equal(den, den0)
