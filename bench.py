@@ -125,9 +125,9 @@ class Clocks:
 # the multiply-add pipe, not issue, bounds the transform.
 NUM_SMS = 152
 FMAHEAVY_CYCLES_PER_WARP_BFLY = 34.7
-# ncu, 3072 rows of 2^16 (the row pass reading its last stages' twiddles from
-# the transposed table): pass A 1.611 + 1.555 GB, pass B 1.849 + 1.557 GB
-NTT_DRAM_BYTES_PER_LIMB = round((1.611e9 + 1.555e9 + 1.849e9 + 1.557e9) / 3072)
+# ncu, 3072 rows of 2^16 in shape 4 (profiles/ntt_pass_ntt-ks-micro.md): DRAM
+# read + write of pass A 1.611 + 1.555 GB, pass B 1.858 + 1.561 GB
+NTT_DRAM_BYTES_PER_LIMB = round((1.611e9 + 1.555e9 + 1.858e9 + 1.561e9) / 3072)
 
 
 def alu_peak_gbfly(sm_mhz):
@@ -250,6 +250,9 @@ def run_gpu(args):
         t = torch.tensor([step_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
+    # the context's pinned staging buffers for host genotypes are allocated by
+    # its first host-input job (once, like the keys): one untimed step
+    step(host)
     ms_e2e, _ = timed(host, max(1, args.steps))
     e2e_ms = float(np.mean(ms_e2e))
     if world > 1:
@@ -342,7 +345,8 @@ def run_gpu(args):
                      # DRAM bytes per limb transform (both passes) from the ncu
                      # capture of the 3072-limb batch (profiles/), against the
                      # algorithmic 1 MiB (each residue read and written once)
-                     "traffic": NTT_DRAM_BYTES_PER_LIMB if W["logN"] == 16 else None,
+                     "traffic": (NTT_DRAM_BYTES_PER_LIMB
+                                 if W["logN"] == 16 and tuned[0] == 4 else None),
                      "traffic_unit": "bytes per limb transform (dram read + write, ncu)",
                      "traffic_algorithmic": (1 << W["logN"]) * 8 * 2,
                      "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -365,7 +369,8 @@ def run_gpu(args):
         "keyswitch_per_s": round(ks_per_job * world / (step_ms / 1e3), 1),
         "keyswitches_per_job": ks_per_job,
         "e2e": {"value": round(snps / (e2e_ms / 1e3), 1), "unit": "SNPs/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": int(launches),
         "phases_ms": phases,
         "autotune": {"ntt_shape": tuned[0], "ms_per_shape": tuned[1],
@@ -376,7 +381,7 @@ def run_gpu(args):
     if mccp:
         out["mccp"] = mccp
     if not args.no_micro:
-        out["micro"] = run_micro(stream, clk_mhz=clk_mhz)
+        out["micro"] = run_micro(stream, clk_mhz=clk_mhz, ntt_shape=args.ntt_shape)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, layout_used == "factored", ks_hist,
                                            gpu=(data, A, num, den))
@@ -411,7 +416,7 @@ def keyswitch_work(logN, l, K, alpha):
             "hbm_bytes": limbs * 8 * N, "key_bytes": 2 * beta * (l + K) * 8 * N}
 
 
-def run_micro(ctx_stream, reps=3, clk_mhz=2070.0):
+def run_micro(ctx_stream, reps=3, clk_mhz=2070.0, ntt_shape=-1):
     """Kernel microbench: a batched negacyclic NTT + inverse NTT over 64
     ciphertexts x 2 polys x 24 limbs (3072 limb transforms, N = 2^16), and 512
     rotations (64 ciphertexts x steps 1, 2, ..., 128) at level 24, each
@@ -426,6 +431,11 @@ def run_micro(ctx_stream, reps=3, clk_mhz=2070.0):
     ctx = gwhe.Context(W["logN"], W["L"], W["q0_bits"], W["scale_bits"], W["K"], W["sp_bits"],
                        W["dnum"], seed=W["seed"], stream=stream.cuda_stream)
     tuned = ctx.autotune()
+    ctx.autotune(rows=32)
+    if ntt_shape >= 0:
+        ctx.set_ntt_variant(ntt_shape)
+        tuned = (ntt_shape, tuned[1])
+    nvtx = torch.cuda.nvtx
     steps = [1 << i for i in range(8)]
     N, L, nct = ctx.N, W["L"], W["n_ct"]
     rows = nct * 2 * L
@@ -440,11 +450,15 @@ def run_micro(ctx_stream, reps=3, clk_mhz=2070.0):
     torch.cuda.synchronize()
     ok = bool(torch.equal(x, ref))
     ms = []
+    # NVTX ranges name the timed work, so that profilers can select it
+    # (ncu --nvtx --nvtx-include "ntt_3072/")
     for _ in range(reps):
+        nvtx.range_push("ntt_3072")
         e0 = ev()
         ctx.ntt_batch(x, nct * 2, L)
         ctx.ntt_batch(x, nct * 2, L, inverse=True)
         e1 = ev()
+        nvtx.range_pop()
         e1.synchronize()
         ms.append(e0.elapsed_time(e1) / 2)  # per transform direction
     t_ntt = min(ms) / 1e3
@@ -473,9 +487,11 @@ def run_micro(ctx_stream, reps=3, clk_mhz=2070.0):
         outs = ctx.rotate_sum_batch(src, [1, 2, 3, 4, 5, 6, 7])
         hm = []
         for _ in range(reps):
+            nvtx.range_push("hoist7_%dx%d" % (cnt, lv))
             e0 = ev()
             ctx.rotate_sum_batch(src, [1, 2, 3, 4, 5, 6, 7], outs)
             e1 = ev()
+            nvtx.range_pop()
             e1.synchronize()
             hm.append(e0.elapsed_time(e1))
         hoist["hoisted7_ms_%dx%dlimbs" % (cnt, lv)] = round(min(hm), 3)
@@ -489,10 +505,12 @@ def run_micro(ctx_stream, reps=3, clk_mhz=2070.0):
     torch.cuda.synchronize()
     ks = []
     for _ in range(reps):
+        nvtx.range_push("ks_level24")
         e0 = ev()
         for r in steps:
             ctx.rotate_batch(cts, r, rescale=True, outs=outs)
         e1 = ev()
+        nvtx.range_pop()
         e1.synchronize()
         ks.append(e0.elapsed_time(e1))
     t_ks = min(ks) / 1e3
@@ -822,7 +840,8 @@ def run_cohorts(args):
     seq = [one(i) for i in range(len(shapes))]
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64)
+    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64,
+                      one_snp_loop=args.one_snp_loop)
     t0 = time.perf_counter()
     ids = [srv.submit(data.X, A, data.y, data.S, kappa=W["kappa"], nonce=i + 1, borrow=True)
            for i, (data, A) in enumerate(inputs)]
@@ -837,7 +856,8 @@ def run_cohorts(args):
            "warmup": 1, "ms_per_step": round(t_srv * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": {"workload": W["name"], "jobs": [list(x) for x in shapes],
-                      "workers": args.workers, "snps": snps},
+                      "workers": args.workers, "snps": snps,
+                      "one_snp_loop_at_a_time": bool(args.one_snp_loop)},
            "one_at_a_time": {"value": round(snps / t_seq, 1), "ms": round(t_seq * 1e3, 1)},
            "speedup_vs_one_at_a_time": round(t_seq / t_srv, 3),
            "same_results_alone_and_batched": bool(same),
@@ -864,7 +884,8 @@ def run_serving(args):
     shapes = [S_["big"] if rng.random() < S_["big_fraction"] else mix[i] for i in range(nreq)]
     ctx = _serving_ctx(gwhe, stream, shapes)
     inputs = _cohort_inputs(shapes, S_["seed"] + 1000)
-    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64)
+    srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64,
+                      one_snp_loop=args.one_snp_loop)
     # calibration: mean service time of the cohort mix alone (4 jobs, one at a time)
     cal = []
     for i in range(min(4, nreq)):
@@ -908,7 +929,8 @@ def run_serving(args):
            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": {"workload": "serving%d" % nreq, "requests": nreq,
                       "big_jobs": sum(1 for x in shapes if x == S_["big"]),
-                      "arrival_rate_per_s": round(rate, 3), "workers": args.workers},
+                      "arrival_rate_per_s": round(rate, 3), "workers": args.workers,
+                      "one_snp_loop_at_a_time": bool(args.one_snp_loop)},
            "latency_ms": {"p50": round(float(np.percentile(tot, 50)), 1),
                           "p99": round(float(np.percentile(tot, 99)), 1),
                           "max": round(float(tot.max()), 1)},
@@ -941,6 +963,9 @@ def main():
                          "N=2^17 with kappa=3; cohorts16: 16 uneven cohorts one at a time and "
                          "batched; serving: Poisson request stream")
     ap.add_argument("--workers", type=int, default=4, help="serving-engine workers")
+    ap.add_argument("--one-snp-loop", action="store_true",
+                    help="serving engine: SNP loops one at a time at high priority, covariate "
+                         "phases overlapping them at low priority")
     ap.add_argument("--ntt-shape", type=int, default=-1,
                     help="use this compiled shape of the N=2^16 transform for every launch "
                          "instead of the autotuned ones (for profiler captures)")
@@ -958,7 +983,8 @@ def main():
         from paper_1902_04303_gb300 import build as pkg_build
         pkg_build.build()
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps(run_micro(torch.cuda.current_stream(), reps=max(1, args.steps))))
+        print(json.dumps(run_micro(torch.cuda.current_stream(), reps=max(1, args.steps),
+                                   ntt_shape=args.ntt_shape)))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -393,11 +393,13 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
  *           the host tier (gwhe_job_set_host_state, min(32, n/4) columns per
  *           chunk) if that fits; ENOMEM if neither fits.
  *   wait:   blocks until the job is done; num[k], den[k] as
- *           gwhe_decrypt_results; times_ms (optional, 6 entries) =
+ *           gwhe_decrypt_results; times_ms (optional, 8 entries) =
  *           {waiting for admission, running, total (host clock, ms), start
- *           and end of the job's work on the device (ms after the server's
- *           creation, device clock), 1 if it ran on the high-priority
- *           stream}; the job's status is returned and the job is forgotten.
+ *           and end of the job's work on the device and start and end of
+ *           its SNP loop there (ms after the server's creation, device
+ *           clock, entries 3, 4, 6, 7), 1 if its SNP loop ran on the
+ *           high-priority stream (entry 5)}; the job's status is returned
+ *           and the job is forgotten.
  *   stats:  {admitted, running, waiting, bytes claimed, peak bytes claimed,
  *           budget, jobs run with Dup(M_j) in the host tier, most jobs
  *           running at once, workers alive}.
@@ -408,6 +410,15 @@ long gwhe_job_footprint(const gwhe_ctx* ctx, int n, int d, long k, int layout, i
 typedef struct gwhe_server gwhe_server;
 int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
                        gwhe_server** out);
+/* flags: GWHE_SERVER_ONE_SNP_LOOP makes the jobs' covariate phases run on
+ * the low-priority streams and their SNP loops one at a time (a job waits
+ * after its fit until no other loop runs), each loop on its worker's
+ * high-priority stream: a loop saturates the GPU by itself, two of them only
+ * contend, while the covariate phases' small launches fill the SMs a loop
+ * leaves idle.  Without the flag the priority goes as described above. */
+#define GWHE_SERVER_ONE_SNP_LOOP 1
+int gwhe_server_create_ex(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
+                          int flags, gwhe_server** out);
 int gwhe_server_submit(gwhe_server* s, int n, int d, long k, int layout, int kappa, uint32_t nonce,
                        const double* X, const double* XtX_inv, const double* y, const double* S,
                        long* id);

@@ -460,7 +460,10 @@ static void ctx_destroy_on_device(Context* c) {
     if (p) cudaFreeHost(p);
   if (c->pin_state) cudaFreeHost(c->pin_state);
   if (c->parent) {  // only the child's own state
-    for (auto& kv : c->masks) cudaFreeAsync(kv.second, c->stream);
+    for (auto& kv : c->masks) {
+      cudaFreeAsync(kv.second.pt, c->stream);
+      cudaEventDestroy(kv.second.done);
+    }
     for (auto& r : c->prof.recs) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -475,7 +478,10 @@ static void ctx_destroy_on_device(Context* c) {
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
                   (void*)c->d_slot_u, (void*)c->d_slot_inv})
     if (p) cudaFree(p);
-  for (auto& kv : c->masks) cudaFreeAsync(kv.second, c->stream);
+  for (auto& kv : c->masks) {
+      cudaFreeAsync(kv.second.pt, c->stream);
+      cudaEventDestroy(kv.second.done);
+    }
   for (u64* p : c->d_pinv)
     if (p) cudaFree(p);
   for (u64* p : c->d_fused)
@@ -1115,17 +1121,27 @@ const u64* mask_pt(Context* c, int kind, long index, int l, double scale,
                    const std::vector<double2>& slots) {
   auto key = std::make_tuple(kind, index, l, scale);
   auto it = c->masks.find(key);
-  if (it != c->masks.end()) return it->second;
+  if (it != c->masks.end()) {
+    // encoded on another stream of this context (a concurrent chain of the
+    // covariate phase): this stream waits for the encoding
+    if (it->second.stream != c->stream)
+      GWHE_CUDA(cudaStreamWaitEvent(c->stream, it->second.done, 0));
+    return it->second.pt;
+  }
   const int M = c->N / 2;
   GWHE_REQUIRE((int)slots.size() == M, ST_EINVAL, "mask must hold N/2 slots");
   Tmp z(c, sizeof(double2) * M);
   GWHE_CUDA(cudaMemcpyAsync(z.p, slots.data(), sizeof(double2) * M, cudaMemcpyHostToDevice,
                             c->stream));
-  // from the stream-ordered pool and without a host wait: the mask is used
-  // only by this context's later launches on the same stream
+  // from the stream-ordered pool and without a host wait: later launches on
+  // this stream are ordered after the encoding, other streams wait for the
+  // event
   u64* pt = dalloc_u64(c, (size_t)l * c->N);
   encode_to_ntt(c, z.as<double2>(), 1, scale, l, pt);
-  c->masks[key] = pt;
+  cudaEvent_t done;
+  GWHE_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  GWHE_CUDA(cudaEventRecord(done, c->stream));
+  c->masks[key] = Context::Mask{pt, c->stream, done};
   return pt;
 }
 

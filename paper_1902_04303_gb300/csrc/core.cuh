@@ -355,8 +355,15 @@ struct Context {
   u64* d_pk = nullptr;            // [2][L][N] NTT domain (b, a)
   std::map<u32, KeySet> ksk;      // key id -> switching key
   bool have_keys = false;
-  // encoded public plaintexts (masks), keyed by (kind, index, level, scale)
-  std::map<std::tuple<int, long, int, double>, u64*> masks;
+  // encoded public plaintexts (masks), keyed by (kind, index, level, scale):
+  // the plaintext, the stream that encoded it and an event recorded after
+  // the encoding (a use on another stream of the context waits for it)
+  struct Mask {
+    u64* pt;
+    cudaStream_t stream;
+    cudaEvent_t done;
+  };
+  std::map<std::tuple<int, long, int, double>, Mask> masks;
   long ks_count = 0;              // key switches issued (relinearisations + automorphisms)
   long launches = 0;              // kernels launched
   long ks_by_level[kMaxRowLimbs + 1] = {};  // key switches per level

@@ -699,6 +699,57 @@ static void make_dup_state(Job* j, Eval& ev) {
   j->sets.push_back(std::move(dd));
 }
 
+// An independent chain of the covariate phase on a second stream of the
+// job's context: fork() orders the side stream after the work queued so far
+// and makes the context issue there, leave() returns to the main stream, and
+// join() makes the main stream wait for everything the chain issued.  Both
+// streams share the context's memory pool (stream-ordered: the fork and
+// join events order reuse across them) and its mask cache (a mask encoded on
+// one stream is waited for on the other).  With the kernel-class timers on,
+// the chain stays on the main stream: the timers' per-class times would
+// otherwise count the overlap twice.
+struct SideChain {
+  Context* c;
+  cudaStream_t main, side = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool on_side = false, joined = true;
+  explicit SideChain(Context* c_) : c(c_), main(c_->stream) {
+    if (c->prof.on) return;
+    int prio = 0;
+    if (cudaStreamGetPriority(main, &prio) != cudaSuccess) {
+      cudaGetLastError();
+      prio = 0;
+    }
+    GWHE_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio));
+    GWHE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  void fork() {
+    if (!side) return;
+    GWHE_CUDA(cudaEventRecord(ev, main));
+    GWHE_CUDA(cudaStreamWaitEvent(side, ev, 0));
+    c->stream = side;
+    on_side = true;
+    joined = false;
+  }
+  void leave() {
+    c->stream = main;
+    on_side = false;
+  }
+  void join() {
+    if (!side) return;
+    GWHE_CUDA(cudaEventRecord(ev, side));
+    GWHE_CUDA(cudaStreamWaitEvent(main, ev, 0));
+    joined = true;
+  }
+  ~SideChain() {
+    c->stream = main;
+    if (!side) return;
+    if (!joined && cudaEventRecord(ev, side) == cudaSuccess) cudaStreamWaitEvent(main, ev, 0);
+    cudaStreamDestroy(side);  // released once its work is done
+    cudaEventDestroy(ev);
+  }
+};
+
 void job_fit(Job* j, int kappa) {
   GWHE_REQUIRE(kappa >= 1, ST_EINVAL, "kappa >= 1");
   GWHE_REQUIRE(!j->X.empty() && j->y && j->beta0, ST_EINVAL,
@@ -707,6 +758,26 @@ void job_fit(Job* j, int kappa) {
   const Layout& lay = j->lay;
   Eval ev{c, lay};
   const int d = lay.d, n = lay.n;
+  // X A: Alg. 3 (CP-MatMult) from X and A dropped to kMLevel limbs, every
+  // column duplicated into all blocks (Alg. 7), and in the factored layout
+  // Dup(X_c) at kFactLevel: they read only the encrypted inputs, so they run
+  // on a second stream beside Alg. 9 and eqs. z, zprime
+  if (j->factored)
+    GWHE_REQUIRE(j->X[0]->l >= kFactLevel, ST_ELEVEL, "need kFactLevel limbs for Dup(X_c)");
+  SideChain side(c);
+  side.fork();
+  std::vector<CtPtr> Alow;
+  for (int rr = 0; rr < d; ++rr) Alow.push_back(ev.view(*j->A[rr], kMLevel));
+  CtSetPtr xa = ev.cp_matmul(j->X, Alow, d);
+  set_ladder(c, *xa, ev.dup_steps());  // Duplicate(XA_r) for every r
+  CtSetPtr dx;
+  if (j->factored) {
+    std::vector<const Ct*> xs;
+    for (int cc = 0; cc < d; ++cc) xs.push_back(j->X[cc].get());
+    dx = ev.gather(xs, kFactLevel);
+    set_ladder(c, *dx, ev.dup_steps());
+  }
+  side.leave();
   // Alg. 9
   CtPtr beta = ev.clone_at(*j->beta0, j->beta0->l);
   CtPtr p, ymp;
@@ -763,23 +834,13 @@ void job_fit(Job* j, int kappa) {
   j->zp = ev.sub(*zv, *xaxtz);
   CtPtr wmv = ev.view(*j->w_m, j->zp->l);
   j->wzp = ev.mult(*wmv, *j->zp);
-  // X A: Alg. 3 (CP-MatMult) from X and A dropped to kMLevel limbs, every
-  // column duplicated into all blocks (Alg. 7)
-  std::vector<CtPtr> Alow;
-  for (int rr = 0; rr < d; ++rr) Alow.push_back(ev.view(*j->A[rr], kMLevel));
-  CtSetPtr xa = ev.cp_matmul(j->X, Alow, d);
-  set_ladder(c, *xa, ev.dup_steps());  // Duplicate(XA_r) for every r
+  side.join();
   if (j->factored) {
     // second form of eq. Sprime: keep Dup((XA)_c) and Dup(X_c) at kFactLevel
-    GWHE_REQUIRE(j->X[0]->l >= kFactLevel, ST_ELEVEL, "need kFactLevel limbs for Dup(X_c)");
     j->DupB.clear();
     j->DupX.clear();
     for (int rr = 0; rr < d; ++rr) j->DupB.push_back(xa->view(rr));
     j->sets.push_back(std::move(xa));
-    std::vector<const Ct*> xs;
-    for (int cc = 0; cc < d; ++cc) xs.push_back(j->X[cc].get());
-    CtSetPtr dx = ev.gather(xs, kFactLevel);
-    set_ladder(c, *dx, ev.dup_steps());
     for (int cc = 0; cc < d; ++cc) j->DupX.push_back(dx->view(cc));
     j->sets.push_back(std::move(dx));
     make_dup_state(j, ev);

@@ -284,7 +284,8 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
 // SNP batches): all G keys' words of the thread's slot stay in registers and
 // the thread walks up to IB items, so each key is read once per IB items.
 template <int IB, int G>
-__global__ void k_ks_inner_hoist1(const u64* __restrict__ c_ntt, size_t c_stride,
+__global__ void __launch_bounds__(256, 4) k_ks_inner_hoist1(const u64* __restrict__ c_ntt,
+                                                           size_t c_stride,
                                   const u64* __restrict__ ext, HoistKeys hk,
                                   u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                   int logN, int cnt, const DevMod* __restrict__ mod) {
@@ -307,6 +308,9 @@ __global__ void k_ks_inner_hoist1(const u64* __restrict__ c_ntt, size_t c_stride
   const DevMod m = mod[mi];
   const int it0 = blockIdx.x * IB;
   const int it1 = min(it0 + IB, cnt);
+  // two items in flight: the gathers of the next item overlap the products
+  // of this one
+#pragma unroll 2
   for (int item = it0; item < it1; ++item) {
     // digit 0 holds every limb below l: those come from c1 itself
     const u64* row = u < l ? c_ntt + (size_t)item * c_stride + (size_t)u * N

@@ -377,10 +377,10 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
         if (ad) v = addmod(v, ad[k], q);
         o[k] = v;
       }
-      return;
-    }
+    } else {
 #pragma unroll
-    for (int m = 0; m < E; ++m) base[((size_t)gB << 8) + rB + TPS * m] = x[m];
+      for (int m = 0; m < E; ++m) base[((size_t)gB << 8) + rB + TPS * m] = x[m];
+    }
   } else {
     // ---- row pass (global stages 15-8), residues from HBM
 #pragma unroll

@@ -46,8 +46,8 @@ struct Request {
   std::string error;
   double t_submit = 0, t_start = 0, t_done = 0;
   // device timeline of the job (ms after the server's reference event)
-  double dev_start = 0, dev_end = 0;
-  bool hi = false;  // ran on its worker's high-priority stream
+  double dev_start = 0, dev_end = 0, dev_snp_start = 0, dev_snp_end = 0;
+  bool hi = false;  // its SNP loop ran on the worker's high-priority stream
   bool done = false;
 };
 typedef std::shared_ptr<Request> ReqPtr;
@@ -71,6 +71,11 @@ struct gwhe_server {
   // one running job at a time holds the high-priority token: its kernels
   // are scheduled first, the others' fill the SMs it leaves idle
   bool hi_taken = false;
+  // GWHE_SERVER_ONE_SNP_LOOP: covariate phases run on low-priority streams
+  // and the SNP loops one at a time (the token), on high-priority streams
+  bool one_snp = false;
+  bool snp_busy = false;
+  std::condition_variable cv_snp;
   // reference point of the jobs' device timelines (recorded at creation)
   cudaEvent_t t0 = nullptr;
   bool stop = false;
@@ -106,7 +111,33 @@ size_t footprint(const Context* c, int n, int d, long k, bool factored, int chun
   return (size_t)(staging + inputs + fit + batch + state);
 }
 
-void run_request(Context* c, Request& r, int chunk) {
+// Worker-owned streams and events of one request's run.
+struct RunRes {
+  cudaStream_t hi, lo;
+  cudaEvent_t t0;        // the server's reference event
+  cudaEvent_t s0, s1;    // start / end of the SNP loop
+  cudaEvent_t sw;        // stream switch
+};
+
+// Holds the server's SNP-loop token for the scope (one_snp servers).
+struct SnpToken {
+  gwhe_server* srv = nullptr;
+  explicit SnpToken(gwhe_server* s) : srv(s) {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->cv_snp.wait(lk, [&] { return !srv->snp_busy; });
+    srv->snp_busy = true;
+  }
+  ~SnpToken() {
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->snp_busy = false;
+    }
+    srv->cv_snp.notify_all();
+  }
+};
+
+void run_request(gwhe_server* srv, Context* c, Request& r, const RunRes& rr) {
+  const int chunk = srv->chunk;
   std::unique_ptr<Job> j(job_create(c, r.n, r.d, r.k, r.layout));
   job_set_nonce(j.get(), r.nonce);
   job_set_host_state(j.get(), r.dupm_chunk);
@@ -114,6 +145,16 @@ void run_request(Context* c, Request& r, int chunk) {
   job_fit(j.get(), r.kappa);
   r.num.assign(r.k, NAN);
   r.den.assign(r.k, NAN);
+  std::unique_ptr<SnpToken> token;
+  if (srv->one_snp) {
+    // the loop runs alone at high priority, ordered after this job's fit
+    token.reset(new SnpToken(srv));
+    GWHE_CUDA(cudaEventRecord(rr.sw, c->stream));
+    GWHE_CUDA(cudaStreamWaitEvent(rr.hi, rr.sw, 0));
+    c->stream = rr.hi;
+    r.hi = true;
+  }
+  GWHE_CUDA(cudaEventRecord(rr.s0, c->stream));
   // the genotypes stay in host memory; each chunk's columns are staged
   std::vector<double> num(r.k), den(r.k);
   for (long b0 = 0; b0 < j->lay.batches; b0 += chunk) {
@@ -127,12 +168,18 @@ void run_request(Context* c, Request& r, int chunk) {
     }
     job_release_results(j.get());
   }
+  GWHE_CUDA(cudaEventRecord(rr.s1, c->stream));
   GWHE_CUDA(cudaStreamSynchronize(c->stream));
+  float a = 0.f, b = 0.f;
+  GWHE_CUDA(cudaEventElapsedTime(&a, rr.t0, rr.s0));
+  GWHE_CUDA(cudaEventElapsedTime(&b, rr.t0, rr.s1));
+  r.dev_snp_start = a;
+  r.dev_snp_end = b;
 }
 
 void worker_main(gwhe_server* srv) {
   cudaStream_t st = nullptr, st_lo = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, es0 = nullptr, es1 = nullptr, esw = nullptr;
   Context* c = nullptr;
   try {
     // a new thread starts on device 0: the streams and the child context
@@ -144,13 +191,16 @@ void worker_main(gwhe_server* srv) {
     GWHE_CUDA(cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, least));
     GWHE_CUDA(cudaEventCreate(&e0));
     GWHE_CUDA(cudaEventCreate(&e1));
+    GWHE_CUDA(cudaEventCreate(&es0));
+    GWHE_CUDA(cudaEventCreate(&es1));
+    GWHE_CUDA(cudaEventCreateWithFlags(&esw, cudaEventDisableTiming));
     c = ctx_child(srv->owner->c, st);
   } catch (const std::exception& e) {
     // without a context this worker takes no work; the others carry on
     if (st) cudaStreamDestroy(st);
     if (st_lo) cudaStreamDestroy(st_lo);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
+    for (cudaEvent_t e : {e0, e1, es0, es1, esw})
+      if (e) cudaEventDestroy(e);
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       ++srv->failed;
@@ -187,16 +237,19 @@ void worker_main(gwhe_server* srv) {
       ++srv->running;
       srv->max_running = std::max(srv->max_running, srv->running);
       if (r->dupm_chunk > 0) ++srv->host_tier;
-      r->hi = !srv->hi_taken;
+      // without the SNP-loop token, the first job admitted while no other
+      // holds it runs on the high-priority stream
+      r->hi = !srv->one_snp && !srv->hi_taken;
       if (r->hi) srv->hi_taken = true;
       r->t_start = now_ms();
     }
     // the previous job on this worker has finished on both streams (its
     // run ended with a synchronisation), so switching needs no ordering
     c->stream = r->hi ? st : st_lo;
+    const bool held_hi = r->hi;
     try {
       GWHE_CUDA(cudaEventRecord(e0, c->stream));
-      run_request(c, *r, srv->chunk);
+      run_request(srv, c, *r, RunRes{st, st_lo, srv->t0, es0, es1, esw});
       GWHE_CUDA(cudaEventRecord(e1, c->stream));
       GWHE_CUDA(cudaEventSynchronize(e1));
       float a = 0.f, b = 0.f;
@@ -215,7 +268,7 @@ void worker_main(gwhe_server* srv) {
     }
     {
       std::lock_guard<std::mutex> lk(srv->mu);
-      if (r->hi) srv->hi_taken = false;
+      if (held_hi) srv->hi_taken = false;
       srv->in_use -= r->footprint;
       --srv->running;
       r->t_done = now_ms();
@@ -234,8 +287,7 @@ void worker_main(gwhe_server* srv) {
   ctx_destroy(c);
   cudaStreamDestroy(st);
   cudaStreamDestroy(st_lo);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (cudaEvent_t e : {e0, e1, es0, es1, esw}) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -244,7 +296,13 @@ extern "C" {
 
 int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
                        gwhe_server** out) {
-  if (!ctx || !ctx->c || !out || workers < 1 || workers > 64 || chunk_batches < 1)
+  return gwhe_server_create_ex(ctx, workers, hbm_budget, chunk_batches, 0, out);
+}
+
+int gwhe_server_create_ex(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chunk_batches,
+                          int flags, gwhe_server** out) {
+  if (!ctx || !ctx->c || !out || workers < 1 || workers > 64 || chunk_batches < 1 ||
+      (flags & ~GWHE_SERVER_ONE_SNP_LOOP))
     return GWHE_EINVAL;
   *out = nullptr;
   Context* c = ctx->c;
@@ -262,6 +320,7 @@ int gwhe_server_create(gwhe_ctx* ctx, int workers, uint64_t hbm_budget, int chun
   std::unique_ptr<gwhe_server> s(new gwhe_server());
   s->owner = ctx;
   s->chunk = chunk_batches;
+  s->one_snp = (flags & GWHE_SERVER_ONE_SNP_LOOP) != 0;
   if (hbm_budget == 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return GWHE_ECUDA;
@@ -380,6 +439,8 @@ int gwhe_server_wait(gwhe_server* s, long id, double* num, double* den, double* 
     times_ms[3] = r->dev_start;              // device timeline
     times_ms[4] = r->dev_end;
     times_ms[5] = r->hi ? 1.0 : 0.0;
+    times_ms[6] = r->dev_snp_start;
+    times_ms[7] = r->dev_snp_end;
   }
   if (r->status != GWHE_OK) {
     s->owner->c->last_error = "server job " + std::to_string(id) + ": " + r->error;

@@ -96,6 +96,7 @@ _SIGS = {
     "gwhe_job_release_results": [_vp],
     "gwhe_ctx_create_child": [_vp, _vp, ctypes.POINTER(_vp)],
     "gwhe_server_create": [_vp, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)],
+    "gwhe_server_create_ex": [_vp, _i, ctypes.c_uint64, _i, _i, ctypes.POINTER(_vp)],
     "gwhe_server_submit": [_vp, _i, _i, _l, _i, _i, _u32, _f64p, _f64p, _f64p, _f64p,
                            ctypes.POINTER(_l)],
     "gwhe_server_wait": [_vp, _l, _f64p, _f64p, _f64p],
@@ -709,11 +710,12 @@ class Server:
     with their own streams share the context's keys; jobs are admitted by
     estimated HBM footprint as memory frees up and overlap on the device."""
 
-    def __init__(self, ctx: Context, workers=4, hbm_budget=0, chunk_batches=64):
+    def __init__(self, ctx: Context, workers=4, hbm_budget=0, chunk_batches=64,
+                 one_snp_loop=False):
         self.ctx = ctx
         h = _vp()
-        ctx._c(lib().gwhe_server_create(ctx.h, workers, hbm_budget, chunk_batches,
-                                        ctypes.byref(h)))
+        ctx._c(lib().gwhe_server_create_ex(ctx.h, workers, hbm_budget, chunk_batches,
+                                           1 if one_snp_loop else 0, ctypes.byref(h)))
         self.h = h
         self._k = {}
         ctx._children.add(self)
@@ -740,11 +742,12 @@ class Server:
         k, _held = self._k.pop(rid)  # a borrowed S stays referenced until here
         num = np.full(k, np.nan)
         den = np.full(k, np.nan)
-        t = np.zeros(6)
+        t = np.zeros(8)
         self.ctx._c(lib().gwhe_server_wait(self.h, rid, num, den, t))
         return num, den, {"queue_ms": t[0], "run_ms": t[1], "latency_ms": t[2],
                           "device_start_ms": t[3], "device_end_ms": t[4],
-                          "high_priority": bool(t[5])}
+                          "high_priority": bool(t[5]), "snp_start_ms": t[6],
+                          "snp_end_ms": t[7]}
 
     def stats(self):
         out = (_l * 9)()

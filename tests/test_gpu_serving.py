@@ -133,3 +133,26 @@ def test_mccp_job_over_budget_runs_in_host_tier(g, setup):
     st = srv.stats()
     assert st["host_tier_jobs"] == 1 and st["peak_bytes_claimed"] < fp
     srv.close()
+
+
+def test_one_snp_loop_at_a_time(g, setup):
+    """With GWHE_SERVER_ONE_SNP_LOOP the SNP loops run one after another on
+    the device while other jobs' covariate phases overlap them; results are
+    still those of the jobs alone."""
+    ctx, reqs, alone = setup
+    srv = g.Server(ctx, workers=3, chunk_batches=2, one_snp_loop=True)
+    ids = [srv.submit(data.X, A, data.y, data.S, nonce=nonce) for data, A, nonce in reqs]
+    loops, spans = [], []
+    for rid, (num0, den0) in zip(ids, alone):
+        num, den, t = srv.wait(rid)
+        assert np.array_equal(num, num0) and np.array_equal(den, den0)
+        assert t["high_priority"]
+        assert t["device_start_ms"] <= t["snp_start_ms"] < t["snp_end_ms"] <= t["device_end_ms"]
+        loops.append((t["snp_start_ms"], t["snp_end_ms"]))
+        spans.append((t["device_start_ms"], t["device_end_ms"]))
+    loops.sort()
+    for (a0, a1), (b0, b1) in zip(loops, loops[1:]):
+        assert b0 >= a1, loops  # never two loops at once
+    overlap = max(sum(1 for a, b in spans if a <= s0 < b) for s0, _ in spans)
+    assert overlap >= 2, spans
+    srv.close()
