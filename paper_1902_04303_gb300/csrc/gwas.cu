@@ -792,6 +792,12 @@ void job_fit(Job* j, int kappa) {
     beta = ev.sub(*bv, *ag);
   }
   j->beta = ev.clone_at(*beta, beta->l);
+  // X beta of eq. z (Alg. 2) needs only beta: on its own stream beside the
+  // weights and Alg. 10
+  SideChain side_xb(c);
+  side_xb.fork();
+  CtPtr xb = ev.cp_matvec(j->X, *beta, d);
+  side_xb.leave();
   // w = p (1 - p); the masked copy feeds Dup(w) and w z'
   CtPtr omp = ev.negate(*p);
   op_add_const(c, *omp, 1.0);
@@ -820,10 +826,10 @@ void job_fit(Job* j, int kappa) {
   }
   CtPtr winv = std::move(g);
   // eq. z
-  CtPtr xb = ev.cp_matvec(j->X, *beta, d);
   int lv = std::min(winv->l, ymp->l);
   CtPtr wi = ev.view(*winv, lv), ym = ev.view(*ymp, lv);
   CtPtr r = ev.mult(*wi, *ym);
+  side_xb.join();
   lv = std::min(xb->l, r->l);
   CtPtr xbv = ev.view(*xb, lv), rv = ev.view(*r, lv);
   j->z = ev.add(*xbv, *rv);

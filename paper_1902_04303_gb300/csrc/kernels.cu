@@ -308,9 +308,6 @@ __global__ void __launch_bounds__(256, 4) k_ks_inner_hoist1(const u64* __restric
   const DevMod m = mod[mi];
   const int it0 = blockIdx.x * IB;
   const int it1 = min(it0 + IB, cnt);
-  // two items in flight: the gathers of the next item overlap the products
-  // of this one
-#pragma unroll 2
   for (int item = it0; item < it1; ++item) {
     // digit 0 holds every limb below l: those come from c1 itself
     const u64* row = u < l ? c_ntt + (size_t)item * c_stride + (size_t)u * N
@@ -1234,6 +1231,17 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
   // more than three automorphisms would cost occupancy: measured slower even
   // for sets of five to eight, where it saves the second read of the keys
   constexpr int IB = G <= 3 ? 8 : 4;
+  if constexpr (G > 3) {
+    if (cnt == 5) {
+      // a set of five (the covariates of the paper's shape) as one group of
+      // five: the keys are read once, at the occupancy of four per thread
+      const dim3 grid(1, blocks_for(c->N), l + K);
+      k_ks_inner_hoist<5, G><<<grid, kThreads, 0, c->stream>>>(
+          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
+          c->d_mod);
+      return;
+    }
+  }
   const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
   k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,
                                                            c->P.L, key_lmax, c->alpha, beta,

@@ -367,13 +367,15 @@ def test_job_width_tensor_sum_at_paper_basis(g, paper_basis):
     assert np.array_equal(got, want)
 
 
-def test_few_item_multi_digit_hoisted_sum_at_paper_basis(g, paper_basis):
-    """6 ciphertexts at 20 limbs (three key digits), seven rotations: the
-    covariate phase's hoisted sums, whose inner product takes all the items
-    in one group; the first and the last equal the oracle's."""
+@pytest.mark.parametrize("cnt", [5, 6])
+def test_few_item_multi_digit_hoisted_sum_at_paper_basis(g, paper_basis, cnt):
+    """5 or 6 ciphertexts at 20 limbs (three key digits), seven rotations: the
+    covariate phase's hoisted sums (five items take one group of five, six
+    a group of four and one of two); the first and the last equal the
+    oracle's."""
     ctx, o = paper_basis
     rs = [1, 2, 3, 4, 5, 6, 7]
-    srcs = [rand_ct(o, 20, 7000 + i) for i in range(6)]
+    srcs = [rand_ct(o, 20, 7000 + 10 * cnt + i) for i in range(cnt)]
     outs = ctx.rotate_sum_batch([ctx.import_ct(a.c, a.scale) for a in srcs], rs)
-    for i in (0, 5):
+    for i in (0, cnt - 1):
         assert np.array_equal(outs[i].export(), o.rotate_sum(srcs[i], rs).c), i
