@@ -918,7 +918,11 @@ void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
   const int lb = kBatchLevel, nbt = Sp->cnt;
   std::vector<CtPtr> spv;
   for (int i = 0; i < nbt; ++i) spv.push_back(Sp->view(i));
-  // numerator = colSum(Dup(w z') S')
+  // numerator = colSum(Dup(w z') S'): its own chain on a second stream,
+  // beside the denominators' (both only read S'); their launches at 1-3
+  // limbs fill the GPU together
+  SideChain side(c);
+  side.fork();
   CtSetPtr num = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
   {
     std::vector<std::pair<const Ct*, const Ct*>> pr;
@@ -926,6 +930,7 @@ void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
     set_mult(c, pr, *num);
   }
   set_ladder(c, *num, ev.colsum_steps());
+  side.leave();
   // WS' = Dup(w) S'
   CtSetPtr ws = set_new(c, nbt, 2, lb - 1, lb - 1, 1.0);
   {
@@ -965,6 +970,7 @@ void batch_body(Job* j, Eval& ev, CtSetPtr Sp, long b0) {
     D->scale = W2->scale * 2.0;
   }
   set_ladder(c, *D, ev.colsum_steps());
+  side.join();
   for (int i = 0; i < nbt; ++i)
     j->out[b0 + i] = {num->view(i), D->view(i), D->view(nbt + i)};
   num->is_output = true;

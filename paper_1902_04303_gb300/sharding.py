@@ -140,6 +140,8 @@ def run_sharded_job(ctx, job, X, A, y, S, kappa: int, rank: int, world: int, gro
     else:
         num = np.full(job.k, np.nan)
         den = np.full(job.k, np.nan)
+    if world == 1:  # one rank: the whole job, nothing to gather
+        return num, den, (b0, b1)
     num, den, complete = gather_results(num, den, b0, b1, job.layout["tau"], group, device)
     if not complete:
         raise RuntimeError("some SNP batches were not evaluated")
