@@ -374,6 +374,7 @@ def run_gpu(args):
         "encrypted-GWAS SNPs/s (245 samples, N=2^17, kappa=3)",
         "value": round(value, 1), "unit": "SNPs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 3),
+        "ms_steps": [round(float(x), 3) for x in ms],
         "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": W["name"], "N": 1 << W["logN"], "q_limbs": W["L"],

@@ -160,6 +160,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   {
     std::vector<ulonglong2> psi((size_t)nm * N), ipsi((size_t)nm * N);
     std::vector<u64> ninv(nm), ninv_sh(nm), pw(N), ipw(N);
+    std::vector<ulonglong2> iw1n(nm);
     for (int u = 0; u < nm; ++u) {
       const u64 q = c->mod[u];
       const u64 r = find_psi(q, P.logN), ri = host_inv(r, q);
@@ -176,6 +177,8 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       }
       ninv[u] = host_inv((u64)N % q, q);
       ninv_sh[u] = shoup_companion(ninv[u], q);
+      const u64 w1n = host_mulmod(ipsi[(size_t)u * N + 1].x, ninv[u], q);
+      iw1n[u] = make_ulonglong2(w1n, shoup_companion(w1n, q));
     }
     c->d_psi = upload(c.get(), psi);
     c->d_ipsi = upload(c.get(), ipsi);
@@ -203,6 +206,7 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
     }
     c->d_ninv = upload(c.get(), ninv);
     c->d_ninv_sh = upload(c.get(), ninv_sh);
+    c->d_iw1n = upload(c.get(), iw1n);
   }
   // rescale: entry (l, i) = q_{l-1}^-1 mod q_i for i < l - 1
   {
@@ -473,7 +477,7 @@ static void ctx_destroy_on_device(Context* c) {
     return;
   }
   for (void* p : {(void*)c->d_psiB, (void*)c->d_ipsiB}) if (p) cudaFree(p);
-  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_rescale,
+  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_iw1n, (void*)c->d_rescale,
                   (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
                   (void*)c->d_slot_u, (void*)c->d_slot_inv})

@@ -224,6 +224,9 @@ struct NttTables {
   const u64* ninv;     // [nmod] N^-1 mod q_u
   const u64* ninv_sh;  // [nmod]
   const DevMod* mod;   // [nmod]
+  // [nmod] ipsi[1] N^-1 mod q_u and its Shoup companion: the last inverse
+  // stage's twiddle with the factor N^-1 merged in
+  const ulonglong2* iw1n;
 };
 
 struct Context;
@@ -326,6 +329,7 @@ struct Context {
   ulonglong2 *d_psi = nullptr, *d_ipsi = nullptr;
   ulonglong2 *d_psiB = nullptr, *d_ipsiB = nullptr;  // row-pass twiddles, N = 2^16
   u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;
+  ulonglong2* d_iw1n = nullptr;
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l - 1 (value, Shoup)
   u64* d_rescale = nullptr;    // [L][L][2]
   // key switches at level l use the first ks_k[l] special primes (fewest
@@ -370,7 +374,7 @@ struct Context {
   Prof prof;
   std::string last_error;
   NttTables tables() const {
-    return NttTables{d_psi, d_ipsi, d_psiB, d_ipsiB, d_ninv, d_ninv_sh, d_mod};
+    return NttTables{d_psi, d_ipsi, d_psiB, d_ipsiB, d_ninv, d_ninv_sh, d_mod, d_iw1n};
   }
 };
 

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 #pragma unroll
     for (int m = 0; m < E; ++m) x[m] = sm[sidx(r + TPS * m)];
 #pragma unroll
-    for (int sp = LE - 1; sp >= 0; --sp) {
+    for (int sp = LE - 1; sp >= (PASSA ? 1 : 0); --sp) {
       const int st = (E / 2) >> sp;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
@@ -181,9 +181,18 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
       }
     }
     if (PASSA) {
+      // global stage 0 (every pair on twiddle index 1) with the factor N^-1
+      // merged in: x = (x + y) N^-1, y = (x - y) (w N^-1), both exact Shoup
+      // products of inputs below 8q, so canonical in [0, q)
       const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+      const ulonglong2 wn = tb.iw1n[u];
+      constexpr int st = E / 2;
 #pragma unroll
-      for (int m = 0; m < E; ++m) x[m] = shoup(x[m], ni, nish, q);
+      for (int m = 0; m < st; ++m) {
+        const u64 a = x[m], b = x[m + st];
+        x[m] = shoup(a + b, ni, nish, q);
+        x[m + st] = shoup(a - b + q4, wn.x, wn.y, q);
+      }
     }
   }
 #pragma unroll
