@@ -15,6 +15,7 @@
 #include <stdexcept>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 namespace gwhe {
@@ -65,6 +66,28 @@ struct Error : std::runtime_error {
   do {                                                   \
     if (!(cond)) throw ::gwhe::Error((code), (msg));     \
   } while (0)
+
+#if defined(__CUDACC__)
+// Launch of a kernel that begins with pdl_wait() (below) on stream st, with
+// programmatic stream serialisation: its CTAs may be scheduled while the
+// previous kernel on the stream drains, which hides the launch gap between
+// dependent kernels.  Every argument of the kernel must be given.
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(cudaStream_t st, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  GWHE_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+#endif
 
 // Per-modulus constants.  R = 2^64 mod q with its Shoup companion, and the
 // 64-bit Barrett factor floor(2^64 / q).
@@ -123,6 +146,17 @@ __device__ __forceinline__ u64 shoup_est(u64 y, u64 w, u64 wsh, u64 nq) {
       : "=l"(r)
       : "l"(y), "l"(w), "l"(wsh), "l"(nq));
   return r;
+}
+
+// Programmatic dependent launch: a kernel started by pdl_launch may become
+// resident while the kernel before it on the stream is still finishing.  It
+// calls pdl_wait() before its first memory access (the wait returns once the
+// previous kernel has completed and its writes are visible; without a
+// programmatic predecessor it returns at once) and then pdl_trigger(), which
+// lets the next kernel on the stream start its own launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 // Harvey-style lazy butterflies on [0, 8q) (q < 2^60, so 8q < 2^63), with the

@@ -23,6 +23,8 @@ struct LimbVals {
 // ------------------------------------------------------------- element-wise
 __global__ void k_addsub(PolyView out, CPolyView a, CPolyView b, int l, int N,
                          const DevMod* __restrict__ mod, int sub) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -33,6 +35,8 @@ __global__ void k_addsub(PolyView out, CPolyView a, CPolyView b, int l, int N,
 }
 
 __global__ void k_negate(PolyView out, CPolyView a, int l, int N, const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -42,6 +46,8 @@ __global__ void k_negate(PolyView out, CPolyView a, int l, int N, const DevMod* 
 
 __global__ void k_mul_scalar(PolyView out, CPolyView a, int l, int N, const DevMod* __restrict__ mod,
                              const LimbVals v) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -50,6 +56,8 @@ __global__ void k_mul_scalar(PolyView out, CPolyView a, int l, int N, const DevM
 }
 
 __global__ void k_add_scalar0(PolyView ct, int N, const DevMod* __restrict__ mod, const LimbVals v) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -59,6 +67,8 @@ __global__ void k_add_scalar0(PolyView ct, int N, const DevMod* __restrict__ mod
 
 __global__ void k_mul_plain(PolyView out, CPolyView a, const u64* __restrict__ pt, int l, int N,
                             const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -68,6 +78,8 @@ __global__ void k_mul_plain(PolyView out, CPolyView a, const u64* __restrict__ p
 
 __global__ void k_add_plain0(PolyView ct, const u64* __restrict__ pt, int N,
                              const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -127,6 +139,8 @@ __global__ void __launch_bounds__(256) k_baseconv(const u64* __restrict__ x, siz
                                                   u64* __restrict__ out, size_t out_pstride,
                                                   const ConvArgs a, int N, int og,
                                                   const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ u64 hs[NI * kMaxRowLimbs];
   const int o0 = blockIdx.y * og;
   const int no = min(og, a.n_out - o0);
@@ -173,6 +187,8 @@ __global__ void k_ks_inner(const u64* __restrict__ c_ntt, size_t c_stride,
                            const u64* __restrict__ ext, const u64* __restrict__ key,
                            u64* __restrict__ acc, int l, int K, int L, int key_lmax, int alpha,
                            int beta, int N, int cnt, const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int u = blockIdx.z;
   const int k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -230,6 +246,8 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
                                  u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                  int alpha, int beta, int logN, int cnt,
                                  const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int u = blockIdx.z;
   const int N = 1 << logN;
   const int k = blockIdx.y * blockDim.x + threadIdx.x;
@@ -289,6 +307,8 @@ __global__ void __launch_bounds__(256, 4) k_ks_inner_hoist1(const u64* __restric
                                   const u64* __restrict__ ext, HoistKeys hk,
                                   u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                   int logN, int cnt, const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int u = blockIdx.z;
   const int N = 1 << logN;
   const int k = blockIdx.y * blockDim.x + threadIdx.x;
@@ -332,6 +352,8 @@ template <int G>
 __global__ void k_automorph_sum(const u64* __restrict__ in, int in_cap, size_t in_stride,
                                 u64* __restrict__ out, int l, int logN, HoistKeys hk,
                                 const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.y;
   const int N = 1 << logN;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -351,6 +373,8 @@ __global__ void k_moddown_combine(const u64* __restrict__ acc, const u64* __rest
                                   const u64* add1, size_t a0_stride, size_t a1_stride,
                                   const u64* __restrict__ pinv, int N,
                                   const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -385,6 +409,8 @@ __global__ void k_fused_prep(const u64* __restrict__ acc, const u64* __restrict_
                              size_t t3_stride, int t3_cap, u64* __restrict__ bp, int l, int K,
                              int L, int N, const u64* __restrict__ fz,
                              const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, nb = K + 1, p = row / nb, j = row - p * nb;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -410,6 +436,8 @@ __global__ void k_fused_combine(const u64* __restrict__ acc, const u64* __restri
                                 u64* __restrict__ out, size_t o_stride, int o_cap, int l, int K,
                                 int N, const u64* __restrict__ fz,
                                 const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int lo = l - 1, row = blockIdx.y, p = row / lo, i = row - p * lo;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -428,6 +456,8 @@ __global__ void k_fused_combine(const u64* __restrict__ acc, const u64* __restri
 // ------------------------------------------------------------- rescale
 __global__ void k_rescale_prep(const u64* __restrict__ last, int l, u64* __restrict__ tmp, int N,
                                const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, lm1 = l - 1, p = row / lm1, i = row - p * lm1;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -447,6 +477,8 @@ __global__ void k_rescale_prep(const u64* __restrict__ last, int l, u64* __restr
 
 __global__ void k_rescale_combine(PolyView ct, const u64* __restrict__ tmp, int l, int N,
                                   const DevMod* __restrict__ mod, const u64* __restrict__ qlinv) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, lm1 = l - 1, p = row / lm1, i = row - p * lm1;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -460,6 +492,8 @@ __global__ void k_rescale_combine(PolyView ct, const u64* __restrict__ tmp, int 
 // NTT slot j holds a(psi^(2 brv(j) + 1)); X -> X^g maps it to slot
 // brv((g (2 brv(j) + 1) mod 2N - 1) / 2) of the input.
 __global__ void k_automorph(PolyView out, CPolyView in, int l, int logN, u64 g) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int N = 1 << logN;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,6 +511,8 @@ __global__ void k_automorph(PolyView out, CPolyView in, int l, int logN, u64 g) 
 __global__ void k_automorph_ladder(const u64* __restrict__ in, int in_cap, size_t in_stride,
                                    u64* __restrict__ out, int out_cap, size_t out_stride, int l,
                                    int logN, u64 g, const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int N = 1 << logN;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,6 +531,8 @@ __global__ void k_automorph_ladder(const u64* __restrict__ in, int in_cap, size_
 // out[item] = src_item * pt_item (both polys), items listed in an array
 __global__ void k_mask_set(const MaskItem* __restrict__ items, u64* __restrict__ out, int out_cap,
                            size_t out_stride, int l, int N, const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -511,6 +549,8 @@ __global__ void k_mask_set(const MaskItem* __restrict__ items, u64* __restrict__
 __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair* __restrict__ pairs,
                                  int npairs, int l, int N, int accumulate,
                                  const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -555,6 +595,8 @@ __global__ void k_tensor_mac_set(PolyView out, size_t out_stride, const MacPair*
 __global__ void k_sum_set(const u64* __restrict__ in, int in_cap, size_t in_stride, int cnt,
                           u64* __restrict__ out, int out_cap, int l, int N,
                           const DevMod* __restrict__ mod) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.y, p = row / l, i = row - p * l;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -1071,15 +1113,16 @@ inline unsigned blocks_for(size_t n, int t = kThreads) { return (unsigned)((n + 
 void ew_addsub(Context* c, PolyView out, CPolyView a, CPolyView b, int npoly, int l, bool sub) {
   ProfScope ps(c, PROF_ELEMWISE, 3.0 * npoly * l * 8.0 * c->N);
   if (npoly * l == 0) return;
-  k_addsub<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, b, l, c->N, c->d_mod,
-                                                                   sub ? 1 : 0);
+  pdl_launch(c->stream, k_addsub, grid_rows(c->N, npoly * l), kThreads, 0, out, a, b, l, c->N,
+             c->d_mod, sub ? 1 : 0);
   GWHE_LAUNCHED(c, 1);
 }
 
 void ew_negate(Context* c, PolyView out, CPolyView a, int npoly, int l) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
   if (npoly * l == 0) return;
-  k_negate<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, l, c->N, c->d_mod);
+  pdl_launch(c->stream, k_negate, grid_rows(c->N, npoly * l), kThreads, 0, out, a, l, c->N,
+             c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1096,31 +1139,31 @@ static LimbVals make_vals(Context* c, int l, const u64* v) {
 void ew_mul_scalar(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* v) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
   if (npoly * l == 0) return;
-  k_mul_scalar<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, l, c->N, c->d_mod,
-                                                                       make_vals(c, l, v));
+  pdl_launch(c->stream, k_mul_scalar, grid_rows(c->N, npoly * l), kThreads, 0, out, a, l, c->N,
+             c->d_mod, make_vals(c, l, v));
   GWHE_LAUNCHED(c, 1);
 }
 
 void ew_add_scalar_poly0(Context* c, PolyView ct, int l, const u64* v) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * l * 8.0 * c->N);
   if (l == 0) return;
-  k_add_scalar0<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, c->N, c->d_mod,
-                                                                make_vals(c, l, v));
+  pdl_launch(c->stream, k_add_scalar0, grid_rows(c->N, l), kThreads, 0, ct, c->N, c->d_mod,
+             make_vals(c, l, v));
   GWHE_LAUNCHED(c, 1);
 }
 
 void ew_mul_plain(Context* c, PolyView out, CPolyView a, int npoly, int l, const u64* pt) {
   ProfScope ps(c, PROF_ELEMWISE, (2.0 * npoly + 1) * l * 8.0 * c->N);
   if (npoly * l == 0) return;
-  k_mul_plain<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, a, pt, l, c->N,
-                                                                      c->d_mod);
+  pdl_launch(c->stream, k_mul_plain, grid_rows(c->N, npoly * l), kThreads, 0, out, a, pt, l, c->N,
+             c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt) {
   ProfScope ps(c, PROF_ELEMWISE, 3.0 * l * 8.0 * c->N);
   if (l == 0) return;
-  k_add_plain0<<<grid_rows(c->N, l), kThreads, 0, c->stream>>>(ct, pt, c->N, c->d_mod);
+  pdl_launch(c->stream, k_add_plain0, grid_rows(c->N, l), kThreads, 0, ct, pt, c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1152,7 +1195,8 @@ static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_
   const dim3 grid(blocks_for(c->N), (a.n_out + og - 1) / og, cnt);
 #define GWHE_CONV_CASE(n)                                                                      \
   case n:                                                                                      \
-    k_baseconv<n><<<grid, kThreads, 0, c->stream>>>(x, xs, out, os, a, c->N, og, c->d_mod); \
+    pdl_launch(c->stream, k_baseconv<n>, grid, kThreads, 0, x, xs, out, os, a, c->N, og,        \
+               c->d_mod);                                                                      \
     break;
   switch (a.n_in) {
     GWHE_CONV_CASE(1) GWHE_CONV_CASE(2) GWHE_CONV_CASE(3) GWHE_CONV_CASE(4)
@@ -1195,9 +1239,9 @@ void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int
                          size_t a0_stride, size_t a1_stride) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * 3 * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
-  k_moddown_combine<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
-      acc, conv, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv[K],
-      c->N, c->d_mod);
+  pdl_launch(c->stream, k_moddown_combine, dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, acc,
+             conv, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv[K], c->N,
+             c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1211,9 +1255,9 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
   GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
   GWHE_REQUIRE(key.d && key.lmax >= l && beta <= key.dk, ST_ENOKEY, "key family does not reach the level");
   constexpr int IB = 8;
-  k_ks_inner<IB><<<dim3((cnt + IB - 1) / IB, blocks_for(c->N), l + K), kThreads, 0,
-                   c->stream>>>(c_ntt, c_stride, ext, key.d, acc, l, K, c->P.L, key.lmax,
-                                c->alpha, beta, c->N, cnt, c->d_mod);
+  pdl_launch(c->stream, k_ks_inner<IB>, dim3((cnt + IB - 1) / IB, blocks_for(c->N), l + K),
+             kThreads, 0, c_ntt, c_stride, ext, key.d, acc, l, K, c->P.L, key.lmax, c->alpha, beta,
+             c->N, cnt, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1223,8 +1267,8 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
   if (beta == 1) {
     constexpr int IB1 = 32;
     const dim3 grid((cnt + IB1 - 1) / IB1, blocks_for(c->N), l + K);
-    k_ks_inner_hoist1<IB1, G><<<grid, kThreads, 0, c->stream>>>(
-        c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
+    pdl_launch(c->stream, k_ks_inner_hoist1<IB1, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk,
+               acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
     return;
   }
   // items per thread (each key word is read once per IB items); eight with
@@ -1236,16 +1280,14 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
       // a set of five (the covariates of the paper's shape) as one group of
       // five: the keys are read once, at the occupancy of four per thread
       const dim3 grid(1, blocks_for(c->N), l + K);
-      k_ks_inner_hoist<5, G><<<grid, kThreads, 0, c->stream>>>(
-          c_ntt, c_stride, ext, hk, acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt,
-          c->d_mod);
+      pdl_launch(c->stream, k_ks_inner_hoist<5, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk,
+                 acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod);
       return;
     }
   }
   const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
-  k_ks_inner_hoist<IB, G><<<grid, kThreads, 0, c->stream>>>(c_ntt, c_stride, ext, hk, acc, l, K,
-                                                           c->P.L, key_lmax, c->alpha, beta,
-                                                           c->logN, cnt, c->d_mod);
+  pdl_launch(c->stream, k_ks_inner_hoist<IB, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk, acc,
+             l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod);
 }
 
 void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
@@ -1275,8 +1317,8 @@ void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, 
   const dim3 grid(blocks_for(c->N), l, cnt);
 #define GWHE_AUTOSUM(G)                                                                          \
   case G:                                                                                        \
-    k_automorph_sum<G><<<grid, kThreads, 0, c->stream>>>(in, in_cap, in_stride, out, l, c->logN, \
-                                                         hk, c->d_mod);                          \
+    pdl_launch(c->stream, k_automorph_sum<G>, grid, kThreads, 0, in, in_cap, in_stride, out, l,  \
+               c->logN, hk, c->d_mod);                                                           \
     break;
   switch (hk.G) {
     GWHE_AUTOSUM(1)
@@ -1296,8 +1338,8 @@ void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride,
                     u64* bp, int l, int K, int cnt) {
   ProfScope ps(c, PROF_ELEMWISE, 3.0 * 2 * (K + 1) * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536 && l >= 2, ST_EINVAL, "bad fused batch");
-  k_fused_prep<<<dim3(blocks_for(c->N), 2 * (K + 1), cnt), kThreads, 0, c->stream>>>(
-      acc, t3, t3_stride, t3_cap, bp, l, K, c->P.L, c->N, c->d_fused[l], c->d_mod);
+  pdl_launch(c->stream, k_fused_prep, dim3(blocks_for(c->N), 2 * (K + 1), cnt), kThreads, 0, acc,
+             t3, t3_stride, t3_cap, bp, l, K, c->P.L, c->N, c->d_fused[l], c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1316,8 +1358,9 @@ void fused_combine_set(Context* c, const u64* acc, const u64* t3, size_t t3_stri
                        int cnt) {
   ProfScope ps(c, PROF_ELEMWISE, 4.0 * 2 * (l - 1) * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536 && l >= 2, ST_EINVAL, "bad fused batch");
-  k_fused_combine<<<dim3(blocks_for(c->N), 2 * (l - 1), cnt), kThreads, 0, c->stream>>>(
-      acc, t3, t3_stride, t3_cap, conv, out, o_stride, o_cap, l, K, c->N, c->d_fused[l], c->d_mod);
+  pdl_launch(c->stream, k_fused_combine, dim3(blocks_for(c->N), 2 * (l - 1), cnt), kThreads, 0, acc,
+             t3, t3_stride, t3_cap, conv, out, o_stride, o_cap, l, K, c->N, c->d_fused[l],
+             c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1325,8 +1368,8 @@ void automorph_ladder_set(Context* c, const u64* in, int in_cap, size_t in_strid
                           int out_cap, size_t out_stride, int l, int cnt, u64 g) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * 2 * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
-  k_automorph_ladder<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
-      in, in_cap, in_stride, out, out_cap, out_stride, l, c->logN, g, c->d_mod);
+  pdl_launch(c->stream, k_automorph_ladder, dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, in,
+             in_cap, in_stride, out, out_cap, out_stride, l, c->logN, g, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1334,8 +1377,8 @@ void mask_set(Context* c, const MaskItem* d_items, int cnt, u64* out, int out_ca
               size_t out_stride, int l) {
   ProfScope ps(c, PROF_ELEMWISE, 5.0 * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
-  k_mask_set<<<dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, c->stream>>>(
-      d_items, out, out_cap, out_stride, l, c->N, c->d_mod);
+  pdl_launch(c->stream, k_mask_set, dim3(blocks_for(c->N), 2 * l, cnt), kThreads, 0, d_items, out,
+             out_cap, out_stride, l, c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
@@ -1343,39 +1386,39 @@ void tensor_mac_set(Context* c, PolyView out3, size_t out_stride, const MacPair*
                     int npairs, int cnt, int l, bool accumulate) {
   ProfScope ps(c, PROF_TENSOR_MAC, (4.0 * npairs + 3.0) * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
-  k_tensor_mac_set<<<dim3(blocks_for(c->N), l, cnt), kThreads, 0, c->stream>>>(
-      out3, out_stride, d_pairs, npairs, l, c->N, accumulate ? 1 : 0, c->d_mod);
+  pdl_launch(c->stream, k_tensor_mac_set, dim3(blocks_for(c->N), l, cnt), kThreads, 0, out3,
+             out_stride, d_pairs, npairs, l, c->N, accumulate ? 1 : 0, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, int cnt, u64* out,
              int out_cap, int l) {
   ProfScope ps(c, PROF_ELEMWISE, (2.0 * cnt + 2.0) * l * 8.0 * c->N);
-  k_sum_set<<<dim3(blocks_for(c->N), 2 * l), kThreads, 0, c->stream>>>(in, in_cap, in_stride, cnt,
-                                                                      out, out_cap, l, c->N,
-                                                                      c->d_mod);
+  pdl_launch(c->stream, k_sum_set, dim3(blocks_for(c->N), 2 * l), kThreads, 0, in, in_cap,
+             in_stride, cnt, out, out_cap, l, c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void rescale_prep(Context* c, const u64* last, int npoly, int l, u64* tmp) {
   ProfScope ps(c, PROF_ELEMWISE, (npoly + npoly * (l - 1.0)) * 8.0 * c->N);
-  k_rescale_prep<<<grid_rows(c->N, npoly * (l - 1)), kThreads, 0, c->stream>>>(last, l, tmp, c->N,
-                                                                               c->d_mod);
+  pdl_launch(c->stream, k_rescale_prep, grid_rows(c->N, npoly * (l - 1)), kThreads, 0, last, l, tmp,
+             c->N, c->d_mod);
   GWHE_LAUNCHED(c, 1);
 }
 
 void rescale_combine(Context* c, PolyView ct, const u64* tmp_ntt, int npoly, int l) {
   ProfScope ps(c, PROF_ELEMWISE, 3.0 * npoly * (l - 1.0) * 8.0 * c->N);
   const u64* qlinv = c->d_rescale + (size_t)l * c->P.L * 2;
-  k_rescale_combine<<<grid_rows(c->N, npoly * (l - 1)), kThreads, 0, c->stream>>>(
-      ct, tmp_ntt, l, c->N, c->d_mod, qlinv);
+  pdl_launch(c->stream, k_rescale_combine, grid_rows(c->N, npoly * (l - 1)), kThreads, 0, ct,
+             tmp_ntt, l, c->N, c->d_mod, qlinv);
   GWHE_LAUNCHED(c, 1);
 }
 
 void automorph_ntt(Context* c, PolyView out, CPolyView in, int npoly, int l, u64 g) {
   ProfScope ps(c, PROF_ELEMWISE, 2.0 * npoly * l * 8.0 * c->N);
   if (npoly * l == 0) return;
-  k_automorph<<<grid_rows(c->N, npoly * l), kThreads, 0, c->stream>>>(out, in, l, c->logN, g);
+  pdl_launch(c->stream, k_automorph, grid_rows(c->N, npoly * l), kThreads, 0, out, in, l, c->logN,
+             g);
   GWHE_LAUNCHED(c, 1);
 }
 

@@ -39,6 +39,8 @@ template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256, int 
 __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
                                                   const NttTables tb, const int groups_per_row,
                                                   const MdEpi epi = MdEpi{}) {
+  pdl_wait();
+  pdl_trigger();
   static_assert(!MD || (FWD && !PASSA), "the ModDown epilogue ends a forward transform");
   constexpr int S = 1 << LS;
   constexpr int LE = E == 16 ? 4 : 5;  // log2 E
@@ -203,6 +205,8 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const RowMap rm,
                                                    const NttTables tb, const int logN) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ u64 sh[];
   const int N = 1 << logN;
   const int row = blockIdx.x;
@@ -480,15 +484,19 @@ static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
   const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
   const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
-    k_ntt_pass<LOGN, LA, true, true, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
+    pdl_launch(c->stream, k_ntt_pass<LOGN, LA, true, true, EA, NA, MB>, rows * gA, NA, 0, data, rm,
+               tb, gA, MdEpi{});
     if (epi)
-      k_ntt_pass<LOGN, LB, false, true, EB, NB, MB, true>
-          <<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB, *epi);
+      pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, true, EB, NB, MB, true>, rows * gB, NB, 0,
+                 data, rm, tb, gB, *epi);
     else
-      k_ntt_pass<LOGN, LB, false, true, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
+      pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, true, EB, NB, MB>, rows * gB, NB, 0, data,
+                 rm, tb, gB, MdEpi{});
   } else {
-    k_ntt_pass<LOGN, LB, false, false, EB, NB, MB><<<rows * gB, NB, 0, c->stream>>>(data, rm, tb, gB);
-    k_ntt_pass<LOGN, LA, true, false, EA, NA, MB><<<rows * gA, NA, 0, c->stream>>>(data, rm, tb, gA);
+    pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, false, EB, NB, MB>, rows * gB, NB, 0, data,
+               rm, tb, gB, MdEpi{});
+    pdl_launch(c->stream, k_ntt_pass<LOGN, LA, true, false, EA, NA, MB>, rows * gA, NA, 0, data, rm,
+               tb, gA, MdEpi{});
   }
   GWHE_LAUNCHED(c, 2);
 }
@@ -571,9 +579,9 @@ static bool ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd,
   const NttTables tb = c->tables();
   const size_t shm = sizeof(u64) << c->logN;
   if (fwd)
-    k_ntt_small<true><<<rows, 256, shm, c->stream>>>(data, rm, tb, c->logN);
+    pdl_launch(c->stream, k_ntt_small<true>, rows, 256, shm, data, rm, tb, c->logN);
   else
-    k_ntt_small<false><<<rows, 256, shm, c->stream>>>(data, rm, tb, c->logN);
+    pdl_launch(c->stream, k_ntt_small<false>, rows, 256, shm, data, rm, tb, c->logN);
   GWHE_LAUNCHED(c, 1);
   return true;
 }
