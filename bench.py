@@ -221,8 +221,15 @@ def run_gpu(args):
         if host_state:
             job.set_host_state(host_state)  # Dup(M_j) in pinned host memory
         job.encrypt_inputs(src["X"], src["A"], src["y"])
-        job.fit(W["kappa"])
-        job.snp_stats(src["S"])
+        if job.factored:
+            # SNP batches encrypted first: the fit computes their S' beside
+            # the covariate phase
+            job.encrypt_snps(src["S"])
+            job.fit(W["kappa"])
+            job.snp_stats(None)
+        else:
+            job.fit(W["kappa"])
+            job.snp_stats(src["S"])
         num, den = job.decrypt_results()
         job.close()
         return num, den

@@ -299,11 +299,22 @@ int gwhe_encrypt_phenotype(gwhe_job* job, const double* y);
  * REP rows of each batch at 4 limbs, with the encryption ids the fused loop
  * uses, so gwhe_snp_stats(job, NULL, ...) then gives the same ciphertexts bit
  * for bit.  They stay on the device until the loop consumes them: 96 N bytes
- * per batch (factored) or 64 n N bytes per batch (M-CCP).  The fused route (gwhe_snp_stats with S) encrypts each set of 64
- * batches right before its tensor sums and never holds more than one set. */
+ * per batch (factored) or 64 n N bytes per batch (M-CCP).  The fused route
+ * (gwhe_snp_stats with S) encrypts each set of 64 batches right before its
+ * tensor sums and never holds more than one set.  In the factored layout,
+ * batches encrypted before gwhe_fit_covariates get their S' (eq. Sprime,
+ * second form, which needs only X, (X^T X)^-1 and S) during the fit, on a
+ * second stream beside the covariate phase: 64 N more bytes per batch until
+ * the loop consumes it, and the same ciphertexts. */
 int gwhe_encrypt_snps(gwhe_job* job, const double* S, long b0, long b1);
 /* Alg. 9 (kappa iterations), Alg. 10, eqs. z / M / zprime, then Dup(M_j),
- * Dup(w), Dup(w z') for the batches (Alg. 7, Alg. 8). */
+ * Dup(w), Dup(w z') for the batches (Alg. 7, Alg. 8).  Factored layout with
+ * batches already encrypted (gwhe_encrypt_snps): also the S' of those
+ * batches, in sets of at most 64 consecutive batches from the first of each
+ * run; the fit's own chain runs on a stream of the next higher priority so
+ * that S' fills the device beside it.  gwhe_snp_stats(job, NULL, b0, b1)
+ * uses a set whose bounds match a set of its loop and computes the others
+ * from the encrypted batches. */
 int gwhe_fit_covariates(gwhe_job* job, int kappa);
 /* Split mode for rings without the fit's depth: the client supplies M (n x n,
  * row-major), w and w*z' (n) in plaintext; they are duplicated and encrypted. */

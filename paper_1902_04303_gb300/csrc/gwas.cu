@@ -466,6 +466,7 @@ void job_import_state(Job* j, const u64* buf, size_t words) {
                    head[3] == (u64)(j->factored ? kLayoutFactored : kLayoutMccp) &&
                    head[4] == (u64)j->lay.n && head[5] == (u64)j->lay.d && cnt == want_cnt,
                ST_EINVAL, "the state buffer was made for another job shape or ring");
+  j->sprime_pre.clear();
   std::vector<u64> meta(2 * cnt);
   GWHE_CUDA(cudaMemcpyAsync(meta.data(), buf + kStateHeader, sizeof(u64) * meta.size(),
                             cudaMemcpyDefault, c->stream));
@@ -574,6 +575,7 @@ static void encrypt_input_parts(Job* j, const double* Xp, const double* Ap, cons
   const int n = lay.n, d = lay.d, L = c->P.L, M = lay.M;
   const double delta = std::ldexp(1.0, c->P.scale_bits);
   const bool cov = parts & kInCov, pheno = parts & kInPheno;
+  if (cov) j->sprime_pre.clear();  // S' made from the previous covariates
   std::vector<double> X, A, y;
   if (cov) {
     X = to_host(c, Xp, (size_t)n * d);
@@ -699,26 +701,33 @@ static void make_dup_state(Job* j, Eval& ev) {
   j->sets.push_back(std::move(dd));
 }
 
-// An independent chain of the covariate phase on a second stream of the
-// job's context: fork() orders the side stream after the work queued so far
-// and makes the context issue there, leave() returns to the main stream, and
+// An independent chain of operations on a second stream of the job's
+// context: fork() orders the side stream after the work queued so far and
+// makes the context issue there, leave() returns to the main stream, and
 // join() makes the main stream wait for everything the chain issued.  Both
 // streams share the context's memory pool (stream-ordered: the fork and
 // join events order reuse across them) and its mask cache (a mask encoded on
-// one stream is waited for on the other).  With the kernel-class timers on,
-// the chain stays on the main stream: the timers' per-class times would
-// otherwise count the overlap twice.
+// one stream is waited for on the other).  The side stream has the main
+// stream's priority, or with raise = true the next higher one (for the
+// critical chain when other work fills the GPU beside it).  With the
+// kernel-class timers on, the chain stays on the main stream: the timers'
+// per-class times would otherwise count the overlap twice.
 struct SideChain {
   Context* c;
   cudaStream_t main, side = nullptr;
   cudaEvent_t ev = nullptr;
   bool on_side = false, joined = true;
-  explicit SideChain(Context* c_) : c(c_), main(c_->stream) {
+  explicit SideChain(Context* c_, bool raise = false) : c(c_), main(c_->stream) {
     if (c->prof.on) return;
     int prio = 0;
     if (cudaStreamGetPriority(main, &prio) != cudaSuccess) {
       cudaGetLastError();
       prio = 0;
+    }
+    if (raise) {
+      int least = 0, greatest = 0;
+      GWHE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      prio = std::max(greatest, prio - 1);  // numerically lower = higher priority
     }
     GWHE_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio));
     GWHE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -750,6 +759,10 @@ struct SideChain {
   }
 };
 
+namespace {
+void precompute_sprime(Job* j, Eval& ev);
+}  // namespace
+
 void job_fit(Job* j, int kappa) {
   GWHE_REQUIRE(kappa >= 1, ST_EINVAL, "kappa >= 1");
   GWHE_REQUIRE(!j->X.empty() && j->y && j->beta0, ST_EINVAL,
@@ -764,6 +777,12 @@ void job_fit(Job* j, int kappa) {
   // on a second stream beside Alg. 9 and eqs. z, zprime
   if (j->factored)
     GWHE_REQUIRE(j->X[0]->l >= kFactLevel, ST_ELEVEL, "need kFactLevel limbs for Dup(X_c)");
+  // factored layout with SNP batches already encrypted: their S' (eq. Sprime,
+  // second form) needs only Dup(X_c) and Dup((XA)_c), so the second stream
+  // goes on from those to the batches' S' while the fit's chain, the critical
+  // path, runs on a stream of higher priority
+  const bool pre = j->factored && !j->enc_snps.empty();
+  j->sprime_pre.clear();
   SideChain side(c);
   side.fork();
   std::vector<CtPtr> Alow;
@@ -777,7 +796,16 @@ void job_fit(Job* j, int kappa) {
     dx = ev.gather(xs, kFactLevel);
     set_ladder(c, *dx, ev.dup_steps());
   }
+  if (pre) {
+    j->DupB.clear();
+    j->DupX.clear();
+    for (int rr = 0; rr < d; ++rr) j->DupB.push_back(xa->view(rr));
+    for (int cc = 0; cc < d; ++cc) j->DupX.push_back(dx->view(cc));
+    precompute_sprime(j, ev);
+  }
   side.leave();
+  SideChain fit(c, true);
+  if (pre) fit.fork();
   // Alg. 9
   CtPtr beta = ev.clone_at(*j->beta0, j->beta0->l);
   CtPtr p, ymp;
@@ -840,6 +868,11 @@ void job_fit(Job* j, int kappa) {
   j->zp = ev.sub(*zv, *xaxtz);
   CtPtr wmv = ev.view(*j->w_m, j->zp->l);
   j->wzp = ev.mult(*wmv, *j->zp);
+  if (pre) {
+    make_dup_state(j, ev);
+    fit.leave();
+    fit.join();
+  }
   side.join();
   if (j->factored) {
     // second form of eq. Sprime: keep Dup((XA)_c) and Dup(X_c) at kFactLevel
@@ -849,7 +882,7 @@ void job_fit(Job* j, int kappa) {
     j->sets.push_back(std::move(xa));
     for (int cc = 0; cc < d; ++cc) j->DupX.push_back(dx->view(cc));
     j->sets.push_back(std::move(dx));
-    make_dup_state(j, ev);
+    if (!pre) make_dup_state(j, ev);
     return;
   }
   // eq. M = I - X A X^T: Alg. 8 (CP-REP-MatMult) on the duplicated columns
@@ -1248,6 +1281,23 @@ CtSetPtr sprime_factored(Job* j, Eval& ev, const SnpSrc* src, long b0, long b1) 
   return Sp;
 }
 
+// S' of every batch encrypted ahead of the loop, in chunks of at most
+// kSnpChunk batches from the first batch of each run of consecutive batches:
+// the chunks the SNP loop makes of such a run (it uses a chunk whose bounds
+// match and computes any other from the encrypted batches, which it keeps
+// until consumed)
+void precompute_sprime(Job* j, Eval& ev) {
+  auto it = j->enc_snps.begin();
+  while (it != j->enc_snps.end()) {
+    const long c0 = it->first;
+    long c1 = c0;
+    while (c1 - c0 < kSnpChunk && j->enc_snps.count(c1)) ++c1;
+    CtSetPtr sp = sprime_factored(j, ev, nullptr, c0, c1);
+    j->sprime_pre[c0] = std::make_pair(c1, std::move(sp));
+    it = j->enc_snps.lower_bound(c1);
+  }
+}
+
 // Runs fn(src, c0, c1) over [b0, b1) in chunks of kSnpChunk batches with the
 // chunk's genotype columns on the device.  Genotypes in host memory (the host
 // tier) are never copied whole: each chunk's columns go through one of two
@@ -1325,15 +1375,27 @@ void job_snp_stats(Job* j, const double* S, long b0, long b1) {
       batch_body(j, ev, sprime_mccp(j, src, c0, c1), c0);
   };
   if (!S) {
-    // the batches' ciphertexts from job_encrypt_snps, freed once consumed
+    // the batches' ciphertexts from job_encrypt_snps, freed once consumed;
+    // a chunk whose S' the fit computed beside the covariate phase goes
+    // straight to the batch core
     for (long bi = b0; bi < b1; ++bi)
       GWHE_REQUIRE(j->enc_snps.count(bi), ST_EINVAL,
                    "batch " + std::to_string(bi) + " was not encrypted (gwhe_encrypt_snps)");
     for (long c0 = b0; c0 < b1; c0 += kSnpChunk) {
       const long c1 = std::min(b1, c0 + kSnpChunk);
-      run_chunk(nullptr, c0, c1);
+      auto pre = j->sprime_pre.find(c0);
+      if (j->factored && pre != j->sprime_pre.end() && pre->second.first == c1) {
+        CtSetPtr sp = std::move(pre->second.second);
+        j->sprime_pre.erase(pre);
+        batch_body(j, ev, std::move(sp), c0);
+      } else {
+        run_chunk(nullptr, c0, c1);
+      }
       for (long bi = c0; bi < c1; ++bi) j->enc_snps.erase(bi);
     }
+    // precomputed chunks that overlap the range but were not used
+    for (auto it = j->sprime_pre.begin(); it != j->sprime_pre.end();)
+      it = (it->first < b1 && it->second.first > b0) ? j->sprime_pre.erase(it) : std::next(it);
     return;
   }
   for_each_snp_chunk(j, S, b0, b1,

@@ -64,6 +64,10 @@ struct Job {
     int first = 0;
   };
   std::map<long, EncBatch> enc_snps;
+  // factored layout: S' of chunks of encrypted batches, computed by the fit
+  // beside the covariate phase (S' needs only X, A and S): chunk start ->
+  // (chunk end, S' at kBatchLevel - 1 limbs); consumed by the SNP loop
+  std::map<long, std::pair<long, CtSetPtr>> sprime_pre;
   ~Job();
 };
 

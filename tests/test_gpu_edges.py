@@ -115,3 +115,42 @@ def test_empty_and_out_of_order_ranges(g):
             assert np.array_equal(parts.ct(which, bi).export(), full.ct(which, bi).export())
     with pytest.raises(g.GwheError):
         parts.snp_stats(data.S, 4, 6)  # past the last batch
+
+
+def test_sprime_beside_the_fit_with_any_later_chunking(g):
+    """Batches encrypted before the fit get their S' during it; the SNP loop
+    uses a precomputed chunk when its bounds match and otherwise computes
+    S' from the kept encrypted batches: ranges that split the precomputed
+    chunks, and a gap in the encrypted batches, give the fused job's
+    ciphertexts bit for bit."""
+    n, d, k = 16, 3, 300  # five batches of 64 SNPs
+    data = make_gwas(n, d, k, seed=36)
+    A = gwas_fp64.xtx_inv(data.X)
+    ctx = g.Context(LOGN, L, K=K, dnum=DNUM, seed=SEED)
+    full = g.Job(ctx, n, d, k, layout="factored")
+    ctx.keygen(rot_steps=full.rotation_steps(), conj=True)
+    full.encrypt_inputs(data.X, A, data.y)
+    full.fit(1)
+    full.snp_stats(data.S)
+    want = [[full.ct(w, bi).export() for w in range(3)] for bi in range(5)]
+    plans = (
+        ([(0, 5)], [(0, 5)], []),                  # one chunk, used as computed
+        ([(0, 5)], [(2, 5), (0, 2)], []),          # split ranges: computed again
+        ([(0, 2), (3, 5)], [(0, 2), (2, 5)], [(2, 3)]),  # a gap, filled after the fit
+    )
+    for before, ranges, after in plans:
+        job = g.Job(ctx, n, d, k, layout="factored")
+        job.encrypt_inputs(data.X, A, data.y)
+        for b0, b1 in before:
+            job.encrypt_snps(data.S, b0, b1)
+        job.fit(1)
+        for b0, b1 in after:
+            job.encrypt_snps(data.S, b0, b1)
+        for b0, b1 in ranges:
+            job.snp_stats(None, b0, b1)
+        for bi in range(5):
+            for w in range(3):
+                assert np.array_equal(job.ct(w, bi).export(), want[bi][w]), (before, bi, w)
+        with pytest.raises(g.GwheError):
+            job.snp_stats(None, 0, 1)  # every batch consumed
+        job.close()

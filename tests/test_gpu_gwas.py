@@ -409,7 +409,8 @@ def _oracle_job(W, lay, steps, data, A, factored, nonce=0):
     return c
 
 
-def test_factored_job_bit_exact_on_two_pass_transforms_and_full_groups(g):
+@pytest.mark.parametrize("snps_first", [False, True])
+def test_factored_job_bit_exact_on_two_pass_transforms_and_full_groups(g, snps_first):
     """The factored job at N = 2^12, the smallest ring on the two-pass
     transform (with its ModDown epilogue) that the paper-shaped job runs on:
     12 batches in one set (the last ragged, 100 SNPs), so the colSum ladder's
@@ -417,7 +418,9 @@ def test_factored_job_bit_exact_on_two_pass_transforms_and_full_groups(g):
     ragged one).  The covariate state (beta, z, z', masked w, Dup(X_c),
     Dup((XA)_c), Dup(w), Dup(w z')) and the outputs of the first and the
     ragged last batch equal the oracle's circuit, which computes its own
-    state batch by batch."""
+    state batch by batch.  snps_first: the batches are encrypted before the
+    fit, which then computes their S' on a second stream beside the
+    covariate phase."""
     W = dict(logN=12, L=21, q0_bits=60, scale_bits=40, K=7, sp_bits=60, dnum=3, seed=14,
              n=16, d=3, k=11 * 256 + 100)
     data = make_gwas(W["n"], W["d"], W["k"], seed=8)
@@ -431,8 +434,13 @@ def test_factored_job_bit_exact_on_two_pass_transforms_and_full_groups(g):
     job.set_nonce(5)
     ks0 = ctx.ks_histogram().copy()
     job.encrypt_inputs(data.X, A, data.y)
-    job.fit(1)
-    job.snp_stats(data.S)
+    if snps_first:
+        job.encrypt_snps(data.S)
+        job.fit(1)
+        job.snp_stats(None)
+    else:
+        job.fit(1)
+        job.snp_stats(data.S)
     want_h, _, _ = job_ks_histogram(W, 1, factored=True)
     assert np.array_equal(ctx.ks_histogram() - ks0, want_h)
     c = _oracle_job(W, lay, steps, data, A, factored=True, nonce=5)
