@@ -162,6 +162,8 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   int no_wait = 0;
   GWHE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no_wait));
 
+  // N^-1 and ipsi[1] per modulus, for the inverse transforms' scale pairs
+  std::vector<u64> h_ninv(nm), h_iw1(nm);
   // NTT tables
   {
     std::vector<ulonglong2> psi((size_t)nm * N), ipsi((size_t)nm * N);
@@ -183,6 +185,8 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
       }
       ninv[u] = host_inv((u64)N % q, q);
       ninv_sh[u] = shoup_companion(ninv[u], q);
+      h_ninv[u] = ninv[u];
+      h_iw1[u] = ipsi[(size_t)u * N + 1].x;
       const u64 w1n = host_mulmod(ipsi[(size_t)u * N + 1].x, ninv[u], q);
       iw1n[u] = make_ulonglong2(w1n, shoup_companion(w1n, q));
     }
@@ -328,6 +332,37 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
     }
     c->d_conv_store = upload(c.get(), store);
     for (auto& f : fix) f.first->dev = c->d_conv_store + f.second;
+    // the scale pairs of every table's inputs (hinv N^-1 and ipsi[1] hinv
+    // N^-1), and per level the ModUp digits' pairs in limb order
+    {
+      std::vector<ulonglong2> sc;
+      std::vector<std::pair<ConvTable*, size_t>> sfix;
+      auto pairs_of = [&](const ConvTable& t, size_t base) {
+        for (int i = 0; i < t.n_in; ++i) {
+          const int mi = t.in_pidx.empty() ? t.in_lo + i : t.in_pidx[i];
+          const u64 q = c->mod[mi];
+          const u64 a = host_mulmod(store[base + i], h_ninv[mi], q);
+          const u64 b = host_mulmod(a, h_iw1[mi], q);
+          sc.push_back(make_ulonglong2(a, shoup_companion(a, q)));
+          sc.push_back(make_ulonglong2(b, shoup_companion(b, q)));
+        }
+      };
+      for (auto& f : fix) {
+        sfix.push_back({f.first, sc.size()});
+        pairs_of(*f.first, f.second);
+      }
+      std::vector<size_t> mfix(L + 1, 0);
+      for (int l = 1; l <= L; ++l) {
+        mfix[l] = sc.size();
+        const int beta = (l + alpha - 1) / alpha;
+        for (int j = 0; j < beta; ++j)
+          for (auto& f : fix)
+            if (f.first == &c->modup[{l, j}]) pairs_of(*f.first, f.second);
+      }
+      c->d_iscale_store = upload(c.get(), sc);
+      for (auto& f : sfix) f.first->iscale = c->d_iscale_store + f.second;
+      for (int l = 1; l <= L; ++l) c->modup_iscale[l] = c->d_iscale_store + mfix[l];
+    }
     // constants of the fused division by P' = P q_{l-1}, per level:
     // [P mod q_i, Shoup](i < l) [P'^-1 mod q_i, Shoup](i < l-1)
     // [-h mod q_i](i < l-1) [h (P'/m_j)^-1 mod m_j](j <= K_l), h = (P' - 1)/2
@@ -483,7 +518,7 @@ static void ctx_destroy_on_device(Context* c) {
     return;
   }
   for (void* p : {(void*)c->d_psiB, (void*)c->d_ipsiB}) if (p) cudaFree(p);
-  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_iw1n, (void*)c->d_rescale,
+  for (void* p : {(void*)c->d_mod, (void*)c->d_psi, (void*)c->d_ipsi, (void*)c->d_ninv, (void*)c->d_ninv_sh, (void*)c->d_iw1n, (void*)c->d_iscale_store, (void*)c->d_rescale,
                   (void*)c->d_conv_store, (void*)c->d_fftW_dec, (void*)c->d_fftT_dec,
                   (void*)c->d_fftWq, (void*)c->d_fftTq,
                   (void*)c->d_slot_u, (void*)c->d_slot_inv})
@@ -866,8 +901,10 @@ static void modup_ext(Context* c, const u64* x, size_t x_stride, int cnt, int l,
   GWHE_CUDA(cudaMemcpy2DAsync(xc.p, sizeof(u64) * l * N, x,
                               sizeof(u64) * std::max<size_t>(x_stride, l * N), sizeof(u64) * l * N,
                               cnt, cudaMemcpyDeviceToDevice, c->stream));
-  ntt_inverse(c, xc.u(), rows_q(cnt, l, l));
-  modup_convert_set(c, xc.u(), l, ext, cnt);
+  // the coefficient form of every digit limb times its conversion's hinv
+  const ulonglong2* isc = c->modup_iscale[l];
+  ntt_inverse(c, xc.u(), rows_q(cnt, l, l), isc);
+  modup_convert_set(c, xc.u(), l, ext, cnt, isc != nullptr);
   // the new limbs of every digit in one transform launch
   RowMap rm;
   rm.npoly = cnt;
@@ -899,9 +936,10 @@ static void moddown_out(Context* c, u64* acc, int cnt, int l, int K, u64* out0, 
     rk.off[k] = (uint16_t)(l + k);
     rk.pidx[k] = (uint8_t)(L + k);
   }
-  ntt_inverse(c, acc, rk);
+  const ulonglong2* isc = c->moddown[K].iscale;  // the conversion's hinv, merged
+  ntt_inverse(c, acc, rk, isc);
   Tmp conv(c, sizeof(u64) * cnt * 2 * l * N);
-  moddown_convert_set(c, acc, l, K, conv.u(), cnt);
+  moddown_convert_set(c, acc, l, K, conv.u(), cnt, isc != nullptr);
   // the transform's row pass ends with (acc - NTT(conv)) P^-1 + add
   const MdEpi epi{acc, l, K, out0, out1, o_stride, add0, add1, a0_stride, a1_stride, c->d_pinv[K]};
   if (ntt_forward_moddown(c, conv.u(), cnt, epi)) return;
@@ -1085,9 +1123,10 @@ static void relin_rescale_items(Context* c, const u64* t3, size_t t3_stride, int
     rb.off[j] = (uint16_t)j;
     rb.pidx[j] = (uint8_t)(j < K ? L + j : l - 1);
   }
-  ntt_inverse(c, bp.u(), rb);
+  const ulonglong2* isc = c->fused[l].iscale;  // the conversion's hinv, merged
+  ntt_inverse(c, bp.u(), rb, isc);
   Tmp conv(c, sizeof(u64) * cnt * 2 * (l - 1) * N);
-  fused_convert_set(c, bp.u(), l, K, conv.u(), cnt);
+  fused_convert_set(c, bp.u(), l, K, conv.u(), cnt, isc != nullptr);
   ntt_forward(c, conv.u(), rows_q(2 * cnt, l - 1, l - 1));
   fused_combine_set(c, acc.u(), t3, t3_stride, t3_cap, conv.u(), out, o_stride, o_cap, l, K, cnt);
 }

@@ -302,6 +302,10 @@ struct Params {
 
 struct ConvTable {  // fast base conversion constants, on the device
   const u64* dev;   // [n_in] hinv, [n_in] hinv_sh, [n_in][n_out] hmod
+  // [n_in][2]: (hinv N^-1, Shoup) and (ipsi[1] hinv N^-1, Shoup) mod the
+  // input's modulus, for an inverse transform whose output is the
+  // conversion's input already multiplied by hinv (ntt_inverse's iscale)
+  const ulonglong2* iscale = nullptr;
   int n_in, n_out;
   int in_lo;                          // first input q-limb (ModUp digits)
   std::vector<uint8_t> in_pidx;       // modulus index of each input limb (empty: in_lo + i)
@@ -381,6 +385,10 @@ struct Context {
   ConvTable fused[kMaxRowLimbs + 1];
   u64* d_fused[kMaxRowLimbs + 1] = {};
   u64* d_conv_store = nullptr; // backing store of all conversion tables
+  ulonglong2* d_iscale_store = nullptr;  // backing store of the iscale arrays
+  // ModUp at level l: the iscale pairs of all l limbs (each from its digit's
+  // table), in limb order, for the one inverse transform of every digit
+  const ulonglong2* modup_iscale[kMaxRowLimbs + 1] = {};
   // encoding procedure tables
   double2* d_fftW_dec = nullptr;
   longlong2* d_fftWq = nullptr;   // [M/2] encoding twiddles, 62 fractional bits
@@ -477,7 +485,10 @@ struct MdEpi {
   const u64* pinv;
 };
 bool ntt_forward_moddown(Context* c, u64* data, int cnt, const MdEpi& epi);
-void ntt_inverse(Context* c, u64* data, const RowMap& rm);
+// iscale (device, optional): [rm.nl][2] pairs (s N^-1, Shoup), (ipsi[1] s
+// N^-1, Shoup) per row-map limb; the output is the inverse transform times s
+// (canonical residues), the factor merged into the last stage
+void ntt_inverse(Context* c, u64* data, const RowMap& rm, const ulonglong2* iscale = nullptr);
 RowMap rows_q(int npoly, int l, int poly_stride);  // limbs 0..l-1 of q-primes
 
 }  // namespace gwhe

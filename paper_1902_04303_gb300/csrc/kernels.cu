@@ -97,11 +97,15 @@ struct ConvArgs {
   // product (mod its modulus) and to each output (mod the output's modulus)
   const u64* in_add = nullptr;
   const u64* out_add = nullptr;
+  // the inputs are already the products x_i hinv_i (canonical), from an
+  // inverse transform scaled by the table's iscale pairs
+  int pre = 0;
   uint8_t out_pidx[kMaxRowLimbs];
   uint16_t out_row[kMaxRowLimbs];
 };
 
-// y_i = [x_i hinv_i]_{m_i};  out_o = sum_i y_i hmod[i][o] mod m_o.
+// y_i = [x_i hinv_i]_{m_i} (or x_i itself when the input already carries
+// the factor);  out_o = sum_i y_i hmod[i][o] mod m_o.
 // Grid: x = coefficients, y = groups of kConvOG outputs, z = items (polynomials).
 // NI (the number of input limbs) is a template parameter, so the products and
 // their 128-bit sums unroll completely; the CTA's slice of the hmod table
@@ -158,7 +162,8 @@ __global__ void __launch_bounds__(256) k_baseconv(const u64* __restrict__ x, siz
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const u64 q = mod[a.in_pidx[i]].q;
-    y[i] = shoup(xp[(size_t)i * N + k], a.tab[i], a.tab[NI + i], q);
+    const u64 xv = xp[(size_t)i * N + k];
+    y[i] = a.pre ? xv : shoup(xv, a.tab[i], a.tab[NI + i], q);
     if (a.in_add) y[i] = addmod(y[i], a.in_add[i], q);
   }
   int o = 0;
@@ -1209,27 +1214,29 @@ static void launch_baseconv(Context* c, const u64* x, size_t xs, u64* out, size_
   GWHE_LAUNCHED(c, 1);
 }
 
-void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt) {
+void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt, bool pre) {
   ProfScope ps(c, PROF_BASECONV, 0.0);
   const int beta = (l + c->alpha - 1) / c->alpha;
   const int ne = l + c->ks_k[l];
   const size_t N = c->N;
   for (int j = 0; j < beta; ++j) {
     const ConvTable& t = c->modup.at({l, j});
-    const ConvArgs a = conv_args(t, t.in_lo);
+    ConvArgs a = conv_args(t, t.in_lo);
+    a.pre = pre;
     ps.bytes += 8.0 * (t.n_in + t.n_out) * N * cnt;
     launch_baseconv(c, x_coeff + (size_t)t.in_lo * N, (size_t)l * N, ext + (size_t)j * ne * N,
                     (size_t)beta * ne * N, cnt, a);
   }
 }
 
-void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt) {
+void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt, bool pre) {
   GWHE_REQUIRE(l >= 1 && l <= c->P.L && K >= 1 && K <= c->P.K && c->d_pinv[K], ST_EINVAL,
                "bad level or special-prime count");
   ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (K + l) * 8.0 * c->N);
   const int ne = l + K;
   ConvArgs a = conv_args(c->moddown[K], c->P.L);  // table rows hold all L outputs
   a.n_out = l;                                    // produce the first l of them
+  a.pre = pre;
   // items: the 2 cnt polynomials of acc ([cnt][2][ne][N]) -> conv ([cnt][2][l][N])
   launch_baseconv(c, acc + (size_t)l * c->N, (size_t)ne * c->N, conv, (size_t)l * c->N, 2 * cnt, a);
 }
@@ -1343,13 +1350,14 @@ void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride,
   GWHE_LAUNCHED(c, 1);
 }
 
-void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt) {
+void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt, bool pre) {
   ProfScope ps(c, PROF_BASECONV, 2.0 * cnt * (K + l) * 8.0 * c->N);
   const ConvTable& t = c->fused[l];
   GWHE_REQUIRE(t.n_in == K + 1 && t.n_out == l - 1, ST_EINVAL, "fused conversion table");
   ConvArgs a = conv_args(t, 0);
   a.out_add = c->d_fused[l] + 2 * l + 2 * (l - 1);
   a.in_add = a.out_add + (l - 1);
+  a.pre = pre;
   launch_baseconv(c, bp, (size_t)(K + 1) * c->N, conv, (size_t)(l - 1) * c->N, 2 * cnt, a);
 }
 

@@ -46,8 +46,11 @@ void ew_add_plain_poly0(Context* c, PolyView ct, int l, const u64* pt);
 // key switching pieces, over cnt items (strides in words).  A switch at level
 // l uses K = ks_k[l] special primes; ext rows: for each digit j, ne = l + K
 // limbs at ext + (j * ne + u) * N.
-void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt);
-void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt);
+// pre: the inputs already carry the conversion's hinv factor (inverse
+// transform with the table's iscale pairs)
+void modup_convert_set(Context* c, const u64* x_coeff, int l, u64* ext, int cnt, bool pre = false);
+void moddown_convert_set(Context* c, const u64* acc, int l, int K, u64* conv, int cnt,
+                         bool pre = false);
 void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
                   const Ksk& key, u64* acc, int cnt);
 void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int K, int cnt,
@@ -59,7 +62,8 @@ void moddown_combine_set(Context* c, const u64* acc, const u64* conv, int l, int
 // their conversion to q_0..q_{l-2} ([cnt][2][l-1][N]), and the combine.
 void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
                     u64* bp, int l, int K, int cnt);
-void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt);
+void fused_convert_set(Context* c, const u64* bp, int l, int K, u64* conv, int cnt,
+                       bool pre = false);
 void fused_combine_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,
                        const u64* conv, u64* out, size_t o_stride, int o_cap, int l, int K,
                        int cnt);

@@ -38,7 +38,8 @@ template <int LOGN, int LS, bool PASSA, bool FWD, int E = 16, int NT = 256, int 
           bool MD = false>
 __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, const RowMap rm,
                                                   const NttTables tb, const int groups_per_row,
-                                                  const MdEpi epi = MdEpi{}) {
+                                                  const MdEpi epi,
+                                                  const ulonglong2* __restrict__ iscale) {
   pdl_wait();
   pdl_trigger();
   static_assert(!MD || (FWD && !PASSA), "the ModDown epilogue ends a forward transform");
@@ -184,10 +185,21 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
     }
     if (PASSA) {
       // global stage 0 (every pair on twiddle index 1) with the factor N^-1
-      // merged in: x = (x + y) N^-1, y = (x - y) (w N^-1), both exact Shoup
-      // products of inputs below 8q, so canonical in [0, q)
-      const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
-      const ulonglong2 wn = tb.iw1n[u];
+      // (times the row's scale s, if given) merged in: x = (x + y) s N^-1,
+      // y = (x - y) (w s N^-1), both exact Shoup products of inputs below 8q,
+      // so canonical in [0, q)
+      u64 ni, nish;
+      ulonglong2 wn;
+      if (iscale) {
+        const ulonglong2 a = iscale[2 * limb];
+        ni = a.x;
+        nish = a.y;
+        wn = iscale[2 * limb + 1];
+      } else {
+        ni = tb.ninv[u];
+        nish = tb.ninv_sh[u];
+        wn = tb.iw1n[u];
+      }
       constexpr int st = E / 2;
 #pragma unroll
       for (int m = 0; m < st; ++m) {
@@ -204,7 +216,8 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 // Whole row in shared memory (N <= 2^11), one CTA per row.
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const RowMap rm,
-                                                   const NttTables tb, const int logN) {
+                                                   const NttTables tb, const int logN,
+                                                   const ulonglong2* __restrict__ iscale) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ u64 sh[];
@@ -244,7 +257,8 @@ __global__ void __launch_bounds__(256) k_ntt_small(u64* __restrict__ data, const
       }
       __syncthreads();
     }
-    const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+    const u64 ni = iscale ? iscale[2 * limb].x : tb.ninv[u];
+    const u64 nish = iscale ? iscale[2 * limb].y : tb.ninv_sh[u];
     for (int i = threadIdx.x; i < N; i += blockDim.x) base[i] = shoup(sh[i], ni, nish, q);
   }
 }
@@ -271,7 +285,7 @@ constexpr size_t kClusterSmem = sizeof(u64) * 32 * kClusterPitchB;
 template <bool FWD, bool MD>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 2)
     k_ntt_cluster(u64* __restrict__ data, const RowMap rm, const NttTables tb,
-                  const MdEpi epi = MdEpi{}) {
+                  const MdEpi epi = MdEpi{}, const ulonglong2* __restrict__ iscale = nullptr) {
   static_assert(!MD || FWD, "the ModDown epilogue ends a forward transform");
   constexpr int LOGN = 16, LS = 8, E = 16, TPS = 16, G = 32;
   extern __shared__ u64 sm[];
@@ -467,7 +481,8 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
         gs_bfly(x[m], x[m + st], w.x, w.y, q4, nq);
       }
     }
-    const u64 ni = tb.ninv[u], nish = tb.ninv_sh[u];
+    const u64 ni = iscale ? iscale[2 * limb].x : tb.ninv[u];
+    const u64 nish = iscale ? iscale[2 * limb].y : tb.ninv_sh[u];
 #pragma unroll
     for (int m = 0; m < E; ++m) base[((size_t)(rA + TPS * m) << 8) + gA] = shoup(x[m], ni, nish, q);
   }
@@ -478,25 +493,25 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
 // (epi: forward only, the row pass ends with the ModDown epilogue)
 template <int LOGN, int LA, int LB, int EA, int NA, int EB, int NB, int MB = 4>
 static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
-                         const MdEpi* epi = nullptr) {
+                         const MdEpi* epi = nullptr, const ulonglong2* iscale = nullptr) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
   const int gA = (1 << (LOGN - LA)) / (NA / ((1 << LA) / EA));
   const int gB = (1 << (LOGN - LB)) / (NB / ((1 << LB) / EB));
   if (fwd) {
     pdl_launch(c->stream, k_ntt_pass<LOGN, LA, true, true, EA, NA, MB>, rows * gA, NA, 0, data, rm,
-               tb, gA, MdEpi{});
+               tb, gA, MdEpi{}, nullptr);
     if (epi)
       pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, true, EB, NB, MB, true>, rows * gB, NB, 0,
-                 data, rm, tb, gB, *epi);
+                 data, rm, tb, gB, *epi, nullptr);
     else
       pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, true, EB, NB, MB>, rows * gB, NB, 0, data,
-                 rm, tb, gB, MdEpi{});
+                 rm, tb, gB, MdEpi{}, nullptr);
   } else {
     pdl_launch(c->stream, k_ntt_pass<LOGN, LB, false, false, EB, NB, MB>, rows * gB, NB, 0, data,
-               rm, tb, gB, MdEpi{});
+               rm, tb, gB, MdEpi{}, nullptr);
     pdl_launch(c->stream, k_ntt_pass<LOGN, LA, true, false, EA, NA, MB>, rows * gA, NA, 0, data, rm,
-               tb, gA, MdEpi{});
+               tb, gA, MdEpi{}, iscale);
   }
   GWHE_LAUNCHED(c, 2);
 }
@@ -505,13 +520,14 @@ static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
 // holds 32 residues per thread in 128-thread CTAs
 template <int LOGN, int LA, int LB>
 static void ntt_two_pass(Context* c, u64* data, const RowMap& rm, bool fwd,
-                         const MdEpi* epi = nullptr) {
+                         const MdEpi* epi = nullptr, const ulonglong2* iscale = nullptr) {
   ntt_two_pass<LOGN, LA, LB, (LA > 8 ? 32 : 16), (LA > 8 ? 128 : 256), (LB > 8 ? 32 : 16),
-               (LB > 8 ? 128 : 256)>(c, data, rm, fwd, epi);
+               (LB > 8 ? 128 : 256)>(c, data, rm, fwd, epi, iscale);
 }
 
 // the one-launch cluster transform of N = 2^16 (k_ntt_cluster)
-static void ntt_cluster_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi) {
+static void ntt_cluster_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi,
+                           const ulonglong2* iscale) {
   const NttTables tb = c->tables();
   const int rows = rm.npoly * rm.nl;
   GWHE_REQUIRE(tb.psiB && tb.ipsiB, ST_EINVAL, "row-pass twiddle table missing");
@@ -533,7 +549,8 @@ static void ntt_cluster_16(Context* c, u64* data, const RowMap& rm, bool fwd, co
   }
   const dim3 grid((unsigned)rows * kClusterCtas);
   if (!fwd)
-    k_ntt_cluster<false, false><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb);
+    k_ntt_cluster<false, false><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb,
+                                                                                   MdEpi{}, iscale);
   else if (epi)
     k_ntt_cluster<true, true><<<grid, kClusterThreads, kClusterSmem, c->stream>>>(data, rm, tb,
                                                                                   *epi);
@@ -544,34 +561,35 @@ static void ntt_cluster_16(Context* c, u64* data, const RowMap& rm, bool fwd, co
 
 // shapes of the N = 2^16 transform (identical results; the autotuner times
 // them on the device and keeps the fastest)
-static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi) {
+static void ntt_2_16(Context* c, u64* data, const RowMap& rm, bool fwd, const MdEpi* epi,
+                     const ulonglong2* iscale) {
   const int rows = rm.npoly * rm.nl;
   switch (rows < kNttSmallRows ? c->ntt_variant_small : c->ntt_variant) {
-    case 6: ntt_cluster_16(c, data, rm, fwd, epi); return;
-    case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd, epi); return;
-    case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd, epi); return;
-    case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd, epi); return;
-    case 4: ntt_two_pass<16, 8, 8, 16, 128, 16, 128, 8>(c, data, rm, fwd, epi); return;
-    case 5: ntt_two_pass<16, 8, 8, 16, 64, 16, 64, 16>(c, data, rm, fwd, epi); return;
-    default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd, epi); return;
+    case 6: ntt_cluster_16(c, data, rm, fwd, epi, iscale); return;
+    case 1: ntt_two_pass<16, 8, 8, 32, 128, 32, 128>(c, data, rm, fwd, epi, iscale); return;
+    case 2: ntt_two_pass<16, 7, 9, 16, 256, 32, 128>(c, data, rm, fwd, epi, iscale); return;
+    case 3: ntt_two_pass<16, 9, 7, 32, 128, 16, 256>(c, data, rm, fwd, epi, iscale); return;
+    case 4: ntt_two_pass<16, 8, 8, 16, 128, 16, 128, 8>(c, data, rm, fwd, epi, iscale); return;
+    case 5: ntt_two_pass<16, 8, 8, 16, 64, 16, 64, 16>(c, data, rm, fwd, epi, iscale); return;
+    default: ntt_two_pass<16, 8, 8, 16, 256, 16, 256>(c, data, rm, fwd, epi, iscale); return;
   }
 }
 
 // true if the ring has a two-pass transform (and epi, if given, was applied)
 static bool ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd,
-                         const MdEpi* epi = nullptr) {
+                         const MdEpi* epi = nullptr, const ulonglong2* iscale = nullptr) {
   const int rows = rm.npoly * rm.nl;
   if (rows <= 0) return true;
   // algorithmic traffic: every residue read once and written once
   ProfScope ps(c, PROF_NTT, 16.0 * rows * c->N);
   GWHE_REQUIRE(rm.nl <= kMaxRowMap, ST_EINVAL, "too many limbs in a row map");
   switch (c->logN) {
-    case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd, epi); return true;
-    case 16: ntt_2_16(c, data, rm, fwd, epi); return true;
-    case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd, epi); return true;
-    case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd, epi); return true;
-    case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd, epi); return true;
-    case 12: ntt_two_pass<12, 6, 6>(c, data, rm, fwd, epi); return true;
+    case 17: ntt_two_pass<17, 9, 8>(c, data, rm, fwd, epi, iscale); return true;
+    case 16: ntt_2_16(c, data, rm, fwd, epi, iscale); return true;
+    case 15: ntt_two_pass<15, 8, 7>(c, data, rm, fwd, epi, iscale); return true;
+    case 14: ntt_two_pass<14, 7, 7>(c, data, rm, fwd, epi, iscale); return true;
+    case 13: ntt_two_pass<13, 7, 6>(c, data, rm, fwd, epi, iscale); return true;
+    case 12: ntt_two_pass<12, 6, 6>(c, data, rm, fwd, epi, iscale); return true;
     default: break;
   }
   if (epi) return false;
@@ -579,9 +597,9 @@ static bool ntt_dispatch(Context* c, u64* data, const RowMap& rm, bool fwd,
   const NttTables tb = c->tables();
   const size_t shm = sizeof(u64) << c->logN;
   if (fwd)
-    pdl_launch(c->stream, k_ntt_small<true>, rows, 256, shm, data, rm, tb, c->logN);
+    pdl_launch(c->stream, k_ntt_small<true>, rows, 256, shm, data, rm, tb, c->logN, nullptr);
   else
-    pdl_launch(c->stream, k_ntt_small<false>, rows, 256, shm, data, rm, tb, c->logN);
+    pdl_launch(c->stream, k_ntt_small<false>, rows, 256, shm, data, rm, tb, c->logN, iscale);
   GWHE_LAUNCHED(c, 1);
   return true;
 }
@@ -593,7 +611,9 @@ bool ntt_forward_moddown(Context* c, u64* data, int cnt, const MdEpi& epi) {
   if (c->logN < 12) return false;
   return ntt_dispatch(c, data, rows_q(2 * cnt, epi.l, epi.l), true, &epi);
 }
-void ntt_inverse(Context* c, u64* data, const RowMap& rm) { ntt_dispatch(c, data, rm, false); }
+void ntt_inverse(Context* c, u64* data, const RowMap& rm, const ulonglong2* iscale) {
+  ntt_dispatch(c, data, rm, false, nullptr, iscale);
+}
 
 RowMap rows_q(int npoly, int l, int poly_stride) {
   GWHE_REQUIRE(l >= 0 && l <= kMaxRowLimbs, ST_EINVAL, "too many limbs");
