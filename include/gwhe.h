@@ -199,17 +199,19 @@ int gwhe_rescale(gwhe_ctx* ctx, gwhe_ct* ct);                         /* drops q
 int gwhe_mult(gwhe_ctx* ctx, const gwhe_ct* a, const gwhe_ct* b, gwhe_ct* out);
 int gwhe_rotate(gwhe_ctx* ctx, const gwhe_ct* a, int steps, gwhe_ct* out); /* out != a */
 int gwhe_conjugate(gwhe_ctx* ctx, const gwhe_ct* a, gwhe_ct* out);         /* out != a */
-/* out = a + sum_i Rotate(a, steps[i]) for 1 <= nsteps <= 7, the rotations'
+/* out = a + sum_i Rotate(a, steps[i]) for 1 <= nsteps <= 15, the rotations'
  * key switches hoisted: one ModUp of c1, each rotation's automorphism applied
  * to the ModUp digits, the inner products with the rotations' keys summed in
- * the extended basis, one ModDown.  Two steps r, 2r of a doubling
- * rotate-and-add ladder (Alg. 1, 4, 5, 7) are the sum over {r, 2r, 3r}; the
- * library's ladders run this way.  out != a; needs the rotations' keys. */
+ * the extended basis, one ModDown.  m steps r, 2r, ... of a doubling
+ * rotate-and-add ladder (Alg. 1, 4, 5, 7) are the sum over {r, 2r, ...,
+ * (2^m - 1) r}; the library's ladders run this way, three steps per sum.
+ * More than seven rotations run their inner products in chunks of seven that
+ * accumulate before the one ModDown.  out != a; needs the rotations' keys. */
 int gwhe_rotate_sum(gwhe_ctx* ctx, const gwhe_ct* a, const int32_t* steps, int nsteps,
                     gwhe_ct* out);
 /* gwhe_rotate_sum for count ciphertexts of one level and scale at once (the
  * batched form the library's ladders use): out[i] = a[i] + sum_r Rotate(a[i], r),
- * nsteps <= 7; out[i] != a[j]. */
+ * nsteps <= 15; out[i] != a[j]. */
 int gwhe_rotate_sum_batch(gwhe_ctx* ctx, const gwhe_ct* const* a, int count,
                           const int32_t* steps, int nsteps, gwhe_ct* const* out);
 /* out[i] = Rotate(a[i], step) for count ciphertexts of one level and scale,

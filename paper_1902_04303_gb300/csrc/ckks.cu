@@ -1002,14 +1002,15 @@ void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs) {
   moddown_out(c, acc.u(), cnt, l, K, s.d, c1, s.stride(), t0.u(), c1, (size_t)l * N, s.stride());
 }
 
-std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps) {
-  // up to kLadderGroup consecutive doubling steps r, 2r, 4r, ... of a ladder
+std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps, int group) {
+  // up to `group` consecutive doubling steps r, 2r, 4r, ... of a ladder
   // merge into one hoisted step over the rotations r, 2r, ..., (2^m - 1) r
   // (the same sum of rotations)
+  GWHE_REQUIRE(group >= 1 && (1 << group) - 1 <= kMaxHoist, ST_EINVAL, "ladder group too long");
   std::vector<std::vector<int>> out;
   for (size_t i = 0; i < steps.size();) {
     size_t m = 1;
-    while (m < (size_t)kLadderGroup && i + m < steps.size() && steps[i + m] == 2 * steps[i + m - 1])
+    while (m < (size_t)group && i + m < steps.size() && steps[i + m] == 2 * steps[i + m - 1])
       ++m;
     std::vector<int> g;
     for (int t = 1; t < (1 << m); ++t) g.push_back(t * steps[i]);
@@ -1019,9 +1020,9 @@ std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps) {
   return out;
 }
 
-void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps) {
+void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps, int group) {
   GWHE_REQUIRE(s.npoly == 2, ST_EINVAL, "ladder needs ciphertexts");
-  for (const auto& rs : ladder_groups(steps)) set_rotate_sum(c, s, rs);
+  for (const auto& rs : ladder_groups(steps, group)) set_rotate_sum(c, s, rs);
 }
 
 void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out) {

@@ -106,15 +106,21 @@ void keyswitch_set(Context* c, const u64* x, size_t x_stride, int cnt, int l, co
                    u64* out0, u64* out1, size_t o_stride, const u64* add0, const u64* add1,
                    size_t a0_stride, size_t a1_stride);
 // s[i] += Rotate(s[i], step) for each step in turn (Alg. 1/4/5/7 ladders),
-// evaluated as hoisted sums over the groups of ladder_groups(steps)
-void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps);
-// s[i] += sum_{r in rs} Rotate(s[i], r) with the key switches hoisted (one
-// ModUp, one ModDown; at most seven rotations)
-void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs);
-// up to kLadderGroup consecutive doubling steps (r, 2r, 4r) -> one group
-// {r, 2r, ..., 7r}; a shorter run -> {r, .., (2^m - 1) r}
+// evaluated as hoisted sums over the groups of ladder_groups(steps, group).
+// Up to `group` consecutive doubling steps (r, 2r, 4r, ...) -> one group
+// {r, 2r, ..., (2^group - 1) r}; a shorter run of m -> {r, .., (2^m - 1) r}.
+// Every ladder of the circuit takes groups of kLadderGroup steps: at the SNP
+// batch levels one ModUp and ModDown of a ciphertext costs about as much as
+// eleven automorphisms' inner products and sums, which makes three steps (7
+// rotations) per group the fastest split of an 8-step ladder (four steps,
+// 15 rotations, measured slower).
 constexpr int kLadderGroup = 3;
-std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps);
+void set_ladder(Context* c, CtSet& s, const std::vector<int>& steps, int group = kLadderGroup);
+// s[i] += sum_{r in rs} Rotate(s[i], r) with the key switches hoisted (one
+// ModUp, one ModDown; at most kMaxHoist = 15 rotations)
+void set_rotate_sum(Context* c, CtSet& s, const std::vector<int>& rs);
+std::vector<std::vector<int>> ladder_groups(const std::vector<int>& steps,
+                                            int group = kLadderGroup);
 // out[i] = automorphism g of a[i] (rotation or conjugation)
 void set_galois(Context* c, const CtSet& a, u32 g, CtSet& out);
 // out[i] = items[i].src * items[i].pt, scale = src scale * pt_scale (then rescale)

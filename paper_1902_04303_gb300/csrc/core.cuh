@@ -204,6 +204,11 @@ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a -
 struct Acc128 {
   u64 lo, hi;
 };
+// a += v on 128 bits
+__device__ __forceinline__ void add128(Acc128& a, u64 v) {
+  a.lo += v;
+  a.hi += a.lo < v;
+}
 // a += x * y on 128 bits, as a schoolbook product of 32-bit halves with
 // multiply-add carry chains: the x0 y0 and x1 y1 partial products go to words
 // 0-1 and 2-3, the two cross products to words 1-2.

@@ -250,7 +250,7 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
                                  const u64* __restrict__ ext, HoistKeys hk,
                                  u64* __restrict__ acc, int l, int K, int L, int key_lmax,
                                  int alpha, int beta, int logN, int cnt,
-                                 const DevMod* __restrict__ mod) {
+                                 const DevMod* __restrict__ mod, int accum) {
   pdl_wait();
   pdl_trigger();
   const int u = blockIdx.z;
@@ -298,6 +298,10 @@ __global__ void k_ks_inner_hoist(const u64* __restrict__ c_ntt, size_t c_stride,
   for (int t = 0; t < IB; ++t) {
     if (t >= nit) break;
     u64* ac = acc + (size_t)(it0 + t) * 2 * ne * N;
+    if (accum) {  // a later chunk of the automorphisms adds to acc
+      add128(s0[t], ac[(size_t)u * N + k]);
+      add128(s1[t], ac[((size_t)ne + u) * N + k]);
+    }
     ac[(size_t)u * N + k] = reduce128(s0[t].lo, s0[t].hi, m);
     ac[((size_t)ne + u) * N + k] = reduce128(s1[t].lo, s1[t].hi, m);
   }
@@ -311,7 +315,8 @@ __global__ void __launch_bounds__(256, 4) k_ks_inner_hoist1(const u64* __restric
                                                            size_t c_stride,
                                   const u64* __restrict__ ext, HoistKeys hk,
                                   u64* __restrict__ acc, int l, int K, int L, int key_lmax,
-                                  int logN, int cnt, const DevMod* __restrict__ mod) {
+                                  int logN, int cnt, const DevMod* __restrict__ mod,
+                                  int accum) {
   pdl_wait();
   pdl_trigger();
   const int u = blockIdx.z;
@@ -340,23 +345,26 @@ __global__ void __launch_bounds__(256, 4) k_ks_inner_hoist1(const u64* __restric
     u64 x[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) x[g] = row[src[g]];
-    Acc128 s0{0, 0}, s1{0, 0};
+    u64* ac = acc + (size_t)item * 2 * ne * N;
+    // a later chunk of the automorphisms adds to the earlier chunks' acc
+    Acc128 s0{accum ? ac[(size_t)u * N + k] : 0, 0};
+    Acc128 s1{accum ? ac[((size_t)ne + u) * N + k] : 0, 0};
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       mac128(s0, x[g], kb[g]);
       mac128(s1, x[g], ka[g]);
     }
-    u64* ac = acc + (size_t)item * 2 * ne * N;
     ac[(size_t)u * N + k] = reduce128(s0.lo, s0.hi, m);
     ac[((size_t)ne + u) * N + k] = reduce128(s1.lo, s1.hi, m);
   }
 }
 
-// out[item][i] = c0[item][i] + sum_g sigma_g(c0[item][i]) (NTT domain)
+// out[item][i] = c0[item][i] + sum_g sigma_g(c0[item][i]) (NTT domain); with
+// accum, out[item][i] += sum_g sigma_g(c0[item][i])
 template <int G>
 __global__ void k_automorph_sum(const u64* __restrict__ in, int in_cap, size_t in_stride,
                                 u64* __restrict__ out, int l, int logN, HoistKeys hk,
-                                const DevMod* __restrict__ mod) {
+                                const DevMod* __restrict__ mod, int accum) {
   pdl_wait();
   pdl_trigger();
   const int i = blockIdx.y;
@@ -366,10 +374,11 @@ __global__ void k_automorph_sum(const u64* __restrict__ in, int in_cap, size_t i
   const size_t item = blockIdx.z;
   const u64* src = in + item * in_stride + (size_t)i * N;
   const u64 q = mod[i].q;
-  u64 v = src[j];
+  u64* o = out + (item * l + i) * N + j;
+  u64 v = accum ? *o : src[j];  // a later chunk adds to the earlier sum
 #pragma unroll
   for (int g = 0; g < G; ++g) v = addmod(v, src[automorph_src((unsigned)j, hk.g[g], logN)], q);
-  out[(item * l + i) * N + j] = v;
+  *o = v;
 }
 
 // out_p[i] = (acc_p[i] - conv_p[i]) P^-1 mod q_i (+ add_p[i])
@@ -1270,12 +1279,13 @@ void ks_inner_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u6
 
 template <int G>
 static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
-                         const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt, int beta) {
+                         const HoistKeys& hk, int key_lmax, int K, u64* acc, int cnt, int beta,
+                         int accum) {
   if (beta == 1) {
     constexpr int IB1 = 32;
     const dim3 grid((cnt + IB1 - 1) / IB1, blocks_for(c->N), l + K);
     pdl_launch(c->stream, k_ks_inner_hoist1<IB1, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk,
-               acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod);
+               acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod, accum);
     return;
   }
   // items per thread (each key word is read once per IB items); eight with
@@ -1288,13 +1298,13 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
       // five: the keys are read once, at the occupancy of four per thread
       const dim3 grid(1, blocks_for(c->N), l + K);
       pdl_launch(c->stream, k_ks_inner_hoist<5, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk,
-                 acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod);
+                 acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod, accum);
       return;
     }
   }
   const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
   pdl_launch(c->stream, k_ks_inner_hoist<IB, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk, acc,
-             l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod);
+             l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod, accum);
 }
 
 void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, const u64* ext,
@@ -1304,41 +1314,59 @@ void ks_inner_hoist_set(Context* c, const u64* c_ntt, size_t c_stride, int l, co
   const int beta = (l + c->alpha - 1) / c->alpha;
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
   GWHE_REQUIRE(beta <= kKsMaxBeta, ST_EINVAL, "more than 4 key digits at one level");
-  switch (hk.G) {
-    case 1: launch_hoist<1>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 2: launch_hoist<2>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 3: launch_hoist<3>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 4: launch_hoist<4>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 5: launch_hoist<5>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 6: launch_hoist<6>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    case 7: launch_hoist<7>(c, c_ntt, c_stride, l, ext, hk, key_lmax, K, acc, cnt, beta); break;
-    default: throw Error(ST_EINVAL, "at most seven hoisted automorphisms");
+  GWHE_REQUIRE(hk.G >= 1 && hk.G <= kMaxHoist, ST_EINVAL, "bad hoisted automorphism count");
+  // chunks of up to kHoistChunk automorphisms; each later chunk adds its
+  // products to acc (exact sums mod each modulus, so the chunking does not
+  // change the result)
+  for (int g0 = 0; g0 < hk.G; g0 += kHoistChunk) {
+    HoistKeys part;
+    part.G = std::min(kHoistChunk, hk.G - g0);
+    for (int g = 0; g < part.G; ++g) {
+      part.key[g] = hk.key[g0 + g];
+      part.g[g] = hk.g[g0 + g];
+    }
+    const int accum = g0 > 0;
+    switch (part.G) {
+#define GWHE_HOIST(n)                                                                             \
+  case n:                                                                                         \
+    launch_hoist<n>(c, c_ntt, c_stride, l, ext, part, key_lmax, K, acc, cnt, beta, accum);        \
+    break;
+      GWHE_HOIST(1) GWHE_HOIST(2) GWHE_HOIST(3) GWHE_HOIST(4) GWHE_HOIST(5) GWHE_HOIST(6)
+      GWHE_HOIST(7)
+#undef GWHE_HOIST
+      default: throw Error(ST_EINVAL, "hoisted chunk out of range");
+    }
+    GWHE_LAUNCHED(c, 1);
   }
-  GWHE_LAUNCHED(c, 1);
 }
 
 void automorph_sum_set(Context* c, const u64* in, int in_cap, size_t in_stride, u64* out, int l,
                        int cnt, const HoistKeys& hk) {
   ProfScope ps(c, PROF_ELEMWISE, (1.0 + hk.G) * l * cnt * 8.0 * c->N);
   GWHE_REQUIRE(cnt >= 1 && cnt < 65536, ST_EINVAL, "batch too large");
+  GWHE_REQUIRE(hk.G >= 1 && hk.G <= kMaxHoist, ST_EINVAL, "bad hoisted automorphism count");
   const dim3 grid(blocks_for(c->N), l, cnt);
+  for (int g0 = 0; g0 < hk.G; g0 += kHoistChunk) {
+    HoistKeys part;
+    part.G = std::min(kHoistChunk, hk.G - g0);
+    for (int g = 0; g < part.G; ++g) {
+      part.key[g] = hk.key[g0 + g];
+      part.g[g] = hk.g[g0 + g];
+    }
+    const int accum = g0 > 0;
 #define GWHE_AUTOSUM(G)                                                                          \
   case G:                                                                                        \
     pdl_launch(c->stream, k_automorph_sum<G>, grid, kThreads, 0, in, in_cap, in_stride, out, l,  \
-               c->logN, hk, c->d_mod);                                                           \
+               c->logN, part, c->d_mod, accum);                                                  \
     break;
-  switch (hk.G) {
-    GWHE_AUTOSUM(1)
-    GWHE_AUTOSUM(2)
-    GWHE_AUTOSUM(3)
-    GWHE_AUTOSUM(4)
-    GWHE_AUTOSUM(5)
-    GWHE_AUTOSUM(6)
-    GWHE_AUTOSUM(7)
-    default: throw Error(ST_EINVAL, "at most seven hoisted automorphisms");
-  }
+    switch (part.G) {
+      GWHE_AUTOSUM(1) GWHE_AUTOSUM(2) GWHE_AUTOSUM(3) GWHE_AUTOSUM(4) GWHE_AUTOSUM(5)
+      GWHE_AUTOSUM(6) GWHE_AUTOSUM(7)
+      default: throw Error(ST_EINVAL, "hoisted chunk out of range");
+    }
 #undef GWHE_AUTOSUM
-  GWHE_LAUNCHED(c, 1);
+    GWHE_LAUNCHED(c, 1);
+  }
 }
 
 void fused_prep_set(Context* c, const u64* acc, const u64* t3, size_t t3_stride, int t3_cap,

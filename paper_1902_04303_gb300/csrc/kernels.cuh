@@ -69,7 +69,10 @@ void fused_combine_set(Context* c, const u64* acc, const u64* t3, size_t t3_stri
                        int cnt);
 // Hoisted key switching of a sum of automorphisms (at most kMaxHoist): the
 // Galois elements and the key family each uses.
-constexpr int kMaxHoist = 7;
+constexpr int kMaxHoist = 15;
+// automorphisms per inner-product launch (the kernels keep a chunk's keys in
+// registers); longer sums run in chunks that accumulate
+constexpr int kHoistChunk = 7;
 struct HoistKeys {
   const u64* key[kMaxHoist];
   u64 g[kMaxHoist];

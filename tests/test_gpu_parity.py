@@ -292,6 +292,20 @@ def test_hoisted_rotation_sum_batch_bit_exact(g, small):
         assert np.array_equal(out.export(), o.rotate_sum(a, rs).c)
 
 
+@pytest.mark.parametrize("l", [2, 6])
+def test_hoisted_sum_of_fifteen_rotations(g, l):
+    """A hoisted sum of 15 rotations (inner products in chunks of 7, 7 and 1
+    that accumulate before the one ModDown, the c0 automorphism sums the
+    same way) over a set of 9 ciphertexts, at one key digit (l = 2) and at
+    three (l = 6): every output equals the oracle's hoisted sum."""
+    rs = list(range(1, 16))
+    ctx, o = pair(g, 10, 6, 3, 3, seed=61, rot=tuple(rs), conj=False)
+    srcs = [rand_ct(o, l, 9000 + 10 * l + i) for i in range(9)]
+    outs = ctx.rotate_sum_batch([ctx.import_ct(a.c, a.scale) for a in srcs], rs)
+    for a, out in zip(srcs, outs):
+        assert np.array_equal(out.export(), o.rotate_sum(a, rs).c)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_every_ntt_shape_is_bit_exact(g, variant):
     """each compiled shape of the N = 2^16 transform gives the oracle's

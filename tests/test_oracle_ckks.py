@@ -319,7 +319,8 @@ def test_keyswitch_noise_invariant_reduced_special_primes(wide, l):
     assert _noise_of(o, u_bad, s2, x) > math.prod(o.q[:l]) // 2 ** 8
 
 
-@pytest.mark.parametrize("l,rs", [(5, [1, 2, 3]), (3, [8, 16, 24]), (2, [-1, -2, -3]), (4, [2])])
+@pytest.mark.parametrize("l,rs", [(5, [1, 2, 3]), (3, [8, 16, 24]), (2, [-1, -2, -3]), (4, [2]),
+                                  (3, list(range(1, 16))), (2, [-r for r in range(1, 16)])])
 def test_hoisted_rotation_sum_is_the_sum_of_automorphisms(small_rot, l, rs):
     """Dec(rotate_sum(a, rs)) = Dec(a) + sum_r sigma_r(Dec(a)) + e with |e|
     < 2^24: the automorphism is exact on the decryption (sigma(c0 + c1 s) =
@@ -363,7 +364,9 @@ def test_hoisted_rotation_sum_is_the_sum_of_automorphisms(small_rot, l, rs):
 @pytest.fixture(scope="module")
 def small_rot():
     o = OracleCKKS(logN=9, L=5, K=4, dnum=2, seed=7)
-    o.keygen(galois=[galois_rot(9, r) for r in (1, 2, 3, 8, 16, 24, -1, -2, -3)])
+    # the rotations of two- and four-step hoisted ladder groups
+    o.keygen(galois=[galois_rot(9, r) for r in sorted(set(range(1, 16)) | {16, 24}
+                                                         | {-r for r in range(1, 16)})])
     return o
 
 
