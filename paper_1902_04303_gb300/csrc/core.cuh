@@ -180,6 +180,12 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wsh, u64 q4, 
 __device__ __forceinline__ u64 reduce_8q(u64 x, u64 q) {
   return csub(csub(csub(x, 4 * q), 2 * q), q);
 }
+// y w mod q in [0, q) for any y < 2^64: the estimated Shoup product (in
+// [0, 4q), fewer 32-bit multiplies than the exact quotient) and two
+// conditional subtractions
+__device__ __forceinline__ u64 shoup_est_canon(u64 y, u64 w, u64 wsh, u64 q, u64 nq) {
+  return csub(csub(shoup_est(y, w, wsh, nq), 2 * q), q);
+}
 
 // (hi 2^64 + lo) mod q: hi 2^64 = hi R (mod q) by a Shoup product, lo by a
 // 64-bit Barrett step (quotient estimate off by at most one).

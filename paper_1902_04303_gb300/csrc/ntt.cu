@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const size_t k = gaddr(r + TPS * m);
-        u64 v = shoup(submod(a[k], x[m], q), pi, pish, q);
+        u64 v = shoup_est_canon(submod(a[k], x[m], q), pi, pish, q, nq);
         if (ad) v = addmod(v, ad[k], q);
         o[k] = v;
       }
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
     if (PASSA) {
       // global stage 0 (every pair on twiddle index 1) with the factor N^-1
       // (times the row's scale s, if given) merged in: x = (x + y) s N^-1,
-      // y = (x - y) (w s N^-1), both exact Shoup products of inputs below 8q,
-      // so canonical in [0, q)
+      // y = (x - y) (w s N^-1), both Shoup products of inputs below 8q made
+      // canonical in [0, q)
       u64 ni, nish;
       ulonglong2 wn;
       if (iscale) {
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(NT, MB) k_ntt_pass(u64* __restrict__ data, con
 #pragma unroll
       for (int m = 0; m < st; ++m) {
         const u64 a = x[m], b = x[m + st];
-        x[m] = shoup(a + b, ni, nish, q);
-        x[m + st] = shoup(a - b + q4, wn.x, wn.y, q);
+        x[m] = shoup_est_canon(a + b, ni, nish, q, nq);
+        x[m + st] = shoup_est_canon(a - b + q4, wn.x, wn.y, q, nq);
       }
     }
   }
@@ -400,7 +400,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const size_t k = ((size_t)gB << 8) + rB + TPS * m;
-        u64 v = shoup(submod(a[k], x[m], q), pi, pish, q);
+        u64 v = shoup_est_canon(submod(a[k], x[m], q), pi, pish, q, nq);
         if (ad) v = addmod(v, ad[k], q);
         o[k] = v;
       }
