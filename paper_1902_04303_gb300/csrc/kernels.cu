@@ -1288,20 +1288,14 @@ static void launch_hoist(Context* c, const u64* c_ntt, size_t c_stride, int l, c
                acc, l, K, c->P.L, key_lmax, c->logN, cnt, c->d_mod, accum);
     return;
   }
-  // items per thread (each key word is read once per IB items); eight with
-  // more than three automorphisms would cost occupancy: measured slower even
-  // for sets of five to eight, where it saves the second read of the keys
-  constexpr int IB = G <= 3 ? 8 : 4;
-  if constexpr (G > 3) {
-    if (cnt == 5) {
-      // a set of five (the covariates of the paper's shape) as one group of
-      // five: the keys are read once, at the occupancy of four per thread
-      const dim3 grid(1, blocks_for(c->N), l + K);
-      pdl_launch(c->stream, k_ks_inner_hoist<5, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk,
-                 acc, l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod, accum);
-      return;
-    }
-  }
+  // items per thread (each key word is read once per IB items): eight with up
+  // to three automorphisms; with more, one.  The multi-digit kernel is bound
+  // by the latency of its key reads and gathers, and one item per thread (46
+  // registers, five CTAs per SM) measured faster than four or five per thread
+  // (72-80 registers, three CTAs per SM), though each key word is then read
+  // once per item; the grid puts a limb's items next to each other in launch
+  // order, so those reads after the first come from L2
+  constexpr int IB = G <= 3 ? 8 : 1;
   const dim3 grid((cnt + IB - 1) / IB, blocks_for(c->N), l + K);
   pdl_launch(c->stream, k_ks_inner_hoist<IB, G>, grid, kThreads, 0, c_ntt, c_stride, ext, hk, acc,
              l, K, c->P.L, key_lmax, c->alpha, beta, c->logN, cnt, c->d_mod, accum);
