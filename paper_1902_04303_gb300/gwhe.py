@@ -461,7 +461,8 @@ class Context:
         return o
 
     def rotate_sum_batch(self, cts, steps, outs=None):
-        """[a + sum_r Rotate(a, r) for a in cts] as one set (shared level/scale)."""
+        """[a + sum_r Rotate(a, r) for a in cts] as one set (shared level/scale),
+        1 to 15 rotations."""
         outs = outs or [self._out(a) for a in cts]
         arr = (ctypes.c_int32 * len(steps))(*steps)
         ins = (_vp * len(cts))(*[a.h for a in cts])
@@ -479,7 +480,7 @@ class Context:
         return outs
 
     def rotate_sum(self, a, steps):
-        """a + sum_r Rotate(a, r) over at most three steps, key switches hoisted."""
+        """a + sum_r Rotate(a, r) over 1 to 15 rotations, key switches hoisted."""
         o = self._out(a)
         arr = (ctypes.c_int32 * len(steps))(*steps)
         self._c(lib().gwhe_rotate_sum(self.h, a.h, arr, len(steps), o.h))
