@@ -155,12 +155,6 @@ Context* ctx_create(const Params& P, u64 seed, cudaStream_t stream) {
   GWHE_CUDA(cudaDeviceGetDefaultMemPool(&pool, c->device));
   uint64_t thr = UINT64_MAX;
   GWHE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-  // a block freed on one stream is reused on another only once the free has
-  // completed (or an event orders them), never by making the allocating
-  // stream wait on the freeing one: such waits would serialise the chains
-  // the library runs side by side on two streams
-  int no_wait = 0;
-  GWHE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no_wait));
 
   // N^-1 and ipsi[1] per modulus, for the inverse transforms' scale pairs
   std::vector<u64> h_ninv(nm), h_iw1(nm);
