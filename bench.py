@@ -905,11 +905,19 @@ def run_serving(args):
     stream = torch.cuda.current_stream()
     S_ = SERVING
     nreq = args.requests
+    t_setup = time.perf_counter()
+
+    def progress(msg):  # a trace on stderr of where a long run stands
+        print("[serving %.0f s] %s" % (time.perf_counter() - t_setup, msg), file=sys.stderr,
+              flush=True)
+
     rng = np.random.Generator(np.random.PCG64(S_["seed"]))
     mix = cohort_shapes(nreq, S_["seed"] + 1)
     shapes = [S_["big"] if rng.random() < S_["big_fraction"] else mix[i] for i in range(nreq)]
     ctx = _serving_ctx(gwhe, stream, shapes)
+    progress("keys and tables ready")
     inputs = _cohort_inputs(shapes, S_["seed"] + 1000)
+    progress("inputs of %d requests generated" % nreq)
     srv = gwhe.Server(ctx, workers=args.workers, chunk_batches=64,
                       one_snp_loop=args.one_snp_loop)
     # calibration: service time t = a + b u of 4 jobs of the mix, one at a time,
@@ -933,14 +941,19 @@ def run_serving(args):
     a, b = max(float(a), 0.0), max(float(b), 1e-9)
     mean_service = a + b * float(np.mean([units(*x) for x in shapes]))
     rate = 0.8 / mean_service if args.rate <= 0 else args.rate  # ~80% busy
+    progress("calibrated: %.3f s mean service, %.3f arrivals/s" % (mean_service, rate))
     gaps = rng.exponential(1.0 / rate, size=nreq)
     lat = [None] * nreq
     lock = threading.Lock()
+    done = [0]
 
     def waiter(i, rid):
         _, _, t = srv.wait(rid)
         with lock:
             lat[i] = t
+            done[0] += 1
+            if done[0] % 20 == 0:
+                progress("%d of %d requests done, server %s" % (done[0], nreq, srv.stats()))
 
     threads = []
     t0 = time.perf_counter()
